@@ -1,0 +1,185 @@
+/*
+ * gaincal.h -- C ABI of the GB300 gain-calibration library (libgaincal.so).
+ *
+ * Method: Smirnov & Tasse, "Radio interferometric gain calibration as a complex
+ * optimization problem" (arXiv:1502.06974).  The library solves, for many independent
+ * solution intervals at once,
+ *
+ *     min_g  sum_{pq s} | d_pqs - g_p m_pqs conj(g_q) |^2               (Sect. 2.3, eq. cal:DI:tf)
+ *     min_G  sum_{pq s} || D_pqs - G_p M_pqs G_q^H ||_F^2                (Sect. 4, eq. cal:DI:pol)
+ *     min_g  sum_{pq s} | d_pqs - sum_d g_p^(d) m^(d)_pqs conj(g_q^(d)) |^2   (Sect. 2.5, eq. cal:dd:unpol)
+ *
+ * with the approximate-inverse iterations of Sect. 3: StefCal (eq. stefcal, with the
+ * GN/average alternation of eq. stefcal-lambda-average), its 2x2 form (eq. update:DI:diag:pol,
+ * computed as [sum D Y^H][sum Y Y^H]^-1) and CohJones (Sect. 3.2.2, N_d x N_d antenna blocks).
+ *
+ * ---------------------------------------------------------------------------------------
+ * Data layout (all kinds)
+ *   A "row" is one (baseline, sample) pair.  Interval i owns the rows
+ *       row_off[i] .. row_off[i] + n_samp[i] * n_bl[i] - 1
+ *   stored sample-major, baseline-minor (row = row_off[i] + s * n_bl[i] + b).  A sample is one
+ *   (time, channel) point of the interval (Sect. 2.3: the sample index s).  Baseline b of
+ *   interval i is the antenna pair (ant1[bl_off[i] + b], ant2[bl_off[i] + b]); antenna numbers
+ *   are local to the interval (0 .. n_ant[i]-1).  Either orientation may be stored, since
+ *   d_qp = conj(d_pq) (Sect. 2.1) and D_qp = D_pq^H (Sect. 4); a pair with ant1 == ant2 is an
+ *   error (autocorrelations are excluded, Sect. 2.1).  Intervals may share baseline tables.
+ *
+ *   Element types (dtype):
+ *     scalar  vis, model, gains: complex (re, im) pairs; GC_DTYPE_C64 = 2 x float,
+ *             GC_DTYPE_C128 = 2 x double.
+ *     jones   one row = a 2x2 complex matrix stored row-major [x00, x01, x10, x11]
+ *             (32 bytes in C64); a gain is one such 2x2 matrix per antenna.
+ *     dd      vis: one complex per row; model: n_dir planes, model[d * n_rows + row];
+ *             gains: gains[(gain_off[i] + p) * n_dir + d].
+ *   Gains of interval i occupy slots gain_off[i] .. gain_off[i] + n_ant[i] - 1.
+ *
+ * Ownership and synchronisation
+ *   - gc_layout and every array it points to are HOST memory, read during the call only.
+ *   - With opt->host_buffers == 0, vis, model, gains and the per-interval outputs are DEVICE
+ *     pointers owned by the caller; work is queued on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) and the call returns once every interval has converged or reached
+ *     max_iter (the host reads a device flag between iteration batches); results are then
+ *     complete on `stream`.
+ *   - With opt->host_buffers == 1 the same pointers are HOST memory (pinned is fastest); the
+ *     library copies inputs to the device, solves, and copies gains and outputs back before
+ *     returning.
+ *   - The library keeps a per-process device workspace that grows on demand; gc_release()
+ *     frees it.  Calls must not run concurrently from several host threads.
+ *
+ * Errors
+ *   Return value: GC_OK (0) when every interval converged; a positive count of intervals whose
+ *   status is not GC_ST_OK; or a negative GC_ERR_* code, in which case nothing was launched
+ *   (argument errors) or the CUDA error is reported (GC_ERR_CUDA).  The library never aborts and
+ *   never traps on the device.
+ */
+#ifndef GAINCAL_H
+#define GAINCAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define GC_OK 0
+#define GC_ERR_ARG (-1)      /* NULL pointer where one is required, or a bad option value     */
+#define GC_ERR_LAYOUT (-2)   /* offsets / counts out of range or inconsistent                 */
+#define GC_ERR_ANTENNA (-3)  /* antenna index outside 0..n_ant-1, or ant1 == ant2            */
+#define GC_ERR_DTYPE (-4)    /* dtype not supported by this entry point                       */
+#define GC_ERR_CUDA (-5)     /* a CUDA runtime call failed (see gc_last_cuda_error)          */
+#define GC_ERR_LIMIT (-6)    /* a size beyond a documented maximum                            */
+
+/* ---- per-interval status (status_out[i]) ---- */
+#define GC_ST_OK 0            /* converged: ||g_k+1 - g_k|| <= tol ||g_k+1||                  */
+#define GC_ST_NOT_CONVERGED 1 /* stopped at max_iter                                           */
+#define GC_ST_NONFINITE 2     /* a NaN/Inf appeared in the gains; the interval was stopped     */
+#define GC_ST_NODATA 3        /* the interval has no rows; gains left unchanged, iters = 0     */
+#define GC_ST_SINGULAR_FLAG 16 /* OR-ed in: at the last update some antenna's J^H J block was
+                                  not invertible (e.g. no unflagged baselines); that antenna's
+                                  gain was left unchanged                                     */
+
+#define GC_DTYPE_C64 0
+#define GC_DTYPE_C128 1
+
+#define GC_SCHED_STEFCAL 0  /* odd k: GN step; even k: LM step with lambda = 1 = average (Sect. 3.1) */
+#define GC_SCHED_GN 1       /* GN step every iteration                                        */
+
+#define GC_MAX_ANT 1024      /* antennas per interval                                          */
+#define GC_MAX_DIR 16        /* directions for the DD entry point                              */
+
+typedef struct gc_layout {
+  int32_t n_intervals;
+  const int64_t* row_off;   /* [n_intervals] first row of each interval                     */
+  const int32_t* n_samp;    /* [n_intervals] samples (time x channel points) per interval   */
+  const int32_t* n_bl;      /* [n_intervals] baselines per interval                         */
+  const int32_t* bl_off;    /* [n_intervals] first entry of the interval in ant1/ant2       */
+  const int32_t* n_ant;     /* [n_intervals] antennas (gain slots) per interval              */
+  const int32_t* gain_off;  /* [n_intervals] first gain slot of the interval                 */
+  int32_t n_bl_table;       /* entries in ant1 / ant2                                         */
+  const int32_t* ant1;      /* [n_bl_table]                                                   */
+  const int32_t* ant2;      /* [n_bl_table]                                                   */
+  int64_t n_rows;           /* rows in vis (and per model plane)                              */
+  int32_t n_gain;           /* gain slots                                                     */
+  int32_t n_dir;            /* directions (dd only; 1 for the DI entry points)                */
+} gc_layout;
+
+typedef struct gc_options {
+  double tol;               /* relative step tolerance (App. C, first criterion)               */
+  int32_t max_iter;         /* >= 1                                                           */
+  int32_t schedule;         /* GC_SCHED_*                                                     */
+  int32_t dtype;            /* GC_DTYPE_*                                                     */
+  int32_t host_buffers;     /* 0: data pointers are device memory; 1: host memory              */
+  int32_t compute_chi2;     /* 1: fill chi2_out with sum |r|^2 at the final gains              */
+  int32_t reserved[3];      /* must be 0                                                      */
+} gc_options;
+
+/*
+ * Direction-independent scalar gains: StefCal (Sect. 3.1, eq. stefcal and
+ * eq. stefcal-lambda-average) over every interval of `layout`.
+ *   vis, model  [n_rows] complex (dtype C64 or C128)
+ *   gains       [n_gain] complex, read as the starting point, overwritten with the solution
+ *   iters_out   [n_intervals] int32, iterations taken (may be NULL)
+ *   chi2_out    [n_intervals] double, sum |r|^2 at the solution when opt->compute_chi2 (may be NULL)
+ *   status_out  [n_intervals] int32 GC_ST_* (may be NULL)
+ */
+int gc_calibrate_di_scalar(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                           const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                           int32_t* status_out, void* stream);
+
+/*
+ * Direction-independent full-Jones 2x2 gains: polarized StefCal (Sect. 4.2,
+ * eq. update:DI:diag:pol, product order [sum_q D_pq Y_pq^H][sum_q Y_pq Y_pq^H]^-1 with
+ * Y_pq = M_pq G_q^H), same schedule and arguments as gc_calibrate_di_scalar; vis, model and
+ * gains hold 2x2 matrices (row-major).
+ */
+int gc_calibrate_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                             const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                             int32_t* status_out, void* stream);
+
+/*
+ * Direction-dependent scalar gains: CohJones (Sect. 3.2.2).  Per antenna p the N_d x N_d
+ * block A_p[c][d] = sum_{q,s} conj(y^(c)) y^(d), y^(d) = m^(d) conj(g_q^(d)) (eq. JHJ:DD:unpol)
+ * is solved against J^H d (eq. JHR:DD:unpol, data form of eq. ghat) by an FP64 Cholesky
+ * factorisation.  The sums over samples are first reduced to per-baseline moments
+ * X^(cd)_pq = sum_s conj(m^(c)) m^(d) and b^(c)_pq = sum_s conj(m^(c)) d (Sect. 3.2.1, the
+ * gains factor out of the sample sum), read once per interval.
+ *   vis    [n_rows] complex64; model [n_dir][n_rows] complex64; gains [n_gain][n_dir] complex64.
+ * Only GC_DTYPE_C64.  n_dir <= GC_MAX_DIR.
+ */
+int gc_calibrate_dd_cohjones(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                             const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                             int32_t* status_out, void* stream);
+
+/*
+ * One accumulation pass, no update: for every gain slot p of every interval, the top half of
+ * J^H d and the diagonal block of J^H J at the given gains (device pointers, work on `stream`,
+ * asynchronous).
+ *   scalar (eqs. JHJ:DI:tf, JHR:DI:tf in data form):
+ *     jhd_out [n_gain] complex  = sum_{q,s} conj(y_pqs) d_pqs,  y_pqs = m_pqs conj(g_q)
+ *     jhj_out [n_gain] real     = sum_{q,s} |y_pqs|^2
+ *   jones (eq. JHJ:pol diagonal and the polarized J^H D):
+ *     jhd_out [n_gain] 2x2 complex = sum_{q,s} D_pqs Y_pqs^H,  Y_pqs = M_pqs G_q^H
+ *     jhj_out [n_gain] 2x2 complex = sum_{q,s} Y_pqs Y_pqs^H   (Hermitian, both triangles written)
+ * Types follow `dtype` (C64: float, C128: double).
+ */
+int gc_jhj_jhr_di_scalar(const void* vis, const void* model, const gc_layout* layout, const void* gains,
+                         int32_t dtype, void* jhd_out, void* jhj_out, void* stream);
+int gc_jhj_jhr_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,
+                           int32_t dtype, void* jhd_out, void* jhj_out, void* stream);
+
+/* Text for a GC_ERR_* return code or a GC_ST_* status. */
+const char* gc_error_string(int code);
+const char* gc_status_string(int status);
+/* The last CUDA error string seen by the library ("" if none). */
+const char* gc_last_cuda_error(void);
+/* Kernels launched by this process so far (a monotone counter, for launch accounting). */
+int64_t gc_launch_count(void);
+/* Free the cached device workspace (safe to call at any time no call is running). */
+int gc_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAINCAL_H */

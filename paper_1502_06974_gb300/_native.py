@@ -1,0 +1,87 @@
+"""ctypes view of ``libgaincal.so`` (the C ABI declared in include/gaincal.h).
+
+Loading fails loudly: there is no CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, 'libgaincal.so')
+
+GC_OK = 0
+GC_ERR = {-1: 'GC_ERR_ARG', -2: 'GC_ERR_LAYOUT', -3: 'GC_ERR_ANTENNA', -4: 'GC_ERR_DTYPE', -5: 'GC_ERR_CUDA',
+          -6: 'GC_ERR_LIMIT'}
+GC_ST_OK, GC_ST_NOT_CONVERGED, GC_ST_NONFINITE, GC_ST_NODATA, GC_ST_SINGULAR_FLAG = 0, 1, 2, 3, 16
+GC_DTYPE_C64, GC_DTYPE_C128 = 0, 1
+GC_SCHED_STEFCAL, GC_SCHED_GN = 0, 1
+GC_MAX_ANT, GC_MAX_DIR = 1024, 16
+
+# Every symbol include/gaincal.h declares (checked by the CPU test suite).
+EXPORTS = [
+    'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones',
+    'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2',
+    'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
+]
+
+_p = C.c_void_p
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+
+
+class GcLayout(C.Structure):
+    _fields_ = [('n_intervals', C.c_int32), ('row_off', _i64p), ('n_samp', _i32p), ('n_bl', _i32p),
+                ('bl_off', _i32p), ('n_ant', _i32p), ('gain_off', _i32p), ('n_bl_table', C.c_int32),
+                ('ant1', _i32p), ('ant2', _i32p), ('n_rows', C.c_int64), ('n_gain', C.c_int32),
+                ('n_dir', C.c_int32)]
+
+
+class GcOptions(C.Structure):
+    _fields_ = [('tol', C.c_double), ('max_iter', C.c_int32), ('schedule', C.c_int32), ('dtype', C.c_int32),
+                ('host_buffers', C.c_int32), ('compute_chi2', C.c_int32), ('reserved', C.c_int32 * 3)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgaincal.so not found at {LIB_PATH}: run paper_1502_06974_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        cal = [_p, _p, C.POINTER(GcLayout), _p, C.POINTER(GcOptions), _p, _p, _p, _p]
+        for name in ('gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones'):
+            f = getattr(L, name)
+            f.argtypes = cal
+            f.restype = C.c_int
+        for name in ('gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2'):
+            f = getattr(L, name)
+            f.argtypes = [_p, _p, C.POINTER(GcLayout), _p, C.c_int32, _p, _p, _p]
+            f.restype = C.c_int
+        L.gc_error_string.argtypes = [C.c_int]
+        L.gc_error_string.restype = C.c_char_p
+        L.gc_status_string.argtypes = [C.c_int]
+        L.gc_status_string.restype = C.c_char_p
+        L.gc_last_cuda_error.argtypes = []
+        L.gc_last_cuda_error.restype = C.c_char_p
+        L.gc_launch_count.argtypes = []
+        L.gc_launch_count.restype = C.c_int64
+        L.gc_release.argtypes = []
+        L.gc_release.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def check(rc: int, what: str) -> int:
+    """Raise on a negative return code; return the count of non-converged intervals otherwise."""
+    if rc < 0:
+        L = lib()
+        msg = L.gc_error_string(rc).decode()
+        if rc == -5:
+            msg += ': ' + L.gc_last_cuda_error().decode()
+        raise RuntimeError(f"{what} failed ({GC_ERR.get(rc, rc)}): {msg}")
+    return rc

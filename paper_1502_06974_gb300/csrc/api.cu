@@ -1,0 +1,534 @@
+// C ABI of the gain-calibration library: argument validation, plans (device copies of the layout
+// and the per-antenna reduction slot lists), the cached workspace, and the iteration loop.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdlib>
+#include <string>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "internal.h"
+#include "dd.h"
+
+namespace gc {
+
+std::atomic<long long> g_launches{0};
+static char g_cuda_err[256] = "";
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  return GC_ERR_CUDA;
+}
+#define GC_CUDA(call)                                       \
+  do {                                                      \
+    cudaError_t e__ = (call);                               \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call);   \
+  } while (0)
+#define GC_CUDA_I(call)                                            \
+  do {                                                             \
+    int e__ = (call);                                              \
+    if (e__ != 0) return cuda_fail((cudaError_t)e__, #call);       \
+  } while (0)
+
+// ------------------------------------------------------------------------------------ workspace
+// Grow-only device buffers, one per named slot.  The device they live on is recorded; a call on
+// another device reallocates.
+struct Slot {
+  void* p = nullptr;
+  size_t n = 0;
+  int dev = -1;
+};
+static std::map<std::string, Slot> g_ws;
+static int* g_pinned_flag = nullptr;
+
+int ws_get(const char* name, size_t bytes, void** out) {
+  int dev = 0;
+  GC_CUDA(cudaGetDevice(&dev));
+  Slot& s = g_ws[name];
+  if (s.p && (s.n < bytes || s.dev != dev)) {
+    int cur = dev;
+    if (s.dev != dev) cudaSetDevice(s.dev);
+    cudaFree(s.p);
+    if (s.dev != dev) cudaSetDevice(cur);
+    s.p = nullptr;
+    s.n = 0;
+  }
+  if (!s.p && bytes > 0) {
+    size_t want = bytes + bytes / 8 + 256;
+    GC_CUDA(cudaMalloc(&s.p, want));
+    s.n = want;
+    s.dev = dev;
+  }
+  *out = s.p;
+  return GC_OK;
+}
+
+int pinned_flag(int** out) {
+  if (!g_pinned_flag) GC_CUDA(cudaHostAlloc((void**)&g_pinned_flag, 64, cudaHostAllocDefault));
+  *out = g_pinned_flag;
+  return GC_OK;
+}
+
+const char* last_cuda_error() { return g_cuda_err; }
+
+// ------------------------------------------------------------------------------------ layout checks
+int validate_layout(const gc_layout* L, int n_dir_required_max) {
+  if (!L) return GC_ERR_ARG;
+  if (L->n_intervals < 0 || L->n_bl_table < 0 || L->n_rows < 0 || L->n_gain < 0) return GC_ERR_LAYOUT;
+  if (L->n_intervals == 0) return GC_OK;
+  if (!L->row_off || !L->n_samp || !L->n_bl || !L->bl_off || !L->n_ant || !L->gain_off) return GC_ERR_ARG;
+  if (L->n_bl_table > 0 && (!L->ant1 || !L->ant2)) return GC_ERR_ARG;
+  if (L->n_dir < 1 || L->n_dir > n_dir_required_max) return GC_ERR_LIMIT;
+  // per-table maximum antenna index (tables identified by (bl_off, n_bl))
+  std::map<std::pair<int, int>, int> tab_max;
+  for (int i = 0; i < L->n_intervals; ++i) {
+    const int64_t ns = L->n_samp[i], nb = L->n_bl[i], na = L->n_ant[i];
+    if (ns < 0 || nb < 0 || na < 1) return GC_ERR_LAYOUT;
+    if (na > GC_MAX_ANT) return GC_ERR_LIMIT;
+    if (L->row_off[i] < 0 || L->row_off[i] + ns * nb > L->n_rows) return GC_ERR_LAYOUT;
+    if (L->bl_off[i] < 0 || (int64_t)L->bl_off[i] + nb > L->n_bl_table) return GC_ERR_LAYOUT;
+    if (L->gain_off[i] < 0 || (int64_t)L->gain_off[i] + na > L->n_gain) return GC_ERR_LAYOUT;
+    auto key = std::make_pair((int)L->bl_off[i], (int)nb);
+    auto f = tab_max.find(key);
+    int mx;
+    if (f == tab_max.end()) {
+      mx = -1;
+      for (int b = 0; b < nb; ++b) {
+        const int p = L->ant1[L->bl_off[i] + b], q = L->ant2[L->bl_off[i] + b];
+        if (p < 0 || q < 0 || p == q) return GC_ERR_ANTENNA;
+        mx = p > mx ? p : mx;
+        mx = q > mx ? q : mx;
+      }
+      tab_max[key] = mx;
+    } else {
+      mx = f->second;
+    }
+    if (mx >= na) return GC_ERR_ANTENNA;
+  }
+  return GC_OK;
+}
+
+static uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+  return h;
+}
+
+uint64_t layout_hash(const gc_layout* L, uint64_t salt) {
+  uint64_t h = 1469598103934665603ull ^ salt;
+  const size_t n = (size_t)L->n_intervals;
+  h = fnv(h, &L->n_intervals, sizeof(int32_t));
+  h = fnv(h, &L->n_rows, sizeof(int64_t));
+  h = fnv(h, &L->n_gain, sizeof(int32_t));
+  h = fnv(h, &L->n_dir, sizeof(int32_t));
+  h = fnv(h, &L->n_bl_table, sizeof(int32_t));
+  if (n) {
+    h = fnv(h, L->row_off, n * 8);
+    h = fnv(h, L->n_samp, n * 4);
+    h = fnv(h, L->n_bl, n * 4);
+    h = fnv(h, L->bl_off, n * 4);
+    h = fnv(h, L->n_ant, n * 4);
+    h = fnv(h, L->gain_off, n * 4);
+  }
+  if (L->n_bl_table) {
+    h = fnv(h, L->ant1, (size_t)L->n_bl_table * 4);
+    h = fnv(h, L->ant2, (size_t)L->n_bl_table * 4);
+  }
+  return h;
+}
+
+// ------------------------------------------------------------------------------------ DI plan
+struct DIPlan {
+  uint64_t key = 0;
+  int n_int = 0, n_items = 0, na_max = 1, n_active0 = 0;
+  int64_t scr_elems = 0;
+  // device copies, carved out of one buffer
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  DIArgs args{};  // layout / plan pointers filled in
+  double* chi2_items = nullptr;
+  double* chi2_out = nullptr;
+  int grid = 0, smem = 0;
+};
+
+static DIPlan g_di_plan[2][2][2];  // [kind][dtype][acc_only]
+static int g_target_rows[2] = {32768, 8192};
+
+static int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v ? atoi(v) : dflt;
+}
+
+// Build the work items, baseline-table reduction lists and device copies for one layout.
+static int build_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, DIPlan& P, void* stream) {
+  const int nc = kind == 0 ? 3 : 12;
+  const int TB = kDIThreads;
+  const int n = L->n_intervals;
+  // baseline tables
+  std::map<std::pair<int, int>, int> tabs;
+  std::vector<int> itab(n), tab_base, tab_nant, csr_off, csr_ent;
+  for (int i = 0; i < n; ++i) {
+    auto key = std::make_pair((int)L->bl_off[i], (int)L->n_bl[i]);
+    auto f = tabs.find(key);
+    if (f != tabs.end()) { itab[i] = f->second; continue; }
+    const int t = (int)tab_base.size();
+    tabs[key] = t;
+    itab[i] = t;
+    const int bo = key.first, nb = key.second;
+    int nat = 0;
+    for (int b = 0; b < nb; ++b) {
+      nat = L->ant1[bo + b] + 1 > nat ? L->ant1[bo + b] + 1 : nat;
+      nat = L->ant2[bo + b] + 1 > nat ? L->ant2[bo + b] + 1 : nat;
+    }
+    tab_base.push_back((int)csr_off.size());
+    tab_nant.push_back(nat);
+    const int ntiles = (nb + TB - 1) / TB;
+    for (int tile = 0; tile < ntiles; ++tile) {
+      std::vector<std::vector<int>> lists(nat);
+      for (int s = 0; s < TB; ++s) {
+        const int b = tile * TB + s;
+        if (b >= nb) break;
+        lists[L->ant1[bo + b]].push_back(s * 2 * nc);        // p side of slot s
+        lists[L->ant2[bo + b]].push_back(s * 2 * nc + nc);   // q side of slot s
+      }
+      for (int a = 0; a < nat; ++a) {
+        csr_off.push_back((int)csr_ent.size());
+        csr_ent.insert(csr_ent.end(), lists[a].begin(), lists[a].end());
+      }
+      csr_off.push_back((int)csr_ent.size());
+    }
+  }
+  if (csr_off.empty()) csr_off.push_back(0);
+  if (csr_ent.empty()) csr_ent.push_back(0);
+  // work items
+  const int target = env_int(kind == 0 ? "GAINCAL_TARGET_ROWS_SCALAR" : "GAINCAL_TARGET_ROWS_JONES", g_target_rows[kind]);
+  std::vector<int> item_int, item_s0, item_s1, n_chunks(n), first_item(n);
+  std::vector<int64_t> item_scr;
+  int64_t scr = 0;
+  int na_max = 1, n_active0 = 0;
+  for (int i = 0; i < n; ++i) {
+    const int ns = L->n_samp[i], nb = L->n_bl[i];
+    na_max = L->n_ant[i] > na_max ? L->n_ant[i] : na_max;
+    first_item[i] = (int)item_int.size();
+    if ((int64_t)ns * nb == 0) { n_chunks[i] = 0; continue; }
+    ++n_active0;
+    int per = nb > 0 ? (target + nb - 1) / nb : ns;
+    per = per < 1 ? 1 : (per > ns ? ns : per);
+    const int nch = (ns + per - 1) / per;
+    n_chunks[i] = nch;
+    for (int c = 0; c < nch; ++c) {
+      item_int.push_back(i);
+      item_s0.push_back(c * per);
+      item_s1.push_back((c + 1) * per < ns ? (c + 1) * per : ns);
+      const int nat = tab_nant[itab[i]];
+      if (nch > 1) { item_scr.push_back(scr); scr += (int64_t)nat * nc; }
+      else item_scr.push_back(-1);
+    }
+  }
+  const int n_items = (int)item_int.size();
+  // pack into one device buffer: int64 arrays first
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  struct Part { const void* src; size_t bytes; size_t off; };
+  std::vector<Part> parts;
+  size_t off = 0;
+  auto add = [&](const void* src, size_t bytes) { parts.push_back({src, bytes, off}); off += al(bytes > 0 ? bytes : 1); return parts.size() - 1; };
+  const size_t p_row_off = add(L->row_off, (size_t)n * 8);
+  const size_t p_item_scr = add(item_scr.data(), item_scr.size() * 8);
+  const size_t p_n_samp = add(L->n_samp, (size_t)n * 4);
+  const size_t p_n_bl = add(L->n_bl, (size_t)n * 4);
+  const size_t p_bl_off = add(L->bl_off, (size_t)n * 4);
+  const size_t p_n_ant = add(L->n_ant, (size_t)n * 4);
+  const size_t p_gain_off = add(L->gain_off, (size_t)n * 4);
+  const size_t p_ant1 = add(L->ant1, (size_t)L->n_bl_table * 4);
+  const size_t p_ant2 = add(L->ant2, (size_t)L->n_bl_table * 4);
+  const size_t p_itab = add(itab.data(), itab.size() * 4);
+  const size_t p_tab_base = add(tab_base.data(), tab_base.size() * 4);
+  const size_t p_tab_nant = add(tab_nant.data(), tab_nant.size() * 4);
+  const size_t p_csr_off = add(csr_off.data(), csr_off.size() * 4);
+  const size_t p_csr_ent = add(csr_ent.data(), csr_ent.size() * 4);
+  const size_t p_item_int = add(item_int.data(), item_int.size() * 4);
+  const size_t p_item_s0 = add(item_s0.data(), item_s0.size() * 4);
+  const size_t p_item_s1 = add(item_s1.data(), item_s1.size() * 4);
+  const size_t p_n_chunks = add(n_chunks.data(), n_chunks.size() * 4);
+  const size_t p_first_item = add(first_item.data(), first_item.size() * 4);
+  // per-call state
+  const size_t p_active = add(nullptr, (size_t)n * 4);
+  const size_t p_iters = add(nullptr, (size_t)n * 4);
+  const size_t p_status = add(nullptr, (size_t)n * 4);
+  const size_t p_counters = add(nullptr, (size_t)n * 4);
+  const size_t p_misc = add(nullptr, 64);
+  const size_t p_chi2 = add(nullptr, (size_t)(n_items > 0 ? n_items : 1) * 8);
+  const size_t p_chi2o = add(nullptr, (size_t)(n > 0 ? n : 1) * 8);
+  const size_t total = off;
+  std::vector<unsigned char> host(total, 0);
+  for (auto& pt : parts)
+    if (pt.src && pt.bytes) memcpy(host.data() + pt.off, pt.src, pt.bytes);
+  if (P.dev && P.dev_bytes < total) { cudaFree(P.dev); P.dev = nullptr; P.dev_bytes = 0; }
+  if (!P.dev) { GC_CUDA(cudaMalloc(&P.dev, total)); P.dev_bytes = total; }
+  GC_CUDA(cudaMemcpyAsync(P.dev, host.data(), total, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  GC_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned char* d = static_cast<unsigned char*>(P.dev);
+  auto at = [&](size_t idx) { return (void*)(d + parts[idx].off); };
+  DIArgs& a = P.args;
+  a = DIArgs{};
+  a.row_off = (const int64_t*)at(p_row_off);
+  a.item_scr = (const int64_t*)at(p_item_scr);
+  a.n_samp = (const int32_t*)at(p_n_samp);
+  a.n_bl = (const int32_t*)at(p_n_bl);
+  a.bl_off = (const int32_t*)at(p_bl_off);
+  a.n_ant = (const int32_t*)at(p_n_ant);
+  a.gain_off = (const int32_t*)at(p_gain_off);
+  a.ant1 = (const int32_t*)at(p_ant1);
+  a.ant2 = (const int32_t*)at(p_ant2);
+  a.itab = (const int32_t*)at(p_itab);
+  a.tab_base = (const int32_t*)at(p_tab_base);
+  a.tab_nant = (const int32_t*)at(p_tab_nant);
+  a.csr_off = (const int32_t*)at(p_csr_off);
+  a.csr_ent = (const int32_t*)at(p_csr_ent);
+  a.item_int = (const int32_t*)at(p_item_int);
+  a.item_s0 = (const int32_t*)at(p_item_s0);
+  a.item_s1 = (const int32_t*)at(p_item_s1);
+  a.n_chunks = (const int32_t*)at(p_n_chunks);
+  a.first_item = (const int32_t*)at(p_first_item);
+  a.active = (int32_t*)at(p_active);
+  a.iters = (int32_t*)at(p_iters);
+  a.status = (int32_t*)at(p_status);
+  a.counters = (int32_t*)at(p_counters);
+  a.n_active = (int32_t*)at(p_misc);
+  a.qhead = (int32_t*)at(p_misc) + 4;
+  a.n_items = n_items;
+  a.na_max = na_max;
+  P.chi2_items = (double*)at(p_chi2);
+  P.chi2_out = (double*)at(p_chi2o);
+  P.n_int = n;
+  P.n_items = n_items;
+  P.na_max = na_max;
+  P.n_active0 = n_active0;
+  P.scr_elems = scr;
+  P.smem = di_smem_bytes(kind, dtype, na_max);
+  int dev = 0, nsm = 0, per_sm = 0, max_smem = 0;
+  GC_CUDA(cudaGetDevice(&dev));
+  GC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  GC_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (P.smem > max_smem) return GC_ERR_LIMIT;
+  GC_CUDA_I(di_max_blocks_per_sm(kind, dtype, acc_only, P.smem, &per_sm));
+  if (per_sm < 1) return GC_ERR_LIMIT;
+  const int cap = env_int("GAINCAL_BLOCKS_PER_SM", per_sm);
+  per_sm = cap < per_sm ? (cap > 0 ? cap : 1) : per_sm;
+  P.grid = nsm * per_sm;
+  if (P.grid > n_items) P.grid = n_items > 0 ? n_items : 1;
+  return GC_OK;
+}
+
+static int get_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, DIPlan** out, void* stream) {
+  DIPlan& P = g_di_plan[kind][dtype][acc_only];
+  int dev = 0;
+  GC_CUDA(cudaGetDevice(&dev));
+  const uint64_t key = layout_hash(L, (uint64_t)(kind * 131 + dtype * 7 + acc_only) ^ ((uint64_t)dev << 40) ^
+                                      ((uint64_t)env_int("GAINCAL_TARGET_ROWS_SCALAR", 0) << 20) ^
+                                      ((uint64_t)env_int("GAINCAL_TARGET_ROWS_JONES", 0) << 48) ^
+                                      ((uint64_t)env_int("GAINCAL_BLOCKS_PER_SM", 0) << 56));
+  if (P.key != key || P.n_int != L->n_intervals || !P.dev) {
+    P.key = 0;
+    int rc = build_di_plan(kind, dtype, acc_only, L, P, stream);
+    if (rc != GC_OK) return rc;
+    P.key = key;
+  }
+  *out = &P;
+  return GC_OK;
+}
+
+static size_t elem_bytes(int kind, int dtype) {
+  const size_t r = dtype == GC_DTYPE_C64 ? 8 : 16;  // one complex
+  return kind == 0 ? r : 4 * r;
+}
+
+// Stage host buffers on the device when opt->host_buffers is set.
+struct Staged {
+  const void* vis;
+  const void* model;
+  void* gains;
+};
+
+static int run_di(int kind, const void* vis, const void* model, const gc_layout* L, void* gains,
+                  const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out, void* stream) {
+  if (!opt || !L) return GC_ERR_ARG;
+  if (opt->dtype != GC_DTYPE_C64 && opt->dtype != GC_DTYPE_C128) return GC_ERR_DTYPE;
+  if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
+    return GC_ERR_ARG;
+  if (opt->host_buffers != 0 && opt->host_buffers != 1) return GC_ERR_ARG;
+  int rc = validate_layout(L, 1);
+  if (rc != GC_OK) return rc;
+  if (L->n_intervals == 0) return GC_OK;
+  if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && !gains)) return GC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DIPlan* P = nullptr;
+  rc = get_di_plan(kind, opt->dtype, 0, L, &P, stream);
+  if (rc != GC_OK) return rc;
+  const size_t eb = elem_bytes(kind, opt->dtype);
+  Staged st{vis, model, gains};
+  if (opt->host_buffers) {
+    void *dv = nullptr, *dm = nullptr, *dg = nullptr;
+    if ((rc = ws_get("h_vis", (size_t)L->n_rows * eb, &dv))) return rc;
+    if ((rc = ws_get("h_model", (size_t)L->n_rows * eb, &dm))) return rc;
+    if ((rc = ws_get("h_gains", (size_t)L->n_gain * eb, &dg))) return rc;
+    if (L->n_rows) {
+      GC_CUDA(cudaMemcpyAsync(dv, vis, (size_t)L->n_rows * eb, cudaMemcpyHostToDevice, s));
+      GC_CUDA(cudaMemcpyAsync(dm, model, (size_t)L->n_rows * eb, cudaMemcpyHostToDevice, s));
+    }
+    GC_CUDA(cudaMemcpyAsync(dg, gains, (size_t)L->n_gain * eb, cudaMemcpyHostToDevice, s));
+    st = Staged{dv, dm, dg};
+  }
+  DIArgs a = P->args;
+  a.vis = st.vis;
+  a.model = st.model;
+  a.gains = st.gains;
+  a.tol = opt->tol;
+  a.max_iter = opt->max_iter;
+  a.schedule = opt->schedule;
+  if (P->scr_elems > 0) {
+    void* scr = nullptr;
+    if ((rc = ws_get("di_scratch", (size_t)P->scr_elems * (opt->dtype == GC_DTYPE_C64 ? 4 : 8), &scr))) return rc;
+    a.scratch = scr;
+  }
+  GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
+  g_launches++;
+  int* flag = nullptr;
+  if ((rc = pinned_flag(&flag))) return rc;
+  const int check_every = env_int("GAINCAL_CHECK_EVERY", 16);
+  for (int k = 1; k <= opt->max_iter; ++k) {
+    a.k = k;
+    GC_CUDA_I(di_launch_iter(kind, opt->dtype, 0, a, P->grid, P->smem, stream));
+    g_launches++;
+    if (k % check_every == 0 || k == opt->max_iter) {
+      GC_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaStreamSynchronize(s));
+      if (*flag <= 0) break;
+    }
+  }
+  if (opt->compute_chi2) {
+    GC_CUDA_I(di_launch_chi2(kind, opt->dtype, a, P->chi2_items, P->chi2_out, P->n_int, P->grid, stream));
+    g_launches += 2;
+  }
+  const cudaMemcpyKind dk = opt->host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (opt->host_buffers) GC_CUDA(cudaMemcpyAsync(gains, st.gains, (size_t)L->n_gain * eb, dk, s));
+  if (iters_out) GC_CUDA(cudaMemcpyAsync(iters_out, a.iters, (size_t)P->n_int * 4, dk, s));
+  if (status_out) GC_CUDA(cudaMemcpyAsync(status_out, a.status, (size_t)P->n_int * 4, dk, s));
+  if (chi2_out && opt->compute_chi2) GC_CUDA(cudaMemcpyAsync(chi2_out, P->chi2_out, (size_t)P->n_int * 8, dk, s));
+  // count intervals not OK
+  std::vector<int32_t> stv(P->n_int);
+  GC_CUDA(cudaMemcpyAsync(stv.data(), a.status, (size_t)P->n_int * 4, cudaMemcpyDeviceToHost, s));
+  GC_CUDA(cudaStreamSynchronize(s));
+  int bad = 0;
+  for (int i = 0; i < P->n_int; ++i) bad += (stv[i] & 15) != GC_ST_OK;
+  return bad;
+}
+
+static int run_di_acc(int kind, const void* vis, const void* model, const gc_layout* L, const void* gains, int dtype,
+                      void* jhd, void* jhj, void* stream) {
+  if (!L) return GC_ERR_ARG;
+  if (dtype != GC_DTYPE_C64 && dtype != GC_DTYPE_C128) return GC_ERR_DTYPE;
+  int rc = validate_layout(L, 1);
+  if (rc != GC_OK) return rc;
+  if (L->n_intervals == 0) return GC_OK;
+  if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && (!gains || !jhd || !jhj))) return GC_ERR_ARG;
+  DIPlan* P = nullptr;
+  rc = get_di_plan(kind, dtype, 1, L, &P, stream);
+  if (rc != GC_OK) return rc;
+  DIArgs a = P->args;
+  a.vis = vis;
+  a.model = model;
+  a.gains = const_cast<void*>(gains);
+  a.jhd_out = jhd;
+  a.jhj_out = jhj;
+  a.k = 1;
+  if (P->scr_elems > 0) {
+    void* scr = nullptr;
+    if ((rc = ws_get("di_scratch", (size_t)P->scr_elems * (dtype == GC_DTYPE_C64 ? 4 : 8), &scr))) return rc;
+    a.scratch = scr;
+  }
+  // zero the outputs of antennas without data, then one pass
+  const size_t eb = elem_bytes(kind, dtype);
+  GC_CUDA(cudaMemsetAsync(jhd, 0, (size_t)L->n_gain * eb, (cudaStream_t)stream));
+  GC_CUDA(cudaMemsetAsync(jhj, 0, (size_t)L->n_gain * (kind == 0 ? eb / 2 : eb), (cudaStream_t)stream));
+  GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
+  GC_CUDA_I(di_launch_iter(kind, dtype, 1, a, P->grid, P->smem, stream));
+  g_launches += 2;
+  return GC_OK;
+}
+
+}  // namespace gc
+
+using namespace gc;
+
+extern "C" {
+
+int gc_calibrate_di_scalar(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                           const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out,
+                           void* stream) {
+  return run_di(0, vis, model, layout, gains, opt, iters_out, chi2_out, status_out, stream);
+}
+
+int gc_calibrate_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                             const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out,
+                             void* stream) {
+  return run_di(1, vis, model, layout, gains, opt, iters_out, chi2_out, status_out, stream);
+}
+
+int gc_jhj_jhr_di_scalar(const void* vis, const void* model, const gc_layout* layout, const void* gains, int32_t dtype,
+                         void* jhd_out, void* jhj_out, void* stream) {
+  return run_di_acc(0, vis, model, layout, gains, dtype, jhd_out, jhj_out, stream);
+}
+
+int gc_jhj_jhr_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,
+                           int32_t dtype, void* jhd_out, void* jhj_out, void* stream) {
+  return run_di_acc(1, vis, model, layout, gains, dtype, jhd_out, jhj_out, stream);
+}
+
+const char* gc_error_string(int code) {
+  switch (code) {
+    case GC_OK: return "ok";
+    case GC_ERR_ARG: return "invalid argument";
+    case GC_ERR_LAYOUT: return "inconsistent layout";
+    case GC_ERR_ANTENNA: return "antenna index out of range or autocorrelation";
+    case GC_ERR_DTYPE: return "unsupported dtype";
+    case GC_ERR_CUDA: return "CUDA error";
+    case GC_ERR_LIMIT: return "size beyond a library limit";
+    default: return code > 0 ? "some intervals did not converge" : "unknown error";
+  }
+}
+
+const char* gc_status_string(int status) {
+  switch (status & 15) {
+    case GC_ST_OK: return (status & GC_ST_SINGULAR_FLAG) ? "converged (singular antenna)" : "converged";
+    case GC_ST_NOT_CONVERGED: return "not converged";
+    case GC_ST_NONFINITE: return "non-finite gains";
+    case GC_ST_NODATA: return "no data";
+    default: return "unknown";
+  }
+}
+
+const char* gc_last_cuda_error(void) { return gc::last_cuda_error(); }
+
+int64_t gc_launch_count(void) { return (int64_t)gc::g_launches.load(); }
+
+int gc_release(void) {
+  for (auto& kv : gc::g_ws) {
+    if (kv.second.p) cudaFree(kv.second.p);
+  }
+  gc::g_ws.clear();
+  for (auto& a : gc::g_di_plan)
+    for (auto& b : a)
+      for (auto& c : b) {
+        if (c.dev) cudaFree(c.dev);
+        c = gc::DIPlan{};
+      }
+  gc::dd_release();
+  if (gc::g_pinned_flag) { cudaFreeHost(gc::g_pinned_flag); gc::g_pinned_flag = nullptr; }
+  return GC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Device helpers shared by the gain-calibration kernels: complex arithmetic on (re, im) pairs,
+// 2x2 complex matrices, compensated (Kahan) accumulation and deterministic block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define GC_DEV __device__ __forceinline__
+
+template <typename T>
+struct Cx {
+  T x, y;  // re, im
+};
+
+template <typename T> GC_DEV Cx<T> cx(T a, T b) { Cx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> GC_DEV Cx<T> conj_(Cx<T> a) { return cx<T>(a.x, -a.y); }
+template <typename T> GC_DEV Cx<T> add_(Cx<T> a, Cx<T> b) { return cx<T>(a.x + b.x, a.y + b.y); }
+template <typename T> GC_DEV Cx<T> sub_(Cx<T> a, Cx<T> b) { return cx<T>(a.x - b.x, a.y - b.y); }
+template <typename T> GC_DEV Cx<T> scale_(Cx<T> a, T s) { return cx<T>(a.x * s, a.y * s); }
+template <typename T> GC_DEV T abs2_(Cx<T> a) { return fma(a.x, a.x, a.y * a.y); }
+// a * b
+template <typename T> GC_DEV Cx<T> mul_(Cx<T> a, Cx<T> b) {
+  return cx<T>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+template <typename T> GC_DEV Cx<T> mulc_(Cx<T> a, Cx<T> b) {
+  return cx<T>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+template <typename T> GC_DEV Cx<T> cmul_(Cx<T> a, Cx<T> b) {
+  return cx<T>(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+// acc += a * b
+template <typename T> GC_DEV void fma_(Cx<T>& acc, Cx<T> a, Cx<T> b) {
+  acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+}
+// acc += a * conj(b)
+template <typename T> GC_DEV void fmac_(Cx<T>& acc, Cx<T> a, Cx<T> b) {
+  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+  acc.y = fma(a.y, b.x, fma(-a.x, b.y, acc.y));
+}
+// acc += conj(a) * b
+template <typename T> GC_DEV void cfma_(Cx<T>& acc, Cx<T> a, Cx<T> b) {
+  acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+  acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+}
+
+// (xr, xi) += a * conj(b)
+template <typename T> GC_DEV void fmac2(T& xr, T& xi, Cx<T> a, Cx<T> b) {
+  xr = fma(a.x, b.x, fma(a.y, b.y, xr));
+  xi = fma(a.y, b.x, fma(-a.x, b.y, xi));
+}
+// (xr, xi) += conj(a) * b
+template <typename T> GC_DEV void cfma2(T& xr, T& xi, Cx<T> a, Cx<T> b) {
+  xr = fma(a.x, b.x, fma(a.y, b.y, xr));
+  xi = fma(a.x, b.y, fma(-a.y, b.x, xi));
+}
+
+// 2x2 complex matrix [[a, b], [c, d]] (row-major storage order a, b, c, d).
+template <typename T>
+struct M2 {
+  Cx<T> a, b, c, d;
+};
+
+template <typename T> GC_DEV M2<T> mm_(const M2<T>& X, const M2<T>& Y) {  // X Y
+  M2<T> r;
+  r.a = mul_(X.a, Y.a); fma_(r.a, X.b, Y.c);
+  r.b = mul_(X.a, Y.b); fma_(r.b, X.b, Y.d);
+  r.c = mul_(X.c, Y.a); fma_(r.c, X.d, Y.c);
+  r.d = mul_(X.c, Y.b); fma_(r.d, X.d, Y.d);
+  return r;
+}
+template <typename T> GC_DEV M2<T> mmh_(const M2<T>& X, const M2<T>& Y) {  // X Y^H
+  M2<T> r;
+  r.a = mulc_(X.a, Y.a); fmac_(r.a, X.b, Y.b);
+  r.b = mulc_(X.a, Y.c); fmac_(r.b, X.b, Y.d);
+  r.c = mulc_(X.c, Y.a); fmac_(r.c, X.d, Y.b);
+  r.d = mulc_(X.c, Y.c); fmac_(r.d, X.d, Y.d);
+  return r;
+}
+
+// Vector loads of one row.  float: complex64 (8 bytes); a 2x2 row is 32 bytes = 2 x float4.
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+  static GC_DEV Cx<float> ld1(const float* p) {
+    float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+    return cx<float>(v.x, v.y);
+  }
+  static GC_DEV M2<float> ld4(const float* p) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    float4 u = __ldcs(q), v = __ldcs(q + 1);
+    M2<float> m;
+    m.a = cx<float>(u.x, u.y); m.b = cx<float>(u.z, u.w);
+    m.c = cx<float>(v.x, v.y); m.d = cx<float>(v.z, v.w);
+    return m;
+  }
+};
+template <> struct Vec<double> {
+  static GC_DEV Cx<double> ld1(const double* p) {
+    double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+    return cx<double>(v.x, v.y);
+  }
+  static GC_DEV M2<double> ld4(const double* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 u0 = __ldcs(q), u1 = __ldcs(q + 1), u2 = __ldcs(q + 2), u3 = __ldcs(q + 3);
+    M2<double> m;
+    m.a = cx<double>(u0.x, u0.y); m.b = cx<double>(u1.x, u1.y);
+    m.c = cx<double>(u2.x, u2.y); m.d = cx<double>(u3.x, u3.y);
+    return m;
+  }
+};
+
+// Compensated (Kahan) addition of v into (s, c); the value is s - c.
+template <typename T> GC_DEV void kahan_add(T& s, T& c, T v) {
+  T y = v - c;
+  T t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Deterministic block-wide sum (fixed shuffle tree, fixed warp order).  `red` holds >= 32 T.
+template <typename T> GC_DEV T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T r = 0;
+  if (warp == 0) {
+    r = lane < nw ? red[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) red[0] = r;
+  }
+  __syncthreads();
+  r = red[0];
+  __syncthreads();
+  return r;
+}
+
+GC_DEV int block_or(int v, int* red) {
+  v = __any_sync(0xffffffffu, v) ? 1 : 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int r = 0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int w = 0; w < nw; ++w) r |= red[w];
+  __syncthreads();
+  return r;
+}

@@ -1,0 +1,68 @@
+// Host/device shared definitions of the gain-calibration library (not part of the public ABI).
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/gaincal.h"
+
+namespace gc {
+
+constexpr int kDIThreads = 256;  // CTA size of the direction-independent kernels
+constexpr int kSubChain = 16;    // samples a thread sums in registers before an antenna reduction
+
+// Arguments of the direction-independent kernels (all pointers device memory).
+struct DIArgs {
+  const void* vis;
+  const void* model;
+  void* gains;
+  // layout
+  const int64_t* row_off;
+  const int32_t* n_samp;
+  const int32_t* n_bl;
+  const int32_t* bl_off;
+  const int32_t* n_ant;
+  const int32_t* gain_off;
+  const int32_t* ant1;
+  const int32_t* ant2;
+  // antenna-reduction plan: per baseline table and tile of kDIThreads baselines, the list of
+  // partial-sum slots (offsets into the CTA's partials array) that belong to each antenna
+  const int32_t* itab;      // [n_int] table of each interval
+  const int32_t* tab_base;  // [n_tab] first csr_off entry of the table
+  const int32_t* tab_nant;  // [n_tab] antennas the table spans
+  const int32_t* csr_off;   // per table: tiles x (tab_nant + 1) offsets into csr_ent
+  const int32_t* csr_ent;   // slot offsets
+  // work items: (interval, sample range); items of one interval are consecutive
+  const int32_t* item_int;
+  const int32_t* item_s0;
+  const int32_t* item_s1;
+  const int64_t* item_scr;  // scratch offset (elements) of the item's per-antenna partials
+  const int32_t* n_chunks;  // [n_int] items per interval
+  const int32_t* first_item;
+  int32_t n_items;
+  int32_t na_max;
+  // iteration state
+  int32_t* active;
+  int32_t* iters;
+  int32_t* status;
+  int32_t* counters;  // [n_int] chunk arrival counters (reset by the last arrival)
+  int32_t* n_active;  // intervals still iterating
+  int32_t* qhead;     // [2] work-queue heads, used alternately by consecutive launches
+  void* scratch;
+  double tol;
+  int32_t max_iter;
+  int32_t schedule;
+  int32_t k;  // iteration number, 1-based
+  // accumulate-only outputs
+  void* jhd_out;
+  void* jhj_out;
+};
+
+// Launchers implemented in di_kernels.cu.  kind: 0 scalar, 1 jones.  Return cudaError_t as int.
+int di_smem_bytes(int kind, int dtype, int na_max);
+int di_max_blocks_per_sm(int kind, int dtype, int acc_only, int smem, int* out);
+int di_launch_iter(int kind, int dtype, int acc_only, const DIArgs& a, int grid, int smem, void* stream);
+int di_launch_init(const DIArgs& a, int n_int, int n_active0, void* stream);
+int di_launch_chi2(int kind, int dtype, const DIArgs& a, double* item_chi2, double* chi2_out, int n_int,
+                   int grid, void* stream);
+
+}  // namespace gc
