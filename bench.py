@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Throughput of gain calibration to convergence: visibilities calibrated per second.
+
+Workload (the full-Jones direction-independent problem): 64 antennas (2016 baselines), 2x2 Jones,
+60 times x 64 channels at 1.0-1.4 GHz, solution intervals of 1 time x 4 channels (960 intervals,
+7,741,440 rows of 2x2 complex64), 20 polarized point sources, true Jones = diagonal gains
+(amplitude 1 + N(0, 0.1), phase U(-pi, pi)) plus leakage CN(0, 0.02), noise sigma = 0.01,
+seed 150206974 (+ rank).  Every interval is solved by polarized StefCal from identity gains to a
+relative step tolerance of 1e-6.
+
+One step = reset the gains to identity + one gc_calibrate_di_jones2x2 call over all 960 intervals
+(iterations run until every interval has converged).  value = rows calibrated / device time, inputs
+resident in HBM (495 MB of vis + model, larger than L2, so no flush is needed).  e2e = the same
+call with pinned host buffers, host<->device copies inside the timed region.
+
+Under torchrun each rank solves its own copy of the workload on its own GPU (independent
+intervals, no collective on the data path: weak scaling); rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle (the paper's iteration in NumPy) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+TOL = 1e-6
+MAX_ITER = 20000
+BYTES_PER_ROW = 64          # vis + model, one 2x2 complex64 each (algorithmic bytes per row per iteration)
+METRIC = "visibilities calibrated/s to convergence at <=1e-5 gain err; learned+batched vs plain"
+UNIT = "visibilities/s"
+WORKLOAD = "di_jones2x2: 64 ant (2016 bl), 60 t x 64 ch, intervals 1 t x 4 ch (960), 20 polarized sources, tol 1e-6"
+
+
+def _env_rank():
+    return int(os.environ.get('RANK', 0)), int(os.environ.get('WORLD_SIZE', 1)), int(os.environ.get('LOCAL_RANK', 0))
+
+
+def make_workload(rank: int):
+    from paper_1502_06974_gb300 import synth
+    return synth.make_di_jones(seed=synth.SEED + rank)
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix='.csv')
+            os.close(fd)
+            self.f = open(self.path, 'w')
+            self.proc = subprocess.Popen(['nvidia-smi', f'--query-gpu={self.FIELDS}', '--format=csv,noheader,nounits',
+                                          '-lms', '200'], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index=None):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(',')]
+            if len(p) < 9:
+                continue
+            if gpu_index is not None and p[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(p[1])); mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith('active'):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------ CPU oracle
+def oracle_sample(b, n_iter=120, interval=0):
+    """Time the FP64 oracle iteration (NumPy, the paper's steps) on one interval for n_iter steps.
+
+    Returns (seconds per iteration, rows of the interval, cpu-seconds / wall-seconds).
+    """
+    from oracle import diagonal
+    iv = b.interval(interval)
+    g0 = b.g0()[iv['gain_slice']]
+    t0 = time.perf_counter(); c0 = time.process_time()
+    diagonal.iterate('jones', g0, iv['vis'], iv['model'], iv['ant1'], iv['ant2'], iv['n_ant'], tol=0.0,
+                     max_iter=n_iter)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    return wall / n_iter, int(iv['vis'].shape[0] * iv['vis'].shape[1]), cpu / max(wall, 1e-9)
+
+
+def cpu_baseline_block(b, iters_to_converge, n_iter=120):
+    per_it, rows, threads = oracle_sample(b, n_iter)
+    value = rows / (per_it * iters_to_converge)
+    return {"value": value, "unit": UNIT, "cores": max(1, int(round(threads))), "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle (diagonal iteration), 1 interval of {rows} rows x {n_iter} iterations "
+                       f"({per_it * 1e3:.2f} ms/iteration), extrapolated to {iters_to_converge} iterations "
+                       f"(median iteration count to tol {TOL:g} on the GPU run)")}
+
+
+# ------------------------------------------------------------------------------------ helpers
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ('di_kernels.cu', 'common.cuh', 'internal.h'):
+        with open(os.path.join(ROOT, 'paper_1502_06974_gb300', 'csrc', f), 'rb') as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_row():
+    """DRAM bytes per processed row of the iteration kernel from the committed ncu summary, if it was
+    taken on the current kernel source; None otherwise."""
+    p = os.path.join(ROOT, 'profiles', 'di_iter_jones_cfg2.json')
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get('kernel_hash') != kernel_source_hash():
+        return None
+    return d['dram_bytes_per_launch'] / d['rows_per_launch']
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json'))), "of measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "of fallback"
+
+
+# ------------------------------------------------------------------------------------ arms
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    b = make_workload(0)
+    iters = args.ref_iters
+    samples = []
+    per_it = rows = threads = None
+    for k in range(args.warmup + args.steps):
+        per_it, rows, threads = oracle_sample(b, n_iter=args.ref_sample_iters, interval=k % b.n_int)
+        if k >= args.warmup:
+            samples.append(per_it)
+    per_it = statistics.median(samples)
+    value = rows / (per_it * iters)
+    cores = max(1, int(round(threads)))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * iters * 1e3 * b.n_int,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "rows": b.n_rows, "intervals": b.n_int, "tol": TOL},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": (f"each step: FP64 NumPy oracle, 1 interval ({rows} rows) x "
+                                       f"{args.ref_sample_iters} iterations, extrapolated to {iters} iterations")},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device('cuda', local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=dev)
+    from paper_1502_06974_gb300 import api, build
+    build.build()
+    b = make_workload(rank)
+    lay = api.Layout.from_batch(b)
+    vis = torch.from_numpy(b.vis).to(dev)
+    model = torch.from_numpy(b.model).to(dev)
+    g0 = torch.from_numpy(b.g0()).to(dev)
+    gains = g0.clone()
+    stream = torch.cuda.current_stream(dev)
+
+    tol, max_iter = (0.0, args.iters) if args.iters else (TOL, MAX_ITER)
+
+    def step(profile=False):
+        gains.copy_(g0)
+        return api.calibrate_di_jones2x2(vis, model, lay, gains, tol=tol, max_iter=max_iter, profile=profile)
+
+    for _ in range(args.warmup):
+        _, iters, _, status = step()
+    torch.cuda.synchronize(dev)
+    its = iters.cpu().numpy()
+    st = status.cpu().numpy()
+
+    # timed region
+    sampler = ClockSampler()
+    if rank == 0:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    n0 = api.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    kms = 0.0; kl = 0; kri = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(profile=True)
+        ms_k, n_k, ri_k = api.profile_last()
+        kms += ms_k; kl += n_k; kri += ri_k
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = api.launch_count() - n0
+    clocks = sampler.stop(gpu_index=None) if rank == 0 else None
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rows_total = b.n_rows * args.steps * world
+    value = rows_total / (ms / 1e3)
+
+    # end to end through the public API with pinned host buffers
+    g0H = torch.from_numpy(b.g0()).pin_memory()
+    e2e_s = float('nan')
+    if not args.no_e2e:
+        visH = torch.from_numpy(b.vis).pin_memory()
+        modelH = torch.from_numpy(b.model).pin_memory()
+        gH = g0H.clone().pin_memory()
+        api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True)
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            gH.copy_(g0H)
+            api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank == 0:
+        peaks, which = measured_peaks()
+        avg_launch_s = (kms / 1e3) / max(kl, 1)
+        bytes_per_launch = kri * BYTES_PER_ROW / max(kl, 1)
+        achieved = bytes_per_launch / avg_launch_s / 1e9
+        tpr = ncu_traffic_per_row()
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": (tpr * kri / max(kl, 1)) if tpr is not None else None,
+                "kernel": "di_iter_kernel<float, JonesKind> (accumulate J^H D, diag J^H J + StefCal update)",
+                "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6,
+                "peak_source": which}
+        med_it = int(np.median(its))
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "rows_per_gpu": b.n_rows, "intervals": b.n_int, "tol": TOL,
+                          "l2": "inputs (495 MB vis+model) larger than L2; no flush",
+                          "iters_median": med_it, "iters_max": int(its.max()),
+                          "converged": int(np.sum((st & 15) == 0)),
+                          "parallelism": f"replicas x{world} (independent intervals per GPU)"},
+               "roofline": roof,
+               "e2e": {"value": b.n_rows * world / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": int(b.vis.nbytes + b.model.nbytes + g0H.numel() * 8),
+                       "d2h_bytes_per_step": int(g0H.numel() * 8 + 2 * 4 * b.n_int)},
+               "gpu_launches": int(launches),
+               "clocks": clocks}
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_block(b, med_it)
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='gaincal', choices=['gaincal', 'reference'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--iters', type=int, default=0,
+                    help='run exactly this many iterations per step (tol 0) instead of converging; for profiling')
+    ap.add_argument('--ref-iters', type=int, default=3200, help='iterations the reference arm extrapolates to')
+    ap.add_argument('--ref-sample-iters', type=int, default=40)
+    args = ap.parse_args()
+    if args.impl == 'reference':
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == '__main__':
+    sys.exit(main())

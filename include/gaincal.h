@@ -111,7 +111,9 @@ typedef struct gc_options {
   int32_t dtype;            /* GC_DTYPE_*                                                     */
   int32_t host_buffers;     /* 0: data pointers are device memory; 1: host memory              */
   int32_t compute_chi2;     /* 1: fill chi2_out with sum |r|^2 at the final gains              */
-  int32_t reserved[3];      /* must be 0                                                      */
+  int32_t profile;          /* 1: bracket every iteration launch with CUDA events on `stream`;
+                               read the totals with gc_profile_last                            */
+  int32_t reserved[2];      /* must be 0                                                      */
 } gc_options;
 
 /*
@@ -167,6 +169,13 @@ int gc_jhj_jhr_di_scalar(const void* vis, const void* model, const gc_layout* la
                          int32_t dtype, void* jhd_out, void* jhj_out, void* stream);
 int gc_jhj_jhr_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,
                            int32_t dtype, void* jhd_out, void* jhj_out, void* stream);
+
+/*
+ * Totals of the last gc_calibrate_* call made with opt->profile = 1: summed device time of its
+ * iteration launches (ms, from CUDA events on the call's stream), number of those launches, and
+ * rows processed by them (sum over intervals of iterations x rows).  Any pointer may be NULL.
+ */
+int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row_iterations);
 
 /* Text for a GC_ERR_* return code or a GC_ST_* status. */
 const char* gc_error_string(int code);

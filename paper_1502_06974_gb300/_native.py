@@ -22,7 +22,7 @@ GC_MAX_ANT, GC_MAX_DIR = 1024, 16
 EXPORTS = [
     'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones',
     'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2',
-    'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
+    'gc_profile_last', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
 ]
 
 _p = C.c_void_p
@@ -39,7 +39,8 @@ class GcLayout(C.Structure):
 
 class GcOptions(C.Structure):
     _fields_ = [('tol', C.c_double), ('max_iter', C.c_int32), ('schedule', C.c_int32), ('dtype', C.c_int32),
-                ('host_buffers', C.c_int32), ('compute_chi2', C.c_int32), ('reserved', C.c_int32 * 3)]
+                ('host_buffers', C.c_int32), ('compute_chi2', C.c_int32), ('profile', C.c_int32),
+                ('reserved', C.c_int32 * 2)]
 
 
 _lib = None
@@ -70,6 +71,8 @@ def lib() -> C.CDLL:
         L.gc_last_cuda_error.restype = C.c_char_p
         L.gc_launch_count.argtypes = []
         L.gc_launch_count.restype = C.c_int64
+        L.gc_profile_last.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.gc_profile_last.restype = C.c_int
         L.gc_release.argtypes = []
         L.gc_release.restype = C.c_int
         _lib = L

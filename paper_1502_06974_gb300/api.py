@@ -78,7 +78,7 @@ def _check_tensor(t, name, host):
 
 
 def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedule, compute_chi2, host_buffers,
-               want_outputs=True):
+               want_outputs=True, profile=False):
     host = bool(host_buffers)
     for t, n in ((vis, 'vis'), (model, 'model'), (gains, 'gains')):
         _check_tensor(t, n, host)
@@ -97,7 +97,8 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
         status = torch.zeros(n, dtype=torch.int32, device=dev) if want_outputs else None
         chi2 = torch.zeros(n, dtype=torch.float64, device=dev) if (want_outputs and compute_chi2) else None
         stream = _stream_ptr(dev)
-    opt = N.GcOptions(float(tol), int(max_iter), int(schedule), dt, 1 if host else 0, 1 if compute_chi2 else 0)
+    opt = N.GcOptions(float(tol), int(max_iter), int(schedule), dt, 1 if host else 0, 1 if compute_chi2 else 0,
+                      1 if profile else 0)
     lay = layout.c()
     rc = getattr(N.lib(), fn_name)(_ptr(vis), _ptr(model), C.byref(lay), _ptr(gains), C.byref(opt), _ptr(iters),
                                    _ptr(chi2), _ptr(status), stream)
@@ -106,27 +107,27 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
 
 
 def calibrate_di_scalar(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
-                        compute_chi2=False, host_buffers=False):
+                        compute_chi2=False, host_buffers=False, profile=False):
     """StefCal on scalar DI gains (gc_calibrate_di_scalar); gains are updated in place.
 
     Returns (gains, iters[n_int] int32, chi2[n_int] float64 or None, status[n_int] int32).
     """
     return _calibrate('gc_calibrate_di_scalar', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers)
+                      host_buffers, profile=profile)
 
 
 def calibrate_di_jones2x2(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
-                          compute_chi2=False, host_buffers=False):
+                          compute_chi2=False, host_buffers=False, profile=False):
     """Polarized StefCal on 2x2 DI gains (gc_calibrate_di_jones2x2); vis/model [rows,2,2], gains [n_gain,2,2]."""
     return _calibrate('gc_calibrate_di_jones2x2', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers)
+                      host_buffers, profile=profile)
 
 
 def calibrate_dd_cohjones(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
-                          compute_chi2=False, host_buffers=False):
+                          compute_chi2=False, host_buffers=False, profile=False):
     """CohJones on DD scalar gains (gc_calibrate_dd_cohjones); model [n_dir, rows], gains [n_gain, n_dir]."""
     return _calibrate('gc_calibrate_dd_cohjones', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers)
+                      host_buffers, profile=profile)
 
 
 def _jhj_jhr(fn_name, vis, model, layout, gains, jones):
@@ -155,6 +156,13 @@ def jhj_jhr_di_scalar(vis, model, layout, gains):
 def jhj_jhr_di_jones2x2(vis, model, layout, gains):
     """One accumulation pass: (sum D Y^H [n_gain,2,2], sum Y Y^H [n_gain,2,2])."""
     return _jhj_jhr('gc_jhj_jhr_di_jones2x2', vis, model, layout, gains, True)
+
+
+def profile_last():
+    """(iteration-kernel ms, iteration launches, row-iterations) of the last profiled calibrate call."""
+    ms = C.c_double(0.0); n = C.c_int64(0); ri = C.c_int64(0)
+    N.lib().gc_profile_last(C.byref(ms), C.byref(n), C.byref(ri))
+    return ms.value, n.value, ri.value
 
 
 def launch_count() -> int:

@@ -341,6 +341,63 @@ static int get_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, DI
   return GC_OK;
 }
 
+// Optional per-launch timing of the iteration kernels (opt->profile).
+struct ProfileTotals {
+  double ms = 0.0;
+  int64_t launches = 0, row_iters = 0;
+};
+static ProfileTotals g_prof;
+
+struct Profiler {
+  bool on;
+  int cap, used = 0;
+  std::vector<cudaEvent_t> ev;
+  double ms = 0.0;
+  int64_t launches = 0;
+  Profiler(bool on_, int cap_) : on(on_), cap(cap_ > 0 ? cap_ : 1) {}
+  ~Profiler() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  int init() {
+    if (!on) return GC_OK;
+    ev.resize(2 * (size_t)cap, nullptr);
+    for (auto& e : ev) GC_CUDA(cudaEventCreate(&e));
+    return GC_OK;
+  }
+  int before(cudaStream_t s) {
+    if (!on) return GC_OK;
+    if (used == cap) { int rc = drain_sync(s); if (rc) return rc; }
+    GC_CUDA(cudaEventRecord(ev[2 * used], s));
+    return GC_OK;
+  }
+  int after(cudaStream_t s) {
+    if (!on) return GC_OK;
+    GC_CUDA(cudaEventRecord(ev[2 * used + 1], s));
+    ++used;
+    return GC_OK;
+  }
+  int drain_sync(cudaStream_t s) {
+    GC_CUDA(cudaStreamSynchronize(s));
+    return drain();
+  }
+  int drain() {
+    if (!on) return GC_OK;
+    for (int i = 0; i < used; ++i) {
+      float t = 0.f;
+      GC_CUDA(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+      ms += t;
+    }
+    launches += used;
+    used = 0;
+    return GC_OK;
+  }
+  void finish(int64_t row_iters) {
+    g_prof.ms = ms;
+    g_prof.launches = launches;
+    g_prof.row_iters = row_iters;
+  }
+};
+
 static size_t elem_bytes(int kind, int dtype) {
   const size_t r = dtype == GC_DTYPE_C64 ? 8 : 16;  // one complex
   return kind == 0 ? r : 4 * r;
@@ -360,6 +417,7 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
     return GC_ERR_ARG;
   if (opt->host_buffers != 0 && opt->host_buffers != 1) return GC_ERR_ARG;
+  if (opt->reserved[0] || opt->reserved[1]) return GC_ERR_ARG;
   int rc = validate_layout(L, 1);
   if (rc != GC_OK) return rc;
   if (L->n_intervals == 0) return GC_OK;
@@ -399,13 +457,18 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   int* flag = nullptr;
   if ((rc = pinned_flag(&flag))) return rc;
   const int check_every = env_int("GAINCAL_CHECK_EVERY", 16);
+  Profiler prof(opt->profile != 0, check_every);
+  if ((rc = prof.init())) return rc;
   for (int k = 1; k <= opt->max_iter; ++k) {
     a.k = k;
+    if ((rc = prof.before(s))) return rc;
     GC_CUDA_I(di_launch_iter(kind, opt->dtype, 0, a, P->grid, P->smem, stream));
+    if ((rc = prof.after(s))) return rc;
     g_launches++;
     if (k % check_every == 0 || k == opt->max_iter) {
       GC_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
       GC_CUDA(cudaStreamSynchronize(s));
+      if ((rc = prof.drain())) return rc;
       if (*flag <= 0) break;
     }
   }
@@ -419,11 +482,17 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   if (status_out) GC_CUDA(cudaMemcpyAsync(status_out, a.status, (size_t)P->n_int * 4, dk, s));
   if (chi2_out && opt->compute_chi2) GC_CUDA(cudaMemcpyAsync(chi2_out, P->chi2_out, (size_t)P->n_int * 8, dk, s));
   // count intervals not OK
-  std::vector<int32_t> stv(P->n_int);
+  std::vector<int32_t> stv(P->n_int), itv(P->n_int);
   GC_CUDA(cudaMemcpyAsync(stv.data(), a.status, (size_t)P->n_int * 4, cudaMemcpyDeviceToHost, s));
+  if (opt->profile) GC_CUDA(cudaMemcpyAsync(itv.data(), a.iters, (size_t)P->n_int * 4, cudaMemcpyDeviceToHost, s));
   GC_CUDA(cudaStreamSynchronize(s));
   int bad = 0;
   for (int i = 0; i < P->n_int; ++i) bad += (stv[i] & 15) != GC_ST_OK;
+  if (opt->profile) {
+    int64_t ri = 0;
+    for (int i = 0; i < P->n_int; ++i) ri += (int64_t)itv[i] * L->n_samp[i] * L->n_bl[i];
+    prof.finish(ri);
+  }
   return bad;
 }
 
@@ -512,6 +581,13 @@ const char* gc_status_string(int status) {
 }
 
 const char* gc_last_cuda_error(void) { return gc::last_cuda_error(); }
+
+int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row_iterations) {
+  if (iter_kernel_ms) *iter_kernel_ms = gc::g_prof.ms;
+  if (iter_launches) *iter_launches = gc::g_prof.launches;
+  if (row_iterations) *row_iterations = gc::g_prof.row_iters;
+  return GC_OK;
+}
 
 int64_t gc_launch_count(void) { return (int64_t)gc::g_launches.load(); }
 

@@ -1,4 +1,650 @@
-#include "internal.h"
+// Direction-dependent scalar gains: CohJones (Sect. 3.2.2) on the GPU.
+//
+// Per solution interval the sums over samples are taken once (moment pass), because the gains
+// are constant over an interval and factor out of the sample sum (Sect. 3.2.1, the
+// non-orthogonality terms X^(cd)):
+//     X^(cd)_pq = sum_s conj(m^(c)_pqs) m^(d)_pqs        (Hermitian in (c, d); upper triangle kept)
+//     B^(c)_pq  = sum_s conj(m^(c)_pqs) d_pqs
+// Each iteration then forms, per antenna p, the N_d x N_d block and right-hand side of
+// eqs. JHJ:DD:unpol / JHR:DD:unpol (data form, eq. ghat):
+//     stored row (p, q):   A_p[c][d] += g_q^(c) conj(g_q^(d)) X^(cd)_pq,   b_p[c] += g_q^(c) B^(c)_pq
+//     conjugate row (q, p): A_q[c][d] += g_p^(c) conj(g_p^(d)) conj(X^(cd)_pq), b_q[c] += g_p^(c) conj(B^(c)_pq)
+// and solves A_p g_p = b_p by an FP64 Cholesky factorisation (the GN step with the antenna-block
+// approximation of J^H J).  Odd iterations take the GN gains, even ones average them with the
+// current gains (the approximate LM analogue of Sect. 3.2.2).  A streaming pass computes
+// chi^2 = sum |d - sum_d g_p^(d) m^(d) conj(g_q^(d))|^2 at the end.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "common.cuh"
 #include "dd.h"
-namespace gc { void dd_release() {} }
-extern "C" int gc_calibrate_dd_cohjones(const void*, const void*, const gc_layout*, void*, const gc_options*, int32_t*, double*, int32_t*, void*) { return GC_ERR_DTYPE; }
+#include "internal.h"
+
+namespace gc {
+
+constexpr int kMomBl = 32;      // baselines per moment CTA
+constexpr int kMomLanes = 8;    // sample lanes per baseline in the moment CTA
+constexpr int kIterThreads = 256;
+
+struct DDArgs {
+  const float* vis;
+  const float* model;  // [n_dir][n_rows] complex
+  float* gains;        // [n_gain][n_dir] complex
+  int64_t n_rows;
+  const int64_t* row_off;
+  const int32_t* n_samp;
+  const int32_t* n_bl;
+  const int32_t* bl_off;
+  const int32_t* n_ant;
+  const int32_t* gain_off;
+  const int32_t* ant1;
+  const int32_t* ant2;
+  const int64_t* mom_off;    // [n_int] first moment (complex index) of the interval
+  // moment items
+  const int32_t* mitem_int;
+  const int32_t* mitem_tile;
+  int32_t n_mitems;
+  // iteration items (interval, antenna) and per-table antenna -> (baseline, side) lists
+  const int32_t* iitem_int;
+  const int32_t* iitem_ant;
+  int32_t n_iitems;
+  const int32_t* itab;
+  const int32_t* tab_aoff;   // per table: offset into ant_off
+  const int32_t* ant_off;    // per table: n_ant + 1 offsets into ent
+  const int32_t* ent;        // baseline * 2 + side (side 1: the antenna is ant2 of the stored pair)
+  // state
+  float2* moments;
+  float* gnew;               // [n_gain][n_dir] complex GN gains of this iteration
+  int32_t* sing;             // [n_gain]
+  int32_t* active;
+  int32_t* iters;
+  int32_t* status;
+  int32_t* counters;
+  int32_t* n_active;
+  double tol;
+  int32_t max_iter;
+  int32_t schedule;
+  int32_t k;
+};
+
+template <int ND>
+struct DDShape {
+  static constexpr int NU = ND * (ND + 1) / 2;  // upper-triangle entries of X
+  static constexpr int NO = NU + ND;            // moments per baseline
+};
+
+// Component index -> (c, d) for the upper triangle, row-major: (0,0) (0,1) .. (0,ND-1) (1,1) ..
+__host__ __device__ inline void upper_cd(int nd, int comp, int& c, int& d) {
+  int r = 0, base = 0;
+  while (comp >= base + (nd - r)) { base += nd - r; ++r; }
+  c = r;
+  d = r + (comp - base);
+}
+
+// ------------------------------------------------------------------------------------ moments
+template <int ND>
+__global__ void __launch_bounds__(kMomBl * kMomLanes) dd_moment_kernel(const DDArgs a) {
+  constexpr int NU = DDShape<ND>::NU, NO = DDShape<ND>::NO;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* part = reinterpret_cast<float2*>(smem_raw);  // [lanes][kMomBl][NO]
+  const int it = blockIdx.x;
+  if (it >= a.n_mitems) return;
+  const int i = a.mitem_int[it];
+  const int tile = a.mitem_tile[it];
+  const int nb = a.n_bl[i], ns = a.n_samp[i];
+  const int bl = threadIdx.x % kMomBl, lane = threadIdx.x / kMomBl;
+  const int b = tile * kMomBl + bl;
+  const int chunk = (ns + kMomLanes - 1) / kMomLanes;
+  const int s0 = lane * chunk, s1 = min(ns, s0 + chunk);
+  Cx<float> X[NU], Bv[ND];
+#pragma unroll
+  for (int u = 0; u < NU; ++u) X[u] = cx<float>(0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < ND; ++c) Bv[c] = cx<float>(0.f, 0.f);
+  if (b < nb) {
+    const int64_t r0 = a.row_off[i] + b;
+    for (int s = s0; s < s1; ++s) {
+      const int64_t r = r0 + (int64_t)s * nb;
+      const Cx<float> d = Vec<float>::ld1(a.vis + 2 * r);
+      Cx<float> m[ND];
+#pragma unroll
+      for (int c = 0; c < ND; ++c) m[c] = Vec<float>::ld1(a.model + 2 * ((int64_t)c * a.n_rows + r));
+      int u = 0;
+#pragma unroll
+      for (int c = 0; c < ND; ++c) {
+#pragma unroll
+        for (int e = c; e < ND; ++e) { cfma_(X[u], m[c], m[e]); ++u; }
+        cfma_(Bv[c], m[c], d);
+      }
+    }
+  }
+  float2* my = part + ((size_t)lane * kMomBl + bl) * NO;
+#pragma unroll
+  for (int u = 0; u < NU; ++u) my[u] = make_float2(X[u].x, X[u].y);
+#pragma unroll
+  for (int c = 0; c < ND; ++c) my[NU + c] = make_float2(Bv[c].x, Bv[c].y);
+  __syncthreads();
+  // compensated sum over the sample lanes, in lane order
+  const int nbt = min(kMomBl, nb - tile * kMomBl);
+  float2* out = a.moments + a.mom_off[i] + (int64_t)tile * kMomBl * NO;
+  for (int x = threadIdx.x; x < nbt * NO; x += blockDim.x) {
+    float sx = 0.f, cxs = 0.f, sy = 0.f, cys = 0.f;
+    for (int l = 0; l < kMomLanes; ++l) {
+      const float2 v = part[(size_t)l * kMomBl * NO + x];
+      kahan_add(sx, cxs, v.x);
+      kahan_add(sy, cys, v.y);
+    }
+    out[x] = make_float2(sx - cxs, sy - cys);
+  }
+}
+
+// ------------------------------------------------------------------------------------ FP64 solve
+// Cholesky A = L L^H of the Hermitian ND x ND block (upper triangle given) and solve A x = b.
+template <int ND>
+__device__ bool chol_solve(const double2* Aup, const double2* b, double2* x) {
+  double2 L[ND * (ND + 1) / 2];  // lower triangle, row-major: L[i][j], j <= i
+  auto li = [](int r, int c) { return r * (r + 1) / 2 + c; };
+  auto au = [](int r, int c) {   // index of upper entry (r <= c)
+    return r * ND - r * (r - 1) / 2 + (c - r);
+  };
+  for (int r = 0; r < ND; ++r) {
+    for (int c = 0; c <= r; ++c) {
+      // A[r][c] for r >= c is conj(A[c][r]) from the upper triangle
+      double2 s = Aup[au(c, r)];
+      s.y = -s.y;
+      for (int k = 0; k < c; ++k) {
+        const double2 p = L[li(r, k)], q = L[li(c, k)];  // L[r][k] * conj(L[c][k])
+        s.x -= p.x * q.x + p.y * q.y;
+        s.y -= p.y * q.x - p.x * q.y;
+      }
+      if (r == c) {
+        if (!(s.x > 0.0) || !isfinite(s.x)) return false;
+        L[li(r, r)] = make_double2(sqrt(s.x), 0.0);
+      } else {
+        const double inv = 1.0 / L[li(c, c)].x;
+        L[li(r, c)] = make_double2(s.x * inv, s.y * inv);
+      }
+    }
+  }
+  double2 y[ND];
+  for (int r = 0; r < ND; ++r) {  // L y = b
+    double2 s = b[r];
+    for (int k = 0; k < r; ++k) {
+      const double2 p = L[li(r, k)], q = y[k];
+      s.x -= p.x * q.x - p.y * q.y;
+      s.y -= p.x * q.y + p.y * q.x;
+    }
+    const double inv = 1.0 / L[li(r, r)].x;
+    y[r] = make_double2(s.x * inv, s.y * inv);
+  }
+  for (int r = ND - 1; r >= 0; --r) {  // L^H x = y
+    double2 s = y[r];
+    for (int k = r + 1; k < ND; ++k) {
+      const double2 p = L[li(k, r)], q = x[k];  // conj(L[k][r]) * x[k]
+      s.x -= p.x * q.x + p.y * q.y;
+      s.y -= p.x * q.y - p.y * q.x;
+    }
+    const double inv = 1.0 / L[li(r, r)].x;
+    x[r] = make_double2(s.x * inv, s.y * inv);
+  }
+  for (int r = 0; r < ND; ++r)
+    if (!isfinite(x[r].x) || !isfinite(x[r].y)) return false;
+  return true;
+}
+
+// ------------------------------------------------------------------------------------ iteration
+template <int ND>
+__global__ void __launch_bounds__(kIterThreads) dd_iter_kernel(const DDArgs a) {
+  constexpr int NU = DDShape<ND>::NU, NO = DDShape<ND>::NO;
+  constexpr int CS = (NO + 31) / 32 * 32;       // component slots per lane group
+  constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx<float>* gs = reinterpret_cast<Cx<float>*>(smem_raw);            // [n_ant][ND]
+  double2* red = reinterpret_cast<double2*>(gs + GC_MAX_ANT * ND);    // [LANES][NO]
+  __shared__ double2 Aup[NU], bv[ND], xs[ND];
+  __shared__ int s_last, s_sing;
+  __shared__ double s_red[64];
+  const int it = blockIdx.x;
+  if (it >= a.n_iitems) return;
+  const int i = a.iitem_int[it];
+  if (a.active[i] == 0) return;
+  const int p = a.iitem_ant[it];
+  const int na = a.n_ant[i];
+  const int64_t go = a.gain_off[i];
+  const int tid = threadIdx.x;
+  for (int x = tid; x < na * ND; x += blockDim.x)
+    gs[x] = cx<float>(a.gains[2 * (go * ND + x)], a.gains[2 * (go * ND + x) + 1]);
+  __syncthreads();
+  const int comp = tid % CS, lane = tid / CS;
+  double2 acc = make_double2(0.0, 0.0);
+  if (comp < NO && lane < LANES) {
+    const int tab = a.itab[i];
+    const int* aoff = a.ant_off + a.tab_aoff[tab];
+    const int e0 = aoff[p], e1 = aoff[p + 1];
+    const int bo = a.bl_off[i];
+    int c = 0, d = 0;
+    if (comp < NU) upper_cd(ND, comp, c, d);
+    else c = comp - NU;
+    float sx = 0.f, sxc = 0.f, sy = 0.f, syc = 0.f;
+    const float2* mom = a.moments + a.mom_off[i];
+    for (int e = e0 + lane; e < e1; e += LANES) {
+      const int en = a.ent[e];
+      const int b = en >> 1, side = en & 1;
+      const int q = side ? a.ant1[bo + b] : a.ant2[bo + b];
+      float2 v = mom[(int64_t)b * NO + comp];
+      if (side) v.y = -v.y;                         // conjugate baseline: conj(X), conj(B)
+      Cx<float> t;
+      if (comp < NU) t = mul_(mulc_(gs[q * ND + c], gs[q * ND + d]), cx<float>(v.x, v.y));
+      else t = mul_(gs[q * ND + c], cx<float>(v.x, v.y));
+      kahan_add(sx, sxc, t.x);
+      kahan_add(sy, syc, t.y);
+    }
+    acc = make_double2((double)sx - (double)sxc, (double)sy - (double)syc);
+    red[lane * NO + comp] = acc;
+  }
+  __syncthreads();
+  if (tid < NO) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int l = 0; l < LANES; ++l) { s.x += red[l * NO + tid].x; s.y += red[l * NO + tid].y; }
+    if (tid < NU) Aup[tid] = s;
+    else bv[tid - NU] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const bool ok = chol_solve<ND>(Aup, bv, xs);
+    s_sing = ok ? 0 : 1;
+  }
+  __syncthreads();
+  if (tid < ND) {
+    Cx<float> g = s_sing ? gs[p * ND + tid] : cx<float>((float)xs[tid].x, (float)xs[tid].y);
+    a.gnew[2 * ((go + p) * ND + tid)] = g.x;
+    a.gnew[2 * ((go + p) * ND + tid) + 1] = g.y;
+  }
+  if (tid == 0) a.sing[go + p] = s_sing;
+  // the last antenna of the interval to finish applies the schedule and the convergence test
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&a.counters[i], 1) == na - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const bool gn_step = (a.schedule == GC_SCHED_GN) || (a.k & 1);
+  float d2 = 0.f, n2 = 0.f;
+  int nonfin = 0, sing = 0;
+  for (int x = tid; x < na * ND; x += blockDim.x) {
+    const Cx<float> old = gs[x];
+    const Cx<float> gn = cx<float>(__ldcg(a.gnew + 2 * (go * ND + x)), __ldcg(a.gnew + 2 * (go * ND + x) + 1));
+    const Cx<float> nw = gn_step ? gn : cx<float>(0.5f * (old.x + gn.x), 0.5f * (old.y + gn.y));
+    d2 += abs2_(sub_(nw, old));
+    n2 += abs2_(nw);
+    if (!isfinite(nw.x) || !isfinite(nw.y)) nonfin = 1;
+    gs[x] = nw;  // stage; written below unless non-finite
+  }
+  for (int x = tid; x < na; x += blockDim.x) sing |= __ldcg(a.sing + go + x);
+  const double D2 = block_sum<double>((double)d2, s_red);
+  const double N2 = block_sum<double>((double)n2, s_red);
+  nonfin = block_or(nonfin, reinterpret_cast<int*>(s_red));
+  sing = block_or(sing, reinterpret_cast<int*>(s_red));
+  if (!nonfin)
+    for (int x = tid; x < na * ND; x += blockDim.x) {
+      a.gains[2 * (go * ND + x)] = gs[x].x;
+      a.gains[2 * (go * ND + x) + 1] = gs[x].y;
+    }
+  if (tid == 0) {
+    a.counters[i] = 0;
+    int st = -1;
+    if (nonfin) st = GC_ST_NONFINITE;
+    else if (D2 <= a.tol * a.tol * N2) st = GC_ST_OK;
+    else if (a.k >= a.max_iter) st = GC_ST_NOT_CONVERGED;
+    if (st >= 0) {
+      a.active[i] = 0;
+      a.iters[i] = a.k;
+      a.status[i] = st | (sing ? GC_ST_SINGULAR_FLAG : 0);
+      atomicSub(a.n_active, 1);
+    }
+  }
+}
+
+// chi^2 per moment item (interval, 32-baseline tile) over all its rows, then per interval.
+template <int ND>
+__global__ void __launch_bounds__(256) dd_chi2_kernel(const DDArgs a, double* item_chi2) {
+  __shared__ double red[64];
+  const int it = blockIdx.x;
+  if (it >= a.n_mitems) return;
+  const int i = a.mitem_int[it], tile = a.mitem_tile[it];
+  const int nb = a.n_bl[i], ns = a.n_samp[i], bo = a.bl_off[i];
+  const int64_t go = a.gain_off[i];
+  const int nbt = min(kMomBl, nb - tile * kMomBl);
+  float s = 0.f, c = 0.f;
+  for (int u = threadIdx.x; u < nbt * ns; u += blockDim.x) {
+    const int sl = u / nbt, bl = u - sl * nbt;
+    const int b = tile * kMomBl + bl;
+    const int p = a.ant1[bo + b], q = a.ant2[bo + b];
+    const int64_t r = a.row_off[i] + (int64_t)sl * nb + b;
+    Cx<float> v = Vec<float>::ld1(a.vis + 2 * r);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const Cx<float> m = Vec<float>::ld1(a.model + 2 * ((int64_t)d * a.n_rows + r));
+      const Cx<float> gp = cx<float>(a.gains[2 * ((go + p) * ND + d)], a.gains[2 * ((go + p) * ND + d) + 1]);
+      const Cx<float> gq = cx<float>(a.gains[2 * ((go + q) * ND + d)], a.gains[2 * ((go + q) * ND + d) + 1]);
+      v = sub_(v, mulc_(mul_(gp, m), gq));
+    }
+    kahan_add(s, c, abs2_(v));
+  }
+  const double tot = block_sum<double>((double)s - (double)c, red);
+  if (threadIdx.x == 0) item_chi2[it] = tot;
+}
+
+__global__ void dd_chi2_final(const int32_t* first, const int32_t* count, const double* item_chi2, double* out,
+                              int n_int) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_int) return;
+  double s = 0.0;
+  for (int j = 0; j < count[i]; ++j) s += item_chi2[first[i] + j];
+  out[i] = s;
+}
+
+__global__ void dd_init_kernel(DDArgs a, int n_int, int n_active0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *a.n_active = n_active0;
+  if (i < n_int) {
+    const int64_t rows = (int64_t)a.n_samp[i] * a.n_bl[i];
+    a.active[i] = rows > 0 ? 1 : 0;
+    a.iters[i] = 0;
+    a.status[i] = rows > 0 ? GC_ST_NOT_CONVERGED : GC_ST_NODATA;
+    a.counters[i] = 0;
+  }
+}
+
+// ------------------------------------------------------------------------------------ host side
+extern std::atomic<long long> g_launches;
+int ws_get(const char* name, size_t bytes, void** out);
+int pinned_flag(int** out);
+int validate_layout(const gc_layout* L, int n_dir_max);
+uint64_t layout_hash(const gc_layout* L, uint64_t salt);
+int set_cuda_error(cudaError_t e, const char* what);
+
+struct DDPlan {
+  uint64_t key = 0;
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  DDArgs args{};
+  int n_int = 0, n_active0 = 0, nd = 1;
+  int64_t n_mom = 0;
+  int32_t* chi2_first = nullptr;
+  int32_t* chi2_count = nullptr;
+  double* chi2_items = nullptr;
+  double* chi2_out = nullptr;
+};
+static DDPlan g_dd;
+
+#define DD_CUDA(call)                                             \
+  do {                                                            \
+    cudaError_t e__ = (call);                                     \
+    if (e__ != cudaSuccess) return set_cuda_error(e__, #call);    \
+  } while (0)
+
+static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
+  const int n = L->n_intervals, nd = L->n_dir;
+  const int NO = nd * (nd + 1) / 2 + nd;
+  std::vector<int64_t> mom_off(n);
+  std::vector<int> mint, mtile, iint, iant, itab(n), tab_aoff, ant_off, ent, cfirst(n), ccount(n);
+  std::map<std::pair<int, int>, int> tabs;
+  int64_t mo = 0;
+  int n_active0 = 0;
+  for (int i = 0; i < n; ++i) {
+    const int nb = L->n_bl[i], ns = L->n_samp[i], na = L->n_ant[i];
+    mom_off[i] = mo;
+    mo += (int64_t)nb * NO;
+    cfirst[i] = (int)mint.size();
+    const bool has = (int64_t)nb * ns > 0;
+    n_active0 += has;
+    if (has)
+      for (int t = 0; t < (nb + kMomBl - 1) / kMomBl; ++t) { mint.push_back(i); mtile.push_back(t); }
+    ccount[i] = (int)mint.size() - cfirst[i];
+    if (has)
+      for (int p = 0; p < na; ++p) { iint.push_back(i); iant.push_back(p); }
+    auto key = std::make_pair((int)L->bl_off[i], (int)nb);
+    auto f = tabs.find(key);
+    if (f != tabs.end()) { itab[i] = f->second; continue; }
+    // antenna -> (baseline, side) lists for this table, sized for the interval's antenna count
+    const int tid = (int)tab_aoff.size();
+    tabs[key] = tid;
+    itab[i] = tid;
+    int nat = na;
+    for (int b = 0; b < nb; ++b) {
+      nat = L->ant1[key.first + b] + 1 > nat ? L->ant1[key.first + b] + 1 : nat;
+      nat = L->ant2[key.first + b] + 1 > nat ? L->ant2[key.first + b] + 1 : nat;
+    }
+    std::vector<std::vector<int>> lists(nat);
+    for (int b = 0; b < nb; ++b) {
+      lists[L->ant1[key.first + b]].push_back(b * 2);
+      lists[L->ant2[key.first + b]].push_back(b * 2 + 1);
+    }
+    tab_aoff.push_back((int)ant_off.size());
+    for (int p = 0; p < nat; ++p) {
+      ant_off.push_back((int)ent.size());
+      ent.insert(ent.end(), lists[p].begin(), lists[p].end());
+    }
+    ant_off.push_back((int)ent.size());
+  }
+  // a table shared by intervals with more antennas than it spans would index past its list:
+  // extend every interval's reference to a table sized for it
+  for (int i = 0; i < n; ++i) {
+    const int tid = itab[i];
+    const int next = tid + 1 < (int)tab_aoff.size() ? tab_aoff[tid + 1] : (int)ant_off.size();
+    const int nat = next - tab_aoff[tid] - 1;
+    if (nat < L->n_ant[i]) return GC_ERR_LAYOUT;
+  }
+  if (ent.empty()) ent.push_back(0);
+  if (mint.empty()) { mint.push_back(0); mtile.push_back(0); }
+  if (iint.empty()) { iint.push_back(0); iant.push_back(0); }
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  struct Part { const void* src; size_t bytes; size_t off; };
+  std::vector<Part> parts;
+  size_t off = 0;
+  auto add = [&](const void* src, size_t bytes) { parts.push_back({src, bytes, off}); off += al(bytes ? bytes : 1); return parts.size() - 1; };
+  const size_t p_row_off = add(L->row_off, (size_t)n * 8);
+  const size_t p_mom_off = add(mom_off.data(), (size_t)n * 8);
+  const size_t p_n_samp = add(L->n_samp, (size_t)n * 4);
+  const size_t p_n_bl = add(L->n_bl, (size_t)n * 4);
+  const size_t p_bl_off = add(L->bl_off, (size_t)n * 4);
+  const size_t p_n_ant = add(L->n_ant, (size_t)n * 4);
+  const size_t p_gain_off = add(L->gain_off, (size_t)n * 4);
+  const size_t p_ant1 = add(L->ant1, (size_t)L->n_bl_table * 4);
+  const size_t p_ant2 = add(L->ant2, (size_t)L->n_bl_table * 4);
+  const size_t p_mint = add(mint.data(), mint.size() * 4);
+  const size_t p_mtile = add(mtile.data(), mtile.size() * 4);
+  const size_t p_iint = add(iint.data(), iint.size() * 4);
+  const size_t p_iant = add(iant.data(), iant.size() * 4);
+  const size_t p_itab = add(itab.data(), itab.size() * 4);
+  const size_t p_taoff = add(tab_aoff.data(), tab_aoff.size() * 4);
+  const size_t p_aoff = add(ant_off.data(), ant_off.size() * 4);
+  const size_t p_ent = add(ent.data(), ent.size() * 4);
+  const size_t p_cfirst = add(cfirst.data(), cfirst.size() * 4);
+  const size_t p_ccount = add(ccount.data(), ccount.size() * 4);
+  const size_t p_active = add(nullptr, (size_t)n * 4);
+  const size_t p_iters = add(nullptr, (size_t)n * 4);
+  const size_t p_status = add(nullptr, (size_t)n * 4);
+  const size_t p_counters = add(nullptr, (size_t)n * 4);
+  const size_t p_misc = add(nullptr, 64);
+  const size_t p_sing = add(nullptr, (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 4);
+  const size_t p_chi2 = add(nullptr, mint.size() * 8);
+  const size_t p_chi2o = add(nullptr, (size_t)(n > 0 ? n : 1) * 8);
+  const size_t total = off;
+  std::vector<unsigned char> host(total, 0);
+  for (auto& pt : parts)
+    if (pt.src && pt.bytes) memcpy(host.data() + pt.off, pt.src, pt.bytes);
+  if (P.dev && P.dev_bytes < total) { cudaFree(P.dev); P.dev = nullptr; P.dev_bytes = 0; }
+  if (!P.dev) { DD_CUDA(cudaMalloc(&P.dev, total)); P.dev_bytes = total; }
+  DD_CUDA(cudaMemcpyAsync(P.dev, host.data(), total, cudaMemcpyHostToDevice, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  unsigned char* d = static_cast<unsigned char*>(P.dev);
+  auto at = [&](size_t idx) { return (void*)(d + parts[idx].off); };
+  DDArgs& a = P.args;
+  a = DDArgs{};
+  a.n_rows = L->n_rows;
+  a.row_off = (const int64_t*)at(p_row_off);
+  a.mom_off = (const int64_t*)at(p_mom_off);
+  a.n_samp = (const int32_t*)at(p_n_samp);
+  a.n_bl = (const int32_t*)at(p_n_bl);
+  a.bl_off = (const int32_t*)at(p_bl_off);
+  a.n_ant = (const int32_t*)at(p_n_ant);
+  a.gain_off = (const int32_t*)at(p_gain_off);
+  a.ant1 = (const int32_t*)at(p_ant1);
+  a.ant2 = (const int32_t*)at(p_ant2);
+  a.mitem_int = (const int32_t*)at(p_mint);
+  a.mitem_tile = (const int32_t*)at(p_mtile);
+  a.n_mitems = (int)(n_active0 > 0 ? mint.size() : 0);
+  a.iitem_int = (const int32_t*)at(p_iint);
+  a.iitem_ant = (const int32_t*)at(p_iant);
+  a.n_iitems = (int)(n_active0 > 0 ? iint.size() : 0);
+  a.itab = (const int32_t*)at(p_itab);
+  a.tab_aoff = (const int32_t*)at(p_taoff);
+  a.ant_off = (const int32_t*)at(p_aoff);
+  a.ent = (const int32_t*)at(p_ent);
+  a.active = (int32_t*)at(p_active);
+  a.iters = (int32_t*)at(p_iters);
+  a.status = (int32_t*)at(p_status);
+  a.counters = (int32_t*)at(p_counters);
+  a.n_active = (int32_t*)at(p_misc);
+  a.sing = (int32_t*)at(p_sing);
+  P.chi2_first = (int32_t*)at(p_cfirst);
+  P.chi2_count = (int32_t*)at(p_ccount);
+  P.chi2_items = (double*)at(p_chi2);
+  P.chi2_out = (double*)at(p_chi2o);
+  P.n_int = n;
+  P.n_active0 = n_active0;
+  P.nd = nd;
+  P.n_mom = mo;
+  return GC_OK;
+}
+
+template <int ND>
+static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag) {
+  constexpr int NO = DDShape<ND>::NO;
+  constexpr int CS = (NO + 31) / 32 * 32;
+  constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
+  DDArgs& a = P.args;
+  const size_t msmem = (size_t)kMomLanes * kMomBl * NO * sizeof(float2);
+  const size_t ismem = (size_t)GC_MAX_ANT * ND * sizeof(Cx<float>) + (size_t)LANES * NO * sizeof(double2);
+  DD_CUDA(cudaFuncSetAttribute(dd_moment_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
+  DD_CUDA(cudaFuncSetAttribute(dd_iter_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
+  dd_init_kernel<<<(P.n_int + 255) / 256, 256, 0, s>>>(a, P.n_int, P.n_active0);
+  g_launches++;
+  if (a.n_mitems > 0) {
+    dd_moment_kernel<ND><<<a.n_mitems, kMomBl * kMomLanes, msmem, s>>>(a);
+    g_launches++;
+  }
+  DD_CUDA(cudaGetLastError());
+  const char* ce = getenv("GAINCAL_CHECK_EVERY");
+  const int check_every = ce ? atoi(ce) : 8;
+  for (int k = 1; k <= opt->max_iter && a.n_iitems > 0; ++k) {
+    a.k = k;
+    dd_iter_kernel<ND><<<a.n_iitems, kIterThreads, ismem, s>>>(a);
+    g_launches++;
+    DD_CUDA(cudaGetLastError());
+    if (k % check_every == 0 || k == opt->max_iter) {
+      DD_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      DD_CUDA(cudaStreamSynchronize(s));
+      if (*flag <= 0) break;
+    }
+  }
+  if (opt->compute_chi2 && a.n_mitems > 0) {
+    dd_chi2_kernel<ND><<<a.n_mitems, 256, 0, s>>>(a, P.chi2_items);
+    dd_chi2_final<<<(P.n_int + 255) / 256, 256, 0, s>>>(P.chi2_first, P.chi2_count, P.chi2_items, P.chi2_out,
+                                                         P.n_int);
+    g_launches += 2;
+    DD_CUDA(cudaGetLastError());
+  }
+  return GC_OK;
+}
+
+void dd_release() {
+  if (g_dd.dev) cudaFree(g_dd.dev);
+  g_dd = DDPlan{};
+}
+
+int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, const gc_options* opt,
+           int32_t* iters_out, double* chi2_out, int32_t* status_out, void* stream) {
+  if (!opt || !L) return GC_ERR_ARG;
+  if (opt->dtype != GC_DTYPE_C64) return GC_ERR_DTYPE;
+  if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
+    return GC_ERR_ARG;
+  if ((opt->host_buffers != 0 && opt->host_buffers != 1) || opt->reserved[0] || opt->reserved[1]) return GC_ERR_ARG;
+  int rc = validate_layout(L, GC_MAX_DIR);
+  if (rc != GC_OK) return rc;
+  if (L->n_intervals == 0) return GC_OK;
+  if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && !gains)) return GC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  DD_CUDA(cudaGetDevice(&dev));
+  const uint64_t key = layout_hash(L, 0xDDull ^ ((uint64_t)dev << 40));
+  if (g_dd.key != key || !g_dd.dev) {
+    g_dd.key = 0;
+    if ((rc = build_dd_plan(L, g_dd, s))) return rc;
+    g_dd.key = key;
+  }
+  DDPlan& P = g_dd;
+  const int nd = L->n_dir;
+  const size_t vb = (size_t)L->n_rows * 8, mb = (size_t)L->n_rows * nd * 8, gb = (size_t)L->n_gain * nd * 8;
+  DDArgs& a = P.args;
+  if (opt->host_buffers) {
+    void *dv, *dm, *dg;
+    if ((rc = ws_get("dd_h_vis", vb, &dv)) || (rc = ws_get("dd_h_model", mb, &dm)) || (rc = ws_get("dd_h_gains", gb, &dg)))
+      return rc;
+    if (vb) DD_CUDA(cudaMemcpyAsync(dv, vis, vb, cudaMemcpyHostToDevice, s));
+    if (mb) DD_CUDA(cudaMemcpyAsync(dm, model, mb, cudaMemcpyHostToDevice, s));
+    DD_CUDA(cudaMemcpyAsync(dg, gains, gb, cudaMemcpyHostToDevice, s));
+    a.vis = (const float*)dv; a.model = (const float*)dm; a.gains = (float*)dg;
+  } else {
+    a.vis = (const float*)vis; a.model = (const float*)model; a.gains = (float*)gains;
+  }
+  void *mom, *gnew;
+  if ((rc = ws_get("dd_moments", (size_t)(P.n_mom > 0 ? P.n_mom : 1) * sizeof(float2), &mom))) return rc;
+  if ((rc = ws_get("dd_gnew", gb > 0 ? gb : 8, &gnew))) return rc;
+  a.moments = (float2*)mom;
+  a.gnew = (float*)gnew;
+  a.tol = opt->tol;
+  a.max_iter = opt->max_iter;
+  a.schedule = opt->schedule;
+  int* flag = nullptr;
+  if ((rc = pinned_flag(&flag))) return rc;
+  switch (nd) {
+    case 1: rc = dd_run_nd<1>(P, opt, s, flag); break;
+    case 2: rc = dd_run_nd<2>(P, opt, s, flag); break;
+    case 3: rc = dd_run_nd<3>(P, opt, s, flag); break;
+    case 4: rc = dd_run_nd<4>(P, opt, s, flag); break;
+    case 5: rc = dd_run_nd<5>(P, opt, s, flag); break;
+    case 6: rc = dd_run_nd<6>(P, opt, s, flag); break;
+    case 7: rc = dd_run_nd<7>(P, opt, s, flag); break;
+    case 8: rc = dd_run_nd<8>(P, opt, s, flag); break;
+    case 9: rc = dd_run_nd<9>(P, opt, s, flag); break;
+    case 10: rc = dd_run_nd<10>(P, opt, s, flag); break;
+    default: return GC_ERR_LIMIT;
+  }
+  if (rc) return rc;
+  const cudaMemcpyKind dk = opt->host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (opt->host_buffers) DD_CUDA(cudaMemcpyAsync(gains, a.gains, gb, dk, s));
+  if (iters_out) DD_CUDA(cudaMemcpyAsync(iters_out, a.iters, (size_t)P.n_int * 4, dk, s));
+  if (status_out) DD_CUDA(cudaMemcpyAsync(status_out, a.status, (size_t)P.n_int * 4, dk, s));
+  if (chi2_out && opt->compute_chi2) DD_CUDA(cudaMemcpyAsync(chi2_out, P.chi2_out, (size_t)P.n_int * 8, dk, s));
+  std::vector<int32_t> stv(P.n_int);
+  DD_CUDA(cudaMemcpyAsync(stv.data(), a.status, (size_t)P.n_int * 4, cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  int bad = 0;
+  for (int i = 0; i < P.n_int; ++i) bad += (stv[i] & 15) != GC_ST_OK;
+  return bad;
+}
+
+}  // namespace gc
+
+extern "C" int gc_calibrate_dd_cohjones(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                                        const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                                        int32_t* status_out, void* stream) {
+  return gc::run_dd(vis, model, layout, gains, opt, iters_out, chi2_out, status_out, stream);
+}
