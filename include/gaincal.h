@@ -86,7 +86,7 @@ extern "C" {
 #define GC_SCHED_GN 1       /* GN step every iteration                                        */
 
 #define GC_MAX_ANT 1024      /* antennas per interval                                          */
-#define GC_MAX_DIR 16        /* directions for the DD entry point                              */
+#define GC_MAX_DIR 10        /* directions for the DD entry point                              */
 
 typedef struct gc_layout {
   int32_t n_intervals;

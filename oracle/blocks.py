@@ -5,7 +5,7 @@ Test infrastructure only (see the package header).
 All sums run over the directed rows [pq s] with p != q (Sect. 2.1 eq. JJ:di and Sect. 2.3):
 every stored baseline (p, q) also stands for its conjugate row (q, p) with
 d_qp = conj(d_pq), m_qp = conj(m_pq) (scalar) or D_qp = D_pq^H, M_qp = M_pq^H (2x2, Sect. 4).
-``np.add.at`` is the only primitive used to sum rows into antennas.
+``np.add.at`` (and, for the N_d x N_d blocks, one matrix product per antenna) sums rows into antennas.
 """
 from __future__ import annotations
 
@@ -98,7 +98,10 @@ def dd_blocks(g, vis, model, a1, a2, n_ant):
     A = np.zeros((n_ant, nd, nd), np.complex128)
     c = np.zeros((n_ant, nd), np.complex128)
     cd = np.zeros((n_ant, nd), np.complex128)
-    np.add.at(A, i, np.einsum('cr,dr->rcd', np.conj(y), y))
-    np.add.at(c, i, (np.conj(y) * r).T)
-    np.add.at(cd, i, (np.conj(y) * d).T)
+    for p in range(n_ant):                        # rows whose first antenna is p: Y_p^H Y_p etc.
+        sel = i == p
+        Yp = y[:, sel].T                          # [rows_p, Nd]
+        A[p] = np.conj(Yp).T @ Yp
+        c[p] = np.conj(Yp).T @ r[sel]
+        cd[p] = np.conj(Yp).T @ d[sel]
     return dict(A=A, c=c, cd=cd)

@@ -16,7 +16,7 @@ GC_ERR = {-1: 'GC_ERR_ARG', -2: 'GC_ERR_LAYOUT', -3: 'GC_ERR_ANTENNA', -4: 'GC_E
 GC_ST_OK, GC_ST_NOT_CONVERGED, GC_ST_NONFINITE, GC_ST_NODATA, GC_ST_SINGULAR_FLAG = 0, 1, 2, 3, 16
 GC_DTYPE_C64, GC_DTYPE_C128 = 0, 1
 GC_SCHED_STEFCAL, GC_SCHED_GN = 0, 1
-GC_MAX_ANT, GC_MAX_DIR = 1024, 16
+GC_MAX_ANT, GC_MAX_DIR = 1024, 10
 
 # Every symbol include/gaincal.h declares (checked by the CPU test suite).
 EXPORTS = [

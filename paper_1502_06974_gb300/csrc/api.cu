@@ -74,6 +74,8 @@ int pinned_flag(int** out) {
 
 const char* last_cuda_error() { return g_cuda_err; }
 
+int set_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
 // ------------------------------------------------------------------------------------ layout checks
 int validate_layout(const gc_layout* L, int n_dir_required_max) {
   if (!L) return GC_ERR_ARG;

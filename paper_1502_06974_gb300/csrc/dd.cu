@@ -15,6 +15,7 @@
 // chi^2 = sum |d - sum_d g_p^(d) m^(d) conj(g_q^(d))|^2 at the end.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -69,6 +70,7 @@ struct DDArgs {
   int32_t max_iter;
   int32_t schedule;
   int32_t k;
+  int32_t na_max;
 };
 
 template <int ND>
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(kIterThreads) dd_iter_kernel(const DDArgs a) {
   constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<float>* gs = reinterpret_cast<Cx<float>*>(smem_raw);            // [n_ant][ND]
-  double2* red = reinterpret_cast<double2*>(gs + GC_MAX_ANT * ND);    // [LANES][NO]
+  double2* red = reinterpret_cast<double2*>(gs + a.na_max * ND);      // [LANES][NO]
   __shared__ double2 Aup[NU], bv[ND], xs[ND];
   __shared__ int s_last, s_sing;
   __shared__ double s_red[64];
@@ -395,9 +397,10 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
   std::vector<int> mint, mtile, iint, iant, itab(n), tab_aoff, ant_off, ent, cfirst(n), ccount(n);
   std::map<std::pair<int, int>, int> tabs;
   int64_t mo = 0;
-  int n_active0 = 0;
+  int n_active0 = 0, na_max = 1;
   for (int i = 0; i < n; ++i) {
     const int nb = L->n_bl[i], ns = L->n_samp[i], na = L->n_ant[i];
+    na_max = na > na_max ? na : na_max;
     mom_off[i] = mo;
     mo += (int64_t)nb * NO;
     cfirst[i] = (int)mint.size();
@@ -513,6 +516,7 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
   a.counters = (int32_t*)at(p_counters);
   a.n_active = (int32_t*)at(p_misc);
   a.sing = (int32_t*)at(p_sing);
+  a.na_max = na_max;
   P.chi2_first = (int32_t*)at(p_cfirst);
   P.chi2_count = (int32_t*)at(p_ccount);
   P.chi2_items = (double*)at(p_chi2);
@@ -531,7 +535,7 @@ static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag
   constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
   DDArgs& a = P.args;
   const size_t msmem = (size_t)kMomLanes * kMomBl * NO * sizeof(float2);
-  const size_t ismem = (size_t)GC_MAX_ANT * ND * sizeof(Cx<float>) + (size_t)LANES * NO * sizeof(double2);
+  const size_t ismem = (size_t)a.na_max * ND * sizeof(Cx<float>) + (size_t)LANES * NO * sizeof(double2) + 16;
   DD_CUDA(cudaFuncSetAttribute(dd_moment_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
   DD_CUDA(cudaFuncSetAttribute(dd_iter_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
   dd_init_kernel<<<(P.n_int + 255) / 256, 256, 0, s>>>(a, P.n_int, P.n_active0);
