@@ -171,6 +171,34 @@ int gc_jhj_jhr_di_jones2x2(const void* vis, const void* model, const gc_layout* 
                            int32_t dtype, void* jhd_out, void* jhj_out, void* stream);
 
 /*
+ * gc_jhj_jhr_di_jones2x2 for callers that cannot allocate device memory.  (This entry point has no
+ * counterpart in the paper; it is a deployment variant of the accumulation pass above.)
+ *
+ * Who needs it: a caller that must not let a library call cudaMalloc -- for example a real-time
+ * pipeline that reserves all device memory when it starts and cannot afford an allocation that
+ * fails or stalls later, or an application whose own allocator owns the device memory.  This call
+ * allocates nothing: apart from the caller's inputs and outputs, everything the kernel needs (a
+ * copy of the layout, the reduction slot lists, work items, per-interval state and the per-item
+ * scratch sums) lives in one static device array of GC_NOALLOC_MAX_BYTES, which every GPU that
+ * loads the library holds until the process exits.
+ *   - Arguments, layouts and results are exactly those of gc_jhj_jhr_di_jones2x2 (device
+ *     pointers; the layout arrays are host memory).  At most 64 distinct baseline tables, n_dir 1.
+ *   - Returns GC_ERR_LIMIT when the layout, its work items and scratch need more than
+ *     GC_NOALLOC_MAX_BYTES; nothing is launched then.
+ *   - The first call on a device, with that device current, looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.
+ *   - All calls share the array and each call overwrites it (its state is re-initialised on the
+ *     device at the start of every call).  Calls whose GPU work overlaps -- on different streams
+ *     or from different host threads -- race; serialise them on one stream.
+ *   - The work is queued on `stream` and the call returns once the layout has been copied out of
+ *     the library's host staging area.
+ */
+#define GC_NOALLOC_MAX_BYTES (4u << 20)
+int gc_jhj_jhr_di_jones2x2_noalloc(const void* vis, const void* model, const gc_layout* layout,
+                                   const void* gains, int32_t dtype, void* jhd_out, void* jhj_out,
+                                   void* stream);
+
+/*
  * Totals of the last gc_calibrate_* call made with opt->profile = 1: summed device time of its
  * iteration launches (ms, from CUDA events on the call's stream), number of those launches, and
  * rows processed by them (sum over intervals of iterations x rows).  Any pointer may be NULL.

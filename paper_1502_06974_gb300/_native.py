@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, 'libgaincal.so')
 GC_OK = 0
 GC_ERR = {-1: 'GC_ERR_ARG', -2: 'GC_ERR_LAYOUT', -3: 'GC_ERR_ANTENNA', -4: 'GC_ERR_DTYPE', -5: 'GC_ERR_CUDA',
           -6: 'GC_ERR_LIMIT'}
+GC_ERR_LIMIT = -6
 GC_ST_OK, GC_ST_NOT_CONVERGED, GC_ST_NONFINITE, GC_ST_NODATA, GC_ST_SINGULAR_FLAG = 0, 1, 2, 3, 16
 GC_DTYPE_C64, GC_DTYPE_C128 = 0, 1
 GC_SCHED_STEFCAL, GC_SCHED_GN = 0, 1
@@ -21,7 +22,7 @@ GC_MAX_ANT, GC_MAX_DIR = 1024, 10
 # Every symbol include/gaincal.h declares (checked by the CPU test suite).
 EXPORTS = [
     'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones',
-    'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2',
+    'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2', 'gc_jhj_jhr_di_jones2x2_noalloc',
     'gc_profile_last', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
 ]
 
@@ -59,7 +60,7 @@ def lib() -> C.CDLL:
             f = getattr(L, name)
             f.argtypes = cal
             f.restype = C.c_int
-        for name in ('gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2'):
+        for name in ('gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2', 'gc_jhj_jhr_di_jones2x2_noalloc'):
             f = getattr(L, name)
             f.argtypes = [_p, _p, C.POINTER(GcLayout), _p, C.c_int32, _p, _p, _p]
             f.restype = C.c_int
