@@ -37,6 +37,9 @@ sys.path.insert(0, ROOT)
 TOL = 1e-6
 MAX_ITER = 20000
 BYTES_PER_ROW = 64          # vis + model, one 2x2 complex64 each (algorithmic bytes per row per iteration)
+MOMENT_BYTES = 192          # per baseline: P (4x4 complex64) + R (4x4 float32), written once by the moment pass
+FLOP_PER_BASELINE_ITER = 320  # per baseline per iteration: 2 x (4x4 complex mat-vec + 4x4 real mat-vec)
+N_PATH_STREAM, N_PATH_RESIDENT, N_PATH_MOMENTS = 1, 2, 3
 METRIC = "visibilities calibrated/s to convergence at <=1e-5 gain err; learned+batched vs plain"
 UNIT = "visibilities/s"
 WORKLOAD = "di_jones2x2: 64 ant (2016 bl), 60 t x 64 ch, intervals 1 t x 4 ch (960), 20 polarized sources, tol 1e-6"
@@ -132,10 +135,23 @@ def cpu_baseline_block(b, iters_to_converge, n_iter=120):
 # ------------------------------------------------------------------------------------ helpers
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ('di_kernels.cu', 'common.cuh', 'internal.h'):
+    for f in ('di_kernels.cu', 'resident.cu', 'kinds.cuh', 'common.cuh', 'internal.h'):
         with open(os.path.join(ROOT, 'paper_1502_06974_gb300', 'csrc', f), 'rb') as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def ncu_traffic(name, unit):
+    """DRAM bytes per launch of a kernel from a committed ncu summary (json) when it was taken on the
+    current kernel sources; None otherwise."""
+    p = os.path.join(ROOT, 'profiles', name)
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get('kernel_hash') != kernel_source_hash():
+        return None
+    return d.get('dram_bytes_per_launch')
 
 
 def ncu_traffic_per_row():
@@ -209,7 +225,8 @@ def run_gpu(args):
 
     def step(profile=False):
         gains.copy_(g0)
-        return api.calibrate_di_jones2x2(vis, model, lay, gains, tol=tol, max_iter=max_iter, profile=profile)
+        return api.calibrate_di_jones2x2(vis, model, lay, gains, tol=tol, max_iter=max_iter, profile=profile,
+                                         path=args.path)
 
     for _ in range(args.warmup):
         _, iters, _, status = step()
@@ -226,12 +243,13 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     n0 = api.launch_count()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    kms = 0.0; kl = 0; kri = 0
+    kms = 0.0; kl = 0; kri = 0; kmom = 0.0; kbi = 0; path_used = None
     e0.record(stream)
     for _ in range(args.steps):
         step(profile=True)
         ms_k, n_k, ri_k = api.profile_last()
-        kms += ms_k; kl += n_k; kri += ri_k
+        mom_k, bi_k, path_used = api.profile_detail()
+        kms += ms_k; kl += n_k; kri += ri_k; kmom += mom_k; kbi += bi_k
     e1.record(stream)
     torch.cuda.synchronize(dev)
     if dist:
@@ -253,13 +271,14 @@ def run_gpu(args):
         visH = torch.from_numpy(b.vis).pin_memory()
         modelH = torch.from_numpy(b.model).pin_memory()
         gH = g0H.clone().pin_memory()
-        api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True)
+        api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True, path=args.path)
         e2e_steps = max(1, min(args.steps, 3))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             gH.copy_(g0H)
-            api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True)
+            api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True,
+                                      path=args.path)
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     if dist:
         t = torch.tensor([e2e_s], device=dev)
@@ -268,16 +287,55 @@ def run_gpu(args):
 
     if rank == 0:
         peaks, which = measured_peaks()
-        avg_launch_s = (kms / 1e3) / max(kl, 1)
-        bytes_per_launch = kri * BYTES_PER_ROW / max(kl, 1)
-        achieved = bytes_per_launch / avg_launch_s / 1e9
-        tpr = ncu_traffic_per_row()
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"],
-                "traffic": (tpr * kri / max(kl, 1)) if tpr is not None else None,
-                "kernel": "di_iter_kernel<float, JonesKind> (accumulate J^H D, diag J^H J + StefCal update)",
-                "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6,
-                "peak_source": which}
+        if path_used == N_PATH_RESIDENT:
+            # dominant kernel: the cluster-resident iteration kernel (one launch per step); the
+            # moment pass (HBM-bound) is reported beside it
+            n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+            sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+            peak_tf = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12        # FP32 FMA lanes x 2 flop x clock
+            flops = kbi * FLOP_PER_BASELINE_ITER
+            achieved = flops / (kms / 1e3) / 1e12
+            tpl = ncu_traffic('di_resident_jones_cfg2.json', 'resident')
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tf, "traffic": (tpl * kl / max(kl, 1)) if tpl is not None else None,
+                    "kernel": "di_resident_kernel<JonesMom> (moment-space J^H D / J^H J + 2x2 update, on chip)",
+                    "flop_per_launch": flops / max(kl, 1), "avg_launch_us": kms * 1e3 / max(kl, 1),
+                    "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
+            mom_bytes = (b.n_rows * BYTES_PER_ROW + b.n_int * int(b.n_bl[0]) * MOMENT_BYTES) * args.steps
+            roof_mom = {"bound": "hbm", "achieved": mom_bytes / (kmom / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": mom_bytes / (kmom / 1e3) / 1e9 / peaks["hbm_gbs"],
+                        "kernel": "di_moment_kernel<JonesMom>", "ms_per_step": kmom / args.steps,
+                        "peak_source": which}
+        elif path_used == N_PATH_MOMENTS:
+            # dominant kernel: the moment-stream iteration kernel, 192 B of moments per active
+            # baseline per iteration (HBM-bound); the one-off moment pass is reported beside it
+            avg_launch_s = (kms / 1e3) / max(kl, 1)
+            bytes_per_launch = kbi * MOMENT_BYTES / max(kl, 1)
+            achieved = bytes_per_launch / avg_launch_s / 1e9
+            tpl = ncu_traffic('di_miter_jones_cfg2.json', 'moments')
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": (tpl * (kbi / max(kl, 1)) / (b.n_int * int(b.n_bl[0]))) if tpl is not None else None,
+                    "kernel": "di_miter_kernel<JonesMom> (moment-space J^H D / diag J^H J + StefCal update)",
+                    "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6, "launches": kl,
+                    "peak_source": which}
+            mom_bytes = (b.n_rows * BYTES_PER_ROW + b.n_int * int(b.n_bl[0]) * MOMENT_BYTES) * args.steps
+            roof_mom = {"bound": "hbm", "achieved": mom_bytes / (kmom / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": mom_bytes / (kmom / 1e3) / 1e9 / peaks["hbm_gbs"],
+                        "kernel": "di_moment_kernel<JonesMom>", "ms_per_step": kmom / args.steps,
+                        "peak_source": which}
+        else:
+            avg_launch_s = (kms / 1e3) / max(kl, 1)
+            bytes_per_launch = kri * BYTES_PER_ROW / max(kl, 1)
+            achieved = bytes_per_launch / avg_launch_s / 1e9
+            tpr = ncu_traffic_per_row()
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": (tpr * kri / max(kl, 1)) if tpr is not None else None,
+                    "kernel": "di_iter_kernel<float, JonesKind> (accumulate J^H D, diag J^H J + StefCal update)",
+                    "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6,
+                    "peak_source": which}
+            roof_mom = None
         med_it = int(np.median(its))
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -288,6 +346,8 @@ def run_gpu(args):
                           "converged": int(np.sum((st & 15) == 0)),
                           "parallelism": f"replicas x{world} (independent intervals per GPU)"},
                "roofline": roof,
+               "roofline_moment_pass": roof_mom,
+               "path": {N_PATH_RESIDENT: "resident", N_PATH_MOMENTS: "moments"}.get(path_used, "stream"),
                "e2e": {"value": b.n_rows * world / e2e_s, "unit": UNIT,
                        "h2d_bytes_per_step": int(b.vis.nbytes + b.model.nbytes + g0H.numel() * 8),
                        "d2h_bytes_per_step": int(g0H.numel() * 8 + 2 * 4 * b.n_int)},
@@ -310,6 +370,7 @@ def main():
     ap.add_argument('--impl', default='gaincal', choices=['gaincal', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--path', type=int, default=0, help='0 auto (moments), 1 raw-row streaming, 2 resident, 3 moments')
     ap.add_argument('--iters', type=int, default=0,
                     help='run exactly this many iterations per step (tol 0) instead of converging; for profiling')
     ap.add_argument('--ref-iters', type=int, default=3200, help='iterations the reference arm extrapolates to')

@@ -111,10 +111,27 @@ typedef struct gc_options {
   int32_t dtype;            /* GC_DTYPE_*                                                     */
   int32_t host_buffers;     /* 0: data pointers are device memory; 1: host memory              */
   int32_t compute_chi2;     /* 1: fill chi2_out with sum |r|^2 at the final gains              */
-  int32_t profile;          /* 1: bracket every iteration launch with CUDA events on `stream`;
-                               read the totals with gc_profile_last                            */
-  int32_t reserved[2];      /* must be 0                                                      */
+  int32_t profile;          /* 1: time the iteration kernels with CUDA events on `stream`;
+                               read the totals with gc_profile_last / gc_profile_detail        */
+  int32_t path;             /* DI entry points: GC_PATH_AUTO / _STREAM / _MOMENTS / _RESIDENT     */
+  int32_t reserved;         /* must be 0                                                      */
 } gc_options;
+
+/* Execution paths of the direction-independent solvers (same results up to FP32 rounding order):
+ *   GC_PATH_STREAM    every iteration is one launch that re-reads all rows of the active intervals;
+ *   GC_PATH_MOMENTS   one pass reduces each interval's samples to per-baseline moments (the gains
+ *                     factor out of the sample sums); every iteration is then one launch that
+ *                     reads the moments of the active intervals (FP32 only);
+ *   GC_PATH_RESIDENT  one pass reduces each interval's samples to per-baseline moments (the gains
+ *                     factor out of the sample sums), then one persistent launch of thread-block
+ *                     clusters iterates every interval to convergence with its moments held on chip.
+ *                     FP32 only; up to 256 antennas and 8 x 512 baselines (scalar: 8 x 2048) per
+ *                     interval.
+ *   GC_PATH_AUTO      MOMENTS for complex64 data, STREAM for complex128. */
+#define GC_PATH_AUTO 0
+#define GC_PATH_STREAM 1
+#define GC_PATH_RESIDENT 2
+#define GC_PATH_MOMENTS 3
 
 /*
  * Direction-independent scalar gains: StefCal (Sect. 3.1, eq. stefcal and
@@ -204,6 +221,9 @@ int gc_jhj_jhr_di_jones2x2_noalloc(const void* vis, const void* model, const gc_
  * rows processed by them (sum over intervals of iterations x rows).  Any pointer may be NULL.
  */
 int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row_iterations);
+/* More of the same profile: the moment-pass time (ms, resident path; 0 otherwise), baselines x
+ * iterations processed, and the path taken (GC_PATH_STREAM, GC_PATH_MOMENTS or GC_PATH_RESIDENT). */
+int gc_profile_detail(double* moment_pass_ms, int64_t* baseline_iterations, int32_t* path);
 
 /* Text for a GC_ERR_* return code or a GC_ST_* status. */
 const char* gc_error_string(int code);

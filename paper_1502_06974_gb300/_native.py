@@ -17,13 +17,14 @@ GC_ERR_LIMIT = -6
 GC_ST_OK, GC_ST_NOT_CONVERGED, GC_ST_NONFINITE, GC_ST_NODATA, GC_ST_SINGULAR_FLAG = 0, 1, 2, 3, 16
 GC_DTYPE_C64, GC_DTYPE_C128 = 0, 1
 GC_SCHED_STEFCAL, GC_SCHED_GN = 0, 1
+GC_PATH_AUTO, GC_PATH_STREAM, GC_PATH_RESIDENT, GC_PATH_MOMENTS = 0, 1, 2, 3
 GC_MAX_ANT, GC_MAX_DIR = 1024, 10
 
 # Every symbol include/gaincal.h declares (checked by the CPU test suite).
 EXPORTS = [
     'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones',
     'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2', 'gc_jhj_jhr_di_jones2x2_noalloc',
-    'gc_profile_last', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
+    'gc_profile_last', 'gc_profile_detail', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
 ]
 
 _p = C.c_void_p
@@ -41,7 +42,7 @@ class GcLayout(C.Structure):
 class GcOptions(C.Structure):
     _fields_ = [('tol', C.c_double), ('max_iter', C.c_int32), ('schedule', C.c_int32), ('dtype', C.c_int32),
                 ('host_buffers', C.c_int32), ('compute_chi2', C.c_int32), ('profile', C.c_int32),
-                ('reserved', C.c_int32 * 2)]
+                ('path', C.c_int32), ('reserved', C.c_int32)]
 
 
 _lib = None
@@ -74,6 +75,8 @@ def lib() -> C.CDLL:
         L.gc_launch_count.restype = C.c_int64
         L.gc_profile_last.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.gc_profile_last.restype = C.c_int
+        L.gc_profile_detail.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        L.gc_profile_detail.restype = C.c_int
         L.gc_release.argtypes = []
         L.gc_release.restype = C.c_int
         _lib = L

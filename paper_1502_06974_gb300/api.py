@@ -78,7 +78,7 @@ def _check_tensor(t, name, host):
 
 
 def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedule, compute_chi2, host_buffers,
-               want_outputs=True, profile=False):
+               want_outputs=True, profile=False, path=N.GC_PATH_AUTO):
     host = bool(host_buffers)
     for t, n in ((vis, 'vis'), (model, 'model'), (gains, 'gains')):
         _check_tensor(t, n, host)
@@ -98,7 +98,7 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
         chi2 = torch.zeros(n, dtype=torch.float64, device=dev) if (want_outputs and compute_chi2) else None
         stream = _stream_ptr(dev)
     opt = N.GcOptions(float(tol), int(max_iter), int(schedule), dt, 1 if host else 0, 1 if compute_chi2 else 0,
-                      1 if profile else 0)
+                      1 if profile else 0, int(path))
     lay = layout.c()
     rc = getattr(N.lib(), fn_name)(_ptr(vis), _ptr(model), C.byref(lay), _ptr(gains), C.byref(opt), _ptr(iters),
                                    _ptr(chi2), _ptr(status), stream)
@@ -107,27 +107,28 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
 
 
 def calibrate_di_scalar(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
-                        compute_chi2=False, host_buffers=False, profile=False):
+                        compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO):
     """StefCal on scalar DI gains (gc_calibrate_di_scalar); gains are updated in place.
 
+    path: GC_PATH_AUTO (default), GC_PATH_STREAM or GC_PATH_RESIDENT (see include/gaincal.h).
     Returns (gains, iters[n_int] int32, chi2[n_int] float64 or None, status[n_int] int32).
     """
     return _calibrate('gc_calibrate_di_scalar', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers, profile=profile)
+                      host_buffers, profile=profile, path=path)
 
 
 def calibrate_di_jones2x2(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
-                          compute_chi2=False, host_buffers=False, profile=False):
+                          compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO):
     """Polarized StefCal on 2x2 DI gains (gc_calibrate_di_jones2x2); vis/model [rows,2,2], gains [n_gain,2,2]."""
     return _calibrate('gc_calibrate_di_jones2x2', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers, profile=profile)
+                      host_buffers, profile=profile, path=path)
 
 
 def calibrate_dd_cohjones(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
-                          compute_chi2=False, host_buffers=False, profile=False):
+                          compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO):
     """CohJones on DD scalar gains (gc_calibrate_dd_cohjones); model [n_dir, rows], gains [n_gain, n_dir]."""
     return _calibrate('gc_calibrate_dd_cohjones', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers, profile=profile)
+                      host_buffers, profile=profile, path=path)
 
 
 def _jhj_jhr(fn_name, vis, model, layout, gains, jones):
@@ -163,6 +164,13 @@ def profile_last():
     ms = C.c_double(0.0); n = C.c_int64(0); ri = C.c_int64(0)
     N.lib().gc_profile_last(C.byref(ms), C.byref(n), C.byref(ri))
     return ms.value, n.value, ri.value
+
+
+def profile_detail():
+    """(moment-pass ms, baselines x iterations, path) of the last profiled calibrate call."""
+    ms = C.c_double(0.0); bi = C.c_int64(0); p = C.c_int32(0)
+    N.lib().gc_profile_detail(C.byref(ms), C.byref(bi), C.byref(p))
+    return ms.value, bi.value, p.value
 
 
 def launch_count() -> int:

@@ -2,6 +2,7 @@
 // and the per-antenna reduction slot lists), the cached workspace, and the iteration loop.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <string>
@@ -14,6 +15,12 @@
 #include "dd.h"
 
 namespace gc {
+
+int res_supported(int kind, const gc_layout* L);
+int res_calibrate(int kind, const gc_layout* L, const void* vis, const void* model, void* gains,
+                  const gc_options* opt, int32_t** iters_dev, int32_t** status_dev, double** chi2_dev,
+                  cudaStream_t s);
+void res_release();
 
 std::atomic<long long> g_launches{0};
 static char g_cuda_err[256] = "";
@@ -154,9 +161,18 @@ struct DIPlan {
   double* chi2_items = nullptr;
   double* chi2_out = nullptr;
   int grid = 0, smem = 0;
+  // moment-stream mode: moment-pass items (interval, 32 baselines), per-item chi^2 bookkeeping
+  int mode = 0;
+  int n_mitems = 0;
+  int64_t n_mom_bl = 0;
+  const int32_t* mitem_int = nullptr;
+  const int32_t* mitem_tile = nullptr;
+  const int32_t* mfirst = nullptr;
+  const int32_t* mcount = nullptr;
+  double* mchi2 = nullptr;
 };
 
-static DIPlan g_di_plan[2][2][2];  // [kind][dtype][acc_only]
+static DIPlan g_di_plan[2][2][2][2];  // [mode][kind][dtype][acc_only]
 static int g_target_rows[2] = {32768, 8192};
 
 static int env_int(const char* name, int dflt) {
@@ -165,7 +181,7 @@ static int env_int(const char* name, int dflt) {
 }
 
 // Build the work items, baseline-table reduction lists and device copies for one layout.
-static int build_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, DIPlan& P, void* stream) {
+static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_layout* L, DIPlan& P, void* stream) {
   const int nc = kind == 0 ? 3 : 12;
   const int TB = kDIThreads;
   const int n = L->n_intervals;
@@ -193,8 +209,8 @@ static int build_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, 
       for (int s = 0; s < TB; ++s) {
         const int b = tile * TB + s;
         if (b >= nb) break;
-        lists[L->ant1[bo + b]].push_back(s * 2 * nc);        // p side of slot s
-        lists[L->ant2[bo + b]].push_back(s * 2 * nc + nc);   // q side of slot s
+        lists[L->ant1[bo + b]].push_back(s * (2 * nc + 1));        // p side of slot s
+        lists[L->ant2[bo + b]].push_back(s * (2 * nc + 1) + nc);   // q side of slot s
       }
       for (int a = 0; a < nat; ++a) {
         csr_off.push_back((int)csr_ent.size());
@@ -205,26 +221,41 @@ static int build_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, 
   }
   if (csr_off.empty()) csr_off.push_back(0);
   if (csr_ent.empty()) csr_ent.push_back(0);
-  // work items
+  // work items: (interval, sample range) for the raw-row kernel; (interval, tile range) for moments
   const int target = env_int(kind == 0 ? "GAINCAL_TARGET_ROWS_SCALAR" : "GAINCAL_TARGET_ROWS_JONES", g_target_rows[kind]);
+  const int tpi = std::max(1, env_int("GAINCAL_TILES_PER_ITEM", 1));
   std::vector<int> item_int, item_s0, item_s1, n_chunks(n), first_item(n);
-  std::vector<int64_t> item_scr;
-  int64_t scr = 0;
+  std::vector<int64_t> item_scr, mom_off(n);
+  std::vector<int> mint, mtile, mfirst(n), mcount(n);
+  int64_t scr = 0, mo = 0;
   int na_max = 1, n_active0 = 0;
   for (int i = 0; i < n; ++i) {
     const int ns = L->n_samp[i], nb = L->n_bl[i];
     na_max = L->n_ant[i] > na_max ? L->n_ant[i] : na_max;
     first_item[i] = (int)item_int.size();
+    mom_off[i] = mo;
+    mo += nb;
+    mfirst[i] = (int)mint.size();
+    if ((int64_t)ns * nb > 0)
+      for (int t = 0; t < (nb + 31) / 32; ++t) { mint.push_back(i); mtile.push_back(t); }
+    mcount[i] = (int)mint.size() - mfirst[i];
     if ((int64_t)ns * nb == 0) { n_chunks[i] = 0; continue; }
     ++n_active0;
-    int per = nb > 0 ? (target + nb - 1) / nb : ns;
-    per = per < 1 ? 1 : (per > ns ? ns : per);
-    const int nch = (ns + per - 1) / per;
+    int per, units;
+    if (mode == 1) {
+      units = (nb + TB - 1) / TB;
+      per = tpi < units ? tpi : units;
+    } else {
+      units = ns;
+      per = nb > 0 ? (target + nb - 1) / nb : ns;
+      per = per < 1 ? 1 : (per > ns ? ns : per);
+    }
+    const int nch = (units + per - 1) / per;
     n_chunks[i] = nch;
     for (int c = 0; c < nch; ++c) {
       item_int.push_back(i);
       item_s0.push_back(c * per);
-      item_s1.push_back((c + 1) * per < ns ? (c + 1) * per : ns);
+      item_s1.push_back((c + 1) * per < units ? (c + 1) * per : units);
       const int nat = tab_nant[itab[i]];
       if (nch > 1) { item_scr.push_back(scr); scr += (int64_t)nat * nc; }
       else item_scr.push_back(-1);
@@ -256,6 +287,15 @@ static int build_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, 
   const size_t p_item_s1 = add(item_s1.data(), item_s1.size() * 4);
   const size_t p_n_chunks = add(n_chunks.data(), n_chunks.size() * 4);
   const size_t p_first_item = add(first_item.data(), first_item.size() * 4);
+  if (mint.empty()) { mint.push_back(0); mtile.push_back(0); }
+  const size_t p_mom_off = add(mom_off.data(), mom_off.size() * 8);
+  const size_t p_mint = add(mint.data(), mint.size() * 4);
+  const size_t p_mtile = add(mtile.data(), mtile.size() * 4);
+  const size_t p_mfirst = add(mfirst.data(), mfirst.size() * 4);
+  const size_t p_mcount = add(mcount.data(), mcount.size() * 4);
+  const size_t p_mchi2 = add(nullptr, mint.size() * 8);
+  const size_t p_ilist = add(nullptr, (size_t)3 * (n_items > 0 ? n_items : 1) * 4);
+  const size_t p_icount = add(nullptr, 16);
   // per-call state
   const size_t p_active = add(nullptr, (size_t)n * 4);
   const size_t p_iters = add(nullptr, (size_t)n * 4);
@@ -303,6 +343,17 @@ static int build_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, 
   a.qhead = (int32_t*)at(p_misc) + 4;
   a.n_items = n_items;
   a.na_max = na_max;
+  a.mom_off = (const int64_t*)at(p_mom_off);
+  a.ilist = mode == 1 ? (int32_t*)at(p_ilist) : nullptr;
+  a.icount = mode == 1 ? (int32_t*)at(p_icount) : nullptr;
+  P.mode = mode;
+  P.n_mitems = n_active0 > 0 ? (int)mint.size() : 0;
+  P.n_mom_bl = mo;
+  P.mitem_int = (const int32_t*)at(p_mint);
+  P.mitem_tile = (const int32_t*)at(p_mtile);
+  P.mfirst = (const int32_t*)at(p_mfirst);
+  P.mcount = (const int32_t*)at(p_mcount);
+  P.mchi2 = (double*)at(p_mchi2);
   P.chi2_items = (double*)at(p_chi2);
   P.chi2_out = (double*)at(p_chi2o);
   P.n_int = n;
@@ -316,7 +367,8 @@ static int build_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, 
   GC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   GC_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (P.smem > max_smem) return GC_ERR_LIMIT;
-  GC_CUDA_I(di_max_blocks_per_sm(kind, dtype, acc_only, P.smem, &per_sm));
+  if (mode == 1) GC_CUDA_I(di_m_max_blocks_per_sm(kind, acc_only, P.smem, &per_sm));
+  else GC_CUDA_I(di_max_blocks_per_sm(kind, dtype, acc_only, P.smem, &per_sm));
   if (per_sm < 1) return GC_ERR_LIMIT;
   const int cap = env_int("GAINCAL_BLOCKS_PER_SM", per_sm);
   per_sm = cap < per_sm ? (cap > 0 ? cap : 1) : per_sm;
@@ -325,17 +377,18 @@ static int build_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, 
   return GC_OK;
 }
 
-static int get_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, DIPlan** out, void* stream) {
-  DIPlan& P = g_di_plan[kind][dtype][acc_only];
+static int get_di_plan(int mode, int kind, int dtype, int acc_only, const gc_layout* L, DIPlan** out, void* stream) {
+  DIPlan& P = g_di_plan[mode][kind][dtype][acc_only];
   int dev = 0;
   GC_CUDA(cudaGetDevice(&dev));
   const uint64_t key = layout_hash(L, (uint64_t)(kind * 131 + dtype * 7 + acc_only) ^ ((uint64_t)dev << 40) ^
                                       ((uint64_t)env_int("GAINCAL_TARGET_ROWS_SCALAR", 0) << 20) ^
                                       ((uint64_t)env_int("GAINCAL_TARGET_ROWS_JONES", 0) << 48) ^
-                                      ((uint64_t)env_int("GAINCAL_BLOCKS_PER_SM", 0) << 56));
+                                      ((uint64_t)env_int("GAINCAL_BLOCKS_PER_SM", 0) << 56) ^
+                                      ((uint64_t)env_int("GAINCAL_TILES_PER_ITEM", 0) << 8) ^ ((uint64_t)mode << 4));
   if (P.key != key || P.n_int != L->n_intervals || !P.dev) {
     P.key = 0;
-    int rc = build_di_plan(kind, dtype, acc_only, L, P, stream);
+    int rc = build_di_plan(mode, kind, dtype, acc_only, L, P, stream);
     if (rc != GC_OK) return rc;
     P.key = key;
   }
@@ -345,10 +398,21 @@ static int get_di_plan(int kind, int dtype, int acc_only, const gc_layout* L, DI
 
 // Optional per-launch timing of the iteration kernels (opt->profile).
 struct ProfileTotals {
-  double ms = 0.0;
-  int64_t launches = 0, row_iters = 0;
+  double ms = 0.0, moment_ms = 0.0;
+  int64_t launches = 0, row_iters = 0, bl_iters = 0;
+  int path = 0;
 };
 static ProfileTotals g_prof;
+
+void profile_record(double iter_ms, int64_t launches, int64_t row_iters, double moment_ms, int64_t bl_iters,
+                    int path) {
+  g_prof.ms = iter_ms;
+  g_prof.launches = launches;
+  g_prof.row_iters = row_iters;
+  g_prof.moment_ms = moment_ms;
+  g_prof.bl_iters = bl_iters;
+  g_prof.path = path;
+}
 
 struct Profiler {
   bool on;
@@ -393,10 +457,8 @@ struct Profiler {
     used = 0;
     return GC_OK;
   }
-  void finish(int64_t row_iters) {
-    g_prof.ms = ms;
-    g_prof.launches = launches;
-    g_prof.row_iters = row_iters;
+  void finish(int64_t row_iters, int64_t bl_iters, double mom_ms, int path) {
+    profile_record(ms, launches, row_iters, mom_ms, bl_iters, path);
   }
 };
 
@@ -419,15 +481,22 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
     return GC_ERR_ARG;
   if (opt->host_buffers != 0 && opt->host_buffers != 1) return GC_ERR_ARG;
-  if (opt->reserved[0] || opt->reserved[1]) return GC_ERR_ARG;
+  if (opt->reserved || opt->path < GC_PATH_AUTO || opt->path > GC_PATH_MOMENTS) return GC_ERR_ARG;
   int rc = validate_layout(L, 1);
   if (rc != GC_OK) return rc;
   if (L->n_intervals == 0) return GC_OK;
   if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && !gains)) return GC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  const bool can_res = opt->dtype == GC_DTYPE_C64 && res_supported(kind, L);
+  if (opt->path == GC_PATH_RESIDENT && !can_res) return GC_ERR_LIMIT;
+  if (opt->path == GC_PATH_MOMENTS && opt->dtype != GC_DTYPE_C64) return GC_ERR_DTYPE;
+  const bool resident = opt->path == GC_PATH_RESIDENT;
+  const int mode = (opt->path == GC_PATH_MOMENTS || (opt->path == GC_PATH_AUTO && opt->dtype == GC_DTYPE_C64)) ? 1 : 0;
   DIPlan* P = nullptr;
-  rc = get_di_plan(kind, opt->dtype, 0, L, &P, stream);
-  if (rc != GC_OK) return rc;
+  if (!resident) {
+    rc = get_di_plan(mode, kind, opt->dtype, 0, L, &P, stream);
+    if (rc != GC_OK) return rc;
+  }
   const size_t eb = elem_bytes(kind, opt->dtype);
   Staged st{vis, model, gains};
   if (opt->host_buffers) {
@@ -441,6 +510,24 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     }
     GC_CUDA(cudaMemcpyAsync(dg, gains, (size_t)L->n_gain * eb, cudaMemcpyHostToDevice, s));
     st = Staged{dv, dm, dg};
+  }
+  if (resident) {
+    int32_t *it_d = nullptr, *st_d = nullptr;
+    double* c2_d = nullptr;
+    rc = res_calibrate(kind, L, st.vis, st.model, st.gains, opt, &it_d, &st_d, &c2_d, s);
+    if (rc != GC_OK) return rc;
+    const cudaMemcpyKind dk = opt->host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int n = L->n_intervals;
+    if (opt->host_buffers) GC_CUDA(cudaMemcpyAsync(gains, st.gains, (size_t)L->n_gain * eb, dk, s));
+    if (iters_out) GC_CUDA(cudaMemcpyAsync(iters_out, it_d, (size_t)n * 4, dk, s));
+    if (status_out) GC_CUDA(cudaMemcpyAsync(status_out, st_d, (size_t)n * 4, dk, s));
+    if (chi2_out && opt->compute_chi2) GC_CUDA(cudaMemcpyAsync(chi2_out, c2_d, (size_t)n * 8, dk, s));
+    std::vector<int32_t> stv(n);
+    GC_CUDA(cudaMemcpyAsync(stv.data(), st_d, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    int bad = 0;
+    for (int i = 0; i < n; ++i) bad += (stv[i] & 15) != GC_ST_OK;
+    return bad;
   }
   DIArgs a = P->args;
   a.vis = st.vis;
@@ -456,6 +543,31 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   }
   GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
   g_launches++;
+  double mom_ms = 0.0;
+  if (mode == 1) {
+    void* mom = nullptr;
+    const int nm = kind == 0 ? 4 : 48;
+    if ((rc = ws_get("di_moments", (size_t)(P->n_mom_bl > 0 ? P->n_mom_bl : 1) * nm * sizeof(float), &mom))) return rc;
+    a.moments = (const float*)mom;
+    cudaEvent_t m0 = nullptr, m1 = nullptr;
+    if (opt->profile) {
+      GC_CUDA(cudaEventCreate(&m0));
+      GC_CUDA(cudaEventCreate(&m1));
+      GC_CUDA(cudaEventRecord(m0, s));
+    }
+    GC_CUDA_I(moment_pass(kind, (const float*)st.vis, (const float*)st.model, (float*)mom, a.row_off, a.mom_off,
+                          a.n_samp, a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, stream));
+    g_launches++;
+    if (opt->profile) {
+      GC_CUDA(cudaEventRecord(m1, s));
+      GC_CUDA(cudaEventSynchronize(m1));
+      float t = 0.f;
+      GC_CUDA(cudaEventElapsedTime(&t, m0, m1));
+      mom_ms = t;
+      cudaEventDestroy(m0);
+      cudaEventDestroy(m1);
+    }
+  }
   int* flag = nullptr;
   if ((rc = pinned_flag(&flag))) return rc;
   const int check_every = env_int("GAINCAL_CHECK_EVERY", 16);
@@ -464,7 +576,8 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   for (int k = 1; k <= opt->max_iter; ++k) {
     a.k = k;
     if ((rc = prof.before(s))) return rc;
-    GC_CUDA_I(di_launch_iter(kind, opt->dtype, 0, a, P->grid, P->smem, stream));
+    if (mode == 1) GC_CUDA_I(di_launch_miter(kind, 0, a, P->grid, P->smem, stream));
+    else GC_CUDA_I(di_launch_iter(kind, opt->dtype, 0, a, P->grid, P->smem, stream));
     if ((rc = prof.after(s))) return rc;
     g_launches++;
     if (k % check_every == 0 || k == opt->max_iter) {
@@ -475,7 +588,12 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     }
   }
   if (opt->compute_chi2) {
-    GC_CUDA_I(di_launch_chi2(kind, opt->dtype, a, P->chi2_items, P->chi2_out, P->n_int, P->grid, stream));
+    if (mode == 1)
+      GC_CUDA_I(moment_chi2(kind, (const float*)st.vis, (const float*)st.model, (const float*)st.gains, a.row_off,
+                            a.n_samp, a.n_bl, a.bl_off, a.gain_off, a.ant1, a.ant2, P->mitem_int, P->mitem_tile,
+                            P->n_mitems, P->mfirst, P->mcount, P->mchi2, P->chi2_out, P->n_int, stream));
+    else
+      GC_CUDA_I(di_launch_chi2(kind, opt->dtype, a, P->chi2_items, P->chi2_out, P->n_int, P->grid, stream));
     g_launches += 2;
   }
   const cudaMemcpyKind dk = opt->host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -491,9 +609,12 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   int bad = 0;
   for (int i = 0; i < P->n_int; ++i) bad += (stv[i] & 15) != GC_ST_OK;
   if (opt->profile) {
-    int64_t ri = 0;
-    for (int i = 0; i < P->n_int; ++i) ri += (int64_t)itv[i] * L->n_samp[i] * L->n_bl[i];
-    prof.finish(ri);
+    int64_t ri = 0, bi = 0;
+    for (int i = 0; i < P->n_int; ++i) {
+      ri += (int64_t)itv[i] * L->n_samp[i] * L->n_bl[i];
+      bi += (int64_t)itv[i] * L->n_bl[i];
+    }
+    prof.finish(ri, bi, mom_ms, mode == 1 ? GC_PATH_MOMENTS : GC_PATH_STREAM);
   }
   return bad;
 }
@@ -507,7 +628,7 @@ static int run_di_acc(int kind, const void* vis, const void* model, const gc_lay
   if (L->n_intervals == 0) return GC_OK;
   if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && (!gains || !jhd || !jhj))) return GC_ERR_ARG;
   DIPlan* P = nullptr;
-  rc = get_di_plan(kind, dtype, 1, L, &P, stream);
+  rc = get_di_plan(0, kind, dtype, 1, L, &P, stream);
   if (rc != GC_OK) return rc;
   DIArgs a = P->args;
   a.vis = vis;
@@ -584,6 +705,13 @@ const char* gc_status_string(int status) {
 
 const char* gc_last_cuda_error(void) { return gc::last_cuda_error(); }
 
+int gc_profile_detail(double* moment_pass_ms, int64_t* baseline_iterations, int32_t* path) {
+  if (moment_pass_ms) *moment_pass_ms = gc::g_prof.moment_ms;
+  if (baseline_iterations) *baseline_iterations = gc::g_prof.bl_iters;
+  if (path) *path = gc::g_prof.path;
+  return GC_OK;
+}
+
 int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row_iterations) {
   if (iter_kernel_ms) *iter_kernel_ms = gc::g_prof.ms;
   if (iter_launches) *iter_launches = gc::g_prof.launches;
@@ -598,13 +726,15 @@ int gc_release(void) {
     if (kv.second.p) cudaFree(kv.second.p);
   }
   gc::g_ws.clear();
-  for (auto& a : gc::g_di_plan)
-    for (auto& b : a)
-      for (auto& c : b) {
-        if (c.dev) cudaFree(c.dev);
-        c = gc::DIPlan{};
-      }
+  for (auto& m : gc::g_di_plan)
+    for (auto& a : m)
+      for (auto& b : a)
+        for (auto& c : b) {
+          if (c.dev) cudaFree(c.dev);
+          c = gc::DIPlan{};
+        }
   gc::dd_release();
+  gc::res_release();
   if (gc::g_pinned_flag) { cudaFreeHost(gc::g_pinned_flag); gc::g_pinned_flag = nullptr; }
   return GC_OK;
 }

@@ -55,6 +55,13 @@ struct DIArgs {
   // accumulate-only outputs
   void* jhd_out;
   void* jhj_out;
+  // moment-stream path: per-baseline moments and each interval's first baseline in them
+  const float* moments;
+  const int64_t* mom_off;
+  // compacted work lists (moment-stream path): iteration k takes items from list[k % 3], appends
+  // the items of intervals that stay active to list[(k + 1) % 3], and clears list (k + 2) % 3
+  int32_t* ilist;    // [3][n_items]
+  int32_t* icount;   // [3]
 };
 
 // Launchers implemented in di_kernels.cu.  kind: 0 scalar, 1 jones.  Return cudaError_t as int.
@@ -62,6 +69,17 @@ int di_smem_bytes(int kind, int dtype, int na_max);
 int di_max_blocks_per_sm(int kind, int dtype, int acc_only, int smem, int* out);
 int di_launch_iter(int kind, int dtype, int acc_only, const DIArgs& a, int grid, int smem, void* stream);
 int di_launch_init(const DIArgs& a, int n_int, int n_active0, void* stream);
+int di_m_max_blocks_per_sm(int kind, int acc_only, int smem, int* out);
+int di_launch_miter(int kind, int acc_only, const DIArgs& a, int grid, int smem, void* stream);
+// moment pass (resident.cu): per-baseline moments of every interval; items are (interval, 32 baselines)
+int moment_pass(int kind, const float* vis, const float* model, float* moments, const int64_t* row_off,
+                const int64_t* mom_off, const int32_t* n_samp, const int32_t* n_bl, const int32_t* item_int,
+                const int32_t* item_tile, int n_items, void* stream);
+int moment_chi2(int kind, const float* vis, const float* model, const float* gains, const int64_t* row_off,
+                const int32_t* n_samp, const int32_t* n_bl, const int32_t* bl_off, const int32_t* gain_off,
+                const int32_t* ant1, const int32_t* ant2, const int32_t* item_int, const int32_t* item_tile,
+                int n_items, const int32_t* first, const int32_t* count, double* item_chi2, double* out, int n_int,
+                void* stream);
 int di_launch_chi2(int kind, int dtype, const DIArgs& a, double* item_chi2, double* chi2_out, int n_int,
                    int grid, void* stream);
 

@@ -149,8 +149,8 @@ static int noalloc_jones_acc(const void* vis, const void* model, const gc_layout
       for (int a = 0; a < nat; ++a) {
         csr_off[co++] = (int32_t)ce;
         for (int s = 0; s < s1; ++s) {
-          if (L->ant1[bo + tile * TB + s] == a) csr_ent[ce++] = s * 2 * NC;
-          if (L->ant2[bo + tile * TB + s] == a) csr_ent[ce++] = s * 2 * NC + NC;
+          if (L->ant1[bo + tile * TB + s] == a) csr_ent[ce++] = s * (2 * NC + 1);
+          if (L->ant2[bo + tile * TB + s] == a) csr_ent[ce++] = s * (2 * NC + 1) + NC;
         }
       }
       csr_off[co++] = (int32_t)ce;

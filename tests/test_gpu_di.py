@@ -15,9 +15,12 @@ import torch
 
 from helpers import device_batch, per_slot_relerr
 from oracle import blocks, diagonal, gauge, wirtinger
+from paper_1502_06974_gb300 import _native as N
 from paper_1502_06974_gb300 import api, synth
 
 pytestmark = pytest.mark.gpu
+PATHS = [pytest.param(N.GC_PATH_STREAM, id='stream'), pytest.param(N.GC_PATH_MOMENTS, id='moments'),
+         pytest.param(N.GC_PATH_RESIDENT, id='resident')]
 
 
 def _oracle_blocks(b, g):
@@ -109,31 +112,35 @@ def test_calibrate_scalar_cfg1_fp64(gpu_lib):
     assert gauge.rel_error('scalar', g.cpu().numpy(), g_gn) < 1e-10
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("k", [1, 2, 3, 6])
-def test_jones_iterates_match(gpu_lib, k):
+def test_jones_iterates_match(gpu_lib, k, path):
     """Iterate-level parity: after exactly k steps (GN, average, GN, ...) the gains agree."""
     b = synth.make_config(2, small=True)
     vis, model, g0, lay = device_batch(b)
-    g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=0.0, max_iter=k)
+    g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=0.0, max_iter=k, path=path)
     gr, its, _ = diagonal.solve_batch(b, tol=0.0, max_iter=k)
     assert (iters.cpu().numpy() == k).all()
     assert per_slot_relerr(g.cpu().numpy(), gr) < 1e-5
 
 
-def test_scalar_iterates_match_fp32(gpu_lib):
+@pytest.mark.parametrize("path", PATHS)
+def test_scalar_iterates_match_fp32(gpu_lib, path):
     b = synth.make_di_scalar(n_ant=24, n_t=6, n_chan=4, t_per=3, f_per=2, dtype=np.complex64)
     vis, model, g0, lay = device_batch(b)
     for k in (1, 2, 5):
-        g, iters, _, _ = api.calibrate_di_scalar(vis, model, lay, g0.clone(), tol=0.0, max_iter=k)
+        g, iters, _, _ = api.calibrate_di_scalar(vis, model, lay, g0.clone(), tol=0.0, max_iter=k, path=path)
         gr, _, _ = diagonal.solve_batch(b, tol=0.0, max_iter=k)
         assert per_slot_relerr(g.cpu().numpy(), gr) < 1e-5
 
 
-def test_jones_converged_small(gpu_lib):
+@pytest.mark.parametrize("path", PATHS)
+def test_jones_converged_small(gpu_lib, path):
     """Run to tol = 1e-6 (the tolerance the throughput measurement uses) and compare."""
     b = synth.make_config(2, small=True)
     vis, model, g0, lay = device_batch(b)
-    g, iters, chi2, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=1e-6, max_iter=20000, compute_chi2=True)
+    g, iters, chi2, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=1e-6, max_iter=20000, compute_chi2=True,
+                                                   path=path)
     gr, its, conv = diagonal.solve_batch(b, tol=1e-6, max_iter=20000)
     assert conv.all() and (st.cpu().numpy() == 0).all()
     e = gauge.rel_error('jones', g.cpu().numpy(), gr, b.n_ant, b.gain_off)
@@ -148,34 +155,37 @@ def test_jones_converged_small(gpu_lib):
         assert abs(ch[i] - ref) <= 1e-4 * ref
 
 
-def test_scalar_multi_interval_fp32(gpu_lib, monkeypatch):
+@pytest.mark.parametrize("path", PATHS)
+def test_scalar_multi_interval_fp32(gpu_lib, monkeypatch, path):
     """Several uneven intervals (different antenna counts and lengths) in one batch, split items."""
     monkeypatch.setenv("GAINCAL_TARGET_ROWS_SCALAR", "700")
     out = synth.make_uneven(n_intervals=12, ant_choices=(4, 9, 23), t_max=5, f_max=6, only='scalar')
     b = out['scalar']
     vis, model, g0, lay = device_batch(b)
-    g, iters, _, st = api.calibrate_di_scalar(vis, model, lay, g0, tol=1e-7, max_iter=2000)
+    g, iters, _, st = api.calibrate_di_scalar(vis, model, lay, g0, tol=1e-7, max_iter=2000, path=path)
     gr, its, conv = diagonal.solve_batch(b, tol=1e-7, max_iter=2000)
     assert (st.cpu().numpy() == 0).all()
     assert gauge.rel_error('scalar', g.cpu().numpy(), gr, b.n_ant, b.gain_off) < 1e-5
 
 
-def test_host_buffers_match_device(gpu_lib):
+@pytest.mark.parametrize("path", PATHS)
+def test_host_buffers_match_device(gpu_lib, path):
     b = synth.make_config(2, small=True)
     vis, model, g0, lay = device_batch(b)
-    gd, itd, _, _ = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=5000)
+    gd, itd, _, _ = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=5000, path=path)
     gh = torch.from_numpy(b.g0()).pin_memory()
     gh, ith, _, _ = api.calibrate_di_jones2x2(vis.cpu().pin_memory(), model.cpu().pin_memory(), lay, gh, tol=1e-6,
-                                              max_iter=5000, host_buffers=True)
+                                              max_iter=5000, host_buffers=True, path=path)
     assert torch.equal(gd.cpu(), gh)
     assert torch.equal(itd.cpu(), ith)
 
 
-def test_bitwise_reproducible(gpu_lib):
+@pytest.mark.parametrize("path", PATHS)
+def test_bitwise_reproducible(gpu_lib, path):
     b = synth.make_config(2, small=True)
     vis, model, g0, lay = device_batch(b)
-    g1, i1, _, _ = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=500)
-    g2, i2, _, _ = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=500)
+    g1, i1, _, _ = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=500, path=path)
+    g2, i2, _, _ = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=500, path=path)
     assert torch.equal(g1, g2) and torch.equal(i1, i2)
 
 
@@ -192,7 +202,8 @@ def test_errors_are_codes(gpu_lib):
         api.calibrate_di_jones2x2(vis, model, bad, g0, tol=1e-6, max_iter=5)
 
 
-def test_nodata_and_singular(gpu_lib):
+@pytest.mark.parametrize("path", PATHS)
+def test_nodata_and_singular(gpu_lib, path):
     """An empty interval reports NODATA; an antenna with no baselines is flagged singular."""
     b = synth.make_di_scalar(n_ant=8, n_t=2, n_chan=2, t_per=1, f_per=2, dtype=np.complex64)
     vis, model, g0, lay = device_batch(b)
@@ -200,8 +211,55 @@ def test_nodata_and_singular(gpu_lib):
     lay.n_ant = lay.n_ant.copy(); lay.n_ant[0] = 9           # antenna 8 has no baselines
     lay.gain_off = np.array([0, 9], np.int32); lay.n_gain = 17
     g0 = torch.ones(17, dtype=torch.complex64, device='cuda')
-    g, iters, _, st = api.calibrate_di_scalar(vis, model, lay, g0, tol=1e-6, max_iter=200)
+    g, iters, _, st = api.calibrate_di_scalar(vis, model, lay, g0, tol=1e-6, max_iter=200, path=path)
     st = st.cpu().numpy()
     assert st[1] == 3 and int(iters[1]) == 0
     assert st[0] == 0 | 16
     assert complex(g[8].cpu()) == 1.0
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_jones_full_size_sampled_iterates(gpu_lib, path):
+    """The full 64-antenna, 960-interval workload in the bench's launch configuration: 40 iterations on
+    the GPU, sampled intervals against the oracle's 40 iterations."""
+    b = synth.make_config(2)
+    vis, model, g0, lay = device_batch(b)
+    g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=0.0, max_iter=40, path=path)
+    gg = g.cpu().numpy()
+    assert (iters.cpu().numpy() == 40).all()
+    for i in (0, 517, 959):
+        gr, _, _ = diagonal.solve_batch(b, tol=0.0, max_iter=40, intervals=[i])
+        iv = b.interval(i)
+        assert per_slot_relerr(gg[iv['gain_slice']], gr) < 1e-5
+
+
+@pytest.mark.parametrize("cluster", ["1", "2", "8"])
+def test_resident_cluster_sizes_agree(gpu_lib, monkeypatch, cluster):
+    """The resident kernel split over 1, 2 or 8 CTAs per interval gives the oracle's iterates."""
+    monkeypatch.setenv("GAINCAL_CLUSTER", cluster)
+    b = synth.make_di_jones(n_ant=24, n_t=3, n_chan=8, t_per=1, f_per=8)
+    vis, model, g0, lay = device_batch(b)
+    g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=0.0, max_iter=9, path=N.GC_PATH_RESIDENT)
+    gr, _, _ = diagonal.solve_batch(b, tol=0.0, max_iter=9)
+    assert per_slot_relerr(g.cpu().numpy(), gr) < 1e-5
+
+
+def test_resident_uneven_jones_batch(gpu_lib):
+    """Uneven 2x2 intervals (antenna counts 6..30, 1..12 samples) in one persistent launch."""
+    out = synth.make_uneven(n_intervals=24, ant_choices=(6, 13, 30), t_max=3, f_max=4, only='jones')
+    b = out['jones']
+    vis, model, g0, lay = device_batch(b)
+    g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=0.0, max_iter=25, path=N.GC_PATH_RESIDENT)
+    gr, _, _ = diagonal.solve_batch(b, tol=0.0, max_iter=25)
+    assert per_slot_relerr(g.cpu().numpy(), gr) < 1e-5
+
+
+@pytest.mark.parametrize("tpi", ["1", "3"])
+def test_moments_multi_item_intervals(gpu_lib, monkeypatch, tpi):
+    """Moment-stream items of 1 or 3 baseline tiles: intervals split over several items (scratch)."""
+    monkeypatch.setenv("GAINCAL_TILES_PER_ITEM", tpi)
+    b = synth.make_di_jones(n_ant=48, n_t=2, n_chan=4, t_per=1, f_per=2)   # 1128 baselines: 5 tiles
+    vis, model, g0, lay = device_batch(b)
+    g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=0.0, max_iter=7, path=N.GC_PATH_MOMENTS)
+    gr, _, _ = diagonal.solve_batch(b, tol=0.0, max_iter=7)
+    assert per_slot_relerr(g.cpu().numpy(), gr) < 1e-5
