@@ -223,7 +223,7 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   if (csr_ent.empty()) csr_ent.push_back(0);
   // work items: (interval, sample range) for the raw-row kernel; (interval, tile range) for moments
   const int target = env_int(kind == 0 ? "GAINCAL_TARGET_ROWS_SCALAR" : "GAINCAL_TARGET_ROWS_JONES", g_target_rows[kind]);
-  const int tpi = std::max(1, env_int("GAINCAL_TILES_PER_ITEM", 1));
+  const int tpi = 1;  // moment path: one item per 256-baseline tile
   std::vector<int> item_int, item_s0, item_s1, n_chunks(n), first_item(n);
   std::vector<int64_t> item_scr, mom_off(n);
   std::vector<int> mint, mtile, mfirst(n), mcount(n);
@@ -234,7 +234,7 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
     na_max = L->n_ant[i] > na_max ? L->n_ant[i] : na_max;
     first_item[i] = (int)item_int.size();
     mom_off[i] = mo;
-    mo += nb;
+    mo += (int64_t)(nb + 255) / 256 * 256;   // tiled moment layout: whole 256-baseline tiles
     mfirst[i] = (int)mint.size();
     if ((int64_t)ns * nb > 0)
       for (int t = 0; t < (nb + 31) / 32; ++t) { mint.push_back(i); mtile.push_back(t); }
@@ -257,7 +257,7 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
       item_s0.push_back(c * per);
       item_s1.push_back((c + 1) * per < units ? (c + 1) * per : units);
       const int nat = tab_nant[itab[i]];
-      if (nch > 1) { item_scr.push_back(scr); scr += (int64_t)nat * nc; }
+      if (nch > 1 || mode == 1) { item_scr.push_back(scr); scr += (int64_t)nat * nc; }
       else item_scr.push_back(-1);
     }
   }
@@ -367,8 +367,13 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   GC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   GC_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (P.smem > max_smem) return GC_ERR_LIMIT;
-  if (mode == 1) GC_CUDA_I(di_m_max_blocks_per_sm(kind, acc_only, P.smem, &per_sm));
-  else GC_CUDA_I(di_max_blocks_per_sm(kind, dtype, acc_only, P.smem, &per_sm));
+  if (mode == 1) {
+    P.smem = di_macc_smem(kind, na_max);
+    if (P.smem > max_smem) return GC_ERR_LIMIT;
+    GC_CUDA_I(di_macc_max_blocks_per_sm(kind, P.smem, &per_sm));
+  } else {
+    GC_CUDA_I(di_max_blocks_per_sm(kind, dtype, acc_only, P.smem, &per_sm));
+  }
   if (per_sm < 1) return GC_ERR_LIMIT;
   const int cap = env_int("GAINCAL_BLOCKS_PER_SM", per_sm);
   per_sm = cap < per_sm ? (cap > 0 ? cap : 1) : per_sm;
@@ -385,7 +390,9 @@ static int get_di_plan(int mode, int kind, int dtype, int acc_only, const gc_lay
                                       ((uint64_t)env_int("GAINCAL_TARGET_ROWS_SCALAR", 0) << 20) ^
                                       ((uint64_t)env_int("GAINCAL_TARGET_ROWS_JONES", 0) << 48) ^
                                       ((uint64_t)env_int("GAINCAL_BLOCKS_PER_SM", 0) << 56) ^
-                                      ((uint64_t)env_int("GAINCAL_TILES_PER_ITEM", 0) << 8) ^ ((uint64_t)mode << 4));
+                                      ((uint64_t)mode << 4) ^
+                                      ((uint64_t)env_int("GAINCAL_RED_CHUNKS", 0) << 36) ^
+                                      ((uint64_t)env_int("GAINCAL_ACC_PREFETCH", 0) << 40));
   if (P.key != key || P.n_int != L->n_intervals || !P.dev) {
     P.key = 0;
     int rc = build_di_plan(mode, kind, dtype, acc_only, L, P, stream);
@@ -557,7 +564,13 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     }
     GC_CUDA_I(moment_pass(kind, (const float*)st.vis, (const float*)st.model, (float*)mom, a.row_off, a.mom_off,
                           a.n_samp, a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, stream));
-    g_launches++;
+    void *aux = nullptr, *gnew = nullptr;
+    if ((rc = ws_get("di_aux", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 4 * sizeof(float), &aux))) return rc;
+    if ((rc = ws_get("di_gnew", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 8 * sizeof(float), &gnew))) return rc;
+    a.aux = (float*)aux;
+    a.gnew = (float*)gnew;
+    GC_CUDA_I(di_launch_maux(kind, (const float*)st.gains, a.aux, L->n_gain, stream));
+    g_launches += 2;
     if (opt->profile) {
       GC_CUDA(cudaEventRecord(m1, s));
       GC_CUDA(cudaEventSynchronize(m1));
@@ -576,12 +589,12 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   for (int k = 1; k <= opt->max_iter; ++k) {
     a.k = k;
     if ((rc = prof.before(s))) return rc;
-    if (mode == 1) GC_CUDA_I(di_launch_miter(kind, 0, a, P->grid, P->smem, stream));
+    if (mode == 1) GC_CUDA_I(di_launch_mstep(kind, a, P->grid, P->smem, P->n_int, stream));
     else GC_CUDA_I(di_launch_iter(kind, opt->dtype, 0, a, P->grid, P->smem, stream));
     if ((rc = prof.after(s))) return rc;
-    g_launches++;
+    g_launches += mode == 1 ? 2 : 1;
     if (k % check_every == 0 || k == opt->max_iter) {
-      GC_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(flag, a.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       GC_CUDA(cudaStreamSynchronize(s));
       if ((rc = prof.drain())) return rc;
       if (*flag <= 0) break;

@@ -151,3 +151,65 @@ GC_DEV int block_or(int v, int* red) {
   __syncthreads();
   return r;
 }
+
+// Fused end-of-update reduction over the block: sums of d2 and n2 (double) and OR of two flags,
+// two barriers.  Every thread gets the totals (warp totals summed in the same order everywhere).
+// `red` holds >= 96 doubles.
+GC_DEV void block_reduce_step(double& d2, double& n2, int& f1, int& f2, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int fl = (f1 ? 1 : 0) | (f2 ? 2 : 0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+  }
+  if (lane == 0) {
+    red[warp] = d2;
+    red[32 + warp] = n2;
+    red[64 + warp] = (double)fl;
+  }
+  __syncthreads();
+  double a = 0.0, b = 0.0;
+  int f = 0;
+  for (int w = 0; w < nw; ++w) {
+    a += red[w];
+    b += red[32 + w];
+    f |= (int)red[64 + w];
+  }
+  __syncthreads();
+  d2 = a;
+  n2 = b;
+  f1 = f & 1;
+  f2 = (f >> 1) & 1;
+}
+
+// Fixed-order reduction of one tile's per-slot partial sums into per-antenna sums.  `off`/`ent`
+// give, per antenna, the list of partial-sum slots (float offsets into `part`).  Each list is cut
+// into CH equal chunks summed in parallel (long lists -- e.g. an antenna's p side over a run of
+// consecutive baselines -- would otherwise serialise the tile), then the chunk sums are added in
+// chunk order and compensated into (acc, cmp).  `ps` holds nat * NC * CH floats.
+template <int NC, int CH>
+GC_DEV void tile_reduce(const float* part, const int* off, const int* ent, int nat, float* acc, float* cmp,
+                        float* ps) {
+  for (int x = threadIdx.x; x < nat * NC * CH; x += blockDim.x) {
+    const int ch = x % CH, r = x / CH, an = r / NC, c = r - an * NC;
+    const int e0 = __ldg(off + an), len = __ldg(off + an + 1) - e0;
+    const int b0 = e0 + (len * ch) / CH, b1 = e0 + (len * (ch + 1)) / CH;
+    float s0 = 0.f, s1 = 0.f;
+    int e = b0;
+    for (; e + 1 < b1; e += 2) {
+      s0 += part[__ldg(ent + e) + c];
+      s1 += part[__ldg(ent + e + 1) + c];
+    }
+    if (e < b1) s0 += part[__ldg(ent + e) + c];
+    ps[x] = s0 + s1;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < nat * NC; x += blockDim.x) {
+    float s = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < CH; ++ch) s += ps[x * CH + ch];
+    kahan_add(acc[x], cmp[x], s);
+  }
+}

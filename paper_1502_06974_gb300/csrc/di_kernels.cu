@@ -19,11 +19,15 @@
 // therefore bitwise reproducible run to run.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include "common.cuh"
 #include "internal.h"
 #include "kinds.cuh"
 
 namespace gc {
+
+constexpr int kRedChunks = 4;  // chunk count of the optional split slot-list reduction (GAINCAL_RED_CHUNKS=4)
 
 // Shared-memory carve-up (elements of T): partials [256][2 NC + 1] (padded: bank-conflict free) |
 // acc [na_max][NC] | comp [na_max][NC] | gains [na_max][GW] | new gains [na_max][GW] |
@@ -31,7 +35,7 @@ namespace gc {
 template <typename T, class K>
 __host__ __device__ inline size_t di_smem_elems(int na_max) {
   return (size_t)kDIThreads * (2 * K::NC + 1) + 2 * (size_t)na_max * K::NC + 2 * (size_t)na_max * K::GW + 64 +
-         4 * (size_t)na_max;
+         4 * (size_t)na_max + (size_t)na_max * K::NC * kRedChunks;
 }
 
 template <typename T, class K, bool ACC_ONLY>
@@ -192,162 +196,178 @@ __global__ void __launch_bounds__(kDIThreads) di_iter_kernel(const DIArgs a) {
 
 
 // ------------------------------------------------------------------------------------------
-// Moment-stream iteration: the same per-iteration structure as di_iter_kernel, but each item is
-// (interval, range of 256-baseline tiles) and each thread turns one baseline's moments (the sample
-// sums with the gains factored out, written once by the moment pass) into its p- and q-side
-// contributions -- 12 independent float4 loads and 160 FMA per 2x2 baseline per iteration.
+// Moment-stream iteration, split in two launches per iteration.
+//
+// di_macc_kernel (accumulate): a grid-stride loop over the tiles (256 baselines) of the intervals
+//   still iterating.  Each thread turns one baseline's moments (the sample sums with the gains
+//   factored out, written once by the moment pass) into its p- and q-side contributions -- 48
+//   coalesced loads and 160 FMA per 2x2 baseline -- and the CTA reduces the tile into per-antenna
+//   partial sums (fixed-order slot lists), written to scratch.  No atomics, no fences: the tile
+//   work is spread evenly over the grid.
+// di_msolve_kernel (update): one CTA per interval; sums its tiles' partials in tile order with
+//   compensation, applies the GN step / average, tests convergence, writes gains and the
+//   per-antenna auxiliaries (G^H G) and, if the interval keeps iterating, appends its tiles to
+//   the next iteration's list (lists rotate over three buffers: launch k reads list k % 3,
+//   appends to (k + 1) % 3; the accumulate launch of k clears (k + 2) % 3).
 // ------------------------------------------------------------------------------------------
-template <class MK, bool ACC_ONLY>
-__global__ void __launch_bounds__(kDIThreads) di_miter_kernel(const DIArgs a) {
+template <class MK, int CH, bool PF>
+__global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const DIArgs a) {
   using K = typename MK::K;
-  using G = typename K::G;
   constexpr int NC = K::NC, GW = K::GW, NM = MK::NM, AW = MK::AW, TB = kDIThreads, PS = 2 * NC + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* part = reinterpret_cast<float*>(smem_raw);
-  float* acc = part + TB * PS;
-  float* cmp = acc + a.na_max * NC;
-  float* gs = cmp + a.na_max * NC;
-  float* ng = gs + a.na_max * GW;
-  float* red = ng + a.na_max * GW;
-  float* ax = red + 64;
-  __shared__ int s_item, s_last;
+  float* part = reinterpret_cast<float*>(smem_raw);   // [TB][PS]
+  float* ps = part + TB * PS;                           // [na_max * NC * CH]
   const int tid = threadIdx.x;
   const int k = a.k;
-  float* gains = static_cast<float*>(a.gains);
-
-  const int cur = k % 3, nxt = (k + 1) % 3;
+  const int cur = k % 3;
   const int* list = a.ilist + (size_t)cur * a.n_items;
-  const int n_list = ACC_ONLY ? a.n_items : a.icount[cur];
-  if (blockIdx.x == 0 && tid == 0) {
-    a.qhead[(k + 1) & 1] = 0;
-    if (!ACC_ONLY) a.icount[(k + 2) % 3] = 0;
-  }
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(&a.qhead[k & 1], 1);
-    __syncthreads();
-    const int slot = s_item;
-    __syncthreads();
-    if (slot >= n_list) break;
-    const int it = ACC_ONLY ? slot : list[slot];
-    const int i = a.item_int[it];
-    if (!ACC_ONLY && a.active[i] == 0) continue;
-    const int nb = a.n_bl[i], na = a.n_ant[i], bo = a.bl_off[i];
+  const int n_list = a.icount[cur];
+  if (blockIdx.x == 0 && tid == 0) a.icount[(k + 2) % 3] = 0;
+  const float* gains = static_cast<const float*>(a.gains);
+  // the moments of the next tile are requested while the current tile is being reduced
+  float m[NM];
+  auto fetch = [&](int slot) {
+    const int it = list[slot];
+    const int i = a.item_int[it], t = a.item_s0[it];
+    if (t * TB + tid < a.n_bl[i]) {
+      const float* src = a.moments + (a.mom_off[i] + (int64_t)t * TB) * NM + tid;
+#pragma unroll
+      for (int c = 0; c < NM; ++c) m[c] = __ldg(src + c * TB);
+    }
+  };
+  int slot = blockIdx.x;
+  if (PF && slot < n_list) fetch(slot);
+  while (slot < n_list) {
+    if (!PF) fetch(slot);
+    const int it = list[slot];
+    const int i = a.item_int[it], t = a.item_s0[it];
+    const int nb = a.n_bl[i], bo = a.bl_off[i];
     const int64_t go = a.gain_off[i];
-    const int t0 = a.item_s0[it], t1 = a.item_s1[it];
+    const int b = t * TB + tid;
+    if (b < nb) {
+      const int p = a.ant1[bo + b], q = a.ant2[bo + b];
+      float pp[NC], pq[NC];
+      MK::partials(m, K::ld_gain(gains + (go + p) * GW), K::ld_gain(gains + (go + q) * GW),
+                   a.aux + (go + p) * AW, a.aux + (go + q) * AW, pp, pq);
+      float* my = part + tid * PS;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { my[c] = pp[c]; my[NC + c] = pq[c]; }
+    }
+    const int next = slot + gridDim.x;
+    if (PF && next < n_list) fetch(next);
+    __syncthreads();
     const int tab = a.itab[i];
     const int nat = a.tab_nant[tab];
-    const int* csr = a.csr_off + a.tab_base[tab];
-    const float* mom = a.moments + a.mom_off[i] * NM;
-    for (int x = tid; x < na * GW; x += TB) gs[x] = gains[go * GW + x];
-    for (int x = tid; x < na * NC; x += TB) { acc[x] = 0.f; cmp[x] = 0.f; }
-    __syncthreads();
-    for (int x = tid; x < na; x += TB) MK::aux(K::ld_gain(gs + x * GW), ax + x * AW);
-    __syncthreads();
-    for (int t = t0; t < t1; ++t) {
-      const int b = t * TB + tid;
-      if (b < nb) {
-        float m[NM];
-        const float4* src = reinterpret_cast<const float4*>(mom + (int64_t)b * NM);
-#pragma unroll
-        for (int c = 0; c < NM / 4; ++c) {
-          const float4 v = __ldg(src + c);
-          m[4 * c] = v.x; m[4 * c + 1] = v.y; m[4 * c + 2] = v.z; m[4 * c + 3] = v.w;
-        }
-        const int p = a.ant1[bo + b], q = a.ant2[bo + b];
-        float pp[NC], pq[NC];
-        MK::partials(m, K::ld_gain(gs + p * GW), K::ld_gain(gs + q * GW), ax + p * AW, ax + q * AW, pp, pq);
-        float* my = part + tid * PS;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) { my[c] = pp[c]; my[NC + c] = pq[c]; }
-      }
-      __syncthreads();
-      const int* off = csr + t * (nat + 1);
+    const int* off = a.csr_off + a.tab_base[tab] + t * (nat + 1);
+    float* scr = static_cast<float*>(a.scratch) + a.item_scr[it];
+    if (CH == 1) {
       for (int x = tid; x < nat * NC; x += TB) {
         const int an = x / NC, c = x - an * NC;
-        float s = 0.f;
         const int e1 = __ldg(off + an + 1);
+        float s = 0.f;
         for (int e = __ldg(off + an); e < e1; ++e) s += part[__ldg(a.csr_ent + e) + c];
-        kahan_add(acc[x], cmp[x], s);
+        scr[x] = s;
+      }
+    } else {
+      for (int x = tid; x < nat * NC * CH; x += TB) {
+        const int ch = x % CH, r = x / CH, an = r / NC, c = r - an * NC;
+        const int e0 = __ldg(off + an), len = __ldg(off + an + 1) - e0;
+        const int b0 = e0 + (len * ch) / CH, b1 = e0 + (len * (ch + 1)) / CH;
+        float s = 0.f;
+        for (int e = b0; e < b1; ++e) s += part[__ldg(a.csr_ent + e) + c];
+        ps[x] = s;
       }
       __syncthreads();
-    }
-    bool finish = true;
-    const int nch = a.n_chunks[i];
-    if (nch > 1) {
-      float* scr = static_cast<float*>(a.scratch) + a.item_scr[it];
-      for (int x = tid; x < nat * NC; x += TB) scr[x] = acc[x] - cmp[x];
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) s_last = (atomicAdd(&a.counters[i], 1) == nch - 1);
-      __syncthreads();
-      finish = s_last;
-      if (finish) {
-        __threadfence();
-        const int fi = a.first_item[i];
-        for (int x = tid; x < nat * NC; x += TB) {
-          float s = 0.f, c = 0.f;
-          for (int j = 0; j < nch; ++j)
-            kahan_add(s, c, __ldcg(static_cast<const float*>(a.scratch) + a.item_scr[fi + j] + x));
-          acc[x] = s;
-          cmp[x] = c;
-        }
-        if (tid == 0) a.counters[i] = 0;
-        __syncthreads();
-      }
-    }
-    if (!finish) continue;
-    if (ACC_ONLY) {
-      float* jhd = static_cast<float*>(a.jhd_out);
-      float* jhj = static_cast<float*>(a.jhj_out);
-      for (int an = tid; an < na; an += TB) {
-        float v[NC];
+      for (int x = tid; x < nat * NC; x += TB) {
+        float s = 0.f;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) v[c] = acc[an * NC + c] - cmp[an * NC + c];
-        K::write_acc(v, jhd, jhj, go + an);
+        for (int ch = 0; ch < CH; ++ch) s += ps[x * CH + ch];
+        scr[x] = s;
       }
-      __syncthreads();
-      continue;
     }
-    float d2 = 0.f, n2 = 0.f;
+    __syncthreads();
+    slot = next;
+  }
+}
+
+template <class MK>
+__global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, int n_int) {
+  using K = typename MK::K;
+  using G = typename K::G;
+  constexpr int NC = K::NC, GW = K::GW, AW = MK::AW, TB = kDIThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tot = reinterpret_cast<float*>(smem_raw);  // [na_max][NC]
+  __shared__ double red[96];
+  const int tid = threadIdx.x;
+  const int k = a.k, nxt = (k + 1) % 3;
+  float* gains = static_cast<float*>(a.gains);
+  const float* scr = static_cast<const float*>(a.scratch);
+  for (int i = blockIdx.x; i < n_int; i += gridDim.x) {
+    if (a.active[i] == 0) continue;
+    const int na = a.n_ant[i];
+    const int64_t go = a.gain_off[i];
+    const int nat = a.tab_nant[a.itab[i]];
+    const int nch = a.n_chunks[i], fi = a.first_item[i];
+    // tile partials summed in tile order, compensated; all (antenna, component) pairs in parallel
+    for (int x = tid; x < na * NC; x += TB) {
+      float s = 0.f, cc = 0.f;
+      if (x < nat * NC) {
+        int j = 0;
+        for (; j + 4 <= nch; j += 4) {
+          const float v0 = __ldcg(scr + a.item_scr[fi + j] + x), v1 = __ldcg(scr + a.item_scr[fi + j + 1] + x);
+          const float v2 = __ldcg(scr + a.item_scr[fi + j + 2] + x), v3 = __ldcg(scr + a.item_scr[fi + j + 3] + x);
+          kahan_add(s, cc, v0); kahan_add(s, cc, v1); kahan_add(s, cc, v2); kahan_add(s, cc, v3);
+        }
+        for (; j < nch; ++j) kahan_add(s, cc, __ldcg(scr + a.item_scr[fi + j] + x));
+      }
+      tot[x] = s - cc;
+    }
+    __syncthreads();
+    double d2 = 0.0, n2 = 0.0;
     int sing = 0, nonfin = 0;
     const bool gn_step = (a.schedule == GC_SCHED_GN) || (k & 1);
     for (int an = tid; an < na; an += TB) {
-      float v[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) v[c] = acc[an * NC + c] - cmp[an * NC + c];
-      const G old = K::ld_gain(gs + an * GW);
+      const G old = K::ld_gain(gains + (go + an) * GW);
       G g;
-      if (!K::solve(v, old, g)) sing = 1;
+      if (!K::solve(tot + an * NC, old, g)) sing = 1;
       const G nw = gn_step ? g : K::avg(old, g);
-      d2 += K::dist2(nw, old);
-      n2 += K::norm2(nw);
+      d2 += (double)K::dist2(nw, old);
+      n2 += (double)K::norm2(nw);
       if (!K::finite(nw)) nonfin = 1;
-      K::st_gain(ng + an * GW, nw);
+      K::st_gain(a.gnew + (go + an) * GW, nw);   // staged until the interval's decision is known
     }
-    d2 = block_sum(d2, red);
-    n2 = block_sum(n2, red);
-    sing = block_or(sing, reinterpret_cast<int*>(red));
-    nonfin = block_or(nonfin, reinterpret_cast<int*>(red));
+    block_reduce_step(d2, n2, sing, nonfin, red);
     if (!nonfin)
-      for (int x = tid; x < na * GW; x += TB) gains[go * GW + x] = ng[x];
+      for (int an = tid; an < na; an += TB) {
+        const G nw = K::ld_gain(a.gnew + (go + an) * GW);
+        K::st_gain(gains + (go + an) * GW, nw);
+        MK::aux(nw, a.aux + (go + an) * AW);
+      }
     if (tid == 0) {
       int st = -1;
       if (nonfin) st = GC_ST_NONFINITE;
-      else if ((double)d2 <= a.tol * a.tol * (double)n2) st = GC_ST_OK;
+      else if (d2 <= a.tol * a.tol * n2) st = GC_ST_OK;
       else if (k >= a.max_iter) st = GC_ST_NOT_CONVERGED;
       if (st >= 0) {
         a.active[i] = 0;
         a.iters[i] = k;
         a.status[i] = st | (sing ? GC_ST_SINGULAR_FLAG : 0);
         atomicSub(a.n_active, 1);
-      } else {  // still iterating: its items go to the next iteration's list
+      } else {
         const int base = atomicAdd(&a.icount[nxt], nch);
-        const int fi = a.first_item[i];
         for (int j = 0; j < nch; ++j) a.ilist[(size_t)nxt * a.n_items + base + j] = fi + j;
       }
     }
     __syncthreads();
   }
+}
+
+// Per-antenna auxiliaries (G^H G or |g|^2) of the starting gains.
+template <class MK>
+__global__ void di_maux_kernel(const float* gains, float* aux, int n_gain) {
+  using K = typename MK::K;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < n_gain) MK::aux(K::ld_gain(gains + (int64_t)x * K::GW), aux + (int64_t)x * MK::AW);
 }
 
 // Per-call state: active flags, statuses, counters.
@@ -422,25 +442,58 @@ static void* pick(int kind, int dtype, int acc_only) {
   return acc_only ? kernel_ptr<double, JonesKind<double>, true>() : kernel_ptr<double, JonesKind<double>, false>();
 }
 
-static void* pick_m(int kind, int acc_only) {
-  if (kind == 0)
-    return acc_only ? reinterpret_cast<void*>(&di_miter_kernel<ScalarMom, true>)
-                    : reinterpret_cast<void*>(&di_miter_kernel<ScalarMom, false>);
-  return acc_only ? reinterpret_cast<void*>(&di_miter_kernel<JonesMom, true>)
-                  : reinterpret_cast<void*>(&di_miter_kernel<JonesMom, false>);
+static int red_chunks() {
+  const char* v = getenv("GAINCAL_RED_CHUNKS");
+  return (v && atoi(v) == kRedChunks) ? kRedChunks : 1;
 }
 
-int di_m_max_blocks_per_sm(int kind, int acc_only, int smem, int* out) {
-  const void* f = pick_m(kind, acc_only);
+static bool acc_prefetch() {
+  const char* v = getenv("GAINCAL_ACC_PREFETCH");
+  return v && atoi(v) == 1;
+}
+
+static const void* pick_acc(int kind) {
+  const int ch = red_chunks();
+  const bool pf = acc_prefetch();
+  if (kind == 0) {
+    if (pf) return ch == 1 ? (const void*)&di_macc_kernel<ScalarMom, 1, true> : (const void*)&di_macc_kernel<ScalarMom, kRedChunks, true>;
+    return ch == 1 ? (const void*)&di_macc_kernel<ScalarMom, 1, false> : (const void*)&di_macc_kernel<ScalarMom, kRedChunks, false>;
+  }
+  if (pf) return ch == 1 ? (const void*)&di_macc_kernel<JonesMom, 1, true> : (const void*)&di_macc_kernel<JonesMom, kRedChunks, true>;
+  return ch == 1 ? (const void*)&di_macc_kernel<JonesMom, 1, false> : (const void*)&di_macc_kernel<JonesMom, kRedChunks, false>;
+}
+
+int di_macc_smem(int kind, int na_max) {
+  const int nc = kind == 0 ? 3 : 12;
+  const int ch = red_chunks() == 1 ? 1 : kRedChunks;
+  return (int)(sizeof(float) * ((size_t)kDIThreads * (2 * nc + 1) + (size_t)na_max * nc * ch + (size_t)na_max * nc));
+}
+
+int di_macc_max_blocks_per_sm(int kind, int smem, int* out) {
+  const void* f = pick_acc(kind);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, f, kDIThreads, smem);
 }
 
-int di_launch_miter(int kind, int acc_only, const DIArgs& a, int grid, int smem, void* stream) {
-  const void* f = pick_m(kind, acc_only);
+int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
   void* args[] = {const_cast<DIArgs*>(&a)};
-  return (int)cudaLaunchKernel(f, dim3(grid), dim3(kDIThreads), args, (size_t)smem, (cudaStream_t)stream);
+  cudaError_t e = cudaLaunchKernel(pick_acc(kind), dim3(grid), dim3(kDIThreads), args, (size_t)smem, s);
+  if (e != cudaSuccess) return (int)e;
+  const int g2 = n_int < 4096 ? n_int : 4096;
+  const size_t sm2 = sizeof(float) * (size_t)a.na_max * (kind == 0 ? 3 : 12);
+  if (kind == 0) di_msolve_kernel<ScalarMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
+  else di_msolve_kernel<JonesMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
+  return (int)cudaGetLastError();
+}
+
+int di_launch_maux(int kind, const float* gains, float* aux, int n_gain, void* stream) {
+  if (n_gain <= 0) return 0;
+  const int g = (n_gain + 255) / 256;
+  if (kind == 0) di_maux_kernel<ScalarMom><<<g, 256, 0, (cudaStream_t)stream>>>(gains, aux, n_gain);
+  else di_maux_kernel<JonesMom><<<g, 256, 0, (cudaStream_t)stream>>>(gains, aux, n_gain);
+  return (int)cudaGetLastError();
 }
 
 int di_smem_bytes(int kind, int dtype, int na_max) {

@@ -147,6 +147,15 @@ struct JonesKind {
   }
 };
 
+// Moments are stored per interval in tiles of kMomTile baselines, component-major inside a tile
+// ([NM][kMomTile] floats), so that a tile is one contiguous block for a bulk copy and threads that
+// own consecutive baselines read consecutive words.  mom_off counts baseline slots (a multiple of
+// kMomTile per interval).
+constexpr int kMomTile = 256;
+__host__ __device__ inline int64_t mom_index(int64_t mom_off, int b, int c, int nm) {
+  return (mom_off + (b & ~(kMomTile - 1))) * nm + (int64_t)c * kMomTile + (b & (kMomTile - 1));
+}
+
 // ------------------------------------------------------------------------------------------
 // Per-baseline moments of an interval (the sample sums with the gains factored out) and the
 // per-antenna contributions computed from them; see resident.cu for the algebra.

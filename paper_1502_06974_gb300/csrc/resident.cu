@@ -81,12 +81,13 @@ __global__ void __launch_bounds__(kMomBl2 * kMomLanes2) di_moment_kernel(const M
 #pragma unroll
   for (int c = 0; c < NM; ++c) my[c] = m[c];
   __syncthreads();
+  // tiled layout: per 256-baseline tile, component-major [NM][256] (see mom_index)
   const int nbt = min(kMomBl2, nb - tile * kMomBl2);
-  float* out = a.moments + (a.mom_off[i] + (int64_t)tile * kMomBl2) * NM;
   for (int x = threadIdx.x; x < nbt * NM; x += blockDim.x) {
-    float s = 0.f, c = 0.f;
-    for (int l = 0; l < kMomLanes2; ++l) kahan_add(s, c, part[(size_t)l * kMomBl2 * NM + x]);
-    out[x] = s - c;
+    const int c = x / nbt, blx = x - c * nbt;
+    float s = 0.f, cc = 0.f;
+    for (int l = 0; l < kMomLanes2; ++l) kahan_add(s, cc, part[((size_t)l * kMomBl2 + blx) * NM + c]);
+    a.moments[mom_index(a.mom_off[i], tile * kMomBl2 + blx, c, NM)] = s - cc;
   }
 }
 
@@ -117,37 +118,6 @@ struct ResArgs {
   int32_t max_iter;
   int32_t schedule;
 };
-
-// Fused end-of-iteration reduction: sum of d2 and n2 (double) and OR of two flags over the block,
-// two barriers.  `red` holds >= 3 * 32 doubles.
-GC_DEV void block_reduce_step(double& d2, double& n2, int& f1, int& f2, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  int fl = (f1 ? 1 : 0) | (f2 ? 2 : 0);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-    fl |= __shfl_xor_sync(0xffffffffu, fl, o);
-  }
-  if (lane == 0) {
-    red[warp] = d2;
-    red[32 + warp] = n2;
-    red[64 + warp] = (double)fl;
-  }
-  __syncthreads();
-  double a = 0.0, b = 0.0;
-  int f = 0;
-  for (int w = 0; w < nw; ++w) {  // every thread sums the warp totals in the same order
-    a += red[w];
-    b += red[32 + w];
-    f |= (int)red[64 + w];
-  }
-  __syncthreads();
-  d2 = a;
-  n2 = b;
-  f1 = f & 1;
-  f2 = (f >> 1) & 1;
-}
 
 template <class MK>
 __global__ void __launch_bounds__(kResThreads, 1) di_resident_kernel(const ResArgs a) {
@@ -197,12 +167,8 @@ __global__ void __launch_bounds__(kResThreads, 1) di_resident_kernel(const ResAr
         const int b = lb0 + lb;
         pa[j] = a.ant1[bo + b];
         qa[j] = a.ant2[bo + b];
-        const float* src = a.moments + (a.mom_off[i] + b) * NM;
 #pragma unroll
-        for (int c = 0; c < NM; c += 4) {
-          const float4 v = __ldcs(reinterpret_cast<const float4*>(src + c));
-          mom[j][c] = v.x; mom[j][c + 1] = v.y; mom[j][c + 2] = v.z; mom[j][c + 3] = v.w;
-        }
+        for (int c = 0; c < NM; ++c) mom[j][c] = __ldcs(a.moments + mom_index(a.mom_off[i], b, c, NM));
       } else {
 #pragma unroll
         for (int c = 0; c < NM; ++c) mom[j][c] = 0.f;
@@ -446,7 +412,7 @@ static int build_res_plan(int kind, const gc_layout* L, ResPlan& P, cudaStream_t
   int64_t mo = 0;
   for (int i = 0; i < n; ++i) {
     mom_off[i] = mo;
-    mo += L->n_bl[i];
+    mo += (int64_t)(L->n_bl[i] + kMomTile - 1) / kMomTile * kMomTile;
     cfirst[i] = (int)mint.size();
     if ((int64_t)L->n_bl[i] * L->n_samp[i] > 0)
       for (int t = 0; t < (L->n_bl[i] + kMomBl2 - 1) / kMomBl2; ++t) { mint.push_back(i); mtile.push_back(t); }

@@ -254,11 +254,12 @@ def test_resident_uneven_jones_batch(gpu_lib):
     assert per_slot_relerr(g.cpu().numpy(), gr) < 1e-5
 
 
-@pytest.mark.parametrize("tpi", ["1", "3"])
-def test_moments_multi_item_intervals(gpu_lib, monkeypatch, tpi):
-    """Moment-stream items of 1 or 3 baseline tiles: intervals split over several items (scratch)."""
-    monkeypatch.setenv("GAINCAL_TILES_PER_ITEM", tpi)
-    b = synth.make_di_jones(n_ant=48, n_t=2, n_chan=4, t_per=1, f_per=2)   # 1128 baselines: 5 tiles
+@pytest.mark.parametrize("chunks", ["1", "4"])
+def test_moments_multi_tile_intervals(gpu_lib, monkeypatch, chunks):
+    """Moment path with intervals spanning several 256-baseline tiles (1128 baselines: 5 tiles), with
+    the per-antenna slot lists summed in 1 or 4 chunks."""
+    monkeypatch.setenv("GAINCAL_RED_CHUNKS", chunks)
+    b = synth.make_di_jones(n_ant=48, n_t=2, n_chan=4, t_per=1, f_per=2)
     vis, model, g0, lay = device_batch(b)
     g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0, tol=0.0, max_iter=7, path=N.GC_PATH_MOMENTS)
     gr, _, _ = diagonal.solve_batch(b, tol=0.0, max_iter=7)
