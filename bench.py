@@ -228,6 +228,9 @@ def run_gpu(args):
         return api.calibrate_di_jones2x2(vis, model, lay, gains, tol=tol, max_iter=max_iter, profile=profile,
                                          path=args.path)
 
+    tuned_ms = None
+    if not args.no_autotune:   # launch shapes picked on this data, before any timing
+        tuned_ms = api.autotune_di(vis, model, lay, gains, iters=24)
     for _ in range(args.warmup):
         _, iters, _, status = step()
     torch.cuda.synchronize(dev)
@@ -344,7 +347,8 @@ def run_gpu(args):
                           "l2": "inputs (495 MB vis+model) larger than L2; no flush",
                           "iters_median": med_it, "iters_max": int(its.max()),
                           "converged": int(np.sum((st & 15) == 0)),
-                          "parallelism": f"replicas x{world} (independent intervals per GPU)"},
+                          "parallelism": f"replicas x{world} (independent intervals per GPU)",
+                          "autotuned": tuned_ms is not None},
                "roofline": roof,
                "roofline_moment_pass": roof_mom,
                "path": {N_PATH_RESIDENT: "resident", N_PATH_MOMENTS: "moments"}.get(path_used, "stream"),
@@ -370,6 +374,7 @@ def main():
     ap.add_argument('--impl', default='gaincal', choices=['gaincal', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
+    ap.add_argument('--no-autotune', action='store_true')
     ap.add_argument('--path', type=int, default=0, help='0 auto (moments), 1 raw-row streaming, 2 resident, 3 moments')
     ap.add_argument('--iters', type=int, default=0,
                     help='run exactly this many iterations per step (tol 0) instead of converging; for profiling')

@@ -216,6 +216,20 @@ int gc_jhj_jhr_di_jones2x2_noalloc(const void* vis, const void* model, const gc_
                                    void* stream);
 
 /*
+ * Autotuner for the direction-independent solvers (launch shapes only; results are the same up to
+ * FP32 summation order).  Runs `iters` iterations (tol 0) of gc_calibrate_di_scalar (kind 0) or
+ * gc_calibrate_di_jones2x2 (kind 1) with each candidate shape -- reduction split, prefetch, CTAs
+ * per SM for the moment path; rows per work item and CTAs per SM for the raw-row path -- on the
+ * caller's data, and records the fastest for the layout's shape bucket (kind, dtype, path, and
+ * the powers of two of the interval count, largest baseline count and mean samples per interval).
+ * Later calls with a layout in that bucket use it.  vis, model and gains are device pointers;
+ * `gains` is restored before returning.  best_ms (may be NULL) receives the fastest time of the
+ * iteration kernels.  Synchronous.
+ */
+int gc_autotune_di(int32_t kind, const void* vis, const void* model, const gc_layout* layout, void* gains,
+                   int32_t dtype, int32_t iters, double* best_ms, void* stream);
+
+/*
  * Totals of the last gc_calibrate_* call made with opt->profile = 1: summed device time of its
  * iteration launches (ms, from CUDA events on the call's stream), number of those launches, and
  * rows processed by them (sum over intervals of iterations x rows).  Any pointer may be NULL.

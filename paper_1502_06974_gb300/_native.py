@@ -24,7 +24,7 @@ GC_MAX_ANT, GC_MAX_DIR = 1024, 10
 EXPORTS = [
     'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones',
     'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2', 'gc_jhj_jhr_di_jones2x2_noalloc',
-    'gc_profile_last', 'gc_profile_detail', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
+    'gc_autotune_di', 'gc_profile_last', 'gc_profile_detail', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
 ]
 
 _p = C.c_void_p
@@ -75,6 +75,9 @@ def lib() -> C.CDLL:
         L.gc_launch_count.restype = C.c_int64
         L.gc_profile_last.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.gc_profile_last.restype = C.c_int
+        L.gc_autotune_di.argtypes = [C.c_int32, _p, _p, C.POINTER(GcLayout), _p, C.c_int32, C.c_int32,
+                                     C.POINTER(C.c_double), _p]
+        L.gc_autotune_di.restype = C.c_int
         L.gc_profile_detail.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.gc_profile_detail.restype = C.c_int
         L.gc_release.argtypes = []

@@ -159,6 +159,22 @@ def jhj_jhr_di_jones2x2(vis, model, layout, gains):
     return _jhj_jhr('gc_jhj_jhr_di_jones2x2', vis, model, layout, gains, True)
 
 
+def autotune_di(vis, model, layout, gains, iters=24):
+    """Pick the fastest launch shape for this layout's shape bucket (gc_autotune_di); gains unchanged.
+
+    Returns the fastest iteration-kernel time in ms.
+    """
+    for t, n in ((vis, 'vis'), (model, 'model'), (gains, 'gains')):
+        _check_tensor(t, n, False)
+    kind = 1 if vis.dim() == 3 else 0
+    best = C.c_double(0.0)
+    lay = layout.c()
+    rc = N.lib().gc_autotune_di(kind, _ptr(vis), _ptr(model), C.byref(lay), _ptr(gains), _dtype_code(vis),
+                                int(iters), C.byref(best), _stream_ptr(vis.device))
+    N.check(rc, 'gc_autotune_di')
+    return best.value
+
+
 def profile_last():
     """(iteration-kernel ms, iteration launches, row-iterations) of the last profiled calibrate call."""
     ms = C.c_double(0.0); n = C.c_int64(0); ri = C.c_int64(0)

@@ -149,6 +149,63 @@ uint64_t layout_hash(const gc_layout* L, uint64_t salt) {
   return h;
 }
 
+// ------------------------------------------------------------------------------------ tunables
+// Launch-shape choices of the DI solvers.  Defaults below; gc_autotune_di measures candidates on
+// the caller's data and records the fastest per shape bucket; GAINCAL_* environment variables
+// override both (for experiments).
+struct Tune {
+  int red_chunks = 1;     // moment path: per-antenna slot lists summed in 1 or 4 chunks
+  int prefetch = 0;       // moment path: request the next tile's moments before reducing this one
+  int bps = 0;            // CTAs per SM of the persistent grid (0 = as many as fit)
+  int check_every = 16;   // iterations per graph segment / between host checks of the active count
+  int target_rows = 0;    // raw-row path: rows per work item (0 = default)
+  int graph = 1;          // capture iteration segments in a CUDA graph
+};
+static std::map<uint64_t, Tune> g_tune;
+static bool g_tune_override_on = false;
+static Tune g_tune_override;
+
+static int ilog2(int64_t v) {
+  int r = 0;
+  while (v > 1) { v >>= 1; ++r; }
+  return r;
+}
+
+static uint64_t tune_bucket(int kind, int dtype, int mode, const gc_layout* L) {
+  int64_t nb_max = 0, rows = 0;
+  for (int i = 0; i < L->n_intervals; ++i) {
+    nb_max = std::max<int64_t>(nb_max, L->n_bl[i]);
+    rows += (int64_t)L->n_bl[i] * L->n_samp[i];
+  }
+  const int64_t ms = L->n_intervals > 0 && nb_max > 0 ? rows / std::max<int64_t>(1, (int64_t)L->n_intervals * nb_max) : 0;
+  return ((uint64_t)kind) | ((uint64_t)dtype << 2) | ((uint64_t)mode << 4) | ((uint64_t)ilog2(L->n_intervals) << 8) |
+         ((uint64_t)ilog2(nb_max) << 16) | ((uint64_t)ilog2(ms) << 24);
+}
+
+static int env_int(const char* name, int dflt);
+
+static Tune effective_tune(int kind, int dtype, int mode, const gc_layout* L) {
+  Tune t;
+  if (g_tune_override_on) {
+    t = g_tune_override;
+  } else {
+    auto f = g_tune.find(tune_bucket(kind, dtype, mode, L));
+    if (f != g_tune.end()) t = f->second;
+  }
+  t.red_chunks = env_int("GAINCAL_RED_CHUNKS", t.red_chunks);
+  t.prefetch = env_int("GAINCAL_ACC_PREFETCH", t.prefetch);
+  t.bps = env_int("GAINCAL_BLOCKS_PER_SM", t.bps);
+  t.check_every = std::max(1, env_int("GAINCAL_CHECK_EVERY", t.check_every));
+  t.target_rows = env_int(kind == 0 ? "GAINCAL_TARGET_ROWS_SCALAR" : "GAINCAL_TARGET_ROWS_JONES", t.target_rows);
+  t.graph = env_int("GAINCAL_GRAPH", t.graph);
+  return t;
+}
+
+static uint64_t tune_hash(const Tune& t) {
+  return (uint64_t)t.red_chunks * 1000003ull ^ (uint64_t)t.prefetch * 7919ull ^ (uint64_t)t.bps * 104729ull ^
+         (uint64_t)t.target_rows * 1299709ull ^ (uint64_t)t.check_every * 15485863ull;
+}
+
 // ------------------------------------------------------------------------------------ DI plan
 struct DIPlan {
   uint64_t key = 0;
@@ -170,6 +227,11 @@ struct DIPlan {
   const int32_t* mfirst = nullptr;
   const int32_t* mcount = nullptr;
   double* mchi2 = nullptr;
+  Tune tune;
+  // captured iteration segment (graph) and the arguments it was captured with
+  cudaGraphExec_t gexec = nullptr;
+  DIArgs gargs{};
+  int gS = 0;
 };
 
 static DIPlan g_di_plan[2][2][2][2];  // [mode][kind][dtype][acc_only]
@@ -181,7 +243,8 @@ static int env_int(const char* name, int dflt) {
 }
 
 // Build the work items, baseline-table reduction lists and device copies for one layout.
-static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_layout* L, DIPlan& P, void* stream) {
+static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_layout* L, const Tune& tune, DIPlan& P,
+                         void* stream) {
   const int nc = kind == 0 ? 3 : 12;
   const int TB = kDIThreads;
   const int n = L->n_intervals;
@@ -222,7 +285,7 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   if (csr_off.empty()) csr_off.push_back(0);
   if (csr_ent.empty()) csr_ent.push_back(0);
   // work items: (interval, sample range) for the raw-row kernel; (interval, tile range) for moments
-  const int target = env_int(kind == 0 ? "GAINCAL_TARGET_ROWS_SCALAR" : "GAINCAL_TARGET_ROWS_JONES", g_target_rows[kind]);
+  const int target = tune.target_rows > 0 ? tune.target_rows : g_target_rows[kind];
   const int tpi = 1;  // moment path: one item per 256-baseline tile
   std::vector<int> item_int, item_s0, item_s1, n_chunks(n), first_item(n);
   std::vector<int64_t> item_scr, mom_off(n);
@@ -341,6 +404,7 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   a.counters = (int32_t*)at(p_counters);
   a.n_active = (int32_t*)at(p_misc);
   a.qhead = (int32_t*)at(p_misc) + 4;
+  a.kbase = (int32_t*)at(p_misc) + 8;
   a.n_items = n_items;
   a.na_max = na_max;
   a.mom_off = (const int64_t*)at(p_mom_off);
@@ -368,15 +432,15 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   GC_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (P.smem > max_smem) return GC_ERR_LIMIT;
   if (mode == 1) {
-    P.smem = di_macc_smem(kind, na_max);
+    P.smem = di_macc_smem(kind, na_max, tune.red_chunks);
     if (P.smem > max_smem) return GC_ERR_LIMIT;
-    GC_CUDA_I(di_macc_max_blocks_per_sm(kind, P.smem, &per_sm));
+    GC_CUDA_I(di_macc_max_blocks_per_sm(kind, P.smem, tune.red_chunks, tune.prefetch, &per_sm));
   } else {
     GC_CUDA_I(di_max_blocks_per_sm(kind, dtype, acc_only, P.smem, &per_sm));
   }
   if (per_sm < 1) return GC_ERR_LIMIT;
-  const int cap = env_int("GAINCAL_BLOCKS_PER_SM", per_sm);
-  per_sm = cap < per_sm ? (cap > 0 ? cap : 1) : per_sm;
+  if (tune.bps > 0 && tune.bps < per_sm) per_sm = tune.bps;
+  P.tune = tune;
   P.grid = nsm * per_sm;
   if (P.grid > n_items) P.grid = n_items > 0 ? n_items : 1;
   return GC_OK;
@@ -386,19 +450,17 @@ static int get_di_plan(int mode, int kind, int dtype, int acc_only, const gc_lay
   DIPlan& P = g_di_plan[mode][kind][dtype][acc_only];
   int dev = 0;
   GC_CUDA(cudaGetDevice(&dev));
+  const Tune tune = effective_tune(kind, dtype, mode, L);
   const uint64_t key = layout_hash(L, (uint64_t)(kind * 131 + dtype * 7 + acc_only) ^ ((uint64_t)dev << 40) ^
-                                      ((uint64_t)env_int("GAINCAL_TARGET_ROWS_SCALAR", 0) << 20) ^
-                                      ((uint64_t)env_int("GAINCAL_TARGET_ROWS_JONES", 0) << 48) ^
-                                      ((uint64_t)env_int("GAINCAL_BLOCKS_PER_SM", 0) << 56) ^
-                                      ((uint64_t)mode << 4) ^
-                                      ((uint64_t)env_int("GAINCAL_RED_CHUNKS", 0) << 36) ^
-                                      ((uint64_t)env_int("GAINCAL_ACC_PREFETCH", 0) << 40));
+                                          ((uint64_t)mode << 4) ^ tune_hash(tune));
   if (P.key != key || P.n_int != L->n_intervals || !P.dev) {
     P.key = 0;
-    int rc = build_di_plan(mode, kind, dtype, acc_only, L, P, stream);
+    if (P.gexec) { cudaGraphExecDestroy(P.gexec); P.gexec = nullptr; }
+    int rc = build_di_plan(mode, kind, dtype, acc_only, L, tune, P, stream);
     if (rc != GC_OK) return rc;
     P.key = key;
   }
+  P.tune = tune;
   *out = &P;
   return GC_OK;
 }
@@ -423,7 +485,7 @@ void profile_record(double iter_ms, int64_t launches, int64_t row_iters, double 
 
 struct Profiler {
   bool on;
-  int cap, used = 0;
+  int cap, used = 0, weight = 1;  // weight: iterations per bracketed launch
   std::vector<cudaEvent_t> ev;
   double ms = 0.0;
   int64_t launches = 0;
@@ -460,7 +522,7 @@ struct Profiler {
       GC_CUDA(cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
       ms += t;
     }
-    launches += used;
+    launches += (int64_t)used * weight;
     used = 0;
     return GC_OK;
   }
@@ -583,21 +645,68 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   }
   int* flag = nullptr;
   if ((rc = pinned_flag(&flag))) return rc;
-  const int check_every = env_int("GAINCAL_CHECK_EVERY", 16);
-  Profiler prof(opt->profile != 0, check_every);
+  const Tune& tn = P->tune;
+  const int S = tn.check_every;
+  const int per_iter = mode == 1 ? 2 : 1;
+  auto launch_iter = [&](const DIArgs& x, cudaStream_t st) -> int {
+    return mode == 1 ? di_launch_mstep(kind, x, P->grid, P->smem, P->n_int, tn.red_chunks, tn.prefetch, st)
+                     : di_launch_iter(kind, opt->dtype, 0, x, P->grid, P->smem, st);
+  };
+  Profiler prof(opt->profile != 0, S);
   if ((rc = prof.init())) return rc;
-  for (int k = 1; k <= opt->max_iter; ++k) {
-    a.k = k;
-    if ((rc = prof.before(s))) return rc;
-    if (mode == 1) GC_CUDA_I(di_launch_mstep(kind, a, P->grid, P->smem, P->n_int, stream));
-    else GC_CUDA_I(di_launch_iter(kind, opt->dtype, 0, a, P->grid, P->smem, stream));
-    if ((rc = prof.after(s))) return rc;
-    g_launches += mode == 1 ? 2 : 1;
-    if (k % check_every == 0 || k == opt->max_iter) {
+  if (tn.graph) {
+    prof.weight = S;
+    // One segment = S iterations captured once (k = *kbase + 1 .. *kbase + S) plus a node that
+    // advances *kbase; segments are relaunched until no interval is active.  Iterations past
+    // max_iter find no active interval and do nothing.
+    DIArgs ga = a;
+    ga.k = 0;
+    if (!P->gexec || P->gS != S || memcmp(&P->gargs, &ga, sizeof(DIArgs)) != 0) {
+      if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+      cudaStream_t cs = nullptr;
+      GC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      GC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      int crc = 0;
+      for (int j = 1; j <= S && !crc; ++j) {
+        DIArgs x = ga;
+        x.k = j;
+        crc = launch_iter(x, cs);
+      }
+      if (!crc) crc = di_launch_advance(a.kbase, S, cs);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+      cudaStreamDestroy(cs);
+      if (crc) return cuda_fail((cudaError_t)crc, "capture of the iteration segment");
+      if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+      const cudaError_t ie = cudaGraphInstantiate(&P->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+      P->gargs = ga;
+      P->gS = S;
+    }
+    for (int k0 = 0; k0 < opt->max_iter; k0 += S) {
+      if ((rc = prof.before(s))) return rc;
+      GC_CUDA(cudaGraphLaunch(P->gexec, s));
+      if ((rc = prof.after(s))) return rc;
+      g_launches += (int64_t)S * per_iter + 1;
       GC_CUDA(cudaMemcpyAsync(flag, a.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       GC_CUDA(cudaStreamSynchronize(s));
       if ((rc = prof.drain())) return rc;
       if (*flag <= 0) break;
+    }
+  } else {
+    for (int k = 1; k <= opt->max_iter; ++k) {
+      a.k = k;
+      if ((rc = prof.before(s))) return rc;
+      GC_CUDA_I(launch_iter(a, s));
+      if ((rc = prof.after(s))) return rc;
+      g_launches += per_iter;
+      if (k % S == 0 || k == opt->max_iter) {
+        GC_CUDA(cudaMemcpyAsync(flag, a.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        GC_CUDA(cudaStreamSynchronize(s));
+        if ((rc = prof.drain())) return rc;
+        if (*flag <= 0) break;
+      }
     }
   }
   if (opt->compute_chi2) {
@@ -644,6 +753,7 @@ static int run_di_acc(int kind, const void* vis, const void* model, const gc_lay
   rc = get_di_plan(0, kind, dtype, 1, L, &P, stream);
   if (rc != GC_OK) return rc;
   DIArgs a = P->args;
+  a.kbase = nullptr;
   a.vis = vis;
   a.model = model;
   a.gains = const_cast<void*>(gains);
@@ -662,6 +772,70 @@ static int run_di_acc(int kind, const void* vis, const void* model, const gc_lay
   GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
   GC_CUDA_I(di_launch_iter(kind, dtype, 1, a, P->grid, P->smem, stream));
   g_launches += 2;
+  return GC_OK;
+}
+
+// Time candidate launch shapes on the caller's data and record the fastest for this shape bucket.
+static int autotune_di(int kind, const void* vis, const void* model, const gc_layout* L, void* gains, int dtype,
+                       int iters, double* best_ms, void* stream) {
+  if (!L || (kind != 0 && kind != 1) || iters < 1) return GC_ERR_ARG;
+  if (dtype != GC_DTYPE_C64 && dtype != GC_DTYPE_C128) return GC_ERR_DTYPE;
+  int rc = validate_layout(L, 1);
+  if (rc != GC_OK) return rc;
+  if (L->n_intervals == 0 || L->n_gain == 0) return GC_OK;
+  const int mode = dtype == GC_DTYPE_C64 ? 1 : 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t gb = (size_t)L->n_gain * elem_bytes(kind, dtype);
+  void* saved = nullptr;
+  if ((rc = ws_get("tune_gains", gb, &saved))) return rc;
+  GC_CUDA(cudaMemcpyAsync(saved, gains, gb, cudaMemcpyDeviceToDevice, s));
+  std::vector<Tune> cands;
+  if (mode == 1) {
+    for (int ch : {1, 4})
+      for (int pf : {0, 1})
+        for (int bps : {0, 2}) {
+          Tune t;
+          t.red_chunks = ch;
+          t.prefetch = pf;
+          t.bps = bps;
+          cands.push_back(t);
+        }
+  } else {
+    for (int tr : {4096, 8192, 16384, 32768})
+      for (int bps : {0, 2}) {
+        Tune t;
+        t.target_rows = tr;
+        t.bps = bps;
+        cands.push_back(t);
+      }
+  }
+  gc_options opt{};
+  opt.tol = 0.0;
+  opt.max_iter = iters;
+  opt.dtype = dtype;
+  opt.profile = 1;
+  double best = 1e300;
+  Tune best_t;
+  for (const Tune& c : cands) {
+    g_tune_override = c;
+    g_tune_override_on = true;
+    double t_c = 1e300;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run builds the plan and captures the graph
+      GC_CUDA(cudaMemcpyAsync(gains, saved, gb, cudaMemcpyDeviceToDevice, s));
+      rc = run_di(kind, vis, model, L, gains, &opt, nullptr, nullptr, nullptr, stream);
+      if (rc < 0) break;
+      t_c = g_prof.ms;
+    }
+    g_tune_override_on = false;
+    if (rc == GC_ERR_CUDA) return rc;
+    if (rc < 0) continue;  // shape not launchable (e.g. shared memory): skip
+    if (t_c < best) { best = t_c; best_t = c; }
+  }
+  g_tune_override_on = false;
+  GC_CUDA(cudaMemcpyAsync(gains, saved, gb, cudaMemcpyDeviceToDevice, s));
+  GC_CUDA(cudaStreamSynchronize(s));
+  if (best < 1e300) g_tune[tune_bucket(kind, dtype, mode, L)] = best_t;
+  if (best_ms) *best_ms = best < 1e300 ? best : -1.0;
   return GC_OK;
 }
 
@@ -691,6 +865,11 @@ int gc_jhj_jhr_di_scalar(const void* vis, const void* model, const gc_layout* la
 int gc_jhj_jhr_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,
                            int32_t dtype, void* jhd_out, void* jhj_out, void* stream) {
   return run_di_acc(1, vis, model, layout, gains, dtype, jhd_out, jhj_out, stream);
+}
+
+int gc_autotune_di(int32_t kind, const void* vis, const void* model, const gc_layout* layout, void* gains,
+                   int32_t dtype, int32_t iters, double* best_ms, void* stream) {
+  return autotune_di(kind, vis, model, layout, gains, dtype, iters, best_ms, stream);
 }
 
 const char* gc_error_string(int code) {
@@ -748,6 +927,7 @@ int gc_release(void) {
         }
   gc::dd_release();
   gc::res_release();
+  gc::g_tune.clear();
   if (gc::g_pinned_flag) { cudaFreeHost(gc::g_pinned_flag); gc::g_pinned_flag = nullptr; }
   return GC_OK;
 }

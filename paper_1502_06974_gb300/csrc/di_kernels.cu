@@ -19,8 +19,6 @@
 // therefore bitwise reproducible run to run.
 #include <cuda_runtime.h>
 
-#include <cstdlib>
-
 #include "common.cuh"
 #include "internal.h"
 #include "kinds.cuh"
@@ -51,7 +49,7 @@ __global__ void __launch_bounds__(kDIThreads) di_iter_kernel(const DIArgs a) {
   T* red = ng + a.na_max * GW;
   __shared__ int s_item, s_last;
   const int tid = threadIdx.x;
-  const int k = a.k;
+  const int k = a.k + (a.kbase ? *a.kbase : 0);
   const T* vis = static_cast<const T*>(a.vis);
   const T* mod = static_cast<const T*>(a.model);
   T* gains = static_cast<T*>(a.gains);
@@ -218,7 +216,7 @@ __global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const D
   float* part = reinterpret_cast<float*>(smem_raw);   // [TB][PS]
   float* ps = part + TB * PS;                           // [na_max * NC * CH]
   const int tid = threadIdx.x;
-  const int k = a.k;
+  const int k = a.k + (a.kbase ? *a.kbase : 0);
   const int cur = k % 3;
   const int* list = a.ilist + (size_t)cur * a.n_items;
   const int n_list = a.icount[cur];
@@ -299,7 +297,7 @@ __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, i
   float* tot = reinterpret_cast<float*>(smem_raw);  // [na_max][NC]
   __shared__ double red[96];
   const int tid = threadIdx.x;
-  const int k = a.k, nxt = (k + 1) % 3;
+  const int k = a.k + (a.kbase ? *a.kbase : 0), nxt = (k + 1) % 3;
   float* gains = static_cast<float*>(a.gains);
   const float* scr = static_cast<const float*>(a.scratch);
   for (int i = blockIdx.x; i < n_int; i += gridDim.x) {
@@ -375,6 +373,7 @@ __global__ void di_init_kernel(const DIArgs a, int n_int, int n_active0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     *a.n_active = n_active0;
+    if (a.kbase) *a.kbase = 0;
     a.qhead[0] = 0;
     a.qhead[1] = 0;
     if (a.icount) { a.icount[1] = a.n_items; a.icount[2] = 0; a.icount[0] = 0; }
@@ -442,49 +441,47 @@ static void* pick(int kind, int dtype, int acc_only) {
   return acc_only ? kernel_ptr<double, JonesKind<double>, true>() : kernel_ptr<double, JonesKind<double>, false>();
 }
 
-static int red_chunks() {
-  const char* v = getenv("GAINCAL_RED_CHUNKS");
-  return (v && atoi(v) == kRedChunks) ? kRedChunks : 1;
-}
-
-static bool acc_prefetch() {
-  const char* v = getenv("GAINCAL_ACC_PREFETCH");
-  return v && atoi(v) == 1;
-}
-
-static const void* pick_acc(int kind) {
-  const int ch = red_chunks();
-  const bool pf = acc_prefetch();
+static const void* pick_acc(int kind, int red_chunks, int prefetch) {
+  const bool c4 = red_chunks == kRedChunks, pf = prefetch != 0;
   if (kind == 0) {
-    if (pf) return ch == 1 ? (const void*)&di_macc_kernel<ScalarMom, 1, true> : (const void*)&di_macc_kernel<ScalarMom, kRedChunks, true>;
-    return ch == 1 ? (const void*)&di_macc_kernel<ScalarMom, 1, false> : (const void*)&di_macc_kernel<ScalarMom, kRedChunks, false>;
+    if (pf) return c4 ? (const void*)&di_macc_kernel<ScalarMom, kRedChunks, true> : (const void*)&di_macc_kernel<ScalarMom, 1, true>;
+    return c4 ? (const void*)&di_macc_kernel<ScalarMom, kRedChunks, false> : (const void*)&di_macc_kernel<ScalarMom, 1, false>;
   }
-  if (pf) return ch == 1 ? (const void*)&di_macc_kernel<JonesMom, 1, true> : (const void*)&di_macc_kernel<JonesMom, kRedChunks, true>;
-  return ch == 1 ? (const void*)&di_macc_kernel<JonesMom, 1, false> : (const void*)&di_macc_kernel<JonesMom, kRedChunks, false>;
+  if (pf) return c4 ? (const void*)&di_macc_kernel<JonesMom, kRedChunks, true> : (const void*)&di_macc_kernel<JonesMom, 1, true>;
+  return c4 ? (const void*)&di_macc_kernel<JonesMom, kRedChunks, false> : (const void*)&di_macc_kernel<JonesMom, 1, false>;
 }
 
-int di_macc_smem(int kind, int na_max) {
+int di_macc_smem(int kind, int na_max, int red_chunks) {
   const int nc = kind == 0 ? 3 : 12;
-  const int ch = red_chunks() == 1 ? 1 : kRedChunks;
+  const int ch = red_chunks == kRedChunks ? kRedChunks : 1;
   return (int)(sizeof(float) * ((size_t)kDIThreads * (2 * nc + 1) + (size_t)na_max * nc * ch + (size_t)na_max * nc));
 }
 
-int di_macc_max_blocks_per_sm(int kind, int smem, int* out) {
-  const void* f = pick_acc(kind);
+int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, int* out) {
+  const void* f = pick_acc(kind, red_chunks, prefetch);
   cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return (int)e;
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, f, kDIThreads, smem);
 }
 
-int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, void* stream) {
+int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
+                    void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   void* args[] = {const_cast<DIArgs*>(&a)};
-  cudaError_t e = cudaLaunchKernel(pick_acc(kind), dim3(grid), dim3(kDIThreads), args, (size_t)smem, s);
+  cudaError_t e = cudaLaunchKernel(pick_acc(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args,
+                                   (size_t)smem, s);
   if (e != cudaSuccess) return (int)e;
   const int g2 = n_int < 4096 ? n_int : 4096;
   const size_t sm2 = sizeof(float) * (size_t)a.na_max * (kind == 0 ? 3 : 12);
   if (kind == 0) di_msolve_kernel<ScalarMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
   else di_msolve_kernel<JonesMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
+  return (int)cudaGetLastError();
+}
+
+__global__ void di_advance_kernel(int* kbase, int by) { *kbase += by; }
+
+int di_launch_advance(int* kbase, int by, void* stream) {
+  di_advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(kbase, by);
   return (int)cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ struct DIArgs {
   // the items of intervals that stay active to list[(k + 1) % 3], and clears list (k + 2) % 3
   int32_t* ilist;    // [3][n_items]
   int32_t* icount;   // [3]
+  int32_t* kbase;    // iteration base added to k (graph-captured iteration segments); may be NULL
   float* aux;        // [n_gain][AW] per-antenna auxiliaries of the current gains (moment path)
   float* gnew;       // [n_gain][GW] staged new gains (moment path)
 };
@@ -71,9 +72,11 @@ int di_smem_bytes(int kind, int dtype, int na_max);
 int di_max_blocks_per_sm(int kind, int dtype, int acc_only, int smem, int* out);
 int di_launch_iter(int kind, int dtype, int acc_only, const DIArgs& a, int grid, int smem, void* stream);
 int di_launch_init(const DIArgs& a, int n_int, int n_active0, void* stream);
-int di_macc_smem(int kind, int na_max);
-int di_macc_max_blocks_per_sm(int kind, int smem, int* out);
-int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, void* stream);
+int di_macc_smem(int kind, int na_max, int red_chunks);
+int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, int* out);
+int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
+                    void* stream);
+int di_launch_advance(int* kbase, int by, void* stream);
 int di_launch_maux(int kind, const float* gains, float* aux, int n_gain, void* stream);
 // moment pass (resident.cu): per-baseline moments of every interval; items are (interval, 32 baselines)
 int moment_pass(int kind, const float* vis, const float* model, float* moments, const int64_t* row_off,
