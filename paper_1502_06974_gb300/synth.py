@@ -354,6 +354,75 @@ def make_uneven(seed=SEED, n_intervals=4096, ant_choices=(16, 24, 32, 48, 64), t
     return out
 
 
+def gp_sqrt(x: np.ndarray, length: float) -> np.ndarray:
+    """A square root L (L L^T = K) of the squared-exponential covariance K_ij = exp(-(x_i-x_j)^2 / 2 l^2).
+
+    Taken from the eigendecomposition with negative eigenvalues clipped (the kernel matrix of a
+    densely sampled smooth process is numerically singular, so Cholesky is not used).
+    """
+    d = x[:, None] - x[None, :]
+    K = np.exp(-0.5 * (d / length) ** 2)
+    w, V = np.linalg.eigh(K)
+    return V * np.sqrt(np.clip(w, 0.0, None))[None, :]
+
+
+def make_warm(seed=SEED, n_ant=64, n_t=720, n_chan=64, f_per=8, dt_s=10.0, t_corr_s=1800.0, f_corr_hz=50e6,
+              amp_sigma=0.1, phase_sigma=1.0, leak_sigma=0.02, n_src=20, frac_sigma=0.05, sigma=0.01,
+              dtype=np.complex64, fmin=1.0e9, fmax=1.4e9, chunk=64):
+    """Gains that evolve smoothly: a separable Gaussian process over time and frequency.
+
+    Intervals are 1 time x f_per channels, ordered time-major (interval i = t * n_fb + fb).  The
+    gain of an interval is the process at the interval's time and centre frequency, constant over
+    the interval's samples.  Per antenna, independent processes (unit variance, squared-exponential
+    kernels with the given correlation lengths) drive: the xx and yy amplitudes (1 + amp_sigma z),
+    the xx and yy phases (phase_sigma z, radians) and the real and imaginary parts of the two
+    leakage terms (leak_sigma z).  Sky, array and noise follow the full-Jones workload.
+    """
+    n_fb = n_chan // f_per
+    rng_sky = rng_for(seed, 5, 0)
+    xy = antenna_positions(rng_sky, n_ant)
+    a1, a2 = baseline_table(n_ant)
+    B, l, m = polarized_sky(rng_sky, n_src, frac_sigma)
+    freqs = np.linspace(fmin, fmax, n_chan)
+    model_f = np.einsum('fbs,sij->fbij', fringe(xy, a1, a2, l, m, freqs), B)      # [f, b, 2, 2]
+    t_c = np.arange(n_t) * dt_s
+    f_c = freqs.reshape(n_fb, f_per).mean(axis=1)
+    Lt = gp_sqrt(t_c, t_corr_s)
+    Lf = gp_sqrt(f_c, f_corr_hz)
+    z = rng_for(seed, 5, 1).normal(0.0, 1.0, (8, n_ant, n_t, n_fb))
+    z = np.einsum('tu,kauv,fv->katf', Lt, z, Lf)                                      # [8, a, t, fb]
+    G = np.zeros((n_t, n_fb, n_ant, 2, 2), np.complex128)
+    zt = np.transpose(z, (0, 2, 3, 1))                                                 # [8, t, fb, a]
+    G[..., 0, 0] = (1.0 + amp_sigma * zt[0]) * np.exp(1j * phase_sigma * zt[2])
+    G[..., 1, 1] = (1.0 + amp_sigma * zt[1]) * np.exp(1j * phase_sigma * zt[3])
+    G[..., 0, 1] = leak_sigma * (zt[4] + 1j * zt[5])
+    G[..., 1, 0] = leak_sigma * (zt[6] + 1j * zt[7])
+    n_int = n_t * n_fb
+    G = G.reshape(n_int, n_ant, 2, 2)
+    nb = len(a1)
+    ns = f_per
+    rows = ns * nb
+    vis = np.empty((n_int * rows, 2, 2), dtype)
+    model = np.empty((n_int * rows, 2, 2), dtype)
+    mod_blocks = model_f.reshape(n_fb, f_per * nb, 2, 2)
+    for c0 in range(0, n_int, chunk):
+        c1 = min(n_int, c0 + chunk)
+        fb = np.arange(c0, c1) % n_fb
+        mod = mod_blocks[fb].reshape(c1 - c0, ns, nb, 2, 2)
+        Gp = G[c0:c1][:, a1][:, None]                                                   # [c, 1, b, 2, 2]
+        Gq = G[c0:c1][:, a2][:, None]
+        v = Gp @ mod @ np.conj(np.swapaxes(Gq, -1, -2))
+        for j, i in enumerate(range(c0, c1)):
+            v[j] += complex_noise(rng_for(seed, 5, 2 + i), (ns, nb, 2, 2), sigma)
+        vis[c0 * rows:c1 * rows] = v.reshape(-1, 2, 2)
+        model[c0 * rows:c1 * rows] = mod.reshape(-1, 2, 2)
+    row_off = np.arange(n_int, dtype=np.int64) * rows
+    return Batch('jones', vis, model, a1, a2, row_off, np.full(n_int, ns, np.int32), np.full(n_int, nb, np.int32),
+                 np.zeros(n_int, np.int32), np.full(n_int, n_ant, np.int32),
+                 (np.arange(n_int) * n_ant).astype(np.int32), G.reshape(n_int * n_ant, 2, 2), 1,
+                 dict(sigma=sigma, n_t=n_t, n_fb=n_fb, n_src=n_src, dt_s=dt_s))
+
+
 def make_config(k: int, seed: int = SEED, small: bool = False):
     """Synthetic stand-ins for the five workloads (small=True: a reduced copy for CPU tests)."""
     if k == 1:
@@ -370,4 +439,8 @@ def make_config(k: int, seed: int = SEED, small: bool = False):
         if small:
             return make_uneven(seed, n_intervals=16, ant_choices=(4, 6, 8), t_max=4, f_max=4)
         return make_uneven(seed)
+    if k == 5:
+        if small:
+            return make_warm(seed, n_ant=16, n_t=48, n_chan=16)
+        return make_warm(seed)
     raise ValueError(f"unknown config {k}")
