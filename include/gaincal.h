@@ -239,6 +239,124 @@ int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row
  * iterations processed, and the path taken (GC_PATH_STREAM, GC_PATH_MOMENTS or GC_PATH_RESIDENT). */
 int gc_profile_detail(double* moment_pass_ms, int64_t* baseline_iterations, int32_t* path);
 
+/*
+ * chi^2 = sum |r|^2 per interval at the given 2x2 gains (eq. cal:DI:pol with the sample sums of
+ * Sect. 2.3), FP32 compensated sums, FP64 totals.  vis/model/gains device pointers, complex64 or
+ * complex128 per dtype; chi2_out [n_intervals] double (device).  Asynchronous on `stream`.
+ */
+int gc_chi2_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,
+                        int32_t dtype, double* chi2_out, void* stream);
+
+/* ---- learned warm start --------------------------------------------------------------------
+ * A small MLP (in -> h1 -> h2 -> out, ReLU on the hidden layers) proposes each interval's starting
+ * gains from the antenna's earlier solutions; the iteration then runs to the usual tolerance from
+ * that start, so the network only changes where the solver starts and a poor proposal costs
+ * iterations, never accuracy.  The paper has no counterpart; its Sect. sec:DI:smooth (gains do not
+ * vary arbitrarily in time and frequency) is what makes earlier solutions informative.
+ * Parameter buffer `params` (float, device): W1 [in][h1] | b1 [h1] | W2 [h1][h2] | b2 [h2] |
+ * W3 [h2][out] | b3 [out], row-major with y = x W + b.  grads, adam_m, adam_v: same size (training
+ * only); params_bf16: same count of bfloat16 (inference; rewritten from params by each inference).
+ * Supported shape: 48, 256, 256, 8 (GC_ERR_LIMIT otherwise).  Buffers are owned by the caller.
+ * Activations are row-major [n][width] floats (device).  All calls asynchronous on `stream`. */
+typedef struct gc_mlp {
+  int32_t in, h1, h2, out;
+  float* params;
+  float* grads;
+  float* adam_m;
+  float* adam_v;
+  void* params_bf16;
+} gc_mlp;
+/* floats of work buffer the FP32 forward / gradient / training calls need for n rows */
+size_t gc_mlp_work_floats(const gc_mlp* net, int32_t n);
+/* FP32 forward: y [n][out] */
+int gc_mlp_forward_f32(const gc_mlp* net, const float* x, int32_t n, float* y, float* work, void* stream);
+/* FP32 gradient of the mean squared error mean((y - t)^2) over n x out: grads (like params), loss
+ * (one float, device) */
+int gc_mlp_grad_f32(const gc_mlp* net, const float* x, const float* t, int32_t n, float* grads, float* loss,
+                    float* work, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected at `step` >= 1) on that gradient */
+int gc_mlp_train_step(gc_mlp* net, const float* x, const float* t, int32_t n, float lr, int32_t step, float* loss,
+                      float* work, void* stream);
+/* BF16 inference (weights converted from params, activations rounded to bfloat16, FP32 sums) */
+int gc_mlp_infer_bf16(const gc_mlp* net, const float* x, int32_t n, float* y, void* stream);
+/* Network inputs per (interval, antenna) row: hist [n][hist_stride >= 32] holds the antenna's 4
+ * previous 2x2 gains newest first (each row-major (re, im) pairs); jhd/jhj [n][8] the 2x2 blocks
+ * C = sum D Y^H and H = sum Y Y^H (as gc_jhj_jhr_di_jones2x2 writes them) at the newest of them
+ * on the target interval; lead [n] the scaled lead time.  With phi = arg of the newest gain's xx
+ * element: x [n][in_width >= 41] = e^{-i phi} [g1 | g1-g2 | g2-g3 | g3-g4 | C H^-1 - g1] | lead |
+ * zeros (the C H^-1 entries are zero where H is singular), rot [n][2] = (cos phi, sin phi). */
+int gc_ws_features_jones(const float* hist, int32_t hist_stride, const float* jhd, const float* jhj, const float* lead,
+                         int32_t n, int32_t in_width, float* x, float* rot, void* stream);
+/* Training target [n][8] = e^{-i phi} (g_next - g1), the network output that would propose g_next. */
+int gc_ws_target_jones(const float* g1, const float* g_next, const float* rot, int32_t n, float* target,
+                       void* stream);
+
+/* Inputs of a warm-started solve. */
+typedef struct gc_warm {
+  const float* solutions;  /* device: earlier 2x2 solutions, [n_solutions][8] floats */
+  int64_t n_solutions;     /* gain slots in `solutions` */
+  const int32_t* hist_off; /* host [n_intervals][4]: slot in `solutions` of antenna 0 of each of the
+                              interval's 4 previous solutions, newest first (n_ant[i] consecutive
+                              slots each; GC_ERR_ARG if any lies outside [0, n_solutions)) */
+  const float* lead;       /* host [n_intervals]: scaled lead time, a network input */
+  const gc_mlp* net;       /* trained network, or NULL: the start is then the newest previous solution */
+  int32_t* used_out;       /* optional, device [n_intervals]: 1 where the proposal was taken */
+  double* dchi2_out;       /* optional, device [n_intervals]: chi^2(proposal) - chi^2(previous) */
+  float* start_out;        /* optional, device [n_gain][8]: the start the iteration took */
+} gc_warm;
+
+/*
+ * gc_calibrate_di_jones2x2 from a learned start.  Per interval, with g1 the newest previous
+ * solution: one pass over the interval's per-baseline moments gives C, H and chi^2 at g1; the
+ * network (BF16) proposes g1 + e^{i phi} delta from the features above; a second pass gives
+ * chi^2 at the proposal; the iteration starts from the proposal if its chi^2 is lower, else from
+ * g1, and runs exactly as gc_calibrate_di_jones2x2 does.  The chi^2 comparison drops the common
+ * term sum |d|^2 and sums the per-antenna terms tr(G H G^H) - 2 Re tr(C G^H) in FP64.
+ * Complex64 device buffers only (opt->dtype GC_DTYPE_C64, host_buffers 0, path AUTO or MOMENTS,
+ * else GC_ERR_DTYPE / GC_ERR_ARG).  The initial content of `gains` is ignored; on return it holds
+ * the solutions.  Returns like gc_calibrate_di_jones2x2.
+ */
+int gc_calibrate_di_jones2x2_warm(const void* vis, const void* model, const gc_layout* layout, const gc_warm* warm,
+                                  void* gains, const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                                  int32_t* status_out, void* stream);
+
+/* A time-major grid of intervals solved as a wavefront with learned starts. */
+typedef struct gc_wavefront {
+  int32_t n_t, n_fb;     /* interval i = t * n_fb + f, t < n_t, f < n_fb; n_t * n_fb = n_intervals, and
+                            every interval of block f has the antennas of interval f (GC_ERR_LAYOUT) */
+  int32_t lag;           /* wave length L in time steps (>= 1) */
+  float lead_scale;      /* network input lead = (t - newest history time) / lead_scale (> 0) */
+  double gate_tol;       /* a wave joins once every interval of its history stopped or took a relative
+                            step <= gate_tol (gate_tol <= tol: only finished histories) */
+  const gc_mlp* net;     /* trained network, or NULL: the start is the newest previous solution */
+  int32_t* used_out;     /* optional, device [n_intervals]: 1 where the proposal was taken */
+  int32_t* wave_k_out;   /* optional, host [ceil(n_t / lag)]: the global iteration after which each
+                            wave joined (0 for the first) */
+} gc_wavefront;
+
+/*
+ * The whole grid in one iteration loop.  The times [wL, (w+1)L) form wave w.  Wave 0 starts from
+ * `gains`; wave w >= 1 starts as gc_calibrate_di_jones2x2_warm does, from the solutions at times
+ * wL-1 .. wL-4 (clamped at 0) of the same block f, each put in the canonical gauge, with lead
+ * t - (wL-1), and joins the running iteration as soon as all of those intervals have finished or
+ * taken a step below gate_tol.  Every interval iterates to opt->tol with its own iteration count
+ * (iters_out counts from its first iteration; the GN / average alternation restarts with it).
+ * On return `gains` holds the solutions in the canonical gauge (see gc_gauge_fix_di).
+ * Complex64 device buffers only, as gc_calibrate_di_jones2x2_warm.  Returns the number of
+ * intervals not converged, or GC_ERR_LIMIT if the loop bound (waves x max_iter iterations) ran out.
+ */
+int gc_calibrate_di_jones2x2_wavefront(const void* vis, const void* model, const gc_layout* layout,
+                                       const gc_wavefront* wf, void* gains, const gc_options* opt, int32_t* iters_out,
+                                       double* chi2_out, int32_t* status_out, void* stream);
+
+/*
+ * Canonical gauge (Sect. 2.1: chi^2 is unchanged by one phase on all antennas): each interval's
+ * gains (device, kind 0 scalar or 1 2x2, dtype C64/C128) are rotated in place so that sum_p g_p
+ * (scalar) or sum_p tr(G_p) (2x2) is real and non-negative; left as they are where that sum is 0.
+ * Synchronous.
+ */
+int gc_gauge_fix_di(int32_t kind, void* gains, const gc_layout* layout, int32_t dtype, void* stream);
+
 /* Text for a GC_ERR_* return code or a GC_ST_* status. */
 const char* gc_error_string(int code);
 const char* gc_status_string(int status);

@@ -24,6 +24,9 @@ GC_MAX_ANT, GC_MAX_DIR = 1024, 10
 EXPORTS = [
     'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones',
     'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2', 'gc_jhj_jhr_di_jones2x2_noalloc',
+    'gc_chi2_di_jones2x2', 'gc_mlp_work_floats', 'gc_mlp_forward_f32', 'gc_mlp_grad_f32', 'gc_mlp_train_step',
+    'gc_mlp_infer_bf16', 'gc_ws_features_jones', 'gc_ws_target_jones', 'gc_calibrate_di_jones2x2_warm',
+    'gc_calibrate_di_jones2x2_wavefront', 'gc_gauge_fix_di',
     'gc_autotune_di', 'gc_profile_last', 'gc_profile_detail', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
 ]
 
@@ -43,6 +46,24 @@ class GcOptions(C.Structure):
     _fields_ = [('tol', C.c_double), ('max_iter', C.c_int32), ('schedule', C.c_int32), ('dtype', C.c_int32),
                 ('host_buffers', C.c_int32), ('compute_chi2', C.c_int32), ('profile', C.c_int32),
                 ('path', C.c_int32), ('reserved', C.c_int32)]
+
+
+class GcMlp(C.Structure):
+    _fields_ = [('in_', C.c_int32), ('h1', C.c_int32), ('h2', C.c_int32), ('out', C.c_int32),
+                ('params', C.c_void_p), ('grads', C.c_void_p), ('adam_m', C.c_void_p), ('adam_v', C.c_void_p),
+                ('params_bf16', C.c_void_p)]
+
+
+class GcWarm(C.Structure):
+    _fields_ = [('solutions', C.c_void_p), ('n_solutions', C.c_int64), ('hist_off', _i32p),
+                ('lead', C.POINTER(C.c_float)), ('net', C.POINTER(GcMlp)), ('used_out', C.c_void_p),
+                ('dchi2_out', C.c_void_p), ('start_out', C.c_void_p)]
+
+
+class GcWavefront(C.Structure):
+    _fields_ = [('n_t', C.c_int32), ('n_fb', C.c_int32), ('lag', C.c_int32), ('lead_scale', C.c_float),
+                ('gate_tol', C.c_double), ('net', C.POINTER(GcMlp)), ('used_out', C.c_void_p),
+                ('wave_k_out', _i32p)]
 
 
 _lib = None
@@ -75,6 +96,31 @@ def lib() -> C.CDLL:
         L.gc_launch_count.restype = C.c_int64
         L.gc_profile_last.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.gc_profile_last.restype = C.c_int
+        L.gc_chi2_di_jones2x2.argtypes = [_p, _p, C.POINTER(GcLayout), _p, C.c_int32, _p, _p]
+        L.gc_chi2_di_jones2x2.restype = C.c_int
+        mlpp = C.POINTER(GcMlp)
+        L.gc_mlp_work_floats.argtypes = [mlpp, C.c_int32]
+        L.gc_mlp_work_floats.restype = C.c_size_t
+        L.gc_mlp_forward_f32.argtypes = [mlpp, _p, C.c_int32, _p, _p, _p]
+        L.gc_mlp_forward_f32.restype = C.c_int
+        L.gc_mlp_grad_f32.argtypes = [mlpp, _p, _p, C.c_int32, _p, _p, _p, _p]
+        L.gc_mlp_grad_f32.restype = C.c_int
+        L.gc_mlp_train_step.argtypes = [mlpp, _p, _p, C.c_int32, C.c_float, C.c_int32, _p, _p, _p]
+        L.gc_mlp_train_step.restype = C.c_int
+        L.gc_mlp_infer_bf16.argtypes = [mlpp, _p, C.c_int32, _p, _p]
+        L.gc_mlp_infer_bf16.restype = C.c_int
+        L.gc_ws_features_jones.argtypes = [_p, C.c_int32, _p, _p, _p, C.c_int32, C.c_int32, _p, _p, _p]
+        L.gc_ws_features_jones.restype = C.c_int
+        L.gc_ws_target_jones.argtypes = [_p, _p, _p, C.c_int32, _p, _p]
+        L.gc_ws_target_jones.restype = C.c_int
+        L.gc_calibrate_di_jones2x2_warm.argtypes = [_p, _p, C.POINTER(GcLayout), C.POINTER(GcWarm), _p,
+                                                    C.POINTER(GcOptions), _p, _p, _p, _p]
+        L.gc_calibrate_di_jones2x2_warm.restype = C.c_int
+        L.gc_calibrate_di_jones2x2_wavefront.argtypes = [_p, _p, C.POINTER(GcLayout), C.POINTER(GcWavefront), _p,
+                                                         C.POINTER(GcOptions), _p, _p, _p, _p]
+        L.gc_calibrate_di_jones2x2_wavefront.restype = C.c_int
+        L.gc_gauge_fix_di.argtypes = [C.c_int32, _p, C.POINTER(GcLayout), C.c_int32, _p]
+        L.gc_gauge_fix_di.restype = C.c_int
         L.gc_autotune_di.argtypes = [C.c_int32, _p, _p, C.POINTER(GcLayout), _p, C.c_int32, C.c_int32,
                                      C.POINTER(C.c_double), _p]
         L.gc_autotune_di.restype = C.c_int

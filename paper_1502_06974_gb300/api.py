@@ -175,6 +175,188 @@ def autotune_di(vis, model, layout, gains, iters=24):
     return best.value
 
 
+# ----------------------------------------------------------------------------- learned warm start
+
+MLP_DIMS = (48, 256, 256, 8)
+
+
+class Mlp:
+    """Device buffers of the warm-start network (gc_mlp): FP32 params, gradients, Adam moments and
+    the BF16 copy used by inference.  ``params`` is a flat float32 vector (layout in gaincal.h)."""
+
+    def __init__(self, params, device, dims=MLP_DIMS):
+        params = np.ascontiguousarray(params, np.float32)
+        self.dims = tuple(int(d) for d in dims)
+        self.params = torch.from_numpy(params).to(device)
+        self.grads = torch.zeros_like(self.params)
+        self.adam_m = torch.zeros_like(self.params)
+        self.adam_v = torch.zeros_like(self.params)
+        self.params_bf16 = torch.zeros(self.params.numel(), dtype=torch.bfloat16, device=device)
+        self.step = 0
+        i, h1, h2, o = self.dims
+        self._c = N.GcMlp(i, h1, h2, o, self.params.data_ptr(), self.grads.data_ptr(), self.adam_m.data_ptr(),
+                          self.adam_v.data_ptr(), self.params_bf16.data_ptr())
+
+    def c(self):
+        return C.byref(self._c)
+
+    def work(self, n):
+        return torch.empty(int(N.lib().gc_mlp_work_floats(self.c(), int(n))), dtype=torch.float32,
+                           device=self.params.device)
+
+
+def _f32(t, name):
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+
+
+def mlp_forward_f32(net: Mlp, x):
+    _f32(x, 'x')
+    n = x.shape[0]
+    y = torch.empty((n, net.dims[3]), dtype=torch.float32, device=x.device)
+    N.check(N.lib().gc_mlp_forward_f32(net.c(), _ptr(x), n, _ptr(y), _ptr(net.work(n)), _stream_ptr(x.device)),
+            'gc_mlp_forward_f32')
+    return y
+
+
+def mlp_grad_f32(net: Mlp, x, t):
+    """(gradient like params, loss) of mean((y - t)^2)."""
+    _f32(x, 'x'); _f32(t, 't')
+    n = x.shape[0]
+    g = torch.empty_like(net.params)
+    loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+    N.check(N.lib().gc_mlp_grad_f32(net.c(), _ptr(x), _ptr(t), n, _ptr(g), _ptr(loss), _ptr(net.work(n)),
+                                    _stream_ptr(x.device)), 'gc_mlp_grad_f32')
+    return g, loss
+
+
+def mlp_train_step(net: Mlp, x, t, lr, work=None, loss=None):
+    """One Adam step; returns the device loss tensor (before the step)."""
+    _f32(x, 'x'); _f32(t, 't')
+    n = x.shape[0]
+    net.step += 1
+    loss = torch.zeros(1, dtype=torch.float32, device=x.device) if loss is None else loss
+    work = net.work(n) if work is None else work
+    N.check(N.lib().gc_mlp_train_step(net.c(), _ptr(x), _ptr(t), n, float(lr), net.step, _ptr(loss), _ptr(work),
+                                      _stream_ptr(x.device)), 'gc_mlp_train_step')
+    return loss
+
+
+def mlp_infer_bf16(net: Mlp, x):
+    _f32(x, 'x')
+    n = x.shape[0]
+    y = torch.empty((n, net.dims[3]), dtype=torch.float32, device=x.device)
+    N.check(N.lib().gc_mlp_infer_bf16(net.c(), _ptr(x), n, _ptr(y), _stream_ptr(x.device)), 'gc_mlp_infer_bf16')
+    return y
+
+
+def _as_f32_view(g):
+    """complex64 [n, 2, 2] -> float32 [n, 8] view (no copy)."""
+    if g.dtype == torch.complex64:
+        return torch.view_as_real(g).reshape(g.shape[0], -1)
+    return g
+
+
+def ws_features_jones(hist, jhd, jhj, lead, in_width=48):
+    """Features (x [n, in_width], rot [n, 2]) from hist [n, 4, 2, 2] c64, jhd/jhj [n, 2, 2] c64, lead [n] f32."""
+    h = torch.view_as_real(hist.contiguous()).reshape(hist.shape[0], 32)
+    n = h.shape[0]
+    x = torch.empty((n, in_width), dtype=torch.float32, device=h.device)
+    rot = torch.empty((n, 2), dtype=torch.float32, device=h.device)
+    N.check(N.lib().gc_ws_features_jones(_ptr(h), 32, _ptr(jhd.contiguous()), _ptr(jhj.contiguous()),
+                                         _ptr(lead.contiguous()), n, in_width, _ptr(x), _ptr(rot),
+                                         _stream_ptr(h.device)), 'gc_ws_features_jones')
+    return x, rot
+
+
+def ws_target_jones(g1, g_next, rot):
+    """Training targets [n, 8] = e^{-i phi} (g_next - g1) from c64 [n, 2, 2] gains and rot [n, 2]."""
+    n = g1.shape[0]
+    t = torch.empty((n, 8), dtype=torch.float32, device=g1.device)
+    N.check(N.lib().gc_ws_target_jones(_ptr(g1.contiguous()), _ptr(g_next.contiguous()), _ptr(rot), n, _ptr(t),
+                                       _stream_ptr(g1.device)), 'gc_ws_target_jones')
+    return t
+
+
+def calibrate_di_jones2x2_warm(vis, model, layout: Layout, solutions, hist_off, lead, net, gains, tol=1e-6,
+                               max_iter=1000, schedule=N.GC_SCHED_STEFCAL, compute_chi2=False, profile=False,
+                               want_start=False):
+    """gc_calibrate_di_jones2x2_warm: solve from the learned start (net=None: previous solution).
+
+    solutions: complex64 device [n_sol, 2, 2]; hist_off: host int32 [n_int, 4]; lead: host float32 [n_int].
+    Returns (gains, iters, chi2 or None, status, used, dchi2, start or None).
+    """
+    for t, nm in ((vis, 'vis'), (model, 'model'), (gains, 'gains'), (solutions, 'solutions')):
+        _check_tensor(t, nm, False)
+        if t.dtype != torch.complex64:
+            raise TypeError(f"{nm} must be complex64")
+    hist_off = np.ascontiguousarray(hist_off, np.int32)
+    lead = np.ascontiguousarray(lead, np.float32)
+    n = layout.n_intervals
+    if hist_off.shape != (n, 4) or lead.shape != (n,):
+        raise ValueError("hist_off must be [n_intervals, 4] and lead [n_intervals]")
+    dev = vis.device
+    iters = torch.zeros(n, dtype=torch.int32, device=dev)
+    status = torch.zeros(n, dtype=torch.int32, device=dev)
+    used = torch.zeros(n, dtype=torch.int32, device=dev)
+    dchi2 = torch.zeros(n, dtype=torch.float64, device=dev)
+    chi2 = torch.zeros(n, dtype=torch.float64, device=dev) if compute_chi2 else None
+    start = torch.empty_like(gains) if want_start else None
+    w = N.GcWarm(solutions.data_ptr(), int(solutions.shape[0]), hist_off.ctypes.data_as(C.POINTER(C.c_int32)),
+                 lead.ctypes.data_as(C.POINTER(C.c_float)), C.pointer(net._c) if net is not None else None,
+                 used.data_ptr(), dchi2.data_ptr(), start.data_ptr() if start is not None else None)
+    opt = N.GcOptions(float(tol), int(max_iter), int(schedule), N.GC_DTYPE_C64, 0, 1 if compute_chi2 else 0,
+                      1 if profile else 0, N.GC_PATH_AUTO)
+    lay = layout.c()
+    rc = N.lib().gc_calibrate_di_jones2x2_warm(_ptr(vis), _ptr(model), C.byref(lay), C.byref(w), _ptr(gains),
+                                               C.byref(opt), _ptr(iters), _ptr(chi2), _ptr(status), _stream_ptr(dev))
+    N.check(rc, 'gc_calibrate_di_jones2x2_warm')
+    return gains, iters, chi2, status, used, dchi2, start
+
+
+def calibrate_di_jones2x2_wavefront(vis, model, layout: Layout, n_t, n_fb, lag, net, gains, tol=1e-6, max_iter=1000,
+                                    gate_tol=1e-4, lead_scale=32.0, schedule=N.GC_SCHED_STEFCAL, compute_chi2=False):
+    """gc_calibrate_di_jones2x2_wavefront: the whole time-major grid in one iteration loop, waves of
+    `lag` times joining with learned starts (net=None: previous solution).  gains: the first wave's
+    start on input, the canonical-gauge solutions on return.
+
+    Returns (gains, iters, chi2 or None, status, used, wave_k [n_waves] host int32).
+    """
+    for t, nm in ((vis, 'vis'), (model, 'model'), (gains, 'gains')):
+        _check_tensor(t, nm, False)
+        if t.dtype != torch.complex64:
+            raise TypeError(f"{nm} must be complex64")
+    n = layout.n_intervals
+    dev = vis.device
+    iters = torch.zeros(n, dtype=torch.int32, device=dev)
+    status = torch.zeros(n, dtype=torch.int32, device=dev)
+    used = torch.zeros(n, dtype=torch.int32, device=dev)
+    chi2 = torch.zeros(n, dtype=torch.float64, device=dev) if compute_chi2 else None
+    n_waves = (int(n_t) + int(lag) - 1) // int(lag)
+    wave_k = np.zeros(max(n_waves, 1), np.int32)
+    wf = N.GcWavefront(int(n_t), int(n_fb), int(lag), float(lead_scale), float(gate_tol),
+                       C.pointer(net._c) if net is not None else None, used.data_ptr(),
+                       wave_k.ctypes.data_as(C.POINTER(C.c_int32)))
+    opt = N.GcOptions(float(tol), int(max_iter), int(schedule), N.GC_DTYPE_C64, 0, 1 if compute_chi2 else 0, 0,
+                      N.GC_PATH_AUTO)
+    lay = layout.c()
+    rc = N.lib().gc_calibrate_di_jones2x2_wavefront(_ptr(vis), _ptr(model), C.byref(lay), C.byref(wf), _ptr(gains),
+                                                    C.byref(opt), _ptr(iters), _ptr(chi2), _ptr(status),
+                                                    _stream_ptr(dev))
+    N.check(rc, 'gc_calibrate_di_jones2x2_wavefront')
+    return gains, iters, chi2, status, used, wave_k[:n_waves]
+
+
+def gauge_fix_di(gains, layout: Layout):
+    """Canonical gauge in place (gc_gauge_fix_di); gains [n_gain] (scalar) or [n_gain, 2, 2]."""
+    _check_tensor(gains, 'gains', False)
+    kind = 1 if gains.dim() == 3 else 0
+    lay = layout.c()
+    N.check(N.lib().gc_gauge_fix_di(kind, _ptr(gains), C.byref(lay), _dtype_code(gains), _stream_ptr(gains.device)),
+            'gc_gauge_fix_di')
+    return gains
+
+
 def profile_last():
     """(iteration-kernel ms, iteration launches, row-iterations) of the last profiled calibrate call."""
     ms = C.c_double(0.0); n = C.c_int64(0); ri = C.c_int64(0)

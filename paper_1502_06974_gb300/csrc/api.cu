@@ -543,8 +543,96 @@ struct Staged {
   void* gains;
 };
 
+// Learned start for the intervals [i_lo, i_lo + n) (moment path, 2x2; the moments, the accumulate
+// scratch and the init launch are in place, `a` holds the plan's pointers):
+//   g1 = newest previous solution (from `sol` at the slots hoff [n][4], each put in the canonical
+//   gauge first when canon != 0); tot, e1 = per-antenna sums and chi^2 - sum|d|^2 at g1 (one
+//   accumulate launch over the range's moments); features -> BF16 MLP -> proposal; e2 at the
+//   proposal; start = proposal where e2 < e1, else g1.  Without a network the start is g1.
+//   The range's gains (and their per-antenna auxiliaries) end up holding the start.
+static int warm_range(const gc_layout* L, DIPlan* P, DIArgs a, const float* sol, const int32_t* hoff,
+                      const float* lead, const gc_mlp* net, int canon, int i_lo, int n, const int32_t* first_item_h,
+                      float* gains, int32_t* used_out, double* dchi2_out, float* start_out, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n <= 0) return GC_OK;
+  const int64_t gbase = L->gain_off[i_lo];
+  int64_t ng = 0;
+  for (int i = i_lo; i < i_lo + n; ++i) ng = std::max<int64_t>(ng, (int64_t)L->gain_off[i] + L->n_ant[i] - gbase);
+  void *meta = nullptr, *fb = nullptr, *eb = nullptr;
+  int rc;
+  if ((rc = ws_get("warm_meta", (size_t)n * 5 * sizeof(int32_t), &meta))) return rc;
+  if ((rc = ws_get("warm_f", (size_t)(ng > 0 ? ng : 1) * (32 + 8 + 1 + 48 + 2 + 8 + 12) * sizeof(float), &fb)))
+    return rc;
+  if ((rc = ws_get("warm_e", (size_t)n * 2 * sizeof(double), &eb))) return rc;
+  int32_t* d_hoff = (int32_t*)meta;
+  float* d_lead = (float*)(d_hoff + 4 * (size_t)n);
+  float* hbuf = (float*)fb;
+  float* g1 = hbuf + ng * 32;
+  float* lead_row = g1 + ng * 8;
+  float* x = lead_row + ng;
+  float* rot = x + ng * 48;
+  float* delta = rot + ng * 2;
+  float* tot = delta + ng * 8;
+  double* e1 = (double*)eb;
+  double* e2 = e1 + n;
+  float* gr = gains + gbase * 8;  // the range's gain slots
+  GC_CUDA(cudaMemcpyAsync(d_hoff, hoff, (size_t)n * 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  GC_CUDA(cudaMemcpyAsync(d_lead, lead, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s));
+  GC_CUDA_I(ws_gather(sol, d_hoff, d_lead, a.gain_off, a.n_ant, i_lo, n, gbase, canon, hbuf, g1, lead_row, stream));
+  GC_CUDA(cudaMemcpyAsync(gr, g1, (size_t)ng * 8 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  g_launches++;
+  if (!net) {
+    if (used_out) GC_CUDA(cudaMemsetAsync(used_out + i_lo, 0, (size_t)n * sizeof(int32_t), s));
+    if (dchi2_out) GC_CUDA(cudaMemsetAsync(dchi2_out + i_lo, 0, (size_t)n * sizeof(double), s));
+  } else {
+    const Tune& tn = P->tune;
+    DIArgs b = a;
+    b.gains = gains;
+    b.xbegin = first_item_h[i_lo];
+    b.xcount = (i_lo + n < P->n_int ? first_item_h[i_lo + n] : P->n_items) - b.xbegin;
+    GC_CUDA_I(di_launch_maux(1, gr, a.aux + gbase * 4, (int)ng, stream));
+    if (b.xcount > 0) GC_CUDA_I(di_launch_macc(1, b, P->grid, P->smem, tn.red_chunks, tn.prefetch, stream));
+    GC_CUDA_I(di_launch_msum(1, b, i_lo, n, tot, e1, stream));
+    GC_CUDA_I(ws_features_packed(hbuf, tot, lead_row, (int)ng, x, rot, stream));
+    if ((rc = mlp_infer(net, x, (int)ng, delta, stream))) return rc;
+    GC_CUDA_I(ws_propose(hbuf, delta, rot, (int)ng, gr, stream));
+    GC_CUDA_I(di_launch_maux(1, gr, a.aux + gbase * 4, (int)ng, stream));
+    if (b.xcount > 0) GC_CUDA_I(di_launch_macc(1, b, P->grid, P->smem, tn.red_chunks, tn.prefetch, stream));
+    GC_CUDA_I(di_launch_msum(1, b, i_lo, n, tot, e2, stream));
+    GC_CUDA_I(ws_choose(g1, e1, e2, a.gain_off, a.n_ant, i_lo, n, gbase, gains, used_out, dchi2_out, stream));
+    g_launches += 9;
+  }
+  GC_CUDA_I(di_launch_maux(1, gr, a.aux + gbase * 4, (int)ng, stream));
+  g_launches++;
+  if (start_out) GC_CUDA(cudaMemcpyAsync(start_out + gbase * 8, gr, (size_t)ng * 8 * sizeof(float),
+                                         cudaMemcpyDeviceToDevice, s));
+  return GC_OK;
+}
+
+static int first_items_host(DIPlan* P, std::vector<int32_t>& out, cudaStream_t s) {
+  out.resize(P->n_int);
+  GC_CUDA(cudaMemcpyAsync(out.data(), P->args.first_item, (size_t)P->n_int * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  GC_CUDA(cudaStreamSynchronize(s));
+  return GC_OK;
+}
+
+// Learned warm start before the iteration of a whole batch (gc_calibrate_di_jones2x2_warm).
+static int warm_prephase(const gc_warm* w, const gc_layout* L, DIPlan* P, DIArgs a, float* gains, void* stream) {
+  std::vector<int32_t> fi;
+  int rc = first_items_host(P, fi, (cudaStream_t)stream);
+  if (rc) return rc;
+  if ((rc = warm_range(L, P, a, w->solutions, w->hist_off, w->lead, w->net, 0, 0, P->n_int, fi.data(), gains,
+                       w->used_out, w->dchi2_out, w->start_out, stream)))
+    return rc;
+  // the range's accumulate launches used fixed item ranges; reset the per-call state all the same
+  GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
+  g_launches++;
+  return GC_OK;
+}
+
 static int run_di(int kind, const void* vis, const void* model, const gc_layout* L, void* gains,
-                  const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out, void* stream) {
+                  const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out, void* stream,
+                  const gc_warm* warm = nullptr) {
   if (!opt || !L) return GC_ERR_ARG;
   if (opt->dtype != GC_DTYPE_C64 && opt->dtype != GC_DTYPE_C128) return GC_ERR_DTYPE;
   if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
@@ -631,6 +719,7 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     if ((rc = ws_get("di_gnew", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 8 * sizeof(float), &gnew))) return rc;
     a.aux = (float*)aux;
     a.gnew = (float*)gnew;
+    if (warm && (rc = warm_prephase(warm, L, P, a, (float*)st.gains, stream))) return rc;
     GC_CUDA_I(di_launch_maux(kind, (const float*)st.gains, a.aux, L->n_gain, stream));
     g_launches += 2;
     if (opt->profile) {
@@ -661,6 +750,7 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     // max_iter find no active interval and do nothing.
     DIArgs ga = a;
     ga.k = 0;
+    if (mode == 1) ga.vis = ga.model = nullptr;  // the moment-space iterations never read the rows
     if (!P->gexec || P->gS != S || memcmp(&P->gargs, &ga, sizeof(DIArgs)) != 0) {
       if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
       cudaStream_t cs = nullptr;
@@ -741,6 +831,183 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   return bad;
 }
 
+static int32_t* g_pinned_ints = nullptr;
+static size_t g_pinned_ints_n = 0;
+
+static int pinned_ints(size_t n, int32_t** out) {
+  if (g_pinned_ints_n < n) {
+    if (g_pinned_ints) cudaFreeHost(g_pinned_ints);
+    g_pinned_ints = nullptr;
+    g_pinned_ints_n = 0;
+    GC_CUDA(cudaHostAlloc((void**)&g_pinned_ints, n * sizeof(int32_t), cudaHostAllocDefault));
+    g_pinned_ints_n = n;
+  }
+  *out = g_pinned_ints;
+  return GC_OK;
+}
+
+// Wavefront solve of a time-major grid of 2x2 intervals with learned starts (one iteration loop;
+// waves join it as soon as their history has passed the gate).
+static int run_wavefront(const void* vis, const void* model, const gc_layout* L, const gc_wavefront* wf, void* gains,
+                         const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out,
+                         void* stream) {
+  if (!wf || !opt || !L) return GC_ERR_ARG;
+  if (opt->dtype != GC_DTYPE_C64) return GC_ERR_DTYPE;
+  if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
+    return GC_ERR_ARG;
+  if (opt->host_buffers != 0 || opt->reserved || (opt->path != GC_PATH_AUTO && opt->path != GC_PATH_MOMENTS))
+    return GC_ERR_ARG;
+  if (wf->n_t < 1 || wf->n_fb < 1 || wf->lag < 1 || !(wf->lead_scale > 0.f) || !(wf->gate_tol >= 0.0))
+    return GC_ERR_ARG;
+  int rc = validate_layout(L, 1);
+  if (rc != GC_OK) return rc;
+  if ((int64_t)wf->n_t * wf->n_fb != L->n_intervals) return GC_ERR_LAYOUT;
+  for (int i = wf->n_fb; i < L->n_intervals; ++i)
+    if (L->n_ant[i] != L->n_ant[i % wf->n_fb]) return GC_ERR_LAYOUT;  // a history slot must hold the same antennas
+  if (wf->net && (rc = mlp_check(wf->net))) return rc;
+  if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && !gains)) return GC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DIPlan* P = nullptr;
+  if ((rc = get_di_plan(1, 1, GC_DTYPE_C64, 0, L, &P, stream))) return rc;
+  const int n_int = P->n_int, nfb = wf->n_fb, lag = wf->lag;
+  DIArgs a = P->args;
+  a.vis = vis;
+  a.model = model;
+  a.gains = gains;
+  a.tol = opt->tol;
+  a.max_iter = opt->max_iter;
+  a.schedule = opt->schedule;
+  void *scr = nullptr, *mom = nullptr, *aux = nullptr, *gnew = nullptr, *st = nullptr;
+  if (P->scr_elems > 0) {
+    if ((rc = ws_get("di_scratch", (size_t)P->scr_elems * 4, &scr))) return rc;
+    a.scratch = scr;
+  }
+  if ((rc = ws_get("di_moments", (size_t)(P->n_mom_bl > 0 ? P->n_mom_bl : 1) * 48 * sizeof(float), &mom))) return rc;
+  if ((rc = ws_get("di_aux", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 4 * sizeof(float), &aux))) return rc;
+  if ((rc = ws_get("di_gnew", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 8 * sizeof(float), &gnew))) return rc;
+  if ((rc = ws_get("wf_state", (size_t)n_int * 2 * sizeof(int32_t), &st))) return rc;
+  a.moments = (const float*)mom;
+  a.aux = (float*)aux;
+  a.gnew = (float*)gnew;
+  a.k0 = (int32_t*)st;
+  a.gate = a.k0 + n_int;
+  a.gate_tol = wf->gate_tol;
+  float* g = (float*)gains;
+  GC_CUDA_I(di_launch_init(a, n_int, P->n_active0, stream));
+  GC_CUDA_I(moment_pass(1, (const float*)vis, (const float*)model, (float*)mom, a.row_off, a.mom_off, a.n_samp,
+                        a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, stream));
+  const int n_waves = (wf->n_t + lag - 1) / lag;
+  auto wave_lo = [&](int w) { return std::min(w * lag, wf->n_t) * nfb; };
+  int n0_active = 0;
+  for (int i = 0; i < wave_lo(1); ++i) n0_active += (int64_t)L->n_samp[i] * L->n_bl[i] > 0;
+  GC_CUDA_I(di_launch_wf_hold(a, n_int, wave_lo(1), n0_active, stream));
+  GC_CUDA_I(di_launch_maux(1, g, a.aux, L->n_gain, stream));
+  g_launches += 4;
+  if (wf->used_out) GC_CUDA(cudaMemsetAsync(wf->used_out, 0, (size_t)n_int * sizeof(int32_t), s));
+  std::vector<int32_t> fi;
+  if ((rc = first_items_host(P, fi, s))) return rc;
+  // the iteration segment: S iterations and the advance of *kbase, captured once per argument set
+  const Tune& tn = P->tune;
+  const int S = tn.check_every;
+  {
+    DIArgs ga = a;
+    ga.k = 0;
+    ga.vis = ga.model = nullptr;
+    if (!P->gexec || P->gS != S || memcmp(&P->gargs, &ga, sizeof(DIArgs)) != 0) {
+      if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+      cudaStream_t cs = nullptr;
+      GC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      GC_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      int crc = 0;
+      for (int j = 1; j <= S && !crc; ++j) {
+        DIArgs x = ga;
+        x.k = j;
+        crc = di_launch_mstep(1, x, P->grid, P->smem, n_int, tn.red_chunks, tn.prefetch, cs);
+      }
+      if (!crc) crc = di_launch_advance(a.kbase, S, cs);
+      cudaGraph_t gr = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(cs, &gr);
+      cudaStreamDestroy(cs);
+      if (crc) return cuda_fail((cudaError_t)crc, "capture of the iteration segment");
+      if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+      const cudaError_t ie = cudaGraphInstantiate(&P->gexec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+      P->gargs = ga;
+      P->gS = S;
+    }
+  }
+  const int gate_n = std::min(4, lag) * nfb + 4 * nfb;  // upper bound of a gate range's intervals
+  int32_t* hb = nullptr;
+  if ((rc = pinned_ints((size_t)(2 + 2 * gate_n), &hb))) return rc;
+  std::vector<int32_t> hoff;
+  std::vector<float> lead;
+  int next = 1, kb = 0;
+  const int64_t max_segments = (int64_t)n_waves * (opt->max_iter / S + 2) + 16;
+  for (int64_t seg = 0; seg < max_segments; ++seg) {
+    GC_CUDA(cudaGraphLaunch(P->gexec, s));
+    g_launches += (int64_t)S * 2 + 1;
+    kb += S;
+    int g_lo = 0, g_n = 0;
+    if (next < n_waves) {
+      const int t1 = next * lag, t0 = std::max(0, t1 - 4);
+      g_lo = t0 * nfb;
+      g_n = (t1 - t0) * nfb;
+    }
+    GC_CUDA(cudaMemcpyAsync(hb, a.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (g_n > 0) {
+      GC_CUDA(cudaMemcpyAsync(hb + 2, a.active + g_lo, (size_t)g_n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(hb + 2 + gate_n, a.gate + g_lo, (size_t)g_n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                              s));
+    }
+    GC_CUDA(cudaStreamSynchronize(s));
+    const int n_active = hb[0];
+    if (next < n_waves) {
+      bool ready = true;
+      for (int j = 0; j < g_n && ready; ++j) ready = hb[2 + j] == 0 || hb[2 + gate_n + j] > 0;
+      if (ready) {
+        const int i_lo = wave_lo(next), n = wave_lo(next + 1) - i_lo, tp = next * lag - 1;
+        hoff.resize((size_t)n * 4);
+        lead.resize(n);
+        for (int b = 0; b < n; ++b) {
+          const int i = i_lo + b, t = i / nfb, f = i % nfb;
+          for (int j = 0; j < 4; ++j) hoff[4 * b + j] = L->gain_off[std::max(0, tp - j) * nfb + f];
+          lead[b] = (float)(t - tp) / wf->lead_scale;
+        }
+        if ((rc = warm_range(L, P, a, g, hoff.data(), lead.data(), wf->net, 1, i_lo, n, fi.data(), g, wf->used_out,
+                             nullptr, nullptr, stream)))
+          return rc;
+        GC_CUDA_I(di_launch_wf_activate(a, i_lo, n, stream));
+        g_launches++;
+        if (wf->wave_k_out) wf->wave_k_out[next] = kb;
+        ++next;
+        continue;
+      }
+    }
+    if (n_active <= 0 && next >= n_waves) break;
+  }
+  if (wf->wave_k_out) wf->wave_k_out[0] = 0;
+  GC_CUDA_I(gauge_fix(1, GC_DTYPE_C64, gains, a.gain_off, a.n_ant, n_int, stream));
+  g_launches++;
+  if (opt->compute_chi2) {
+    GC_CUDA_I(moment_chi2(1, (const float*)vis, (const float*)model, g, a.row_off, a.n_samp, a.n_bl, a.bl_off,
+                          a.gain_off, a.ant1, a.ant2, P->mitem_int, P->mitem_tile, P->n_mitems, P->mfirst, P->mcount,
+                          P->mchi2, P->chi2_out, n_int, stream));
+    g_launches += 2;
+  }
+  if (iters_out) GC_CUDA(cudaMemcpyAsync(iters_out, a.iters, (size_t)n_int * 4, cudaMemcpyDeviceToDevice, s));
+  if (status_out) GC_CUDA(cudaMemcpyAsync(status_out, a.status, (size_t)n_int * 4, cudaMemcpyDeviceToDevice, s));
+  if (chi2_out && opt->compute_chi2)
+    GC_CUDA(cudaMemcpyAsync(chi2_out, P->chi2_out, (size_t)n_int * 8, cudaMemcpyDeviceToDevice, s));
+  std::vector<int32_t> stv(n_int);
+  GC_CUDA(cudaMemcpyAsync(stv.data(), a.status, (size_t)n_int * 4, cudaMemcpyDeviceToHost, s));
+  GC_CUDA(cudaStreamSynchronize(s));
+  int bad = 0;
+  for (int i = 0; i < n_int; ++i) bad += (stv[i] & 15) != GC_ST_OK;
+  if (next < n_waves) return GC_ERR_LIMIT;  // the segment bound ran out before every wave joined
+  return bad;
+}
+
 static int run_di_acc(int kind, const void* vis, const void* model, const gc_layout* L, const void* gains, int dtype,
                       void* jhd, void* jhj, void* stream) {
   if (!L) return GC_ERR_ARG;
@@ -771,6 +1038,26 @@ static int run_di_acc(int kind, const void* vis, const void* model, const gc_lay
   GC_CUDA(cudaMemsetAsync(jhj, 0, (size_t)L->n_gain * (kind == 0 ? eb / 2 : eb), (cudaStream_t)stream));
   GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
   GC_CUDA_I(di_launch_iter(kind, dtype, 1, a, P->grid, P->smem, stream));
+  g_launches += 2;
+  return GC_OK;
+}
+
+static int run_chi2(int kind, const void* vis, const void* model, const gc_layout* L, const void* gains, int dtype,
+                    double* chi2_out, void* stream) {
+  if (!L || !chi2_out) return GC_ERR_ARG;
+  if (dtype != GC_DTYPE_C64 && dtype != GC_DTYPE_C128) return GC_ERR_DTYPE;
+  int rc = validate_layout(L, 1);
+  if (rc != GC_OK) return rc;
+  if (L->n_intervals == 0) return GC_OK;
+  if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && !gains)) return GC_ERR_ARG;
+  DIPlan* P = nullptr;
+  if ((rc = get_di_plan(0, kind, dtype, 1, L, &P, stream))) return rc;
+  DIArgs a = P->args;
+  a.kbase = nullptr;
+  a.vis = vis;
+  a.model = model;
+  a.gains = const_cast<void*>(gains);
+  GC_CUDA_I(di_launch_chi2(kind, dtype, a, P->chi2_items, chi2_out, P->n_int, P->grid, stream));
   g_launches += 2;
   return GC_OK;
 }
@@ -857,6 +1144,52 @@ int gc_calibrate_di_jones2x2(const void* vis, const void* model, const gc_layout
   return run_di(1, vis, model, layout, gains, opt, iters_out, chi2_out, status_out, stream);
 }
 
+int gc_calibrate_di_jones2x2_warm(const void* vis, const void* model, const gc_layout* layout, const gc_warm* warm,
+                                  void* gains, const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                                  int32_t* status_out, void* stream) {
+  if (!warm || !opt || !layout || !warm->solutions || !warm->hist_off || !warm->lead || warm->n_solutions < 0)
+    return GC_ERR_ARG;
+  if (opt->dtype != GC_DTYPE_C64) return GC_ERR_DTYPE;
+  if (opt->host_buffers != 0 || (opt->path != GC_PATH_AUTO && opt->path != GC_PATH_MOMENTS)) return GC_ERR_ARG;
+  int rc = validate_layout(layout, 1);
+  if (rc != GC_OK) return rc;
+  for (int i = 0; i < layout->n_intervals; ++i)
+    for (int j = 0; j < 4; ++j) {
+      const int64_t o = warm->hist_off[4 * i + j];
+      if (o < 0 || o + layout->n_ant[i] > warm->n_solutions) return GC_ERR_ARG;
+    }
+  if (warm->net && (rc = mlp_check(warm->net))) return rc;
+  gc_options o2 = *opt;
+  o2.path = GC_PATH_MOMENTS;
+  return run_di(1, vis, model, layout, gains, &o2, iters_out, chi2_out, status_out, stream, warm);
+}
+
+int gc_calibrate_di_jones2x2_wavefront(const void* vis, const void* model, const gc_layout* layout,
+                                       const gc_wavefront* wf, void* gains, const gc_options* opt, int32_t* iters_out,
+                                       double* chi2_out, int32_t* status_out, void* stream) {
+  return run_wavefront(vis, model, layout, wf, gains, opt, iters_out, chi2_out, status_out, stream);
+}
+
+int gc_gauge_fix_di(int32_t kind, void* gains, const gc_layout* layout, int32_t dtype, void* stream) {
+  if (!layout || (kind != 0 && kind != 1)) return GC_ERR_ARG;
+  if (dtype != GC_DTYPE_C64 && dtype != GC_DTYPE_C128) return GC_ERR_DTYPE;
+  int rc = validate_layout(layout, 1);
+  if (rc != GC_OK) return rc;
+  const int n = layout->n_intervals;
+  if (n == 0 || layout->n_gain == 0) return GC_OK;
+  if (!gains) return GC_ERR_ARG;
+  void* dv = nullptr;
+  if ((rc = ws_get("gauge_meta", (size_t)n * 8, &dv))) return rc;
+  int32_t* d = (int32_t*)dv;
+  cudaStream_t s = (cudaStream_t)stream;
+  GC_CUDA(cudaMemcpyAsync(d, layout->gain_off, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  GC_CUDA(cudaMemcpyAsync(d + n, layout->n_ant, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  GC_CUDA_I(gauge_fix(kind, dtype, gains, d, d + n, n, stream));
+  g_launches++;
+  GC_CUDA(cudaStreamSynchronize(s));
+  return GC_OK;
+}
+
 int gc_jhj_jhr_di_scalar(const void* vis, const void* model, const gc_layout* layout, const void* gains, int32_t dtype,
                          void* jhd_out, void* jhj_out, void* stream) {
   return run_di_acc(0, vis, model, layout, gains, dtype, jhd_out, jhj_out, stream);
@@ -865,6 +1198,11 @@ int gc_jhj_jhr_di_scalar(const void* vis, const void* model, const gc_layout* la
 int gc_jhj_jhr_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,
                            int32_t dtype, void* jhd_out, void* jhj_out, void* stream) {
   return run_di_acc(1, vis, model, layout, gains, dtype, jhd_out, jhj_out, stream);
+}
+
+int gc_chi2_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,
+                        int32_t dtype, double* chi2_out, void* stream) {
+  return run_chi2(1, vis, model, layout, gains, dtype, chi2_out, stream);
 }
 
 int gc_autotune_di(int32_t kind, const void* vis, const void* model, const gc_layout* layout, void* gains,
@@ -923,12 +1261,14 @@ int gc_release(void) {
       for (auto& b : a)
         for (auto& c : b) {
           if (c.dev) cudaFree(c.dev);
+          if (c.gexec) cudaGraphExecDestroy(c.gexec);
           c = gc::DIPlan{};
         }
   gc::dd_release();
   gc::res_release();
   gc::g_tune.clear();
   if (gc::g_pinned_flag) { cudaFreeHost(gc::g_pinned_flag); gc::g_pinned_flag = nullptr; }
+  if (gc::g_pinned_ints) { cudaFreeHost(gc::g_pinned_ints); gc::g_pinned_ints = nullptr; gc::g_pinned_ints_n = 0; }
   return GC_OK;
 }
 

@@ -218,14 +218,16 @@ __global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const D
   const int tid = threadIdx.x;
   const int k = a.k + (a.kbase ? *a.kbase : 0);
   const int cur = k % 3;
+  const bool fixed = a.xcount > 0;
   const int* list = a.ilist + (size_t)cur * a.n_items;
-  const int n_list = a.icount[cur];
-  if (blockIdx.x == 0 && tid == 0) a.icount[(k + 2) % 3] = 0;
+  const int n_list = fixed ? a.xcount : a.icount[cur];
+  if (!fixed && blockIdx.x == 0 && tid == 0) a.icount[(k + 2) % 3] = 0;
   const float* gains = static_cast<const float*>(a.gains);
   // the moments of the next tile are requested while the current tile is being reduced
   float m[NM];
+  auto item = [&](int slot) { return fixed ? a.xbegin + slot : list[slot]; };
   auto fetch = [&](int slot) {
-    const int it = list[slot];
+    const int it = item(slot);
     const int i = a.item_int[it], t = a.item_s0[it];
     if (t * TB + tid < a.n_bl[i]) {
       const float* src = a.moments + (a.mom_off[i] + (int64_t)t * TB) * NM + tid;
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const D
   if (PF && slot < n_list) fetch(slot);
   while (slot < n_list) {
     if (!PF) fetch(slot);
-    const int it = list[slot];
+    const int it = item(slot);
     const int i = a.item_int[it], t = a.item_s0[it];
     const int nb = a.n_bl[i], bo = a.bl_off[i];
     const int64_t go = a.gain_off[i];
@@ -288,6 +290,26 @@ __global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const D
   }
 }
 
+// An interval's tile partials summed in tile order with compensation, all (antenna, component)
+// pairs in parallel; antennas the baseline table does not reach get zeros.
+template <int NC>
+__device__ __forceinline__ void combine_tiles(const DIArgs& a, const float* scr, int na, int nat, int nch, int fi,
+                                              float* tot) {
+  for (int x = threadIdx.x; x < na * NC; x += blockDim.x) {
+    float s = 0.f, cc = 0.f;
+    if (x < nat * NC) {
+      int j = 0;
+      for (; j + 4 <= nch; j += 4) {
+        const float v0 = __ldcg(scr + a.item_scr[fi + j] + x), v1 = __ldcg(scr + a.item_scr[fi + j + 1] + x);
+        const float v2 = __ldcg(scr + a.item_scr[fi + j + 2] + x), v3 = __ldcg(scr + a.item_scr[fi + j + 3] + x);
+        kahan_add(s, cc, v0); kahan_add(s, cc, v1); kahan_add(s, cc, v2); kahan_add(s, cc, v3);
+      }
+      for (; j < nch; ++j) kahan_add(s, cc, __ldcg(scr + a.item_scr[fi + j] + x));
+    }
+    tot[x] = s - cc;
+  }
+}
+
 template <class MK>
 __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, int n_int) {
   using K = typename MK::K;
@@ -306,24 +328,12 @@ __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, i
     const int64_t go = a.gain_off[i];
     const int nat = a.tab_nant[a.itab[i]];
     const int nch = a.n_chunks[i], fi = a.first_item[i];
-    // tile partials summed in tile order, compensated; all (antenna, component) pairs in parallel
-    for (int x = tid; x < na * NC; x += TB) {
-      float s = 0.f, cc = 0.f;
-      if (x < nat * NC) {
-        int j = 0;
-        for (; j + 4 <= nch; j += 4) {
-          const float v0 = __ldcg(scr + a.item_scr[fi + j] + x), v1 = __ldcg(scr + a.item_scr[fi + j + 1] + x);
-          const float v2 = __ldcg(scr + a.item_scr[fi + j + 2] + x), v3 = __ldcg(scr + a.item_scr[fi + j + 3] + x);
-          kahan_add(s, cc, v0); kahan_add(s, cc, v1); kahan_add(s, cc, v2); kahan_add(s, cc, v3);
-        }
-        for (; j < nch; ++j) kahan_add(s, cc, __ldcg(scr + a.item_scr[fi + j] + x));
-      }
-      tot[x] = s - cc;
-    }
+    combine_tiles<NC>(a, scr, na, nat, nch, fi, tot);
     __syncthreads();
     double d2 = 0.0, n2 = 0.0;
     int sing = 0, nonfin = 0;
-    const bool gn_step = (a.schedule == GC_SCHED_GN) || (k & 1);
+    const int kl = k - (a.k0 ? a.k0[i] : 0);  // the interval's own iteration number
+    const bool gn_step = (a.schedule == GC_SCHED_GN) || (kl & 1);
     for (int an = tid; an < na; an += TB) {
       const G old = K::ld_gain(gains + (go + an) * GW);
       G g;
@@ -345,10 +355,11 @@ __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, i
       int st = -1;
       if (nonfin) st = GC_ST_NONFINITE;
       else if (d2 <= a.tol * a.tol * n2) st = GC_ST_OK;
-      else if (k >= a.max_iter) st = GC_ST_NOT_CONVERGED;
+      else if (kl >= a.max_iter) st = GC_ST_NOT_CONVERGED;
+      if (a.gate && a.gate[i] == 0 && (st >= 0 || d2 <= a.gate_tol * a.gate_tol * n2)) a.gate[i] = kl;
       if (st >= 0) {
         a.active[i] = 0;
-        a.iters[i] = k;
+        a.iters[i] = kl;
         a.status[i] = st | (sing ? GC_ST_SINGULAR_FLAG : 0);
         atomicSub(a.n_active, 1);
       } else {
@@ -356,6 +367,44 @@ __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, i
         for (int j = 0; j < nch; ++j) a.ilist[(size_t)nxt * a.n_items + base + j] = fi + j;
       }
     }
+    __syncthreads();
+  }
+}
+
+// di_msum_kernel: after an accumulate launch at the current gains, per interval: the combined
+//   per-antenna sums (tot_out [n_gain][NC], the partial-sum component order) and
+//   e_out[i] = chi^2(g) - sum |d|^2 over the interval.  Each baseline feeds both of its antennas,
+//   and both orientations of a row have the same residual norm, so the interval's chi^2 is half the
+//   sum of the per-antenna energies plus the constant sum |d|^2, which cancels when two gain sets of
+//   the same interval are compared.  Gains, flags and work lists are left untouched.
+template <class MK>
+__global__ void __launch_bounds__(kDIThreads) di_msum_kernel(const DIArgs a, int i_lo, int n, float* tot_out,
+                                                             double* e_out) {
+  using K = typename MK::K;
+  constexpr int NC = K::NC, GW = K::GW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tot = reinterpret_cast<float*>(smem_raw);  // [na_max][NC]
+  __shared__ double red[32];
+  const float* gains = static_cast<const float*>(a.gains);
+  const float* scr = static_cast<const float*>(a.scratch);
+  const int64_t gbase = a.gain_off[i_lo];
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    const int i = i_lo + j;
+    const int na = a.n_ant[i];
+    const int64_t go = a.gain_off[i] - gbase;  // tot_out rows start at the range's first gain slot
+    if ((int64_t)a.n_samp[i] * a.n_bl[i] == 0) {
+      for (int x = threadIdx.x; x < na * NC; x += blockDim.x) tot_out[go * NC + x] = 0.f;
+      if (threadIdx.x == 0) e_out[j] = 0.0;
+      continue;
+    }
+    combine_tiles<NC>(a, scr, na, a.tab_nant[a.itab[i]], a.n_chunks[i], a.first_item[i], tot);
+    __syncthreads();
+    for (int x = threadIdx.x; x < na * NC; x += blockDim.x) tot_out[go * NC + x] = tot[x];
+    const float* gi = gains + (int64_t)a.gain_off[i] * GW;
+    double e = 0.0;
+    for (int an = threadIdx.x; an < na; an += blockDim.x) e += K::energy(tot + an * NC, K::ld_gain(gi + an * GW));
+    e = block_sum<double>(e, red);
+    if (threadIdx.x == 0) e_out[j] = 0.5 * e;
     __syncthreads();
   }
 }
@@ -475,6 +524,74 @@ int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, in
   const size_t sm2 = sizeof(float) * (size_t)a.na_max * (kind == 0 ? 3 : 12);
   if (kind == 0) di_msolve_kernel<ScalarMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
   else di_msolve_kernel<JonesMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
+  return (int)cudaGetLastError();
+}
+
+int di_launch_macc(int kind, const DIArgs& a, int grid, int smem, int red_chunks, int prefetch, void* stream) {
+  void* args[] = {const_cast<DIArgs*>(&a)};
+  return (int)cudaLaunchKernel(pick_acc(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args, (size_t)smem,
+                               (cudaStream_t)stream);
+}
+
+int di_launch_msum(int kind, const DIArgs& a, int i_lo, int n, float* tot_out, double* e_out, void* stream) {
+  if (n <= 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int g2 = n < 4096 ? n : 4096;
+  const size_t sm2 = sizeof(float) * (size_t)a.na_max * (kind == 0 ? 3 : 12);
+  if (kind == 0) di_msum_kernel<ScalarMom><<<g2, kDIThreads, sm2, s>>>(a, i_lo, n, tot_out, e_out);
+  else di_msum_kernel<JonesMom><<<g2, kDIThreads, sm2, s>>>(a, i_lo, n, tot_out, e_out);
+  return (int)cudaGetLastError();
+}
+
+// After the init launch: intervals from i_hold on wait (inactive, not in work list 1); every
+// interval starts its own count at 0 and has no gate yet.  Items are numbered by interval, so the
+// items of the first i_hold intervals are 0 .. first_item[i_hold] - 1.
+__global__ void di_wf_hold_kernel(const DIArgs a, int n_int, int i_hold, int n_active0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *a.n_active = n_active0;
+    a.icount[1] = i_hold < n_int ? a.first_item[i_hold] : a.n_items;
+  }
+  if (i < n_int) {
+    a.k0[i] = 0;
+    a.gate[i] = 0;
+    if (i >= i_hold) a.active[i] = 0;
+  }
+}
+
+int di_launch_wf_hold(const DIArgs& a, int n_int, int i_hold, int n_active0, void* stream) {
+  const int g = (n_int + 255) / 256 > 0 ? (n_int + 255) / 256 : 1;
+  di_wf_hold_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(a, n_int, i_hold, n_active0);
+  return (int)cudaGetLastError();
+}
+
+// Intervals [i_lo, i_lo + n) join the running iteration: they take iteration *kbase + 1 as their
+// first (k0 = *kbase) and their items go to that iteration's work list.
+__global__ void di_wf_activate_kernel(const DIArgs a, int i_lo, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int i = i_lo + j;
+  const int kb = *a.kbase;
+  const int cur = (kb + 1) % 3;
+  a.k0[i] = kb;
+  a.gate[i] = 0;
+  a.iters[i] = 0;
+  a.counters[i] = 0;
+  if ((int64_t)a.n_samp[i] * a.n_bl[i] == 0) {
+    a.status[i] = GC_ST_NODATA;
+    return;
+  }
+  a.status[i] = GC_ST_NOT_CONVERGED;
+  a.active[i] = 1;
+  const int nch = a.n_chunks[i], fi = a.first_item[i];
+  const int base = atomicAdd(&a.icount[cur], nch);
+  for (int c = 0; c < nch; ++c) a.ilist[(size_t)cur * a.n_items + base + c] = fi + c;
+  atomicAdd(a.n_active, 1);
+}
+
+int di_launch_wf_activate(const DIArgs& a, int i_lo, int n, void* stream) {
+  if (n <= 0) return 0;
+  di_wf_activate_kernel<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(a, i_lo, n);
   return (int)cudaGetLastError();
 }
 

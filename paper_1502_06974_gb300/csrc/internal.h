@@ -65,6 +65,16 @@ struct DIArgs {
   int32_t* kbase;    // iteration base added to k (graph-captured iteration segments); may be NULL
   float* aux;        // [n_gain][AW] per-antenna auxiliaries of the current gains (moment path)
   float* gnew;       // [n_gain][GW] staged new gains (moment path)
+  // intervals that join a running iteration (wavefront solve): interval i counts its own
+  // iterations from k - k0[i]; gate[i] records the first of them whose relative step fell below
+  // gate_tol (0 = not yet).  Both may be NULL (every interval starts at k = 1, no gate).
+  int32_t* k0;
+  int32_t* gate;
+  double gate_tol;
+  // an accumulate launch with xcount > 0 takes the items xbegin .. xbegin + xcount - 1 instead of
+  // its iteration's work list (and leaves the work lists alone)
+  int32_t xbegin;
+  int32_t xcount;
 };
 
 // Launchers implemented in di_kernels.cu.  kind: 0 scalar, 1 jones.  Return cudaError_t as int.
@@ -77,6 +87,13 @@ int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, 
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
                     void* stream);
 int di_launch_advance(int* kbase, int by, void* stream);
+// accumulate launch alone (iteration a.k's work list) and the per-interval combine without a solve
+int di_launch_macc(int kind, const DIArgs& a, int grid, int smem, int red_chunks, int prefetch, void* stream);
+int di_launch_msum(int kind, const DIArgs& a, int i_lo, int n, float* tot_out, double* e_out, void* stream);
+// wavefront solve: hold every interval from i_hold on (pending) after the init launch; activate
+// the intervals [i_lo, i_lo + n) so that they join at iteration *kbase + 1
+int di_launch_wf_hold(const DIArgs& a, int n_int, int i_hold, int n_active0, void* stream);
+int di_launch_wf_activate(const DIArgs& a, int i_lo, int n, void* stream);
 int di_launch_maux(int kind, const float* gains, float* aux, int n_gain, void* stream);
 // moment pass (resident.cu): per-baseline moments of every interval; items are (interval, 32 baselines)
 int moment_pass(int kind, const float* vis, const float* model, float* moments, const int64_t* row_off,
@@ -89,5 +106,19 @@ int moment_chi2(int kind, const float* vis, const float* model, const float* gai
                 void* stream);
 int di_launch_chi2(int kind, int dtype, const DIArgs& a, double* item_chi2, double* chi2_out, int n_int,
                    int grid, void* stream);
+
+// learned warm start (mlp.cu)
+int mlp_check(const gc_mlp* net);
+int mlp_infer(const gc_mlp* net, const float* x, int n, float* y, void* stream);
+int ws_gather(const float* sol, const int32_t* hoff, const float* lead, const int32_t* gain_off, const int32_t* n_ant,
+              int i_lo, int n, int64_t gbase, int canon, float* hbuf, float* g1, float* lead_row, void* stream);
+int ws_features_packed(const float* hbuf, const float* tot, const float* lead_row, int n, float* x, float* rot,
+                       void* stream);
+int ws_propose(const float* hbuf, const float* delta, const float* rot, int n, float* gains, void* stream);
+int ws_choose(const float* g1, const double* e_prev, const double* e_prop, const int32_t* gain_off,
+              const int32_t* n_ant, int i_lo, int n, int64_t gbase, float* gains, int32_t* used, double* dchi2,
+              void* stream);
+int gauge_fix(int kind, int dtype, void* gains, const int32_t* gain_off, const int32_t* n_ant, int n_int,
+              void* stream);
 
 }  // namespace gc

@@ -52,6 +52,11 @@ struct ScalarKind {
     out = cx<T>(v[0] * inv, v[1] * inv);
     return true;
   }
+  // sum over the antenna's rows of |d - g y|^2 - |d|^2 = A |g|^2 - 2 Re(conj(g) c), from its sums at g
+  static GC_DEV double energy(const T* v, const G& g) {
+    const double gx = g.x, gy = g.y;
+    return (double)v[2] * (gx * gx + gy * gy) - 2.0 * ((double)v[0] * gx + (double)v[1] * gy);
+  }
   static GC_DEV G avg(const G& a, const G& b) { return cx<T>(T(0.5) * (a.x + b.x), T(0.5) * (a.y + b.y)); }
   static GC_DEV T dist2(const G& a, const G& b) { return abs2_(sub_(a, b)); }
   static GC_DEV T norm2(const G& a) { return abs2_(a); }
@@ -124,6 +129,21 @@ struct JonesKind {
     out.c = scale_(sub_(scale_(C10, h11), mulc_(C11, h01)), inv);
     out.d = scale_(sub_(scale_(C11, h00), mul_(C10, h01)), inv);
     return true;
+  }
+  // sum over the antenna's rows of ||D - G Y||^2 - ||D||^2 = tr(G H G^H) - 2 Re tr(C G^H), from its
+  // sums at G (each row (x, y) of G adds h00 |x|^2 + h11 |y|^2 + 2 Re(x h01 conj(y)))
+  static GC_DEV double energy(const T* v, const G& g) {
+    const double h00 = v[8], h11 = v[9], hr = v[10], hi = v[11];
+    auto row = [&](const Cx<T>& x, const Cx<T>& y) {
+      const double xr = x.x, xi = x.y, yr = y.x, yi = y.y;
+      // x h01 conj(y): real part of (xr + i xi)(hr + i hi)(yr - i yi)
+      const double ar = xr * hr - xi * hi, ai = xr * hi + xi * hr;
+      return h00 * (xr * xr + xi * xi) + h11 * (yr * yr + yi * yi) + 2.0 * (ar * yr + ai * yi);
+    };
+    const double gh = row(g.a, g.b) + row(g.c, g.d);
+    const double cg = (double)v[0] * g.a.x + (double)v[1] * g.a.y + (double)v[2] * g.b.x + (double)v[3] * g.b.y +
+                      (double)v[4] * g.c.x + (double)v[5] * g.c.y + (double)v[6] * g.d.x + (double)v[7] * g.d.y;
+    return gh - 2.0 * cg;
   }
   static GC_DEV G avg(const G& x, const G& y) {
     G r;

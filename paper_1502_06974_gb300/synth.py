@@ -20,6 +20,7 @@ Data layout produced for every problem (a "batch" of solution intervals):
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field
 from typing import Optional
 
@@ -405,17 +406,30 @@ def make_warm(seed=SEED, n_ant=64, n_t=720, n_chan=64, f_per=8, dt_s=10.0, t_cor
     vis = np.empty((n_int * rows, 2, 2), dtype)
     model = np.empty((n_int * rows, 2, 2), dtype)
     mod_blocks = model_f.reshape(n_fb, f_per * nb, 2, 2)
-    for c0 in range(0, n_int, chunk):
+
+    def fill(c0):
+        # chunks write disjoint rows and draw their noise per interval: the result does not depend
+        # on the chunking or the thread count
         c1 = min(n_int, c0 + chunk)
         fb = np.arange(c0, c1) % n_fb
         mod = mod_blocks[fb].reshape(c1 - c0, ns, nb, 2, 2)
         Gp = G[c0:c1][:, a1][:, None]                                                   # [c, 1, b, 2, 2]
-        Gq = G[c0:c1][:, a2][:, None]
-        v = Gp @ mod @ np.conj(np.swapaxes(Gq, -1, -2))
+        Gq = np.conj(G[c0:c1][:, a2][:, None])
+        # V = Gp M Gq^H written out entry by entry (elementwise products run in parallel threads,
+        # stacked 2x2 matmuls do not)
+        A = [[Gp[..., r, 0] * mod[..., 0, c] + Gp[..., r, 1] * mod[..., 1, c] for c in range(2)] for r in range(2)]
+        v = np.empty(mod.shape, np.complex128)
+        for r in range(2):
+            for c in range(2):
+                v[..., r, c] = A[r][0] * Gq[..., c, 0] + A[r][1] * Gq[..., c, 1]
         for j, i in enumerate(range(c0, c1)):
             v[j] += complex_noise(rng_for(seed, 5, 2 + i), (ns, nb, 2, 2), sigma)
         vis[c0 * rows:c1 * rows] = v.reshape(-1, 2, 2)
         model[c0 * rows:c1 * rows] = mod.reshape(-1, 2, 2)
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(fill, range(0, n_int, chunk)))
     row_off = np.arange(n_int, dtype=np.int64) * rows
     return Batch('jones', vis, model, a1, a2, row_off, np.full(n_int, ns, np.int32), np.full(n_int, nb, np.int32),
                  np.zeros(n_int, np.int32), np.full(n_int, n_ant, np.int32),
