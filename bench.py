@@ -202,6 +202,86 @@ def run_reference(args):
     return 0
 
 
+WARM_LAG = 16           # wave length (time steps) of the learned wavefront
+WARM_GATE = 0.0         # a wave joins once its history has finished (0: no early start)
+WARM_WORKLOAD = ("di_jones2x2 warm start: 64 ant (2016 bl), 720 t x 64 ch, intervals 1 t x 8 ch (5760), GP gains "
+                 "(30 min / 50 MHz correlation, amplitude 0.1, phase 1 rad), tol 1e-6")
+
+
+def warm_start_block(dev, args):
+    """Learned warm start + batched path vs the plain batched solver on the GP-gain workload.
+
+    The network is trained first (its own observation, another seed), then three solves of the
+    same 5760 intervals are timed with the data resident: plain (all intervals from unit gains in
+    one call), previous-solution wavefront and learned wavefront (one call each)."""
+    import torch
+    from paper_1502_06974_gb300 import api, synth, warmstart
+    t0 = time.perf_counter()
+    bt = synth.make_warm(seed=synth.SEED + 1000, n_t=160)
+    vt, mt = torch.from_numpy(bt.vis).to(dev), torch.from_numpy(bt.model).to(dev)
+    gt = warmstart.Grid.from_batch(bt)
+    sol_t, _, st_t = warmstart.solve_plain(vt, mt, gt, TOL, MAX_ITER)
+    x, t = warmstart.training_set(vt, mt, gt, sol_t, WARM_LAG, np.random.default_rng(0), n_samples=50000)
+    res = warmstart.train(x, t, epochs=40, batch=1024, lr=1e-3)
+    del vt, mt, sol_t, x, t
+    prep_s = time.perf_counter() - t0
+    be = synth.make_config(5)
+    ve, me = torch.from_numpy(be.vis).to(dev), torch.from_numpy(be.model).to(dev)
+    del be.vis, be.model
+    ge = warmstart.Grid.from_batch(be)
+    n_int = ge.n_t * ge.n_fb
+    lay = ge.layout(n_int)
+    if not args.no_autotune:
+        api.autotune_di(ve, me, lay, warmstart._identity(n_int * ge.n_ant, dev), iters=24)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()                                   # warm-up (plan, graph capture)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return out, e0.elapsed_time(e1)
+
+    (gp, itp, stp), ms_plain = timed(lambda: warmstart.solve_plain(ve, me, ge, TOL, MAX_ITER))
+    prev, ms_prev = timed(lambda: warmstart.solve_pipelined(ve, me, ge, WARM_LAG, None, TOL, MAX_ITER, WARM_GATE))
+    lrn, ms_lrn = timed(lambda: warmstart.solve_pipelined(ve, me, ge, WARM_LAG, res.net, TOL, MAX_ITER, WARM_GATE))
+    itp = itp.cpu().numpy()
+    rows = ge.rows * n_int
+    g_true = be.g_true
+
+    def err_truth(g):
+        # max over antennas of ||G e^{i phi} - G_true|| / ||G_true||, phi the least-squares global
+        # phase of each interval (solutions are defined up to that phase)
+        est = g.cpu().numpy().astype(np.complex128).reshape(n_int, ge.n_ant, 4)
+        ref = g_true.reshape(n_int, ge.n_ant, 4)
+        ph = np.exp(1j * np.angle(np.sum(ref * np.conj(est), axis=(1, 2))))
+        d = np.linalg.norm(est * ph[:, None, None] - ref, axis=2) / np.linalg.norm(ref, axis=2)
+        return float(d.max())
+
+    def entry(ms, iters, status, extra=None):
+        d = {"ms": ms, "value": rows / (ms / 1e3), "iters_mean": float(np.mean(iters)),
+             "iters_max": int(np.max(iters)), "interval_iterations": int(np.sum(iters)),
+             "converged": int(np.sum((status & 15) == 0))}
+        d.update(extra or {})
+        return d
+
+    return {"workload": WARM_WORKLOAD, "metric": METRIC, "unit": UNIT, "lag": WARM_LAG, "gate_tol": WARM_GATE,
+            "plain": entry(ms_plain, itp, stp.cpu().numpy(), {"max_err_vs_truth": err_truth(gp)}),
+            "previous_solution": entry(ms_prev, prev.iters, prev.status, {"max_err_vs_truth": err_truth(prev.gains)}),
+            "learned": entry(ms_lrn, lrn.iters, lrn.status,
+                             {"proposals_taken": float(np.mean(lrn.used[np.repeat(np.arange(ge.n_t), ge.n_fb)
+                                                                       >= WARM_LAG])),
+                              "max_err_vs_truth": err_truth(lrn.gains)}),
+            "speedup_learned_vs_plain": ms_plain / ms_lrn,
+            "speedup_learned_vs_previous_solution": ms_prev / ms_lrn,
+            "training": {"trajectories": 50000, "observation": "160 t x 64 ch of the same array, another seed",
+                         "adam_steps": res.steps, "train_s": res.seconds, "prep_s": prep_s,
+                         "val_mse": res.val_mse, "val_mse_previous_solution": res.val_mse_zero}}
+
+
 def run_gpu(args):
     import torch
     rank, world, local = _env_rank()
@@ -359,6 +439,10 @@ def run_gpu(args):
                "clocks": clocks}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_block(b, med_it)
+        if not args.no_warm and world == 1:
+            del vis, model
+            torch.cuda.empty_cache()
+            out["warm_start"] = warm_start_block(dev, args)
         print(json.dumps(out))
     if dist:
         dist.barrier()
@@ -375,6 +459,7 @@ def main():
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--no-autotune', action='store_true')
+    ap.add_argument('--no-warm', action='store_true', help='skip the learned warm start comparison')
     ap.add_argument('--path', type=int, default=0, help='0 auto (moments), 1 raw-row streaming, 2 resident, 3 moments')
     ap.add_argument('--iters', type=int, default=0,
                     help='run exactly this many iterations per step (tol 0) instead of converging; for profiling')

@@ -251,7 +251,7 @@ int gc_chi2_di_jones2x2(const void* vis, const void* model, const gc_layout* lay
  * A small MLP (in -> h1 -> h2 -> out, ReLU on the hidden layers) proposes each interval's starting
  * gains from the antenna's earlier solutions; the iteration then runs to the usual tolerance from
  * that start, so the network only changes where the solver starts and a poor proposal costs
- * iterations, never accuracy.  The paper has no counterpart; its Sect. sec:DI:smooth (gains do not
+ * iterations, never accuracy.  The paper has no counterpart; its Sect. 3.4 (gains do not
  * vary arbitrarily in time and frequency) is what makes earlier solutions informative.
  * Parameter buffer `params` (float, device): W1 [in][h1] | b1 [h1] | W2 [h1][h2] | b2 [h2] |
  * W3 [h2][out] | b3 [out], row-major with y = x W + b.  grads, adam_m, adam_v: same size (training
@@ -325,6 +325,8 @@ typedef struct gc_wavefront {
   int32_t n_t, n_fb;     /* interval i = t * n_fb + f, t < n_t, f < n_fb; n_t * n_fb = n_intervals, and
                             every interval of block f has the antennas of interval f (GC_ERR_LAYOUT) */
   int32_t lag;           /* wave length L in time steps (>= 1) */
+  int32_t max_lead;      /* the newest history time may lie up to max_lead (>= 1) steps before the
+                            wave's first time: 1 = always the 4 times just before the wave */
   float lead_scale;      /* network input lead = (t - newest history time) / lead_scale (> 0) */
   double gate_tol;       /* a wave joins once every interval of its history stopped or took a relative
                             step <= gate_tol (gate_tol <= tol: only finished histories) */
@@ -336,10 +338,12 @@ typedef struct gc_wavefront {
 
 /*
  * The whole grid in one iteration loop.  The times [wL, (w+1)L) form wave w.  Wave 0 starts from
- * `gains`; wave w >= 1 starts as gc_calibrate_di_jones2x2_warm does, from the solutions at times
- * wL-1 .. wL-4 (clamped at 0) of the same block f, each put in the canonical gauge, with lead
- * t - (wL-1), and joins the running iteration as soon as all of those intervals have finished or
- * taken a step below gate_tol.  Every interval iterates to opt->tol with its own iteration count
+ * `gains`; wave w >= 1 joins the running iteration as soon as, for some history time th with
+ * wL - max_lead <= th < wL, every interval at times th-3 .. th (clamped at 0) has finished or taken
+ * a step below gate_tol (the newest such th is used).  It then starts as
+ * gc_calibrate_di_jones2x2_warm does, from the solutions at th .. th-3 of the same block f, each put
+ * in the canonical gauge, with lead t - th.  Every interval iterates to opt->tol with its own
+ * iteration count
  * (iters_out counts from its first iteration; the GN / average alternation restarts with it).
  * On return `gains` holds the solutions in the canonical gauge (see gc_gauge_fix_di).
  * Complex64 device buffers only, as gc_calibrate_di_jones2x2_warm.  Returns the number of

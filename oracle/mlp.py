@@ -2,14 +2,16 @@
 
 Test infrastructure only (see the package header).  The network is not from the paper: it is the
 learned warm start that proposes an interval's starting gains from earlier solutions (the paper's
-Sect. sec:DI:smooth notes that gains do not vary arbitrarily in time and frequency, which is what
+Sect. 3.4 notes that gains do not vary arbitrarily in time and frequency, which is what
 makes earlier solutions informative).  Everything here is the textbook definition:
 
   h1 = relu(x W1 + b1),  h2 = relu(h1 W2 + b2),  y = h2 W3 + b3,
   loss = mean over all n * out entries of (y - t)^2,
 
 with gradients by the chain rule (the derivative of relu taken as 0 at 0) and Adam with
-bias correction (Kingma & Ba 2015, Algorithm 1).
+bias correction (Kingma & Ba 2015, Algorithm 1).  ``forward_bf16`` is the inference precision of
+the warm start: weights, inputs and hidden activations rounded to bfloat16 (round to nearest, ties
+to even, from float32), products and sums exact here (FP64).
 
 Parameters are one flat vector: W1 [in][h1] | b1 [h1] | W2 [h1][h2] | b2 [h2] | W3 [h2][out] | b3 [out],
 each matrix row-major.
@@ -54,6 +56,21 @@ def forward(params, dims, x):
     h2 = np.maximum(h1 @ W2 + b2, 0.0)
     y = h2 @ W3 + b3
     return h1, h2, y
+
+
+def bf16(a):
+    """Round float32 values to the nearest bfloat16 (ties to even), returned as float64."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, dims, x):
+    """Output of the network with bfloat16 weights, inputs and hidden activations."""
+    W1, b1, W2, b2, W3, b3 = (bf16(np.asarray(w, np.float32)) for w in unpack(params, dims))
+    h1 = bf16(np.maximum(bf16(np.asarray(x, np.float32)) @ W1 + b1, 0.0))
+    h2 = bf16(np.maximum(h1 @ W2 + b2, 0.0))
+    return h2 @ W3 + b3
 
 
 def loss_and_grad(params, dims, x, t):

@@ -1,7 +1,7 @@
 """Learned warm start for the 2x2 solver: features, proposal, start selection, gauge, FP64.
 
 Test infrastructure only (see the package header).  The warm start is an addition to the paper's
-method (motivated by Sect. sec:DI:smooth: gains vary smoothly in time and frequency); it only
+method (motivated by Sect. 3.4: gains vary smoothly in time and frequency); it only
 chooses where the paper's iteration starts, and the iteration then runs to the same tolerance.
 
 Per (interval, antenna) row, with g1..g4 the antenna's four previous 2x2 solutions (newest first)

@@ -61,7 +61,8 @@ class GcWarm(C.Structure):
 
 
 class GcWavefront(C.Structure):
-    _fields_ = [('n_t', C.c_int32), ('n_fb', C.c_int32), ('lag', C.c_int32), ('lead_scale', C.c_float),
+    _fields_ = [('n_t', C.c_int32), ('n_fb', C.c_int32), ('lag', C.c_int32), ('max_lead', C.c_int32),
+                ('lead_scale', C.c_float),
                 ('gate_tol', C.c_double), ('net', C.POINTER(GcMlp)), ('used_out', C.c_void_p),
                 ('wave_k_out', _i32p)]
 

@@ -315,7 +315,8 @@ def calibrate_di_jones2x2_warm(vis, model, layout: Layout, solutions, hist_off, 
 
 
 def calibrate_di_jones2x2_wavefront(vis, model, layout: Layout, n_t, n_fb, lag, net, gains, tol=1e-6, max_iter=1000,
-                                    gate_tol=1e-4, lead_scale=32.0, schedule=N.GC_SCHED_STEFCAL, compute_chi2=False):
+                                    gate_tol=0.0, lead_scale=32.0, max_lead=1, schedule=N.GC_SCHED_STEFCAL,
+                                    compute_chi2=False):
     """gc_calibrate_di_jones2x2_wavefront: the whole time-major grid in one iteration loop, waves of
     `lag` times joining with learned starts (net=None: previous solution).  gains: the first wave's
     start on input, the canonical-gauge solutions on return.
@@ -334,7 +335,7 @@ def calibrate_di_jones2x2_wavefront(vis, model, layout: Layout, n_t, n_fb, lag, 
     chi2 = torch.zeros(n, dtype=torch.float64, device=dev) if compute_chi2 else None
     n_waves = (int(n_t) + int(lag) - 1) // int(lag)
     wave_k = np.zeros(max(n_waves, 1), np.int32)
-    wf = N.GcWavefront(int(n_t), int(n_fb), int(lag), float(lead_scale), float(gate_tol),
+    wf = N.GcWavefront(int(n_t), int(n_fb), int(lag), int(max_lead), float(lead_scale), float(gate_tol),
                        C.pointer(net._c) if net is not None else None, used.data_ptr(),
                        wave_k.ctypes.data_as(C.POINTER(C.c_int32)))
     opt = N.GcOptions(float(tol), int(max_iter), int(schedule), N.GC_DTYPE_C64, 0, 1 if compute_chi2 else 0, 0,

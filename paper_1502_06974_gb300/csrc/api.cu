@@ -160,6 +160,8 @@ struct Tune {
   int check_every = 16;   // iterations per graph segment / between host checks of the active count
   int target_rows = 0;    // raw-row path: rows per work item (0 = default)
   int graph = 1;          // capture iteration segments in a CUDA graph
+  int loop = 0;           // moment path: run segments in one persistent cooperative launch instead
+                          // (grid barriers between the phases; measured slower than graph segments)
 };
 static std::map<uint64_t, Tune> g_tune;
 static bool g_tune_override_on = false;
@@ -198,12 +200,13 @@ static Tune effective_tune(int kind, int dtype, int mode, const gc_layout* L) {
   t.check_every = std::max(1, env_int("GAINCAL_CHECK_EVERY", t.check_every));
   t.target_rows = env_int(kind == 0 ? "GAINCAL_TARGET_ROWS_SCALAR" : "GAINCAL_TARGET_ROWS_JONES", t.target_rows);
   t.graph = env_int("GAINCAL_GRAPH", t.graph);
+  t.loop = env_int("GAINCAL_LOOP", t.loop);
   return t;
 }
 
 static uint64_t tune_hash(const Tune& t) {
   return (uint64_t)t.red_chunks * 1000003ull ^ (uint64_t)t.prefetch * 7919ull ^ (uint64_t)t.bps * 104729ull ^
-         (uint64_t)t.target_rows * 1299709ull ^ (uint64_t)t.check_every * 15485863ull;
+         (uint64_t)t.target_rows * 1299709ull ^ (uint64_t)t.check_every * 15485863ull ^ (uint64_t)t.loop * 32452843ull;
 }
 
 // ------------------------------------------------------------------------------------ DI plan
@@ -218,6 +221,7 @@ struct DIPlan {
   double* chi2_items = nullptr;
   double* chi2_out = nullptr;
   int grid = 0, smem = 0;
+  int lgrid = 0, lsmem = 0;  // persistent loop kernel (moment mode): co-resident grid, shared memory
   // moment-stream mode: moment-pass items (interval, 32 baselines), per-item chi^2 bookkeeping
   int mode = 0;
   int n_mitems = 0;
@@ -443,6 +447,14 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   P.tune = tune;
   P.grid = nsm * per_sm;
   if (P.grid > n_items) P.grid = n_items > 0 ? n_items : 1;
+  if (mode == 1) {
+    P.lsmem = di_mloop_smem(kind, na_max, tune.red_chunks);
+    if (P.lsmem > max_smem) return GC_ERR_LIMIT;
+    int cap = 0;
+    GC_CUDA_I(di_mloop_max_grid(kind, P.lsmem, tune.red_chunks, tune.prefetch, &cap));
+    if (tune.bps > 0 && tune.bps * nsm < cap) cap = tune.bps * nsm;
+    P.lgrid = cap;
+  }
   return GC_OK;
 }
 
@@ -609,6 +621,16 @@ static int warm_range(const gc_layout* L, DIPlan* P, DIArgs a, const float* sol,
   return GC_OK;
 }
 
+// Two barrier words and an error flag for the persistent loop kernel, zeroed on `s`.
+static int loop_barrier(unsigned** out, cudaStream_t s) {
+  void* p = nullptr;
+  int rc = ws_get("loop_barrier", 4 * sizeof(unsigned), &p);
+  if (rc) return rc;
+  GC_CUDA(cudaMemsetAsync(p, 0, 4 * sizeof(unsigned), s));
+  *out = (unsigned*)p;
+  return GC_OK;
+}
+
 static int first_items_host(DIPlan* P, std::vector<int32_t>& out, cudaStream_t s) {
   out.resize(P->n_int);
   GC_CUDA(cudaMemcpyAsync(out.data(), P->args.first_item, (size_t)P->n_int * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -743,7 +765,25 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   };
   Profiler prof(opt->profile != 0, S);
   if ((rc = prof.init())) return rc;
-  if (tn.graph) {
+  if (mode == 1 && tn.loop && P->lgrid > 0) {
+    prof.weight = S;
+    unsigned* bar = nullptr;
+    if ((rc = loop_barrier(&bar, s))) return rc;
+    int* err = (int*)(bar + 2);
+    for (int k0 = 0; k0 < opt->max_iter; k0 += S) {
+      if ((rc = prof.before(s))) return rc;
+      GC_CUDA_I(di_launch_mloop(kind, a, P->lgrid, P->lsmem, P->n_int, S, tn.red_chunks, tn.prefetch, bar, err,
+                                stream));
+      if ((rc = prof.after(s))) return rc;
+      g_launches++;
+      GC_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(flag + 1, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaStreamSynchronize(s));
+      if ((rc = prof.drain())) return rc;
+      if (flag[1]) return cuda_fail(cudaErrorLaunchTimeout, "grid barrier of the iteration loop timed out");
+      if (*flag <= 0) break;
+    }
+  } else if (tn.graph) {
     prof.weight = S;
     // One segment = S iterations captured once (k = *kbase + 1 .. *kbase + S) plus a node that
     // advances *kbase; segments are relaunched until no interval is active.  Iterations past
@@ -857,7 +897,8 @@ static int run_wavefront(const void* vis, const void* model, const gc_layout* L,
     return GC_ERR_ARG;
   if (opt->host_buffers != 0 || opt->reserved || (opt->path != GC_PATH_AUTO && opt->path != GC_PATH_MOMENTS))
     return GC_ERR_ARG;
-  if (wf->n_t < 1 || wf->n_fb < 1 || wf->lag < 1 || !(wf->lead_scale > 0.f) || !(wf->gate_tol >= 0.0))
+  if (wf->n_t < 1 || wf->n_fb < 1 || wf->lag < 1 || wf->max_lead < 1 || !(wf->lead_scale > 0.f) ||
+      !(wf->gate_tol >= 0.0))
     return GC_ERR_ARG;
   int rc = validate_layout(L, 1);
   if (rc != GC_OK) return rc;
@@ -909,7 +950,8 @@ static int run_wavefront(const void* vis, const void* model, const gc_layout* L,
   // the iteration segment: S iterations and the advance of *kbase, captured once per argument set
   const Tune& tn = P->tune;
   const int S = tn.check_every;
-  {
+  const bool use_loop = tn.loop && P->lgrid > 0;
+  if (!use_loop) {
     DIArgs ga = a;
     ga.k = 0;
     ga.vis = ga.model = nullptr;
@@ -937,42 +979,70 @@ static int run_wavefront(const void* vis, const void* model, const gc_layout* L,
       P->gS = S;
     }
   }
-  const int gate_n = std::min(4, lag) * nfb + 4 * nfb;  // upper bound of a gate range's intervals
+  // the host reads the state of the win = max_lead + 3 times before the next wave
+  const int ml = wf->max_lead, win = ml + 3;
+  const int gate_n = win * nfb;
   int32_t* hb = nullptr;
-  if ((rc = pinned_ints((size_t)(2 + 2 * gate_n), &hb))) return rc;
+  if ((rc = pinned_ints((size_t)(3 + 2 * gate_n), &hb))) return rc;
+  int32_t* h_act = hb + 3;
+  int32_t* h_gate = hb + 3 + gate_n;
   std::vector<int32_t> hoff;
   std::vector<float> lead;
   int next = 1, kb = 0;
   const int64_t max_segments = (int64_t)n_waves * (opt->max_iter / S + 2) + 16;
+  unsigned* bar = nullptr;
+  if (use_loop && (rc = loop_barrier(&bar, s))) return rc;
+  int* lerr = use_loop ? (int*)(bar + 2) : nullptr;
   for (int64_t seg = 0; seg < max_segments; ++seg) {
-    GC_CUDA(cudaGraphLaunch(P->gexec, s));
-    g_launches += (int64_t)S * 2 + 1;
-    kb += S;
-    int g_lo = 0, g_n = 0;
-    if (next < n_waves) {
-      const int t1 = next * lag, t0 = std::max(0, t1 - 4);
-      g_lo = t0 * nfb;
-      g_n = (t1 - t0) * nfb;
+    if (use_loop) {
+      GC_CUDA_I(di_launch_mloop(1, a, P->lgrid, P->lsmem, n_int, S, tn.red_chunks, tn.prefetch, bar, lerr, stream));
+      g_launches++;
+    } else {
+      GC_CUDA(cudaGraphLaunch(P->gexec, s));
+      g_launches += (int64_t)S * 2 + 1;
     }
+    int t_lo = 0, tw = 0;
+    if (next < n_waves) {
+      tw = next * lag;
+      t_lo = std::max(0, tw - win);
+    }
+    const int g_n = (tw - t_lo) * nfb;
     GC_CUDA(cudaMemcpyAsync(hb, a.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (use_loop) GC_CUDA(cudaMemcpyAsync(hb + 1, lerr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaMemcpyAsync(hb + 2, a.kbase, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     if (g_n > 0) {
-      GC_CUDA(cudaMemcpyAsync(hb + 2, a.active + g_lo, (size_t)g_n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      GC_CUDA(cudaMemcpyAsync(hb + 2 + gate_n, a.gate + g_lo, (size_t)g_n * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                              s));
+      GC_CUDA(cudaMemcpyAsync(h_act, a.active + t_lo * nfb, (size_t)g_n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(h_gate, a.gate + t_lo * nfb, (size_t)g_n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     }
     GC_CUDA(cudaStreamSynchronize(s));
+    kb = hb[2];
+    if (use_loop && hb[1]) return cuda_fail(cudaErrorLaunchTimeout, "grid barrier of the iteration loop timed out");
     const int n_active = hb[0];
     if (next < n_waves) {
-      bool ready = true;
-      for (int j = 0; j < g_n && ready; ++j) ready = hb[2 + j] == 0 || hb[2 + gate_n + j] > 0;
-      if (ready) {
-        const int i_lo = wave_lo(next), n = wave_lo(next + 1) - i_lo, tp = next * lag - 1;
+      // every time before the wave belongs to a wave already running: it is done once all of its
+      // blocks have stopped or passed the gate
+      auto done = [&](int t) {
+        for (int f = 0; f < nfb; ++f) {
+          const int j = (t - t_lo) * nfb + f;
+          if (!(h_act[j] == 0 || h_gate[j] > 0)) return false;
+        }
+        return true;
+      };
+      // the newest history time th (tw - max_lead <= th < tw) whose 4 solutions are all done
+      int th = -1;
+      for (int c = tw - 1; c >= std::max(0, tw - ml) && th < 0; --c) {
+        bool ok = true;
+        for (int j = 0; j < 4 && ok; ++j) ok = done(std::max(0, c - j));
+        if (ok) th = c;
+      }
+      if (th >= 0) {
+        const int i_lo = wave_lo(next), n = wave_lo(next + 1) - i_lo;
         hoff.resize((size_t)n * 4);
         lead.resize(n);
         for (int b = 0; b < n; ++b) {
           const int i = i_lo + b, t = i / nfb, f = i % nfb;
-          for (int j = 0; j < 4; ++j) hoff[4 * b + j] = L->gain_off[std::max(0, tp - j) * nfb + f];
-          lead[b] = (float)(t - tp) / wf->lead_scale;
+          for (int j = 0; j < 4; ++j) hoff[4 * b + j] = L->gain_off[std::max(0, th - j) * nfb + f];
+          lead[b] = (float)(t - th) / wf->lead_scale;
         }
         if ((rc = warm_range(L, P, a, g, hoff.data(), lead.data(), wf->net, 1, i_lo, n, fi.data(), g, wf->used_out,
                              nullptr, nullptr, stream)))

@@ -19,6 +19,8 @@
 // therefore bitwise reproducible run to run.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 #include "kinds.cuh"
@@ -208,24 +210,43 @@ __global__ void __launch_bounds__(kDIThreads) di_iter_kernel(const DIArgs a) {
 //   the next iteration's list (lists rotate over three buffers: launch k reads list k % 3,
 //   appends to (k + 1) % 3; the accumulate launch of k clears (k + 2) % 3).
 // ------------------------------------------------------------------------------------------
-template <class MK, int CH, bool PF>
-__global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const DIArgs a) {
+// Loads of data other CTAs of the same launch write (gains, auxiliaries, work lists) go through L2
+// (ld.global.cg) in the persistent loop kernel, whose CTAs do not meet at a launch boundary.
+template <bool COH>
+__device__ __forceinline__ float ldc(const float* p) { return COH ? __ldcg(p) : *p; }
+template <bool COH>
+__device__ __forceinline__ int ldc(const int* p) { return COH ? __ldcg(p) : *p; }
+
+template <class K, bool COH>
+__device__ __forceinline__ typename K::G ld_gain_c(const float* g) {
+  if constexpr (!COH) {
+    return K::ld_gain(g);
+  } else {
+    float v[K::GW];
+#pragma unroll
+    for (int c = 0; c < K::GW; ++c) v[c] = __ldcg(g + c);
+    return K::ld_gain(v);
+  }
+}
+
+// Accumulate phase of iteration k (see di_macc_kernel); `smem` holds [TB][2 NC + 1] partials and
+// [na_max * NC * CH] chunk sums.
+template <class MK, int CH, bool PF, bool COH>
+__device__ __forceinline__ void macc_phase(const DIArgs& a, int k, float* smem) {
   using K = typename MK::K;
   constexpr int NC = K::NC, GW = K::GW, NM = MK::NM, AW = MK::AW, TB = kDIThreads, PS = 2 * NC + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* part = reinterpret_cast<float*>(smem_raw);   // [TB][PS]
-  float* ps = part + TB * PS;                           // [na_max * NC * CH]
+  float* part = smem;           // [TB][PS]
+  float* ps = part + TB * PS;   // [na_max * NC * CH]
   const int tid = threadIdx.x;
-  const int k = a.k + (a.kbase ? *a.kbase : 0);
   const int cur = k % 3;
   const bool fixed = a.xcount > 0;
   const int* list = a.ilist + (size_t)cur * a.n_items;
-  const int n_list = fixed ? a.xcount : a.icount[cur];
+  const int n_list = fixed ? a.xcount : ldc<COH>(a.icount + cur);
   if (!fixed && blockIdx.x == 0 && tid == 0) a.icount[(k + 2) % 3] = 0;
   const float* gains = static_cast<const float*>(a.gains);
   // the moments of the next tile are requested while the current tile is being reduced
   float m[NM];
-  auto item = [&](int slot) { return fixed ? a.xbegin + slot : list[slot]; };
+  auto item = [&](int slot) { return fixed ? a.xbegin + slot : ldc<COH>(list + slot); };
   auto fetch = [&](int slot) {
     const int it = item(slot);
     const int i = a.item_int[it], t = a.item_s0[it];
@@ -246,9 +267,14 @@ __global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const D
     const int b = t * TB + tid;
     if (b < nb) {
       const int p = a.ant1[bo + b], q = a.ant2[bo + b];
-      float pp[NC], pq[NC];
-      MK::partials(m, K::ld_gain(gains + (go + p) * GW), K::ld_gain(gains + (go + q) * GW),
-                   a.aux + (go + p) * AW, a.aux + (go + q) * AW, pp, pq);
+      float pp[NC], pq[NC], ap[AW], aq[AW];
+#pragma unroll
+      for (int c = 0; c < AW; ++c) {
+        ap[c] = ldc<COH>(a.aux + (go + p) * AW + c);
+        aq[c] = ldc<COH>(a.aux + (go + q) * AW + c);
+      }
+      MK::partials(m, ld_gain_c<K, COH>(gains + (go + p) * GW), ld_gain_c<K, COH>(gains + (go + q) * GW), ap, aq,
+                   pp, pq);
       float* my = part + tid * PS;
 #pragma unroll
       for (int c = 0; c < NC; ++c) { my[c] = pp[c]; my[NC + c] = pq[c]; }
@@ -290,6 +316,12 @@ __global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const D
   }
 }
 
+template <class MK, int CH, bool PF>
+__global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const DIArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  macc_phase<MK, CH, PF, false>(a, a.k + (a.kbase ? *a.kbase : 0), reinterpret_cast<float*>(smem_raw));
+}
+
 // An interval's tile partials summed in tile order with compensation, all (antenna, component)
 // pairs in parallel; antennas the baseline table does not reach get zeros.
 template <int NC>
@@ -310,20 +342,18 @@ __device__ __forceinline__ void combine_tiles(const DIArgs& a, const float* scr,
   }
 }
 
-template <class MK>
-__global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, int n_int) {
+// Solve phase of iteration k (see di_msolve_kernel); `tot` holds [na_max][NC] floats.
+template <class MK, bool COH>
+__device__ __forceinline__ void msolve_phase(const DIArgs& a, int k, int n_int, float* tot, double* red) {
   using K = typename MK::K;
   using G = typename K::G;
   constexpr int NC = K::NC, GW = K::GW, AW = MK::AW, TB = kDIThreads;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* tot = reinterpret_cast<float*>(smem_raw);  // [na_max][NC]
-  __shared__ double red[96];
   const int tid = threadIdx.x;
-  const int k = a.k + (a.kbase ? *a.kbase : 0), nxt = (k + 1) % 3;
+  const int nxt = (k + 1) % 3;
   float* gains = static_cast<float*>(a.gains);
   const float* scr = static_cast<const float*>(a.scratch);
   for (int i = blockIdx.x; i < n_int; i += gridDim.x) {
-    if (a.active[i] == 0) continue;
+    if (ldc<COH>(a.active + i) == 0) continue;
     const int na = a.n_ant[i];
     const int64_t go = a.gain_off[i];
     const int nat = a.tab_nant[a.itab[i]];
@@ -332,10 +362,10 @@ __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, i
     __syncthreads();
     double d2 = 0.0, n2 = 0.0;
     int sing = 0, nonfin = 0;
-    const int kl = k - (a.k0 ? a.k0[i] : 0);  // the interval's own iteration number
+    const int kl = k - (a.k0 ? ldc<COH>(a.k0 + i) : 0);  // the interval's own iteration number
     const bool gn_step = (a.schedule == GC_SCHED_GN) || (kl & 1);
     for (int an = tid; an < na; an += TB) {
-      const G old = K::ld_gain(gains + (go + an) * GW);
+      const G old = ld_gain_c<K, COH>(gains + (go + an) * GW);
       G g;
       if (!K::solve(tot + an * NC, old, g)) sing = 1;
       const G nw = gn_step ? g : K::avg(old, g);
@@ -369,6 +399,67 @@ __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, i
     }
     __syncthreads();
   }
+}
+
+template <class MK>
+__global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, int n_int) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[96];
+  msolve_phase<MK, false>(a, a.k + (a.kbase ? *a.kbase : 0), n_int, reinterpret_cast<float*>(smem_raw), red);
+}
+
+// Grid-wide barrier of the persistent loop kernel (a cooperative launch, so every CTA is
+// resident): arrival counter bar[0], generation bar[1].  The wait is bounded: after
+// kBarrierSpins polls the CTA records the timeout in *err and the kernel returns, so a barrier
+// that cannot complete ends the launch with an error status instead of hanging the GPU.
+constexpr unsigned kBarrierSpins = 1u << 25;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned n = 0;
+      while (*vgen == gen) {
+        if (++n > kBarrierSpins) { ok = 0; atomicExch(err, 1); break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_ok = ok && *(volatile int*)err == 0;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Persistent iteration loop: up to S iterations (k = *kbase + 1 ..) in one cooperative launch,
+// the accumulate and solve phases separated by grid barriers; stops early once no interval is
+// active and leaves *kbase at the last iteration done.  Same arithmetic, in the same order, as
+// the two-launch iteration.
+template <class MK, int CH, bool PF>
+__global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_mloop_kernel(const DIArgs a, int n_int, int S,
+                                                                          unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[96];
+  __shared__ int s_ok;
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int base = *a.kbase;
+  int j = 1;
+  for (; j <= S; ++j) {
+    if (__ldcg(a.n_active) <= 0) break;
+    macc_phase<MK, CH, PF, true>(a, base + j, sm);
+    if (!grid_barrier(bar, err, &s_ok)) return;
+    msolve_phase<MK, true>(a, base + j, n_int, sm, red);
+    if (!grid_barrier(bar, err, &s_ok)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.kbase = base + j - 1;
 }
 
 // di_msum_kernel: after an accumulate launch at the current gains, per interval: the combined
@@ -513,6 +604,43 @@ int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, 
   return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, f, kDIThreads, smem);
 }
 
+constexpr int kSolveGrid = 1216;  // 8 CTAs on each of 152 SMs
+
+static const void* pick_loop(int kind, int red_chunks, int prefetch) {
+  const bool c4 = red_chunks == kRedChunks, pf = prefetch != 0;
+  if (kind == 0) {
+    if (pf) return c4 ? (const void*)&di_mloop_kernel<ScalarMom, kRedChunks, true> : (const void*)&di_mloop_kernel<ScalarMom, 1, true>;
+    return c4 ? (const void*)&di_mloop_kernel<ScalarMom, kRedChunks, false> : (const void*)&di_mloop_kernel<ScalarMom, 1, false>;
+  }
+  if (pf) return c4 ? (const void*)&di_mloop_kernel<JonesMom, kRedChunks, true> : (const void*)&di_mloop_kernel<JonesMom, 1, true>;
+  return c4 ? (const void*)&di_mloop_kernel<JonesMom, kRedChunks, false> : (const void*)&di_mloop_kernel<JonesMom, 1, false>;
+}
+
+int di_mloop_smem(int kind, int na_max, int red_chunks) {
+  const int nc = kind == 0 ? 3 : 12;
+  return std::max(di_macc_smem(kind, na_max, red_chunks), (int)(sizeof(float) * (size_t)na_max * nc));
+}
+
+int di_mloop_max_grid(int kind, int smem, int red_chunks, int prefetch, int* out) {
+  const void* f = pick_loop(kind, red_chunks, prefetch);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return (int)e;
+  int per_sm = 0, dev = 0, nsm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kDIThreads, smem);
+  if (e != cudaSuccess) return (int)e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
+  *out = per_sm * nsm;
+  return 0;
+}
+
+int di_launch_mloop(int kind, const DIArgs& a, int grid, int smem, int n_int, int S, int red_chunks, int prefetch,
+                    unsigned* bar, int* err, void* stream) {
+  void* args[] = {const_cast<DIArgs*>(&a), &n_int, &S, &bar, &err};
+  return (int)cudaLaunchCooperativeKernel(pick_loop(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args,
+                                          (size_t)smem, (cudaStream_t)stream);
+}
+
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
                     void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
@@ -520,7 +648,7 @@ int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, in
   cudaError_t e = cudaLaunchKernel(pick_acc(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args,
                                    (size_t)smem, s);
   if (e != cudaSuccess) return (int)e;
-  const int g2 = n_int < 4096 ? n_int : 4096;
+  const int g2 = n_int < kSolveGrid ? n_int : kSolveGrid;  // CTAs loop over the intervals
   const size_t sm2 = sizeof(float) * (size_t)a.na_max * (kind == 0 ? 3 : 12);
   if (kind == 0) di_msolve_kernel<ScalarMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
   else di_msolve_kernel<JonesMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);

@@ -87,6 +87,12 @@ int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, 
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
                     void* stream);
 int di_launch_advance(int* kbase, int by, void* stream);
+// persistent iteration loop (cooperative launch): up to S iterations from *kbase + 1, stops early
+// when no interval is active; bar = 2 zeroed words, *err set if a grid barrier timed out
+int di_mloop_smem(int kind, int na_max, int red_chunks);
+int di_mloop_max_grid(int kind, int smem, int red_chunks, int prefetch, int* out);
+int di_launch_mloop(int kind, const DIArgs& a, int grid, int smem, int n_int, int S, int red_chunks, int prefetch,
+                    unsigned* bar, int* err, void* stream);
 // accumulate launch alone (iteration a.k's work list) and the per-interval combine without a solve
 int di_launch_macc(int kind, const DIArgs& a, int grid, int smem, int red_chunks, int prefetch, void* stream);
 int di_launch_msum(int kind, const DIArgs& a, int i_lo, int n, float* tot_out, double* e_out, void* stream);

@@ -425,11 +425,12 @@ size_t gc_mlp_work_floats(const gc_mlp* net, int32_t n) {
 }
 
 int gc_mlp_forward_f32(const gc_mlp* net, const float* x, int32_t n, float* y, float* work, void* stream) {
-  if (!net || !x || !y || !work || n < 0) return GC_ERR_ARG;
+  if (!net || n < 0) return GC_ERR_ARG;
   const MlpDims d{net->in, net->h1, net->h2, net->out};
   int rc = check_dims(d);
   if (rc) return rc;
   if (n == 0) return GC_OK;
+  if (!net->params || !x || !y || !work) return GC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = forward(d, net->params, x, n, work, s))) return set_cuda_error((cudaError_t)rc, "mlp forward");
   const float* yw = work + (size_t)n * (d.h1 + d.h2);
@@ -466,11 +467,12 @@ int gc_mlp_train_step(gc_mlp* net, const float* x, const float* t, int32_t n, fl
 }
 
 int gc_mlp_infer_bf16(const gc_mlp* net, const float* x, int32_t n, float* y, void* stream) {
-  if (!net || !net->params_bf16 || !x || !y || n < 0) return GC_ERR_ARG;
+  if (!net || n < 0) return GC_ERR_ARG;
   const MlpDims d{net->in, net->h1, net->h2, net->out};
   int rc = check_dims(d);
   if (rc) return rc;
   if (n == 0) return GC_OK;
+  if (!net->params || !net->params_bf16 || !x || !y) return GC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t np = d.np();
   __nv_bfloat16* wq = reinterpret_cast<__nv_bfloat16*>(net->params_bf16);
@@ -492,8 +494,9 @@ int gc_mlp_infer_bf16(const gc_mlp* net, const float* x, int32_t n, float* y, vo
 
 int gc_ws_features_jones(const float* hist, int32_t hist_stride, const float* jhd, const float* jhj, const float* lead,
                          int32_t n, int32_t in_width, float* x, float* rot, void* stream) {
-  if (!hist || !jhd || !jhj || !lead || !x || !rot || n < 0 || in_width < 41 || hist_stride < 32) return GC_ERR_ARG;
+  if (n < 0 || in_width < 41 || hist_stride < 32) return GC_ERR_ARG;
   if (n == 0) return GC_OK;
+  if (!hist || !jhd || !jhj || !lead || !x || !rot) return GC_ERR_ARG;
   ws_features_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(hist, hist_stride, jhd, 8, jhj, 8, 0, lead, n,
                                                                        in_width, x, rot);
   g_launches++;
@@ -503,8 +506,9 @@ int gc_ws_features_jones(const float* hist, int32_t hist_stride, const float* jh
 
 int gc_ws_target_jones(const float* g1, const float* g_next, const float* rot, int32_t n, float* target,
                        void* stream) {
-  if (!g1 || !g_next || !rot || !target || n < 0) return GC_ERR_ARG;
+  if (n < 0) return GC_ERR_ARG;
   if (n == 0) return GC_OK;
+  if (!g1 || !g_next || !rot || !target) return GC_ERR_ARG;
   ws_target_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(g1, g_next, rot, n, target);
   g_launches++;
   cudaError_t e = cudaGetLastError();

@@ -84,9 +84,10 @@ def _hist_index(t_new, f, n_fb):
 def training_set(vis, model, grid: Grid, sols, lag, rng, n_samples=None):
     """(x [m, 48], target [m, 8]) float32 device tensors from solved, gauge-fixed intervals.
 
-    For every interval (t, f) with t >= 4 a lead l in 1..min(lag, t-3) is drawn; its history is
-    the solutions at t-l .. t-l-3 and its target the solution at t.  The features need C and H
-    at g1 = solution(t-l) on interval t's data: one accumulation pass over all intervals.
+    For every interval (t, f) with t >= 4 a lead l in 1..min(lag, t-3) is drawn (lag: the largest
+    lead the solve will ask for); its history is the solutions at t-l .. t-l-3 and its target the
+    solution at t.  The features need C and H at g1 = solution(t-l) on interval t's data: one
+    accumulation pass over all intervals.
     """
     n_int = grid.n_t * grid.n_fb
     na = grid.n_ant
@@ -207,9 +208,10 @@ class WavefrontResult:
     launches: int
 
 
-def solve_pipelined(vis, model, grid: Grid, lag, net, tol, max_iter, gate_tol=1e-4):
+def solve_pipelined(vis, model, grid: Grid, lag, net, tol, max_iter, gate_tol=0.0, max_lead=1):
     """The whole grid in one library call: waves of `lag` times join the running iteration as soon
-    as their history has passed the gate (gc_calibrate_di_jones2x2_wavefront)."""
+    as a history of 4 finished times lies within `max_lead` steps before them
+    (gc_calibrate_di_jones2x2_wavefront)."""
     n_int = grid.n_t * grid.n_fb
     dev = vis.device
     g = _identity(n_int * grid.n_ant, dev)
@@ -219,7 +221,7 @@ def solve_pipelined(vis, model, grid: Grid, lag, net, tol, max_iter, gate_tol=1e
     g, it, _, st, used, wave_k = api.calibrate_di_jones2x2_wavefront(vis, model, grid.layout(n_int), grid.n_t,
                                                                      grid.n_fb, lag, net, g, tol=tol,
                                                                      max_iter=max_iter, gate_tol=gate_tol,
-                                                                     lead_scale=LEAD_SCALE)
+                                                                     lead_scale=LEAD_SCALE, max_lead=max_lead)
     torch.cuda.synchronize(dev)
     sec = time.perf_counter() - t0
     r = WavefrontResult(g, it.cpu().numpy(), st.cpu().numpy(), used.cpu().numpy(), sec,

@@ -68,6 +68,26 @@ def test_adam_first_step_is_signed_learning_rate():
     np.testing.assert_allclose(v, 0.001 * g * g)
 
 
+def test_bf16_rounding():
+    """Round to nearest, ties to even, at 7 stored mantissa bits (ulp 2^-7 at 1)."""
+    u = 2.0 ** -7
+    cases = [(1.0, 1.0), (1 + u / 2, 1.0), (1 + u / 2 + 2 ** -20, 1 + u), (1 + 1.5 * u, 1 + 2 * u),
+             (1 + u, 1 + u), (-3.0, -3.0), (2.0 ** -130, 2.0 ** -130), (0.0, 0.0)]
+    for a, want in cases:
+        assert mlp.bf16(np.float32(a)) == np.float64(np.float32(want)), a
+
+
+def test_bf16_forward_is_close_to_fp64():
+    """The bfloat16 forward pass differs from FP64 by rounding only (a few parts in 1e3)."""
+    dims = (6, 16, 16, 3)
+    r = np.random.default_rng(8)
+    p = mlp.init_params(dims, r)
+    x = r.normal(size=(20, 6))
+    y = mlp.forward(p, dims, x)[2]
+    yb = mlp.forward_bf16(p, dims, x)
+    assert 0 < np.max(np.abs(yb - y)) <= 2e-2 * np.sqrt(np.mean(y ** 2))
+
+
 # ------------------------------------------------------------------------------------ features
 
 def test_step_feature_is_the_polarized_stefcal_step():
