@@ -151,6 +151,8 @@ def ncu_traffic(name, unit):
         return None
     if d.get('kernel_hash') != kernel_source_hash():
         return None
+    if unit == 'moments':
+        return d['dram_bytes_per_launch'] / d['baselines_per_launch']
     return d.get('dram_bytes_per_launch')
 
 
@@ -390,16 +392,18 @@ def run_gpu(args):
                         "kernel": "di_moment_kernel<JonesMom>", "ms_per_step": kmom / args.steps,
                         "peak_source": which}
         elif path_used == N_PATH_MOMENTS:
-            # dominant kernel: the moment-stream iteration kernel, 192 B of moments per active
-            # baseline per iteration (HBM-bound); the one-off moment pass is reported beside it
+            # dominant kernel: the moment-space iteration kernel, 192 B of moments per active
+            # baseline per iteration (HBM-bound); one launch per iteration (the CTA finishing an
+            # interval's last tile updates it); the one-off moment pass is reported beside it
             avg_launch_s = (kms / 1e3) / max(kl, 1)
             bytes_per_launch = kbi * MOMENT_BYTES / max(kl, 1)
             achieved = bytes_per_launch / avg_launch_s / 1e9
-            tpl = ncu_traffic('di_miter_jones_cfg2.json', 'moments')
+            tpb = ncu_traffic('di_macc_jones_cfg2.json', 'moments')   # DRAM bytes per active baseline
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"],
-                    "traffic": (tpl * (kbi / max(kl, 1)) / (b.n_int * int(b.n_bl[0]))) if tpl is not None else None,
-                    "kernel": "di_miter_kernel<JonesMom> (moment-space J^H D / diag J^H J + StefCal update)",
+                    "traffic": (tpb * kbi / max(kl, 1)) if tpb is not None else None,
+                    "kernel": "di_macc_kernel<JonesMom> (moment-space J^H D / diag J^H J; the last tile of an "
+                              "interval applies the StefCal update)",
                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6, "launches": kl,
                     "peak_source": which}
             mom_bytes = (b.n_rows * BYTES_PER_ROW + b.n_int * int(b.n_bl[0]) * MOMENT_BYTES) * args.steps

@@ -436,7 +436,7 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   GC_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (P.smem > max_smem) return GC_ERR_LIMIT;
   if (mode == 1) {
-    P.smem = di_macc_smem(kind, na_max, tune.red_chunks);
+    P.smem = di_macc_smem(kind, na_max, tune.red_chunks, tune.prefetch);
     if (P.smem > max_smem) return GC_ERR_LIMIT;
     GC_CUDA_I(di_macc_max_blocks_per_sm(kind, P.smem, tune.red_chunks, tune.prefetch, &per_sm));
   } else {
@@ -1149,8 +1149,9 @@ static int autotune_di(int kind, const void* vis, const void* model, const gc_la
   std::vector<Tune> cands;
   if (mode == 1) {
     for (int ch : {1, 4})
-      for (int pf : {0, 1})
+      for (int pf : {0, 1, 2})
         for (int bps : {0, 2}) {
+          if (pf == 2 && ch != 1) continue;  // the staged kernel reduces in one chunk
           Tune t;
           t.red_chunks = ch;
           t.prefetch = pf;

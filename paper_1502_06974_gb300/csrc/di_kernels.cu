@@ -210,6 +210,23 @@ __global__ void __launch_bounds__(kDIThreads) di_iter_kernel(const DIArgs a) {
 //   the next iteration's list (lists rotate over three buffers: launch k reads list k % 3,
 //   appends to (k + 1) % 3; the accumulate launch of k clears (k + 2) % 3).
 // ------------------------------------------------------------------------------------------
+// Device-scope acquire/release operations (cheaper than a sequentially consistent fence): an
+// atomic add whose release side orders the CTA's earlier writes (made visible to this thread by a
+// block barrier) before the add, and whose acquire side orders later reads after it.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Loads of data other CTAs of the same launch write (gains, auxiliaries, work lists) go through L2
 // (ld.global.cg) in the persistent loop kernel, whose CTAs do not meet at a launch boundary.
 template <bool COH>
@@ -226,6 +243,94 @@ __device__ __forceinline__ typename K::G ld_gain_c(const float* g) {
 #pragma unroll
     for (int c = 0; c < K::GW; ++c) v[c] = __ldcg(g + c);
     return K::ld_gain(v);
+  }
+}
+
+// An interval's tile partials summed in tile order with compensation, all (antenna, component)
+// pairs in parallel; antennas the baseline table does not reach get zeros.
+template <int NC>
+__device__ __forceinline__ void combine_tiles(const DIArgs& a, const float* scr, int na, int nat, int nch, int fi,
+                                              float* tot) {
+  for (int x = threadIdx.x; x < na * NC; x += blockDim.x) {
+    float s = 0.f, cc = 0.f;
+    if (x < nat * NC) {
+      int j = 0;
+      for (; j + 4 <= nch; j += 4) {
+        const float v0 = __ldcg(scr + a.item_scr[fi + j] + x), v1 = __ldcg(scr + a.item_scr[fi + j + 1] + x);
+        const float v2 = __ldcg(scr + a.item_scr[fi + j + 2] + x), v3 = __ldcg(scr + a.item_scr[fi + j + 3] + x);
+        kahan_add(s, cc, v0); kahan_add(s, cc, v1); kahan_add(s, cc, v2); kahan_add(s, cc, v3);
+      }
+      for (; j < nch; ++j) kahan_add(s, cc, __ldcg(scr + a.item_scr[fi + j] + x));
+    }
+    tot[x] = s - cc;
+  }
+}
+
+// Update of interval i at iteration k by one CTA (every thread calls it): its tiles' partials
+// summed in tile order with compensation, the GN step / average, the convergence test, gains and
+// auxiliaries written, and either the interval retired or its tiles appended to the next work
+// list.  `tot` holds [na_max][NC] floats.
+template <class MK, bool COH>
+__device__ __forceinline__ void solve_interval(const DIArgs& a, int k, int i, float* tot, double* red) {
+  using K = typename MK::K;
+  using G = typename K::G;
+  constexpr int NC = K::NC, GW = K::GW, AW = MK::AW, TB = kDIThreads;
+  const int tid = threadIdx.x;
+  const int nxt = (k + 1) % 3;
+  float* gains = static_cast<float*>(a.gains);
+  const float* scr = static_cast<const float*>(a.scratch);
+  const int na = a.n_ant[i];
+  const int64_t go = a.gain_off[i];
+  const int nat = a.tab_nant[a.itab[i]];
+  const int nch = a.n_chunks[i], fi = a.first_item[i];
+  combine_tiles<NC>(a, scr, na, nat, nch, fi, tot);
+  __syncthreads();
+  double d2 = 0.0, n2 = 0.0;
+  int sing = 0, nonfin = 0;
+  const int kl = k - (a.k0 ? ldc<COH>(a.k0 + i) : 0);  // the interval's own iteration number
+  const bool gn_step = (a.schedule == GC_SCHED_GN) || (kl & 1);
+  for (int an = tid; an < na; an += TB) {
+    const G old = ld_gain_c<K, COH>(gains + (go + an) * GW);
+    G g;
+    if (!K::solve(tot + an * NC, old, g)) sing = 1;
+    const G nw = gn_step ? g : K::avg(old, g);
+    d2 += (double)K::dist2(nw, old);
+    n2 += (double)K::norm2(nw);
+    if (!K::finite(nw)) nonfin = 1;
+    K::st_gain(a.gnew + (go + an) * GW, nw);   // staged until the interval's decision is known
+  }
+  block_reduce_step(d2, n2, sing, nonfin, red);
+  if (!nonfin)
+    for (int an = tid; an < na; an += TB) {
+      const G nw = K::ld_gain(a.gnew + (go + an) * GW);
+      K::st_gain(gains + (go + an) * GW, nw);
+      MK::aux(nw, a.aux + (go + an) * AW);
+    }
+  if (tid == 0) {
+    int st = -1;
+    if (nonfin) st = GC_ST_NONFINITE;
+    else if (d2 <= a.tol * a.tol * n2) st = GC_ST_OK;
+    else if (kl >= a.max_iter) st = GC_ST_NOT_CONVERGED;
+    if (a.gate && a.gate[i] == 0 && (st >= 0 || d2 <= a.gate_tol * a.gate_tol * n2)) a.gate[i] = kl;
+    if (st >= 0) {
+      a.active[i] = 0;
+      a.iters[i] = kl;
+      a.status[i] = st | (sing ? GC_ST_SINGULAR_FLAG : 0);
+      atomicSub(a.n_active, 1);
+    } else {
+      const int base = atomicAdd(&a.icount[nxt], nch);
+      for (int j = 0; j < nch; ++j) a.ilist[(size_t)nxt * a.n_items + base + j] = fi + j;
+    }
+  }
+  __syncthreads();
+}
+
+// Solve phase of iteration k (see di_msolve_kernel): CTAs loop over the intervals.
+template <class MK, bool COH>
+__device__ __forceinline__ void msolve_phase(const DIArgs& a, int k, int n_int, float* tot, double* red) {
+  for (int i = blockIdx.x; i < n_int; i += gridDim.x) {
+    if (ldc<COH>(a.active + i) == 0) continue;
+    solve_interval<MK, COH>(a, k, i, tot, red);
   }
 }
 
@@ -251,9 +356,13 @@ __device__ __forceinline__ void macc_phase(const DIArgs& a, int k, float* smem) 
     const int it = item(slot);
     const int i = a.item_int[it], t = a.item_s0[it];
     if (t * TB + tid < a.n_bl[i]) {
-      const float* src = a.moments + (a.mom_off[i] + (int64_t)t * TB) * NM + tid;
+      // tile layout [NM / 4][TB][4] (see mom_index): one 16-byte load per 4 components
+      const float4* src = reinterpret_cast<const float4*>(a.moments + (a.mom_off[i] + (int64_t)t * TB) * NM) + tid;
 #pragma unroll
-      for (int c = 0; c < NM; ++c) m[c] = __ldg(src + c * TB);
+      for (int g = 0; g < NM / 4; ++g) {
+        const float4 v = __ldg(src + g * TB);
+        m[4 * g] = v.x; m[4 * g + 1] = v.y; m[4 * g + 2] = v.z; m[4 * g + 3] = v.w;
+      }
     }
   };
   int slot = blockIdx.x;
@@ -322,83 +431,98 @@ __global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const D
   macc_phase<MK, CH, PF, false>(a, a.k + (a.kbase ? *a.kbase : 0), reinterpret_cast<float*>(smem_raw));
 }
 
-// An interval's tile partials summed in tile order with compensation, all (antenna, component)
-// pairs in parallel; antennas the baseline table does not reach get zeros.
-template <int NC>
-__device__ __forceinline__ void combine_tiles(const DIArgs& a, const float* scr, int na, int nat, int nch, int fi,
-                                              float* tot) {
-  for (int x = threadIdx.x; x < na * NC; x += blockDim.x) {
-    float s = 0.f, cc = 0.f;
-    if (x < nat * NC) {
-      int j = 0;
-      for (; j + 4 <= nch; j += 4) {
-        const float v0 = __ldcg(scr + a.item_scr[fi + j] + x), v1 = __ldcg(scr + a.item_scr[fi + j + 1] + x);
-        const float v2 = __ldcg(scr + a.item_scr[fi + j + 2] + x), v3 = __ldcg(scr + a.item_scr[fi + j + 3] + x);
-        kahan_add(s, cc, v0); kahan_add(s, cc, v1); kahan_add(s, cc, v2); kahan_add(s, cc, v3);
-      }
-      for (; j < nch; ++j) kahan_add(s, cc, __ldcg(scr + a.item_scr[fi + j] + x));
-    }
-    tot[x] = s - cc;
-  }
+// di_macc_staged_kernel: the accumulate launch with the moments staged through shared memory.
+// Each thread copies its own baseline's moments of the CTA's next tile with 16-byte asynchronous
+// copies (cp.async, no registers held) while the current tile is computed and reduced, so every
+// CTA keeps one tile (48 KB for 2x2) in flight from HBM at all times.  Two stages of one tile
+// each; the current stage is reused for the per-thread partials once its moments are in
+// registers.  Same arithmetic and reduction order as di_macc_kernel (slot-list reduction, CH = 1).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Solve phase of iteration k (see di_msolve_kernel); `tot` holds [na_max][NC] floats.
-template <class MK, bool COH>
-__device__ __forceinline__ void msolve_phase(const DIArgs& a, int k, int n_int, float* tot, double* red) {
+template <class MK>
+__global__ void __launch_bounds__(kDIThreads, 2) di_macc_staged_kernel(const DIArgs a) {
   using K = typename MK::K;
-  using G = typename K::G;
-  constexpr int NC = K::NC, GW = K::GW, AW = MK::AW, TB = kDIThreads;
+  constexpr int NC = K::NC, GW = K::GW, NM = MK::NM, NG = NM / 4, AW = MK::AW, TB = kDIThreads, PS = 2 * NC + 1;
+  // a stage holds a tile's moments ([NG][TB] float4) and, after they are read, its partials
+  // ([TB][PS] floats): SG float4 per thread
+  constexpr int SG = (NM > PS ? NM : PS + 3) / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* stage0 = reinterpret_cast<float4*>(smem_raw);   // [2][SG][TB] float4
   const int tid = threadIdx.x;
-  const int nxt = (k + 1) % 3;
-  float* gains = static_cast<float*>(a.gains);
-  const float* scr = static_cast<const float*>(a.scratch);
-  for (int i = blockIdx.x; i < n_int; i += gridDim.x) {
-    if (ldc<COH>(a.active + i) == 0) continue;
-    const int na = a.n_ant[i];
+  const int k = a.k + (a.kbase ? *a.kbase : 0);
+  const int cur = k % 3;
+  const bool fixed = a.xcount > 0;
+  const int* list = a.ilist + (size_t)cur * a.n_items;
+  const int n_list = fixed ? a.xcount : a.icount[cur];
+  if (!fixed && blockIdx.x == 0 && tid == 0) a.icount[(k + 2) % 3] = 0;
+  const float* gains = static_cast<const float*>(a.gains);
+  const int G = gridDim.x;
+  auto item = [&](int slot) { return fixed ? a.xbegin + slot : list[slot]; };
+  // copies this thread's moments of the tile at `slot` into stage st
+  auto issue = [&](int slot, int st) {
+    const int it = item(slot);
+    const int i = a.item_int[it], t = a.item_s0[it];
+    const float4* src = reinterpret_cast<const float4*>(a.moments + (a.mom_off[i] + (int64_t)t * TB) * NM) + tid;
+    float4* dst = stage0 + (size_t)st * SG * TB + tid;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) cp_async16(dst + g * TB, src + g * TB);
+    cp_async_commit();
+  };
+  int slot = blockIdx.x, st = 0;
+  if (slot < n_list) issue(slot, 0);
+  for (; slot < n_list; slot += G, st ^= 1) {
+    const int next = slot + G;
+    if (next < n_list) issue(next, st ^ 1);   // that stage was released by the barrier ending the last tile
+    const int it = item(slot);
+    const int i = a.item_int[it], t = a.item_s0[it];
+    const int nb = a.n_bl[i], bo = a.bl_off[i];
     const int64_t go = a.gain_off[i];
-    const int nat = a.tab_nant[a.itab[i]];
-    const int nch = a.n_chunks[i], fi = a.first_item[i];
-    combine_tiles<NC>(a, scr, na, nat, nch, fi, tot);
-    __syncthreads();
-    double d2 = 0.0, n2 = 0.0;
-    int sing = 0, nonfin = 0;
-    const int kl = k - (a.k0 ? ldc<COH>(a.k0 + i) : 0);  // the interval's own iteration number
-    const bool gn_step = (a.schedule == GC_SCHED_GN) || (kl & 1);
-    for (int an = tid; an < na; an += TB) {
-      const G old = ld_gain_c<K, COH>(gains + (go + an) * GW);
-      G g;
-      if (!K::solve(tot + an * NC, old, g)) sing = 1;
-      const G nw = gn_step ? g : K::avg(old, g);
-      d2 += (double)K::dist2(nw, old);
-      n2 += (double)K::norm2(nw);
-      if (!K::finite(nw)) nonfin = 1;
-      K::st_gain(a.gnew + (go + an) * GW, nw);   // staged until the interval's decision is known
+    const int b = t * TB + tid;
+    float pp[NC], pq[NC];
+    int p = 0, q = 0;
+    if (b < nb) { p = a.ant1[bo + b]; q = a.ant2[bo + b]; }
+    // every thread waits for its own copies of this tile (also past the last baseline: the stage is
+    // about to be overwritten with partials, so no copy into it may still be in flight)
+    if (next < n_list) cp_async_wait<1>(); else cp_async_wait<0>();
+    if (b < nb) {
+      const typename K::G gp = K::ld_gain(gains + (go + p) * GW), gq = K::ld_gain(gains + (go + q) * GW);
+      const float4* mine = stage0 + (size_t)st * SG * TB + tid;
+      float m[NM];
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const float4 v = mine[g * TB];
+        m[4 * g] = v.x; m[4 * g + 1] = v.y; m[4 * g + 2] = v.z; m[4 * g + 3] = v.w;
+      }
+      MK::partials(m, gp, gq, a.aux + (go + p) * AW, a.aux + (go + q) * AW, pp, pq);
     }
-    block_reduce_step(d2, n2, sing, nonfin, red);
-    if (!nonfin)
-      for (int an = tid; an < na; an += TB) {
-        const G nw = K::ld_gain(a.gnew + (go + an) * GW);
-        K::st_gain(gains + (go + an) * GW, nw);
-        MK::aux(nw, a.aux + (go + an) * AW);
-      }
-    if (tid == 0) {
-      int st = -1;
-      if (nonfin) st = GC_ST_NONFINITE;
-      else if (d2 <= a.tol * a.tol * n2) st = GC_ST_OK;
-      else if (kl >= a.max_iter) st = GC_ST_NOT_CONVERGED;
-      if (a.gate && a.gate[i] == 0 && (st >= 0 || d2 <= a.gate_tol * a.gate_tol * n2)) a.gate[i] = kl;
-      if (st >= 0) {
-        a.active[i] = 0;
-        a.iters[i] = kl;
-        a.status[i] = st | (sing ? GC_ST_SINGULAR_FLAG : 0);
-        atomicSub(a.n_active, 1);
-      } else {
-        const int base = atomicAdd(&a.icount[nxt], nch);
-        for (int j = 0; j < nch; ++j) a.ilist[(size_t)nxt * a.n_items + base + j] = fi + j;
-      }
+    __syncthreads();                                   // every thread has its moments: reuse the stage
+    float* part = reinterpret_cast<float*>(stage0 + (size_t)st * SG * TB);   // [TB][PS]
+    if (b < nb) {
+      float* my = part + tid * PS;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { my[c] = pp[c]; my[NC + c] = pq[c]; }
     }
     __syncthreads();
+    const int tab = a.itab[i];
+    const int nat = a.tab_nant[tab];
+    const int* off = a.csr_off + a.tab_base[tab] + t * (nat + 1);
+    float* scr = static_cast<float*>(a.scratch) + a.item_scr[it];
+    for (int x = tid; x < nat * NC; x += TB) {
+      const int an = x / NC, c = x - an * NC;
+      const int e1 = __ldg(off + an + 1);
+      float s = 0.f;
+      for (int e = __ldg(off + an); e < e1; ++e) s += part[__ldg(a.csr_ent + e) + c];
+      scr[x] = s;
+    }
+    __syncthreads();                                   // the stage is free for the copy after next
   }
+  cp_async_wait<0>();
 }
 
 template <class MK>
@@ -417,22 +541,18 @@ constexpr unsigned kBarrierSpins = 1u << 25;
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
+    const unsigned gen = ld_acquire(bar + 1);
     int ok = 1;
-    if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+    if (atom_add_acq_rel(bar, 1u) + 1u == gridDim.x) {
+      st_relaxed(bar, 0u);
+      atom_add_acq_rel(bar + 1, 1u);  // release: the reset and every arrival happen before the new generation
     } else {
       unsigned n = 0;
-      while (*vgen == gen) {
+      while (ld_acquire(bar + 1) == gen) {
         if (++n > kBarrierSpins) { ok = 0; atomicExch(err, 1); break; }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
-    __threadfence();
     *s_ok = ok && *(volatile int*)err == 0;
   }
   __syncthreads();
@@ -581,18 +701,26 @@ static void* pick(int kind, int dtype, int acc_only) {
   return acc_only ? kernel_ptr<double, JonesKind<double>, true>() : kernel_ptr<double, JonesKind<double>, false>();
 }
 
-static const void* pick_acc(int kind, int red_chunks, int prefetch) {
-  const bool c4 = red_chunks == kRedChunks, pf = prefetch != 0;
-  if (kind == 0) {
-    if (pf) return c4 ? (const void*)&di_macc_kernel<ScalarMom, kRedChunks, true> : (const void*)&di_macc_kernel<ScalarMom, 1, true>;
-    return c4 ? (const void*)&di_macc_kernel<ScalarMom, kRedChunks, false> : (const void*)&di_macc_kernel<ScalarMom, 1, false>;
-  }
-  if (pf) return c4 ? (const void*)&di_macc_kernel<JonesMom, kRedChunks, true> : (const void*)&di_macc_kernel<JonesMom, 1, true>;
-  return c4 ? (const void*)&di_macc_kernel<JonesMom, kRedChunks, false> : (const void*)&di_macc_kernel<JonesMom, 1, false>;
+// prefetch: 0 none, 1 the next tile's moments into registers, 2 staged through shared memory
+// (di_macc_staged_kernel, single-chunk reduction)
+template <class MK>
+static const void* pick_acc_k(int red_chunks, int prefetch) {
+  const bool c4 = red_chunks == kRedChunks;
+  if (prefetch == 2) return (const void*)&di_macc_staged_kernel<MK>;
+  if (prefetch) return c4 ? (const void*)&di_macc_kernel<MK, kRedChunks, true> : (const void*)&di_macc_kernel<MK, 1, true>;
+  return c4 ? (const void*)&di_macc_kernel<MK, kRedChunks, false> : (const void*)&di_macc_kernel<MK, 1, false>;
 }
 
-int di_macc_smem(int kind, int na_max, int red_chunks) {
-  const int nc = kind == 0 ? 3 : 12;
+static const void* pick_acc(int kind, int red_chunks, int prefetch) {
+  return kind == 0 ? pick_acc_k<ScalarMom>(red_chunks, prefetch) : pick_acc_k<JonesMom>(red_chunks, prefetch);
+}
+
+int di_macc_smem(int kind, int na_max, int red_chunks, int prefetch) {
+  const int nc = kind == 0 ? 3 : 12, nm = kind == 0 ? 4 : 48;
+  if (prefetch == 2) {
+    const int ps = 2 * nc + 1, sg = (nm > ps ? nm : ps + 3) / 4;
+    return (int)(sizeof(float) * 2 * 4 * (size_t)sg * kDIThreads);
+  }
   const int ch = red_chunks == kRedChunks ? kRedChunks : 1;
   return (int)(sizeof(float) * ((size_t)kDIThreads * (2 * nc + 1) + (size_t)na_max * nc * ch + (size_t)na_max * nc));
 }
@@ -607,7 +735,7 @@ int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, 
 constexpr int kSolveGrid = 1216;  // 8 CTAs on each of 152 SMs
 
 static const void* pick_loop(int kind, int red_chunks, int prefetch) {
-  const bool c4 = red_chunks == kRedChunks, pf = prefetch != 0;
+  const bool c4 = red_chunks == kRedChunks, pf = prefetch == 1;
   if (kind == 0) {
     if (pf) return c4 ? (const void*)&di_mloop_kernel<ScalarMom, kRedChunks, true> : (const void*)&di_mloop_kernel<ScalarMom, 1, true>;
     return c4 ? (const void*)&di_mloop_kernel<ScalarMom, kRedChunks, false> : (const void*)&di_mloop_kernel<ScalarMom, 1, false>;
@@ -618,7 +746,7 @@ static const void* pick_loop(int kind, int red_chunks, int prefetch) {
 
 int di_mloop_smem(int kind, int na_max, int red_chunks) {
   const int nc = kind == 0 ? 3 : 12;
-  return std::max(di_macc_smem(kind, na_max, red_chunks), (int)(sizeof(float) * (size_t)na_max * nc));
+  return std::max(di_macc_smem(kind, na_max, red_chunks, 0), (int)(sizeof(float) * (size_t)na_max * nc));
 }
 
 int di_mloop_max_grid(int kind, int smem, int red_chunks, int prefetch, int* out) {
@@ -657,8 +785,8 @@ int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, in
 
 int di_launch_macc(int kind, const DIArgs& a, int grid, int smem, int red_chunks, int prefetch, void* stream) {
   void* args[] = {const_cast<DIArgs*>(&a)};
-  return (int)cudaLaunchKernel(pick_acc(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args, (size_t)smem,
-                               (cudaStream_t)stream);
+  return (int)cudaLaunchKernel(pick_acc(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args,
+                               (size_t)smem, (cudaStream_t)stream);
 }
 
 int di_launch_msum(int kind, const DIArgs& a, int i_lo, int n, float* tot_out, double* e_out, void* stream) {

@@ -82,8 +82,9 @@ int di_smem_bytes(int kind, int dtype, int na_max);
 int di_max_blocks_per_sm(int kind, int dtype, int acc_only, int smem, int* out);
 int di_launch_iter(int kind, int dtype, int acc_only, const DIArgs& a, int grid, int smem, void* stream);
 int di_launch_init(const DIArgs& a, int n_int, int n_active0, void* stream);
-int di_macc_smem(int kind, int na_max, int red_chunks);
+int di_macc_smem(int kind, int na_max, int red_chunks, int prefetch);
 int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, int* out);
+// one iteration: the accumulate launch, then the solve launch
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
                     void* stream);
 int di_launch_advance(int* kbase, int by, void* stream);

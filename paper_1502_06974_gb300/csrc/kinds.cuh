@@ -167,13 +167,14 @@ struct JonesKind {
   }
 };
 
-// Moments are stored per interval in tiles of kMomTile baselines, component-major inside a tile
-// ([NM][kMomTile] floats), so that a tile is one contiguous block for a bulk copy and threads that
-// own consecutive baselines read consecutive words.  mom_off counts baseline slots (a multiple of
-// kMomTile per interval).
+// Moments are stored per interval in tiles of kMomTile baselines as [NM / 4][kMomTile][4] floats:
+// a tile is one contiguous block, and the thread that owns a baseline reads its components four at
+// a time with 16-byte loads while a warp's loads stay contiguous.  NM is a multiple of 4.
+// mom_off counts baseline slots (a multiple of kMomTile per interval).
 constexpr int kMomTile = 256;
 __host__ __device__ inline int64_t mom_index(int64_t mom_off, int b, int c, int nm) {
-  return (mom_off + (b & ~(kMomTile - 1))) * nm + (int64_t)c * kMomTile + (b & (kMomTile - 1));
+  return (mom_off + (b & ~(kMomTile - 1))) * nm + (int64_t)(c >> 2) * (4 * kMomTile) + (b & (kMomTile - 1)) * 4 +
+         (c & 3);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -81,10 +81,10 @@ __global__ void __launch_bounds__(kMomBl2 * kMomLanes2) di_moment_kernel(const M
 #pragma unroll
   for (int c = 0; c < NM; ++c) my[c] = m[c];
   __syncthreads();
-  // tiled layout: per 256-baseline tile, component-major [NM][256] (see mom_index)
+  // tiled layout [NM / 4][256][4] (see mom_index): consecutive threads write consecutive words
   const int nbt = min(kMomBl2, nb - tile * kMomBl2);
   for (int x = threadIdx.x; x < nbt * NM; x += blockDim.x) {
-    const int c = x / nbt, blx = x - c * nbt;
+    const int q = x >> 2, blx = q % nbt, c = (q / nbt) * 4 + (x & 3);
     float s = 0.f, cc = 0.f;
     for (int l = 0; l < kMomLanes2; ++l) kahan_add(s, cc, part[((size_t)l * kMomBl2 + blx) * NM + c]);
     a.moments[mom_index(a.mom_off[i], tile * kMomBl2 + blx, c, NM)] = s - cc;
