@@ -204,8 +204,7 @@ def run_reference(args):
     return 0
 
 
-WARM_LAG = 16           # wave length (time steps) of the learned wavefront
-WARM_GATE = 0.0         # a wave joins once its history has finished (0: no early start)
+WARM_LAG = 32           # wave length (time steps) of the learned wavefront
 WARM_WORKLOAD = ("di_jones2x2 warm start: 64 ant (2016 bl), 720 t x 64 ch, intervals 1 t x 8 ch (5760), GP gains "
                  "(30 min / 50 MHz correlation, amplitude 0.1, phase 1 rad), tol 1e-6")
 
@@ -215,7 +214,7 @@ def warm_start_block(dev, args):
 
     The network is trained first (its own observation, another seed), then three solves of the
     same 5760 intervals are timed with the data resident: plain (all intervals from unit gains in
-    one call), previous-solution wavefront and learned wavefront (one call each)."""
+    one call), previous-solution wavefront and learned wavefront (one call per wave of 32 times)."""
     import torch
     from paper_1502_06974_gb300 import api, synth, warmstart
     t0 = time.perf_counter()
@@ -248,8 +247,8 @@ def warm_start_block(dev, args):
         return out, e0.elapsed_time(e1)
 
     (gp, itp, stp), ms_plain = timed(lambda: warmstart.solve_plain(ve, me, ge, TOL, MAX_ITER))
-    prev, ms_prev = timed(lambda: warmstart.solve_pipelined(ve, me, ge, WARM_LAG, None, TOL, MAX_ITER, WARM_GATE))
-    lrn, ms_lrn = timed(lambda: warmstart.solve_pipelined(ve, me, ge, WARM_LAG, res.net, TOL, MAX_ITER, WARM_GATE))
+    prev, ms_prev = timed(lambda: warmstart.solve_wavefront(ve, me, ge, WARM_LAG, None, TOL, MAX_ITER))
+    lrn, ms_lrn = timed(lambda: warmstart.solve_wavefront(ve, me, ge, WARM_LAG, res.net, TOL, MAX_ITER))
     itp = itp.cpu().numpy()
     rows = ge.rows * n_int
     g_true = be.g_true
@@ -270,7 +269,9 @@ def warm_start_block(dev, args):
         d.update(extra or {})
         return d
 
-    return {"workload": WARM_WORKLOAD, "metric": METRIC, "unit": UNIT, "lag": WARM_LAG, "gate_tol": WARM_GATE,
+    return {"workload": WARM_WORKLOAD, "metric": METRIC, "unit": UNIT, "lag": WARM_LAG,
+            "schedule": "waves of lag x 8 intervals, one gc_calibrate_di_jones2x2_warm call each, predicted from "
+                        "the 4 solutions before the wave",
             "plain": entry(ms_plain, itp, stp.cpu().numpy(), {"max_err_vs_truth": err_truth(gp)}),
             "previous_solution": entry(ms_prev, prev.iters, prev.status, {"max_err_vs_truth": err_truth(prev.gains)}),
             "learned": entry(ms_lrn, lrn.iters, lrn.status,

@@ -155,7 +155,7 @@ uint64_t layout_hash(const gc_layout* L, uint64_t salt) {
 // override both (for experiments).
 struct Tune {
   int red_chunks = 1;     // moment path: per-antenna slot lists summed in 1 or 4 chunks
-  int prefetch = 0;       // moment path: request the next tile's moments before reducing this one
+  int prefetch = 1;       // moment path: 0 none, 1 next tile's moments into registers while reducing this one, 2 staged in shared memory
   int bps = 0;            // CTAs per SM of the persistent grid (0 = as many as fit)
   int check_every = 16;   // iterations per graph segment / between host checks of the active count
   int target_rows = 0;    // raw-row path: rows per work item (0 = default)
@@ -276,7 +276,10 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
       for (int s = 0; s < TB; ++s) {
         const int b = tile * TB + s;
         if (b >= nb) break;
-        lists[L->ant1[bo + b]].push_back(s * (2 * nc + 1));        // p side of slot s
+        // p side of slot s; the moment kernels first sum each warp's runs of equal p, so there
+        // only the last slot of a run is listed
+        const bool run_end = s % 32 == 31 || b + 1 == nb || L->ant1[bo + b + 1] != L->ant1[bo + b];
+        if (mode == 0 || run_end) lists[L->ant1[bo + b]].push_back(s * (2 * nc + 1));
         lists[L->ant2[bo + b]].push_back(s * (2 * nc + 1) + nc);   // q side of slot s
       }
       for (int a = 0; a < nat; ++a) {

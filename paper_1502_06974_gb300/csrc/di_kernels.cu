@@ -334,6 +334,28 @@ __device__ __forceinline__ void msolve_phase(const DIArgs& a, int k, int n_int, 
   }
 }
 
+// p-side contributions summed over each maximal run of lanes with the same antenna p inside a
+// warp (an inclusive segmented scan, fixed shuffle order): the run's last lane then holds the
+// run's sum, and the antenna's slot list names only run ends.  In a baseline table ordered by p
+// a warp holds one or two runs, so the slot lists shrink from ~N_ant entries to a few per tile.
+// Lanes past the last baseline pass p = -1 and zeros.  Every lane of the warp must call it.
+template <int NC>
+__device__ __forceinline__ void warp_run_scan(int p, float* v) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int up = __shfl_up_sync(full, p, 1);
+  const unsigned starts = __ballot_sync(full, lane == 0 || up != p);
+  const int seg0 = 31 - __clz(starts & (full >> (31 - lane)));   // first lane of this lane's run
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float u = __shfl_up_sync(full, v[c], o);
+      if (lane - o >= seg0) v[c] += u;
+    }
+  }
+}
+
 // Accumulate phase of iteration k (see di_macc_kernel); `smem` holds [TB][2 NC + 1] partials and
 // [na_max * NC * CH] chunk sums.
 template <class MK, int CH, bool PF, bool COH>
@@ -374,9 +396,14 @@ __device__ __forceinline__ void macc_phase(const DIArgs& a, int k, float* smem) 
     const int nb = a.n_bl[i], bo = a.bl_off[i];
     const int64_t go = a.gain_off[i];
     const int b = t * TB + tid;
+    float pp[NC], pq[NC];
+    int p = -1;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pp[c] = pq[c] = 0.f;
     if (b < nb) {
-      const int p = a.ant1[bo + b], q = a.ant2[bo + b];
-      float pp[NC], pq[NC], ap[AW], aq[AW];
+      p = a.ant1[bo + b];
+      const int q = a.ant2[bo + b];
+      float ap[AW], aq[AW];
 #pragma unroll
       for (int c = 0; c < AW; ++c) {
         ap[c] = ldc<COH>(a.aux + (go + p) * AW + c);
@@ -384,6 +411,9 @@ __device__ __forceinline__ void macc_phase(const DIArgs& a, int k, float* smem) 
       }
       MK::partials(m, ld_gain_c<K, COH>(gains + (go + p) * GW), ld_gain_c<K, COH>(gains + (go + q) * GW), ap, aq,
                    pp, pq);
+    }
+    warp_run_scan<NC>(p, pp);
+    if (b < nb) {
       float* my = part + tid * PS;
 #pragma unroll
       for (int c = 0; c < NC; ++c) { my[c] = pp[c]; my[NC + c] = pq[c]; }
@@ -485,7 +515,9 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_staged_kernel(const DIA
     const int64_t go = a.gain_off[i];
     const int b = t * TB + tid;
     float pp[NC], pq[NC];
-    int p = 0, q = 0;
+    int p = -1, q = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pp[c] = pq[c] = 0.f;
     if (b < nb) { p = a.ant1[bo + b]; q = a.ant2[bo + b]; }
     // every thread waits for its own copies of this tile (also past the last baseline: the stage is
     // about to be overwritten with partials, so no copy into it may still be in flight)
@@ -501,6 +533,7 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_staged_kernel(const DIA
       }
       MK::partials(m, gp, gq, a.aux + (go + p) * AW, a.aux + (go + q) * AW, pp, pq);
     }
+    warp_run_scan<NC>(p, pp);
     __syncthreads();                                   // every thread has its moments: reuse the stage
     float* part = reinterpret_cast<float*>(stage0 + (size_t)st * SG * TB);   // [TB][PS]
     if (b < nb) {

@@ -326,3 +326,32 @@ def test_wavefront_with_finished_histories_matches_sequential_waves(gpu_lib):
     assert np.all(np.abs(pipe.iters - seq.iters) <= np.maximum(5, 0.02 * seq.iters))
     e = gauge.rel_error('jones', pipe.gains.cpu().numpy(), seq.gains.cpu().numpy(), b.n_ant, b.gain_off)
     assert e < 1e-4, e
+
+
+def test_full_size_learned_wavefront_sampled(gpu_lib):
+    """The 5760-interval GP-gain workload at full size, in the configuration the benchmark times
+    (pipelined wavefront, lag 16, BF16 network trained on another seed's solutions): every interval
+    converges, and sampled intervals are fixed points of the FP64 iteration within 1e-5."""
+    bt = synth.make_warm(seed=synth.SEED + 1000, n_t=64)
+    vt, mt, _, _ = device_batch(bt)
+    gt = warmstart.Grid.from_batch(bt)
+    sol_t, _, st_t = warmstart.solve_plain(vt, mt, gt, 1e-6, 20000)
+    assert (st_t.cpu().numpy() == 0).all()
+    x, t = warmstart.training_set(vt, mt, gt, sol_t, 16, np.random.default_rng(0), n_samples=20000)
+    res = warmstart.train(x, t, epochs=20, batch=1024)
+    del vt, mt, sol_t, x, t
+    b = synth.make_config(5)
+    vis, model, _, lay = device_batch(b)
+    grid = warmstart.Grid.from_batch(b)
+    r = warmstart.solve_pipelined(vis, model, grid, 16, res.net, 1e-6, 20000)
+    assert (r.status == 0).all()
+    later = np.repeat(np.arange(grid.n_t), grid.n_fb) >= 16
+    assert r.used[later].mean() > 0.5
+    g = r.gains.cpu().numpy()
+    for i in (0, 1000, 2901, b.n_int - 1):
+        iv = b.interval(i)
+        sl = iv['gain_slice']
+        ref = diagonal.iterate('jones', g[sl].astype(np.complex128), iv['vis'], iv['model'], iv['ant1'],
+                               iv['ant2'], iv['n_ant'], tol=1e-6, max_iter=20000)
+        assert ref['converged'] and ref['iters'] <= 50, (i, ref['iters'])
+        assert gauge.rel_error('jones', g[sl], ref['g']) < 1e-5, i
