@@ -393,9 +393,9 @@ def run_gpu(args):
                         "kernel": "di_moment_kernel<JonesMom>", "ms_per_step": kmom / args.steps,
                         "peak_source": which}
         elif path_used == N_PATH_MOMENTS:
-            # dominant kernel: the moment-space iteration kernel, 192 B of moments per active
-            # baseline per iteration (HBM-bound); one launch per iteration (the CTA finishing an
-            # interval's last tile updates it); the one-off moment pass is reported beside it
+            # dominant kernel: the moment-space accumulate kernel, 192 B of moments per active
+            # baseline per iteration (HBM-bound), timed together with the solve launch of the same
+            # iteration; the one-off moment pass is reported beside it
             avg_launch_s = (kms / 1e3) / max(kl, 1)
             bytes_per_launch = kbi * MOMENT_BYTES / max(kl, 1)
             achieved = bytes_per_launch / avg_launch_s / 1e9
@@ -403,9 +403,11 @@ def run_gpu(args):
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"],
                     "traffic": (tpb * kbi / max(kl, 1)) if tpb is not None else None,
-                    "kernel": "di_macc_kernel<JonesMom> (moment-space J^H D / diag J^H J; the last tile of an "
-                              "interval applies the StefCal update)",
+                    "kernel": "di_macc_kernel<JonesMom> + di_msolve_kernel (one iteration: moment-space J^H D / "
+                              "diag J^H J per tile, then the per-interval StefCal update)",
                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6, "launches": kl,
+                    "timed": "each iteration's accumulate + solve launches (CUDA events around the graph "
+                             "segments on the call's stream); 'launches' counts iterations",
                     "peak_source": which}
             mom_bytes = (b.n_rows * BYTES_PER_ROW + b.n_int * int(b.n_bl[0]) * MOMENT_BYTES) * args.steps
             roof_mom = {"bound": "hbm", "achieved": mom_bytes / (kmom / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
