@@ -160,6 +160,7 @@ struct Tune {
   int check_every = 16;   // iterations per graph segment / between host checks of the active count
   int target_rows = 0;    // raw-row path: rows per work item (0 = default)
   int graph = 1;          // capture iteration segments in a CUDA graph
+  int step1 = 0;          // moment path: one cooperative launch per iteration (update + accumulate)
   int loop = 0;           // moment path: run segments in one persistent cooperative launch instead
                           // (grid barriers between the phases; measured slower than graph segments)
 };
@@ -201,12 +202,14 @@ static Tune effective_tune(int kind, int dtype, int mode, const gc_layout* L) {
   t.target_rows = env_int(kind == 0 ? "GAINCAL_TARGET_ROWS_SCALAR" : "GAINCAL_TARGET_ROWS_JONES", t.target_rows);
   t.graph = env_int("GAINCAL_GRAPH", t.graph);
   t.loop = env_int("GAINCAL_LOOP", t.loop);
+  t.step1 = env_int("GAINCAL_STEP1", t.step1);
   return t;
 }
 
 static uint64_t tune_hash(const Tune& t) {
   return (uint64_t)t.red_chunks * 1000003ull ^ (uint64_t)t.prefetch * 7919ull ^ (uint64_t)t.bps * 104729ull ^
-         (uint64_t)t.target_rows * 1299709ull ^ (uint64_t)t.check_every * 15485863ull ^ (uint64_t)t.loop * 32452843ull;
+         (uint64_t)t.target_rows * 1299709ull ^ (uint64_t)t.check_every * 15485863ull ^ (uint64_t)t.loop * 32452843ull ^
+         (uint64_t)t.step1 * 49979687ull;
 }
 
 // ------------------------------------------------------------------------------------ DI plan
@@ -222,6 +225,7 @@ struct DIPlan {
   double* chi2_out = nullptr;
   int grid = 0, smem = 0;
   int lgrid = 0, lsmem = 0;  // persistent loop kernel (moment mode): co-resident grid, shared memory
+  int sgrid = 0, ssmem = 0;  // single-launch iteration kernel (moment mode)
   // moment-stream mode: moment-pass items (interval, 32 baselines), per-item chi^2 bookkeeping
   int mode = 0;
   int n_mitems = 0;
@@ -457,6 +461,11 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
     GC_CUDA_I(di_mloop_max_grid(kind, P.lsmem, tune.red_chunks, tune.prefetch, &cap));
     if (tune.bps > 0 && tune.bps * nsm < cap) cap = tune.bps * nsm;
     P.lgrid = cap;
+    P.ssmem = di_mstep1_smem(kind, na_max, tune.red_chunks);
+    if (P.ssmem > max_smem) return GC_ERR_LIMIT;
+    GC_CUDA_I(di_mstep1_max_grid(kind, P.ssmem, tune.red_chunks, tune.prefetch, &cap));
+    if (tune.bps > 0 && tune.bps * nsm < cap) cap = tune.bps * nsm;
+    P.sgrid = cap;
   }
   return GC_OK;
 }
@@ -723,6 +732,17 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     if ((rc = ws_get("di_scratch", (size_t)P->scr_elems * (opt->dtype == GC_DTYPE_C64 ? 4 : 8), &scr))) return rc;
     a.scratch = scr;
   }
+  // single-launch iterations: publication flags, an error word, and work list 2 first
+  const bool s1 = mode == 1 && P->tune.step1 && !P->tune.loop && P->sgrid > 0;
+  int* s1err = nullptr;
+  if (s1) {
+    void* fv = nullptr;
+    if ((rc = ws_get("di_flags", (size_t)(P->n_int + 4) * sizeof(int32_t), &fv))) return rc;
+    a.flag = (int32_t*)fv;
+    s1err = a.flag + P->n_int;
+    GC_CUDA(cudaMemsetAsync(s1err, 0, sizeof(int32_t), s));
+    a.first_list = 2;
+  }
   GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
   g_launches++;
   double mom_ms = 0.0;
@@ -761,33 +781,25 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   if ((rc = pinned_flag(&flag))) return rc;
   const Tune& tn = P->tune;
   const int S = tn.check_every;
-  const int per_iter = mode == 1 ? 2 : 1;
+  const int per_iter = mode == 1 && !s1 ? 2 : 1;
+  // the single-launch scheme updates iteration k in launch k + 1: one more launch at the end
+  const int last_k = opt->max_iter + (s1 ? 1 : 0);
   auto launch_iter = [&](const DIArgs& x, cudaStream_t st) -> int {
+    if (s1) return di_launch_mstep1(kind, x, P->sgrid, P->ssmem, P->n_int, tn.red_chunks, tn.prefetch, s1err, st);
     return mode == 1 ? di_launch_mstep(kind, x, P->grid, P->smem, P->n_int, tn.red_chunks, tn.prefetch, st)
                      : di_launch_iter(kind, opt->dtype, 0, x, P->grid, P->smem, st);
   };
+  auto check_s1 = [&]() -> int {
+    if (!s1) return GC_OK;
+    GC_CUDA(cudaMemcpyAsync(flag + 4, s1err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (flag[4]) return cuda_fail(cudaErrorLaunchTimeout, "wait for an interval's update timed out");
+    return GC_OK;
+  };
   Profiler prof(opt->profile != 0, S);
   if ((rc = prof.init())) return rc;
-  if (mode == 1 && tn.loop && P->lgrid > 0) {
-    prof.weight = S;
-    unsigned* bar = nullptr;
-    if ((rc = loop_barrier(&bar, s))) return rc;
-    int* err = (int*)(bar + 2);
-    for (int k0 = 0; k0 < opt->max_iter; k0 += S) {
-      if ((rc = prof.before(s))) return rc;
-      GC_CUDA_I(di_launch_mloop(kind, a, P->lgrid, P->lsmem, P->n_int, S, tn.red_chunks, tn.prefetch, bar, err,
-                                stream));
-      if ((rc = prof.after(s))) return rc;
-      g_launches++;
-      GC_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-      GC_CUDA(cudaMemcpyAsync(flag + 1, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-      GC_CUDA(cudaStreamSynchronize(s));
-      if ((rc = prof.drain())) return rc;
-      if (flag[1]) return cuda_fail(cudaErrorLaunchTimeout, "grid barrier of the iteration loop timed out");
-      if (*flag <= 0) break;
-    }
-  } else if (tn.graph) {
-    prof.weight = S;
+  bool use_graph = tn.graph != 0;
+  if (use_graph && !(mode == 1 && tn.loop && P->lgrid > 0)) {
     // One segment = S iterations captured once (k = *kbase + 1 .. *kbase + S) plus a node that
     // advances *kbase; segments are relaunched until no interval is active.  Iterations past
     // max_iter find no active interval and do nothing.
@@ -809,15 +821,42 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
       cudaGraph_t g = nullptr;
       const cudaError_t ee = cudaStreamEndCapture(cs, &g);
       cudaStreamDestroy(cs);
-      if (crc) return cuda_fail((cudaError_t)crc, "capture of the iteration segment");
-      if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
-      const cudaError_t ie = cudaGraphInstantiate(&P->gexec, g, 0);
-      cudaGraphDestroy(g);
-      if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
-      P->gargs = ga;
-      P->gS = S;
+      cudaError_t ie = cudaSuccess;
+      if (!crc && ee == cudaSuccess) ie = cudaGraphInstantiate(&P->gexec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (crc || ee != cudaSuccess || ie != cudaSuccess) {
+        if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+        if (!s1)
+          return cuda_fail(crc ? (cudaError_t)crc : (ee != cudaSuccess ? ee : ie), "capture of the iteration segment");
+        cudaGetLastError();  // a cooperative launch that cannot be captured: launch one by one instead
+        use_graph = false;
+      } else {
+        P->gargs = ga;
+        P->gS = S;
+      }
     }
+  }
+  if (mode == 1 && tn.loop && P->lgrid > 0) {
+    prof.weight = S;
+    unsigned* bar = nullptr;
+    if ((rc = loop_barrier(&bar, s))) return rc;
+    int* err = (int*)(bar + 2);
     for (int k0 = 0; k0 < opt->max_iter; k0 += S) {
+      if ((rc = prof.before(s))) return rc;
+      GC_CUDA_I(di_launch_mloop(kind, a, P->lgrid, P->lsmem, P->n_int, S, tn.red_chunks, tn.prefetch, bar, err,
+                                stream));
+      if ((rc = prof.after(s))) return rc;
+      g_launches++;
+      GC_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(flag + 1, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaStreamSynchronize(s));
+      if ((rc = prof.drain())) return rc;
+      if (flag[1]) return cuda_fail(cudaErrorLaunchTimeout, "grid barrier of the iteration loop timed out");
+      if (*flag <= 0) break;
+    }
+  } else if (use_graph) {
+    prof.weight = S;
+    for (int k0 = 0; k0 < last_k; k0 += S) {
       if ((rc = prof.before(s))) return rc;
       GC_CUDA(cudaGraphLaunch(P->gexec, s));
       if ((rc = prof.after(s))) return rc;
@@ -825,19 +864,21 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
       GC_CUDA(cudaMemcpyAsync(flag, a.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
       GC_CUDA(cudaStreamSynchronize(s));
       if ((rc = prof.drain())) return rc;
+      if ((rc = check_s1())) return rc;
       if (*flag <= 0) break;
     }
   } else {
-    for (int k = 1; k <= opt->max_iter; ++k) {
+    for (int k = 1; k <= last_k; ++k) {
       a.k = k;
       if ((rc = prof.before(s))) return rc;
       GC_CUDA_I(launch_iter(a, s));
       if ((rc = prof.after(s))) return rc;
       g_launches += per_iter;
-      if (k % S == 0 || k == opt->max_iter) {
+      if (k % S == 0 || k == last_k) {
         GC_CUDA(cudaMemcpyAsync(flag, a.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         GC_CUDA(cudaStreamSynchronize(s));
         if ((rc = prof.drain())) return rc;
+        if ((rc = check_s1())) return rc;
         if (*flag <= 0) break;
       }
     }

@@ -268,15 +268,14 @@ __device__ __forceinline__ void combine_tiles(const DIArgs& a, const float* scr,
 
 // Update of interval i at iteration k by one CTA (every thread calls it): its tiles' partials
 // summed in tile order with compensation, the GN step / average, the convergence test, gains and
-// auxiliaries written, and either the interval retired or its tiles appended to the next work
-// list.  `tot` holds [na_max][NC] floats.
+// auxiliaries written, and either the interval retired or its tiles appended to work list nxt.
+// `tot` holds [na_max][NC] floats.
 template <class MK, bool COH>
-__device__ __forceinline__ void solve_interval(const DIArgs& a, int k, int i, float* tot, double* red) {
+__device__ __forceinline__ void solve_interval(const DIArgs& a, int k, int i, float* tot, double* red, int nxt) {
   using K = typename MK::K;
   using G = typename K::G;
   constexpr int NC = K::NC, GW = K::GW, AW = MK::AW, TB = kDIThreads;
   const int tid = threadIdx.x;
-  const int nxt = (k + 1) % 3;
   float* gains = static_cast<float*>(a.gains);
   const float* scr = static_cast<const float*>(a.scratch);
   const int na = a.n_ant[i];
@@ -330,7 +329,7 @@ template <class MK, bool COH>
 __device__ __forceinline__ void msolve_phase(const DIArgs& a, int k, int n_int, float* tot, double* red) {
   for (int i = blockIdx.x; i < n_int; i += gridDim.x) {
     if (ldc<COH>(a.active + i) == 0) continue;
-    solve_interval<MK, COH>(a, k, i, tot, red);
+    solve_interval<MK, COH>(a, k, i, tot, red, (k + 1) % 3);
   }
 }
 
@@ -565,6 +564,163 @@ __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, i
   msolve_phase<MK, false>(a, a.k + (a.kbase ? *a.kbase : 0), n_int, reinterpret_cast<float*>(smem_raw), red);
 }
 
+// di_mstep1_kernel: one launch per iteration (cooperative launch, so every CTA is resident).
+//   Phase S: each CTA updates its intervals from the previous iteration's tile partials (the solve
+//   of di_msolve_kernel), appends the survivors' tiles to work list (k-1) % 3, and publishes
+//   flag[i] = k (release), or -k when the interval stopped.  An interval in its first iteration
+//   is only published and listed.
+//   Phase A: the accumulate of iteration k over the tiles of list (k+1) % 3 (the survivors of the
+//   update before last, a superset of the current ones); a tile waits (acquire, bounded) for its
+//   interval's flag, skips the interval if it stopped, and otherwise runs exactly the accumulate
+//   of di_macc_kernel.  Tiles of intervals updated early start while other CTAs still solve.
+//   Lists rotate over three buffers: launch k clears list k % 3 (read two launches ago).
+//   Same arithmetic and order as the two-launch iteration, so the results are bitwise equal.
+__device__ __forceinline__ int ld_acquire_i(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_i(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+constexpr unsigned kFlagSpins = 1u << 24;
+
+template <class MK, int CH, bool PF>
+__global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_mstep1_kernel(const DIArgs a, int n_int, int* err) {
+  using K = typename MK::K;
+  constexpr int NC = K::NC, GW = K::GW, NM = MK::NM, AW = MK::AW, TB = kDIThreads, PS = 2 * NC + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* part = reinterpret_cast<float*>(smem_raw);   // [TB][PS]
+  float* ps = part + TB * PS;                           // [na_max * NC * CH]
+  float* tot = ps + (size_t)a.na_max * NC * CH;         // [na_max][NC]
+  __shared__ double red[96];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x;
+  const int k = a.k + *a.kbase;
+  if (blockIdx.x == 0 && tid == 0) a.icount[k % 3] = 0;
+  // ---- phase S: the update of iteration k - 1
+  const int ls = (k + 2) % 3;  // = (k - 1) % 3
+  for (int i = blockIdx.x; i < n_int; i += gridDim.x) {
+    if (__ldcg(a.active + i) == 0) {  // stopped earlier or without data: any tile of it is skipped
+      if (tid == 0) st_release_i(a.flag + i, -k);
+      continue;
+    }
+    const int kp = k - 1 - (a.k0 ? __ldcg(a.k0 + i) : 0);  // the interval's own number of the previous iteration
+    if (kp >= 1) {
+      solve_interval<MK, true>(a, k - 1, i, tot, red, ls);
+    } else if (tid == 0) {
+      const int nch = a.n_chunks[i], fi = a.first_item[i];
+      const int base = atomicAdd(&a.icount[ls], nch);
+      for (int j = 0; j < nch; ++j) a.ilist[(size_t)ls * a.n_items + base + j] = fi + j;
+    }
+    __syncthreads();
+    if (tid == 0) st_release_i(a.flag + i, __ldcg(a.active + i) ? k : -k);
+  }
+  // ---- phase A: the accumulate of iteration k
+  const int la = (k + 1) % 3;
+  const int* list = a.ilist + (size_t)la * a.n_items;
+  const int n_list = __ldcg(a.icount + la);
+  const float* gains = static_cast<const float*>(a.gains);
+  float m[NM];
+  auto fetch = [&](int slot) {
+    const int it = __ldcg(list + slot);
+    const int i = a.item_int[it], t = a.item_s0[it];
+    if (t * TB + tid < a.n_bl[i]) {
+      const float4* src = reinterpret_cast<const float4*>(a.moments + (a.mom_off[i] + (int64_t)t * TB) * NM) + tid;
+#pragma unroll
+      for (int g = 0; g < NM / 4; ++g) {
+        const float4 v = __ldg(src + g * TB);
+        m[4 * g] = v.x; m[4 * g + 1] = v.y; m[4 * g + 2] = v.z; m[4 * g + 3] = v.w;
+      }
+    }
+  };
+  int slot = blockIdx.x;
+  if (PF && slot < n_list) fetch(slot);
+  while (slot < n_list) {
+    if (!PF) fetch(slot);
+    const int it = __ldcg(list + slot);
+    const int i = a.item_int[it], t = a.item_s0[it];
+    const int next = slot + gridDim.x;
+    if (tid == 0) {
+      int f = ld_acquire_i(a.flag + i);
+      unsigned n = 0;
+      while (f != k && f != -k) {
+        if (++n > kFlagSpins) { atomicExch(err, 1); f = 0; break; }
+        __nanosleep(64);
+        f = ld_acquire_i(a.flag + i);
+      }
+      s_flag = f;
+    }
+    __syncthreads();
+    const int f = s_flag;
+    if (f == 0) return;            // a wait timed out: the host reports the error
+    if (f != k) {                  // the interval stopped at the last update
+      if (PF && next < n_list) fetch(next);
+      __syncthreads();
+      slot = next;
+      continue;
+    }
+    const int nb = a.n_bl[i], bo = a.bl_off[i];
+    const int64_t go = a.gain_off[i];
+    const int b = t * TB + tid;
+    float pp[NC], pq[NC];
+    int p = -1;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pp[c] = pq[c] = 0.f;
+    if (b < nb) {
+      p = a.ant1[bo + b];
+      const int q = a.ant2[bo + b];
+      float ap[AW], aq[AW];
+#pragma unroll
+      for (int c = 0; c < AW; ++c) {
+        ap[c] = __ldcg(a.aux + (go + p) * AW + c);
+        aq[c] = __ldcg(a.aux + (go + q) * AW + c);
+      }
+      MK::partials(m, ld_gain_c<K, true>(gains + (go + p) * GW), ld_gain_c<K, true>(gains + (go + q) * GW), ap,
+                   aq, pp, pq);
+    }
+    warp_run_scan<NC>(p, pp);
+    if (b < nb) {
+      float* my = part + tid * PS;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { my[c] = pp[c]; my[NC + c] = pq[c]; }
+    }
+    if (PF && next < n_list) fetch(next);
+    __syncthreads();
+    const int tab = a.itab[i];
+    const int nat = a.tab_nant[tab];
+    const int* off = a.csr_off + a.tab_base[tab] + t * (nat + 1);
+    float* scr = static_cast<float*>(a.scratch) + a.item_scr[it];
+    if (CH == 1) {
+      for (int x = tid; x < nat * NC; x += TB) {
+        const int an = x / NC, c = x - an * NC;
+        const int e1 = __ldg(off + an + 1);
+        float s = 0.f;
+        for (int e = __ldg(off + an); e < e1; ++e) s += part[__ldg(a.csr_ent + e) + c];
+        scr[x] = s;
+      }
+    } else {
+      for (int x = tid; x < nat * NC * CH; x += TB) {
+        const int ch = x % CH, r = x / CH, an = r / NC, c = r - an * NC;
+        const int e0 = __ldg(off + an), len = __ldg(off + an + 1) - e0;
+        const int b0 = e0 + (len * ch) / CH, b1 = e0 + (len * (ch + 1)) / CH;
+        float s = 0.f;
+        for (int e = b0; e < b1; ++e) s += part[__ldg(a.csr_ent + e) + c];
+        ps[x] = s;
+      }
+      __syncthreads();
+      for (int x = tid; x < nat * NC; x += TB) {
+        float s = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < CH; ++ch) s += ps[x * CH + ch];
+        scr[x] = s;
+      }
+    }
+    __syncthreads();
+    slot = next;
+  }
+}
+
 // Grid-wide barrier of the persistent loop kernel (a cooperative launch, so every CTA is
 // resident): arrival counter bar[0], generation bar[1].  The wait is bounded: after
 // kBarrierSpins polls the CTA records the timeout in *err and the kernel returns, so a barrier
@@ -669,12 +825,17 @@ __global__ void di_init_kernel(const DIArgs a, int n_int, int n_active0) {
     if (a.kbase) *a.kbase = 0;
     a.qhead[0] = 0;
     a.qhead[1] = 0;
-    if (a.icount) { a.icount[1] = a.n_items; a.icount[2] = 0; a.icount[0] = 0; }
+    if (a.icount) {
+      a.icount[0] = a.icount[1] = a.icount[2] = 0;
+      a.icount[a.first_list ? a.first_list : 1] = a.n_items;
+    }
   }
   if (a.ilist)  // iteration 1 takes every item
-    for (int j = i; j < a.n_items; j += gridDim.x * blockDim.x) a.ilist[(size_t)1 * a.n_items + j] = j;
+    for (int j = i; j < a.n_items; j += gridDim.x * blockDim.x)
+      a.ilist[(size_t)(a.first_list ? a.first_list : 1) * a.n_items + j] = j;
   if (i < n_int) {
     const int64_t rows = (int64_t)a.n_samp[i] * a.n_bl[i];
+    if (a.flag) a.flag[i] = 0;
     a.active[i] = rows > 0 ? 1 : 0;
     a.iters[i] = 0;
     a.status[i] = rows > 0 ? GC_ST_NOT_CONVERGED : GC_ST_NODATA;
@@ -800,6 +961,49 @@ int di_launch_mloop(int kind, const DIArgs& a, int grid, int smem, int n_int, in
   void* args[] = {const_cast<DIArgs*>(&a), &n_int, &S, &bar, &err};
   return (int)cudaLaunchCooperativeKernel(pick_loop(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args,
                                           (size_t)smem, (cudaStream_t)stream);
+}
+
+static const void* pick_step1(int kind, int red_chunks, int prefetch) {
+  const bool c4 = red_chunks == kRedChunks, pf = prefetch == 1;
+  if (kind == 0) {
+    if (pf) return c4 ? (const void*)&di_mstep1_kernel<ScalarMom, kRedChunks, true> : (const void*)&di_mstep1_kernel<ScalarMom, 1, true>;
+    return c4 ? (const void*)&di_mstep1_kernel<ScalarMom, kRedChunks, false> : (const void*)&di_mstep1_kernel<ScalarMom, 1, false>;
+  }
+  if (pf) return c4 ? (const void*)&di_mstep1_kernel<JonesMom, kRedChunks, true> : (const void*)&di_mstep1_kernel<JonesMom, 1, true>;
+  return c4 ? (const void*)&di_mstep1_kernel<JonesMom, kRedChunks, false> : (const void*)&di_mstep1_kernel<JonesMom, 1, false>;
+}
+
+int di_mstep1_smem(int kind, int na_max, int red_chunks) {
+  return di_macc_smem(kind, na_max, red_chunks, 0);  // partials, chunk sums and the solve's [na_max][NC]
+}
+
+int di_mstep1_max_grid(int kind, int smem, int red_chunks, int prefetch, int* out) {
+  const void* f = pick_step1(kind, red_chunks, prefetch);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return (int)e;
+  int per_sm = 0, dev = 0, nsm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kDIThreads, smem)) != cudaSuccess) return (int)e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
+  *out = per_sm * nsm;
+  return 0;
+}
+
+// one iteration in one cooperative launch (the launch attribute keeps it capturable in a graph)
+int di_launch_mstep1(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch, int* err,
+                     void* stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kDIThreads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {const_cast<DIArgs*>(&a), &n_int, &err};
+  return (int)cudaLaunchKernelExC(&cfg, pick_step1(kind, red_chunks, prefetch), args);
 }
 
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,

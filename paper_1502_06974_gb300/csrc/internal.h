@@ -75,6 +75,10 @@ struct DIArgs {
   // its iteration's work list (and leaves the work lists alone)
   int32_t xbegin;
   int32_t xcount;
+  // single-launch iteration (di_mstep1_kernel): per-interval publication flags, and the work list
+  // the init launch fills (0 = list 1, the two-launch scheme's first list)
+  int32_t* flag;
+  int32_t first_list;
 };
 
 // Launchers implemented in di_kernels.cu.  kind: 0 scalar, 1 jones.  Return cudaError_t as int.
@@ -87,6 +91,12 @@ int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, 
 // one iteration: the accumulate launch, then the solve launch
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
                     void* stream);
+// one iteration in one cooperative launch: the update of the previous iteration and, interval by
+// interval as each update is published, the accumulate of this one (*err set if a wait timed out)
+int di_mstep1_smem(int kind, int na_max, int red_chunks);
+int di_mstep1_max_grid(int kind, int smem, int red_chunks, int prefetch, int* out);
+int di_launch_mstep1(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch, int* err,
+                     void* stream);
 int di_launch_advance(int* kbase, int by, void* stream);
 // persistent iteration loop (cooperative launch): up to S iterations from *kbase + 1, stops early
 // when no interval is active; bar = 2 zeroed words, *err set if a grid barrier timed out

@@ -268,22 +268,25 @@ def test_moments_multi_tile_intervals(gpu_lib, monkeypatch, chunks):
 
 @pytest.mark.parametrize("path", [N.GC_PATH_STREAM, N.GC_PATH_MOMENTS])
 def test_graph_and_plain_loops_agree(gpu_lib, monkeypatch, path):
-    """Graph-captured iteration segments, one launch per iteration, the persistent loop kernel and
-    the accumulate variants give bitwise identical results, including a max_iter that is not a
-    multiple of the segment length."""
+    """Graph-captured iteration segments, one launch per iteration, the persistent loop kernel, the
+    single-launch iteration and the accumulate variants give bitwise identical results, including a
+    max_iter that is not a multiple of the segment length."""
     b = synth.make_config(2, small=True)
     vis, model, g0, lay = device_batch(b)
     out = []
     # (graph, persistent loop): one launch per iteration, graph segments, and (moment path) the
     # persistent cooperative loop kernel with grid barriers between the two phases
-    # and (moment path) the accumulate kernel with register prefetch or shared-memory staging
-    modes = [("0", "0", "0"), ("1", "0", "0")]
+    # and (moment path) the accumulate kernel with register prefetch or shared-memory staging, and
+    # one cooperative launch per iteration (update of k - 1, then accumulate of k) vs two launches
+    modes = [("0", "0", "0", "0"), ("1", "0", "0", "0")]
     if path == N.GC_PATH_MOMENTS:
-        modes += [("0", "1", "0"), ("1", "0", "1"), ("1", "0", "2"), ("0", "0", "2")]
-    for graph, loop, pf in modes:
+        modes += [("0", "1", "0", "0"), ("1", "0", "1", "0"), ("1", "0", "2", "0"), ("0", "0", "2", "0"),
+                  ("1", "0", "1", "1"), ("0", "0", "1", "1"), ("1", "0", "0", "1")]
+    for graph, loop, pf, step1 in modes:
         monkeypatch.setenv("GAINCAL_GRAPH", graph)
         monkeypatch.setenv("GAINCAL_LOOP", loop)
         monkeypatch.setenv("GAINCAL_ACC_PREFETCH", pf)
+        monkeypatch.setenv("GAINCAL_STEP1", step1)
         g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=37, path=path)
         out.append((g.cpu(), iters.cpu(), st.cpu()))
     for o in out[1:]:
