@@ -112,6 +112,8 @@ typedef struct gc_options {
   int32_t host_buffers;     /* 0: data pointers are device memory; 1: host memory              */
   int32_t compute_chi2;     /* 1: fill chi2_out with sum |r|^2 at the final gains              */
   int32_t profile;          /* 1: time the iteration kernels with CUDA events on `stream`;
+                               2 (moment path): time the accumulate launches alone, one launch
+                               per iteration without graph segments;
                                read the totals with gc_profile_last / gc_profile_detail        */
   int32_t path;             /* DI entry points: GC_PATH_AUTO / _STREAM / _MOMENTS / _RESIDENT     */
   int32_t reserved;         /* must be 0                                                      */
@@ -230,9 +232,10 @@ int gc_autotune_di(int32_t kind, const void* vis, const void* model, const gc_la
                    int32_t dtype, int32_t iters, double* best_ms, void* stream);
 
 /*
- * Totals of the last gc_calibrate_* call made with opt->profile = 1: summed device time of its
- * iteration launches (ms, from CUDA events on the call's stream), number of those launches, and
- * rows processed by them (sum over intervals of iterations x rows).  Any pointer may be NULL.
+ * Totals of the last gc_calibrate_* call made with opt->profile = 1 or 2: summed device time of
+ * its iteration launches (profile 2: of its accumulate launches only) in ms from CUDA events on the
+ * call's stream, the number of iterations timed, and rows processed by them (sum over intervals
+ * of iterations x rows).  Any pointer may be NULL.
  */
 int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row_iterations);
 /* More of the same profile: the moment-pass time (ms, resident path; 0 otherwise), baselines x

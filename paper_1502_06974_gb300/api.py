@@ -98,7 +98,7 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
         chi2 = torch.zeros(n, dtype=torch.float64, device=dev) if (want_outputs and compute_chi2) else None
         stream = _stream_ptr(dev)
     opt = N.GcOptions(float(tol), int(max_iter), int(schedule), dt, 1 if host else 0, 1 if compute_chi2 else 0,
-                      1 if profile else 0, int(path))
+                      int(profile), int(path))
     lay = layout.c()
     rc = getattr(N.lib(), fn_name)(_ptr(vis), _ptr(model), C.byref(lay), _ptr(gains), C.byref(opt), _ptr(iters),
                                    _ptr(chi2), _ptr(status), stream)
@@ -111,6 +111,7 @@ def calibrate_di_scalar(vis, model, layout, gains, tol=1e-6, max_iter=1000, sche
     """StefCal on scalar DI gains (gc_calibrate_di_scalar); gains are updated in place.
 
     path: GC_PATH_AUTO (default), GC_PATH_STREAM or GC_PATH_RESIDENT (see include/gaincal.h).
+    profile: 0 off, 1 (or True) time the iteration launches, 2 time the accumulate launches alone.
     Returns (gains, iters[n_int] int32, chi2[n_int] float64 or None, status[n_int] int32).
     """
     return _calibrate('gc_calibrate_di_scalar', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,

@@ -673,6 +673,7 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     return GC_ERR_ARG;
   if (opt->host_buffers != 0 && opt->host_buffers != 1) return GC_ERR_ARG;
   if (opt->reserved || opt->path < GC_PATH_AUTO || opt->path > GC_PATH_MOMENTS) return GC_ERR_ARG;
+  if (opt->profile < 0 || opt->profile > 2) return GC_ERR_ARG;
   int rc = validate_layout(L, 1);
   if (rc != GC_OK) return rc;
   if (L->n_intervals == 0) return GC_OK;
@@ -798,7 +799,9 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   };
   Profiler prof(opt->profile != 0, S);
   if ((rc = prof.init())) return rc;
-  bool use_graph = tn.graph != 0;
+  // profile 2: the accumulate launches timed alone (moment path, two launches per iteration)
+  const bool acc_prof = opt->profile == 2 && mode == 1 && !s1 && !(tn.loop && P->lgrid > 0);
+  bool use_graph = tn.graph != 0 && !acc_prof;
   if (use_graph && !(mode == 1 && tn.loop && P->lgrid > 0)) {
     // One segment = S iterations captured once (k = *kbase + 1 .. *kbase + S) plus a node that
     // advances *kbase; segments are relaunched until no interval is active.  Iterations past
@@ -871,8 +874,14 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     for (int k = 1; k <= last_k; ++k) {
       a.k = k;
       if ((rc = prof.before(s))) return rc;
-      GC_CUDA_I(launch_iter(a, s));
-      if ((rc = prof.after(s))) return rc;
+      if (acc_prof) {
+        GC_CUDA_I(di_launch_macc(kind, a, P->grid, P->smem, tn.red_chunks, tn.prefetch, stream));
+        if ((rc = prof.after(s))) return rc;
+        GC_CUDA_I(di_launch_msolve(kind, a, P->n_int, stream));
+      } else {
+        GC_CUDA_I(launch_iter(a, s));
+        if ((rc = prof.after(s))) return rc;
+      }
       g_launches += per_iter;
       if (k % S == 0 || k == last_k) {
         GC_CUDA(cudaMemcpyAsync(flag, a.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -1006,6 +1006,15 @@ int di_launch_mstep1(int kind, const DIArgs& a, int grid, int smem, int n_int, i
   return (int)cudaLaunchKernelExC(&cfg, pick_step1(kind, red_chunks, prefetch), args);
 }
 
+int di_launch_msolve(int kind, const DIArgs& a, int n_int, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int g2 = n_int < kSolveGrid ? n_int : kSolveGrid;
+  const size_t sm2 = sizeof(float) * (size_t)a.na_max * (kind == 0 ? 3 : 12);
+  if (kind == 0) di_msolve_kernel<ScalarMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
+  else di_msolve_kernel<JonesMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
+  return (int)cudaGetLastError();
+}
+
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
                     void* stream) {
   cudaStream_t s = (cudaStream_t)stream;

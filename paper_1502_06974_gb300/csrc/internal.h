@@ -91,6 +91,7 @@ int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, 
 // one iteration: the accumulate launch, then the solve launch
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
                     void* stream);
+int di_launch_msolve(int kind, const DIArgs& a, int n_int, void* stream);
 // one iteration in one cooperative launch: the update of the previous iteration and, interval by
 // interval as each update is published, the accumulate of this one (*err set if a wait timed out)
 int di_mstep1_smem(int kind, int na_max, int red_chunks);

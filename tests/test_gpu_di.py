@@ -289,6 +289,14 @@ def test_graph_and_plain_loops_agree(gpu_lib, monkeypatch, path):
         monkeypatch.setenv("GAINCAL_STEP1", step1)
         g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=37, path=path)
         out.append((g.cpu(), iters.cpu(), st.cpu()))
+    if path == N.GC_PATH_MOMENTS:   # accumulate launches timed alone (profile 2): same results
+        for v in ("GAINCAL_GRAPH", "GAINCAL_LOOP", "GAINCAL_ACC_PREFETCH", "GAINCAL_STEP1"):
+            monkeypatch.delenv(v)
+        g, iters, _, st = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=37, path=path,
+                                                    profile=2)
+        out.append((g.cpu(), iters.cpu(), st.cpu()))
+        ms, n, _ = api.profile_last()
+        assert ms > 0 and n == int(iters.max())
     for o in out[1:]:
         assert torch.equal(out[0][0], o[0]) and torch.equal(out[0][1], o[1]) and torch.equal(out[0][2], o[2])
     assert (out[0][1].numpy() <= 37).all()
