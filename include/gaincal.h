@@ -238,8 +238,10 @@ int gc_autotune_di(int32_t kind, const void* vis, const void* model, const gc_la
  * of iterations x rows).  Any pointer may be NULL.
  */
 int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row_iterations);
-/* More of the same profile: the moment-pass time (ms, resident path; 0 otherwise), baselines x
- * iterations processed, and the path taken (GC_PATH_STREAM, GC_PATH_MOMENTS or GC_PATH_RESIDENT). */
+/* More of the same profile: the moment-pass time (ms; 0 on the streaming path), baselines x
+ * iterations processed, and the path taken (GC_PATH_STREAM, GC_PATH_MOMENTS or GC_PATH_RESIDENT;
+ * GC_PATH_MOMENTS for gc_calibrate_dd_cohjones, whose iteration launches are the per-antenna
+ * N_d x N_d solves over the moments). */
 int gc_profile_detail(double* moment_pass_ms, int64_t* baseline_iterations, int32_t* path);
 
 /*

@@ -528,8 +528,45 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
   return GC_OK;
 }
 
+void profile_record(double iter_ms, int64_t launches, int64_t row_iters, double moment_ms, int64_t bl_iters, int path);
+
+// opt->profile: the moment pass and every iteration launch bracketed by CUDA events on `s`
+struct DDTimer {
+  bool on;
+  std::vector<cudaEvent_t> ev;
+  int used = 0;
+  double ms = 0.0;
+  int64_t launches = 0;
+  explicit DDTimer(bool on_, int cap) : on(on_) {
+    if (on)
+      for (int i = 0; i < 2 * cap; ++i) {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        ev.push_back(e);
+      }
+  }
+  ~DDTimer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+  void before(cudaStream_t s) {
+    if (on) cudaEventRecord(ev[2 * used], s);
+  }
+  void after(cudaStream_t s) {
+    if (on) { cudaEventRecord(ev[2 * used + 1], s); ++used; }
+  }
+  void drain() {  // after a synchronize of the stream
+    for (int i = 0; i < used; ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+      ms += t;
+    }
+    launches += used;
+    used = 0;
+  }
+};
+
 template <int ND>
-static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag) {
+static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag, double* prof_ms) {
   constexpr int NO = DDShape<ND>::NO;
   constexpr int CS = (NO + 31) / 32 * 32;
   constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
@@ -540,24 +577,41 @@ static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag
   DD_CUDA(cudaFuncSetAttribute(dd_iter_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
   dd_init_kernel<<<(P.n_int + 255) / 256, 256, 0, s>>>(a, P.n_int, P.n_active0);
   g_launches++;
+  const char* ce = getenv("GAINCAL_CHECK_EVERY");
+  const int check_every = ce && atoi(ce) > 0 ? atoi(ce) : 8;
+  DDTimer mt(opt->profile != 0, 1), it(opt->profile != 0, check_every);
   if (a.n_mitems > 0) {
+    mt.before(s);
     dd_moment_kernel<ND><<<a.n_mitems, kMomBl * kMomLanes, msmem, s>>>(a);
+    mt.after(s);
     g_launches++;
   }
   DD_CUDA(cudaGetLastError());
-  const char* ce = getenv("GAINCAL_CHECK_EVERY");
-  const int check_every = ce ? atoi(ce) : 8;
+  int k_done = 0;
   for (int k = 1; k <= opt->max_iter && a.n_iitems > 0; ++k) {
     a.k = k;
+    it.before(s);
     dd_iter_kernel<ND><<<a.n_iitems, kIterThreads, ismem, s>>>(a);
+    it.after(s);
     g_launches++;
+    k_done = k;
     DD_CUDA(cudaGetLastError());
     if (k % check_every == 0 || k == opt->max_iter) {
       DD_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
       DD_CUDA(cudaStreamSynchronize(s));
+      if (it.on) it.drain();
       if (*flag <= 0) break;
     }
   }
+  if (opt->profile) {
+    DD_CUDA(cudaStreamSynchronize(s));
+    it.drain();
+    mt.drain();
+    prof_ms[0] = it.ms;
+    prof_ms[1] = (double)it.launches;
+    prof_ms[2] = mt.ms;
+  }
+  (void)k_done;
   if (opt->compute_chi2 && a.n_mitems > 0) {
     dd_chi2_kernel<ND><<<a.n_mitems, 256, 0, s>>>(a, P.chi2_items);
     dd_chi2_final<<<(P.n_int + 255) / 256, 256, 0, s>>>(P.chi2_first, P.chi2_count, P.chi2_items, P.chi2_out,
@@ -618,17 +672,18 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
   a.schedule = opt->schedule;
   int* flag = nullptr;
   if ((rc = pinned_flag(&flag))) return rc;
+  double prof[3] = {0.0, 0.0, 0.0};
   switch (nd) {
-    case 1: rc = dd_run_nd<1>(P, opt, s, flag); break;
-    case 2: rc = dd_run_nd<2>(P, opt, s, flag); break;
-    case 3: rc = dd_run_nd<3>(P, opt, s, flag); break;
-    case 4: rc = dd_run_nd<4>(P, opt, s, flag); break;
-    case 5: rc = dd_run_nd<5>(P, opt, s, flag); break;
-    case 6: rc = dd_run_nd<6>(P, opt, s, flag); break;
-    case 7: rc = dd_run_nd<7>(P, opt, s, flag); break;
-    case 8: rc = dd_run_nd<8>(P, opt, s, flag); break;
-    case 9: rc = dd_run_nd<9>(P, opt, s, flag); break;
-    case 10: rc = dd_run_nd<10>(P, opt, s, flag); break;
+    case 1: rc = dd_run_nd<1>(P, opt, s, flag, prof); break;
+    case 2: rc = dd_run_nd<2>(P, opt, s, flag, prof); break;
+    case 3: rc = dd_run_nd<3>(P, opt, s, flag, prof); break;
+    case 4: rc = dd_run_nd<4>(P, opt, s, flag, prof); break;
+    case 5: rc = dd_run_nd<5>(P, opt, s, flag, prof); break;
+    case 6: rc = dd_run_nd<6>(P, opt, s, flag, prof); break;
+    case 7: rc = dd_run_nd<7>(P, opt, s, flag, prof); break;
+    case 8: rc = dd_run_nd<8>(P, opt, s, flag, prof); break;
+    case 9: rc = dd_run_nd<9>(P, opt, s, flag, prof); break;
+    case 10: rc = dd_run_nd<10>(P, opt, s, flag, prof); break;
     default: return GC_ERR_LIMIT;
   }
   if (rc) return rc;
@@ -637,11 +692,20 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
   if (iters_out) DD_CUDA(cudaMemcpyAsync(iters_out, a.iters, (size_t)P.n_int * 4, dk, s));
   if (status_out) DD_CUDA(cudaMemcpyAsync(status_out, a.status, (size_t)P.n_int * 4, dk, s));
   if (chi2_out && opt->compute_chi2) DD_CUDA(cudaMemcpyAsync(chi2_out, P.chi2_out, (size_t)P.n_int * 8, dk, s));
-  std::vector<int32_t> stv(P.n_int);
+  std::vector<int32_t> stv(P.n_int), itv(P.n_int);
   DD_CUDA(cudaMemcpyAsync(stv.data(), a.status, (size_t)P.n_int * 4, cudaMemcpyDeviceToHost, s));
+  if (opt->profile) DD_CUDA(cudaMemcpyAsync(itv.data(), a.iters, (size_t)P.n_int * 4, cudaMemcpyDeviceToHost, s));
   DD_CUDA(cudaStreamSynchronize(s));
   int bad = 0;
   for (int i = 0; i < P.n_int; ++i) bad += (stv[i] & 15) != GC_ST_OK;
+  if (opt->profile) {
+    int64_t ri = 0, bi = 0;
+    for (int i = 0; i < P.n_int; ++i) {
+      ri += (int64_t)itv[i] * L->n_samp[i] * L->n_bl[i];
+      bi += (int64_t)itv[i] * L->n_bl[i];
+    }
+    profile_record(prof[0], (int64_t)prof[1], ri, prof[2], bi, GC_PATH_MOMENTS);
+  }
   return bad;
 }
 
