@@ -145,56 +145,81 @@ __global__ void __launch_bounds__(kMomBl * kMomLanes) dd_moment_kernel(const DDA
 }
 
 // ------------------------------------------------------------------------------------ FP64 solve
-// Cholesky A = L L^H of the Hermitian ND x ND block (upper triangle given) and solve A x = b.
+// Cholesky A = L L^H of the Hermitian ND x ND block (upper triangle given) and solve A x = b, in
+// FP64, by one warp (right-looking: at column k one lane takes the square root of the pivot, the
+// lanes scale the column below it and update the trailing lower triangle in parallel; then the
+// two triangular solves, column by column).  Am: [ND][ND] double2 and dinv: [ND] double of shared
+// memory.  Every lane of the warp calls it and gets the same result; false when a pivot is not
+// positive (the block is not numerically positive definite).
 template <int ND>
-__device__ bool chol_solve(const double2* Aup, const double2* b, double2* x) {
-  double2 L[ND * (ND + 1) / 2];  // lower triangle, row-major: L[i][j], j <= i
-  auto li = [](int r, int c) { return r * (r + 1) / 2 + c; };
-  auto au = [](int r, int c) {   // index of upper entry (r <= c)
-    return r * ND - r * (r - 1) / 2 + (c - r);
-  };
-  for (int r = 0; r < ND; ++r) {
-    for (int c = 0; c <= r; ++c) {
-      // A[r][c] for r >= c is conj(A[c][r]) from the upper triangle
-      double2 s = Aup[au(c, r)];
-      s.y = -s.y;
-      for (int k = 0; k < c; ++k) {
-        const double2 p = L[li(r, k)], q = L[li(c, k)];  // L[r][k] * conj(L[c][k])
-        s.x -= p.x * q.x + p.y * q.y;
-        s.y -= p.y * q.x - p.x * q.y;
-      }
-      if (r == c) {
-        if (!(s.x > 0.0) || !isfinite(s.x)) return false;
-        L[li(r, r)] = make_double2(sqrt(s.x), 0.0);
+__device__ bool chol_solve_warp(const double2* Aup, const double2* b, double2* x, double2* Am, double* dinv,
+                                int* ok_s) {
+  const int lane = threadIdx.x & 31;
+  auto au = [](int r, int c) { return r * ND - r * (r - 1) / 2 + (c - r); };  // upper entry (r <= c)
+  for (int e = lane; e < ND * ND; e += 32) {  // lower triangle of A (conjugates of the upper entries)
+    const int r = e / ND, c = e % ND;
+    if (c <= r) {
+      double2 v = Aup[au(c, r)];
+      v.y = -v.y;
+      Am[e] = v;
+    }
+  }
+  for (int r = lane; r < ND; r += 32) x[r] = b[r];
+  if (lane == 0) *ok_s = 1;
+  __syncwarp();
+  for (int k = 0; k < ND; ++k) {
+    if (lane == 0) {
+      const double akk = Am[k * ND + k].x;
+      if (!(akk > 0.0) || !isfinite(akk)) {
+        *ok_s = 0;
       } else {
-        const double inv = 1.0 / L[li(c, c)].x;
-        L[li(r, c)] = make_double2(s.x * inv, s.y * inv);
+        const double l = sqrt(akk);
+        Am[k * ND + k] = make_double2(l, 0.0);
+        dinv[k] = 1.0 / l;
       }
     }
-  }
-  double2 y[ND];
-  for (int r = 0; r < ND; ++r) {  // L y = b
-    double2 s = b[r];
-    for (int k = 0; k < r; ++k) {
-      const double2 p = L[li(r, k)], q = y[k];
-      s.x -= p.x * q.x - p.y * q.y;
-      s.y -= p.x * q.y + p.y * q.x;
+    __syncwarp();
+    if (!*ok_s) return false;
+    for (int i = k + 1 + lane; i < ND; i += 32) {
+      const double2 v = Am[i * ND + k];
+      Am[i * ND + k] = make_double2(v.x * dinv[k], v.y * dinv[k]);
     }
-    const double inv = 1.0 / L[li(r, r)].x;
-    y[r] = make_double2(s.x * inv, s.y * inv);
-  }
-  for (int r = ND - 1; r >= 0; --r) {  // L^H x = y
-    double2 s = y[r];
-    for (int k = r + 1; k < ND; ++k) {
-      const double2 p = L[li(k, r)], q = x[k];  // conj(L[k][r]) * x[k]
-      s.x -= p.x * q.x + p.y * q.y;
-      s.y -= p.x * q.y - p.y * q.x;
+    __syncwarp();
+    // A[i][j] -= L[i][k] conj(L[j][k]) for k < j <= i
+    const int m = ND - 1 - k;
+    for (int t = lane; t < m * (m + 1) / 2; t += 32) {
+      int i = 0;
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      const int j = t - i * (i + 1) / 2;
+      const int ii = k + 1 + i, jj = k + 1 + j;
+      const double2 p = Am[ii * ND + k], q = Am[jj * ND + k];
+      double2 v = Am[ii * ND + jj];
+      v.x -= p.x * q.x + p.y * q.y;
+      v.y -= p.y * q.x - p.x * q.y;
+      Am[ii * ND + jj] = v;
     }
-    const double inv = 1.0 / L[li(r, r)].x;
-    x[r] = make_double2(s.x * inv, s.y * inv);
+    __syncwarp();
   }
-  for (int r = 0; r < ND; ++r)
-    if (!isfinite(x[r].x) || !isfinite(x[r].y)) return false;
+  for (int k = 0; k < ND; ++k) {  // L y = b (y in x)
+    if (lane == 0) x[k] = make_double2(x[k].x * dinv[k], x[k].y * dinv[k]);
+    __syncwarp();
+    for (int i = k + 1 + lane; i < ND; i += 32) {
+      const double2 p = Am[i * ND + k], q = x[k];
+      x[i].x -= p.x * q.x - p.y * q.y;
+      x[i].y -= p.x * q.y + p.y * q.x;
+    }
+    __syncwarp();
+  }
+  for (int k = ND - 1; k >= 0; --k) {  // L^H x = y
+    if (lane == 0) x[k] = make_double2(x[k].x * dinv[k], x[k].y * dinv[k]);
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) {  // x[i] -= conj(L[k][i]) x[k]
+      const double2 p = Am[k * ND + i], q = x[k];
+      x[i].x -= p.x * q.x + p.y * q.y;
+      x[i].y -= p.x * q.y - p.y * q.x;
+    }
+    __syncwarp();
+  }
   return true;
 }
 
@@ -256,9 +281,12 @@ __global__ void __launch_bounds__(kIterThreads) dd_iter_kernel(const DDArgs a) {
     else bv[tid - NU] = s;
   }
   __syncthreads();
-  if (tid == 0) {
-    const bool ok = chol_solve<ND>(Aup, bv, xs);
-    s_sing = ok ? 0 : 1;
+  if (tid < 32) {
+    __shared__ double2 Am[ND * ND];
+    __shared__ double dinv[ND];
+    __shared__ int s_ok;
+    const bool ok = chol_solve_warp<ND>(Aup, bv, xs, Am, dinv, &s_ok);
+    if (tid == 0) s_sing = ok ? 0 : 1;
   }
   __syncthreads();
   if (tid < ND) {
