@@ -258,17 +258,32 @@ __global__ void __launch_bounds__(kIterThreads) dd_iter_kernel(const DDArgs a) {
     else c = comp - NU;
     float sx = 0.f, sxc = 0.f, sy = 0.f, syc = 0.f;
     const float2* mom = a.moments + a.mom_off[i];
-    for (int e = e0 + lane; e < e1; e += LANES) {
-      const int en = a.ent[e];
-      const int b = en >> 1, side = en & 1;
-      const int q = side ? a.ant1[bo + b] : a.ant2[bo + b];
-      float2 v = mom[(int64_t)b * NO + comp];
-      if (side) v.y = -v.y;                         // conjugate baseline: conj(X), conj(B)
-      Cx<float> t;
-      if (comp < NU) t = mul_(mulc_(gs[q * ND + c], gs[q * ND + d]), cx<float>(v.x, v.y));
-      else t = mul_(gs[q * ND + c], cx<float>(v.x, v.y));
-      kahan_add(sx, sxc, t.x);
-      kahan_add(sy, syc, t.y);
+    // entries e0 + lane, + LANES, ... in that order; four at a time so that their dependent loads
+    // (entry -> baseline, antenna -> moment) are in flight together
+    constexpr int U = 4;
+    for (int e = e0 + lane; e < e1; e += U * LANES) {
+      int q[U];
+      float2 v[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = e + u * LANES;
+        ok[u] = idx < e1;
+        const int en = ok[u] ? a.ent[idx] : 0;
+        const int b = en >> 1, side = en & 1;
+        q[u] = ok[u] ? (side ? a.ant1[bo + b] : a.ant2[bo + b]) : 0;
+        v[u] = ok[u] ? mom[(int64_t)b * NO + comp] : make_float2(0.f, 0.f);
+        if (side) v[u].y = -v[u].y;                 // conjugate baseline: conj(X), conj(B)
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!ok[u]) continue;
+        Cx<float> t;
+        if (comp < NU) t = mul_(mulc_(gs[q[u] * ND + c], gs[q[u] * ND + d]), cx<float>(v[u].x, v[u].y));
+        else t = mul_(gs[q[u] * ND + c], cx<float>(v[u].x, v[u].y));
+        kahan_add(sx, sxc, t.x);
+        kahan_add(sy, syc, t.y);
+      }
     }
     acc = make_double2((double)sx - (double)sxc, (double)sy - (double)syc);
     red[lane * NO + comp] = acc;
