@@ -53,10 +53,10 @@ struct DDArgs {
   const int32_t* iitem_int;
   const int32_t* iitem_ant;
   int32_t n_iitems;
-  const int32_t* itab;
-  const int32_t* tab_aoff;   // per table: offset into ant_off
-  const int32_t* ant_off;    // per table: n_ant + 1 offsets into ent
   const int32_t* ent;        // baseline * 2 + side (side 1: the antenna is ant2 of the stored pair)
+  const int32_t* entq;       // the other antenna of each entry's baseline
+  const int32_t* iitem_e0;   // per iteration item: its antenna's entries [e0, e1) in ent / entq
+  const int32_t* iitem_e1;
   // state
   float2* moments;
   float* gnew;               // [n_gain][n_dir] complex GN gains of this iteration
@@ -66,10 +66,11 @@ struct DDArgs {
   int32_t* status;
   int32_t* counters;
   int32_t* n_active;
+  int32_t* kbase;            // iterations before this launch's segment (advanced on the device)
   double tol;
   int32_t max_iter;
   int32_t schedule;
-  int32_t k;
+  int32_t k;                 // position within the segment: the iteration is *kbase + k
   int32_t na_max;
 };
 
@@ -88,17 +89,45 @@ __host__ __device__ inline void upper_cd(int nd, int comp, int& c, int& d) {
 }
 
 // ------------------------------------------------------------------------------------ moments
+// Rows reach shared memory by cp.async, NST samples ahead of the arithmetic, so that the bytes in
+// flight per SM do not depend on registers (the N_d = 9 accumulators already take most of them).
+// Each thread reads back only the elements it copied itself, so a wait on its own copy groups is
+// enough; the staging area is reused for the lane partials after the sample loop.
+template <int ND>
+struct DDMomStages {
+  static constexpr int R = DDShape<ND>::NO / (ND + 1);  // stages that fit where the partials go
+  static constexpr int N = R < 3 ? 3 : (R > 6 ? 6 : R);
+};
+
+__device__ __forceinline__ void dd_cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void dd_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void dd_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int ND>
+constexpr size_t dd_moment_smem() {
+  constexpr size_t part = (size_t)kMomLanes * kMomBl * DDShape<ND>::NO * sizeof(float2);
+  constexpr size_t stage = (size_t)DDMomStages<ND>::N * (ND + 1) * kMomLanes * kMomBl * sizeof(float2);
+  return part > stage ? part : stage;
+}
+
 template <int ND>
 __global__ void __launch_bounds__(kMomBl * kMomLanes) dd_moment_kernel(const DDArgs a) {
   constexpr int NU = DDShape<ND>::NU, NO = DDShape<ND>::NO;
+  constexpr int NST = DDMomStages<ND>::N, NP = ND + 1, NT = kMomBl * kMomLanes;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* part = reinterpret_cast<float2*>(smem_raw);  // [lanes][kMomBl][NO]
+  float2* part = reinterpret_cast<float2*>(smem_raw);   // [lanes][kMomBl][NO], after the sample loop
+  float2* stage = reinterpret_cast<float2*>(smem_raw);  // [NST][NP][NT], during it
   const int it = blockIdx.x;
   if (it >= a.n_mitems) return;
   const int i = a.mitem_int[it];
   const int tile = a.mitem_tile[it];
   const int nb = a.n_bl[i], ns = a.n_samp[i];
-  const int bl = threadIdx.x % kMomBl, lane = threadIdx.x / kMomBl;
+  const int tid = threadIdx.x;
+  const int bl = tid % kMomBl, lane = tid / kMomBl;
   const int b = tile * kMomBl + bl;
   const int chunk = (ns + kMomLanes - 1) / kMomLanes;
   const int s0 = lane * chunk, s1 = min(ns, s0 + chunk);
@@ -107,14 +136,32 @@ __global__ void __launch_bounds__(kMomBl * kMomLanes) dd_moment_kernel(const DDA
   for (int u = 0; u < NU; ++u) X[u] = cx<float>(0.f, 0.f);
 #pragma unroll
   for (int c = 0; c < ND; ++c) Bv[c] = cx<float>(0.f, 0.f);
-  if (b < nb) {
+  if (b < nb && s1 > s0) {
     const int64_t r0 = a.row_off[i] + b;
-    for (int s = s0; s < s1; ++s) {
-      const int64_t r = r0 + (int64_t)s * nb;
-      const Cx<float> d = Vec<float>::ld1(a.vis + 2 * r);
+    const int cnt = s1 - s0;
+    // sample j of this thread's chunk goes to stage slot j % NST: plane 0 is vis, plane 1 + c model c
+    auto issue = [&](int j, int slot) {
+      if (j < cnt) {
+        const int64_t r = r0 + (int64_t)(s0 + j) * nb;
+        float2* st = stage + (size_t)slot * NP * NT + tid;
+        dd_cp_async8(st, a.vis + 2 * r);
+#pragma unroll
+        for (int c = 0; c < ND; ++c) dd_cp_async8(st + (c + 1) * NT, a.model + 2 * ((int64_t)c * a.n_rows + r));
+      }
+      dd_cp_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < NST - 1; ++j) issue(j, j);
+    int slot = 0;
+    for (int j = 0; j < cnt; ++j) {
+      // refill the slot read in the previous step (by this thread only) with sample j + NST - 1
+      issue(j + NST - 1, slot == 0 ? NST - 1 : slot - 1);
+      dd_cp_wait<NST - 1>();
+      const float2* st = stage + (size_t)slot * NP * NT + tid;
+      const Cx<float> d = cx<float>(st[0].x, st[0].y);
       Cx<float> m[ND];
 #pragma unroll
-      for (int c = 0; c < ND; ++c) m[c] = Vec<float>::ld1(a.model + 2 * ((int64_t)c * a.n_rows + r));
+      for (int c = 0; c < ND; ++c) m[c] = cx<float>(st[(c + 1) * NT].x, st[(c + 1) * NT].y);
       int u = 0;
 #pragma unroll
       for (int c = 0; c < ND; ++c) {
@@ -122,8 +169,11 @@ __global__ void __launch_bounds__(kMomBl * kMomLanes) dd_moment_kernel(const DDA
         for (int e = c; e < ND; ++e) { cfma_(X[u], m[c], m[e]); ++u; }
         cfma_(Bv[c], m[c], d);
       }
+      slot = slot + 1 == NST ? 0 : slot + 1;
     }
+    dd_cp_wait<0>();
   }
+  __syncthreads();  // every thread is done with the staging area
   float2* my = part + ((size_t)lane * kMomBl + bl) * NO;
 #pragma unroll
   for (int u = 0; u < NU; ++u) my[u] = make_float2(X[u].x, X[u].y);
@@ -223,89 +273,226 @@ __device__ bool chol_solve_warp(const double2* Aup, const double2* b, double2* x
   return true;
 }
 
+// Float-float ("double-float") arithmetic on the FP32 pipe: an unevaluated sum hi + lo with
+// |lo| <= ulp(hi) / 2.  Knuth's TwoSum gives a sum's rounding error exactly; an FMA gives a
+// product's (the TwoProduct of Ogita, Rump and Oishi).  GB300 runs FP32 many times faster than
+// FP64, so the iteration keeps its extra precision in these pairs instead of in doubles.
+struct FF {
+  float hi, lo;
+};
+// (the _rn intrinsics are never contracted into FMAs, which would break the exact error terms)
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = ff_two_sum(x.hi, y.hi);
+  const float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  const float hi = __fadd_rn(s.hi, lo);  // renormalise (fast TwoSum, |s.hi| >= |lo|)
+  return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+// x - a * b, with the product's rounding error carried into lo
+__device__ __forceinline__ FF ff_sub_prod(FF x, float a, float b) {
+  const float p = __fmul_rn(a, b), e = __fmaf_rn(a, b, -p);
+  const FF s = ff_two_sum(x.hi, -p);
+  const float lo = __fadd_rn(s.lo, __fsub_rn(x.lo, e));
+  const float hi = __fadd_rn(s.hi, lo);
+  return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+
+// The factorisation in FP32 followed by one step of iterative refinement (Moler's
+// mixed-precision scheme): the residual r = b - A x0 in float-float against the float-float
+// block, then the correction solved with the FP32 factor; one step takes the error from about
+// kappa(A) u_32 to about (kappa(A) u_32)^2.  Ah + Al is the upper triangle of A and bh + bl the
+// right-hand side, each an unevaluated float-float sum.  Called by one whole warp: lane r keeps
+// row r of the block in registers and the columns are factored right-looking with shuffles (lanes
+// r >= ND shadow row ND - 1 and store nothing).  False when an FP32 pivot is not positive: the
+// caller then runs the FP64 factorisation, which alone decides singularity.
+// Ls: [ND][ND] of shared memory (the factor, rows); the solution goes to x.
+template <int ND>
+__device__ bool chol_solve_warp_mixed(const Cx<float>* Ah, const Cx<float>* Al, const Cx<float>* bh,
+                                      const Cx<float>* bl, Cx<float>* x, Cx<float>* Ls) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int r = lane < ND ? lane : ND - 1;
+  auto au = [](int i, int j) { return i * ND - i * (i - 1) / 2 + (j - i); };  // upper entry (i <= j)
+  auto shfl = [&](Cx<float> v, int src) {
+    return cx<float>(__shfl_sync(kAll, v.x, src), __shfl_sync(kAll, v.y, src));
+  };
+  float dinv[ND];
+  {
+    Cx<float> L[ND];  // row r: A[r][j], becoming L[r][j] for j <= r
+#pragma unroll
+    for (int j = 0; j < ND; ++j) L[j] = r <= j ? Ah[au(r, j)] : conj_(Ah[au(j, r)]);
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      const float akk = __shfl_sync(kAll, L[k].x, k);
+      if (!(akk > 0.f) || !isfinite(akk)) return false;  // the same pivot in every lane
+      const float l = sqrtf(akk);
+      dinv[k] = __frcp_rn(l);
+      if (r == k) L[k] = cx<float>(l, 0.f);
+      else if (r > k) L[k] = scale_(L[k], dinv[k]);
+#pragma unroll
+      for (int j = k + 1; j < ND; ++j) {  // A[r][j] -= L[r][k] conj(L[j][k]) for j <= r
+        const Cx<float> ljk = shfl(L[k], j);
+        if (r >= j) L[j] = sub_(L[j], mulc_(L[k], ljk));
+      }
+    }
+    if (lane < ND) {
+#pragma unroll
+      for (int j = 0; j < ND; ++j)
+        if (j <= r) Ls[r * ND + j] = L[j];
+    }
+  }
+  __syncwarp();
+  // L L^H v = w for the w held by lane r: forward with row r of L, backward with column r
+  auto subst = [&](Cx<float> v) {
+    Cx<float> row[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) row[k] = k < r ? Ls[r * ND + k] : cx<float>(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      if (r == k) v = scale_(v, dinv[k]);
+      const Cx<float> vk = shfl(v, k);
+      if (r > k) v = sub_(v, mul_(row[k], vk));
+    }
+    Cx<float> col[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) col[k] = k > r ? Ls[k * ND + r] : cx<float>(0.f, 0.f);
+#pragma unroll
+    for (int k = ND - 1; k >= 0; --k) {
+      if (r == k) v = scale_(v, dinv[k]);
+      const Cx<float> vk = shfl(v, k);
+      if (r < k) v = sub_(v, cmul_(col[k], vk));  // v_r -= conj(L[k][r]) v_k
+    }
+    return v;
+  };
+  const Cx<float> x0 = subst(bh[r]);
+  // residual in float-float: r_r = b_r - sum_j A[r][j] x0_j, two interleaved partial sums per part
+  FF rx0{bh[r].x, bl[r].x}, ry0{bh[r].y, bl[r].y}, rx1{0.f, 0.f}, ry1{0.f, 0.f};
+  float lox = 0.f, loy = 0.f;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const int u = r <= j ? au(r, j) : au(j, r);
+    Cx<float> h = Ah[u], lo = Al[u];
+    if (r > j) { h.y = -h.y; lo.y = -lo.y; }
+    const Cx<float> xj = shfl(x0, j);
+    FF& ax = (j & 1) ? rx1 : rx0;
+    FF& ay = (j & 1) ? ry1 : ry0;
+    ax = ff_sub_prod(ax, h.x, xj.x);
+    ax = ff_sub_prod(ax, -h.y, xj.y);
+    ay = ff_sub_prod(ay, h.x, xj.y);
+    ay = ff_sub_prod(ay, h.y, xj.x);
+    lox = fmaf(lo.x, xj.x, fmaf(-lo.y, xj.y, lox));
+    loy = fmaf(lo.x, xj.y, fmaf(lo.y, xj.x, loy));
+  }
+  const FF rx = ff_add(rx0, rx1), ry = ff_add(ry0, ry1);
+  const Cx<float> dres = cx<float>(rx.hi + (rx.lo - lox), ry.hi + (ry.lo - loy));
+  const Cx<float> d = subst(dres);
+  if (lane < ND) x[lane] = add_(x0, d);
+  __syncwarp();
+  return true;
+}
+
 // ------------------------------------------------------------------------------------ iteration
 template <int ND>
-__global__ void __launch_bounds__(kIterThreads) dd_iter_kernel(const DDArgs a) {
+__global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a) {
   constexpr int NU = DDShape<ND>::NU, NO = DDShape<ND>::NO;
   constexpr int CS = (NO + 31) / 32 * 32;       // component slots per lane group
   constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<float>* gs = reinterpret_cast<Cx<float>*>(smem_raw);            // [n_ant][ND]
-  double2* red = reinterpret_cast<double2*>(gs + a.na_max * ND);      // [LANES][NO]
-  __shared__ double2 Aup[NU], bv[ND], xs[ND];
+  float4* red = reinterpret_cast<float4*>(gs + a.na_max * ND);       // [LANES][NO] float-float (re, im)
+  __shared__ Cx<float> Ah[NU], Al[NU], bh[ND], bl[ND], xs[ND];
   __shared__ int s_last, s_sing;
   __shared__ double s_red[64];
+  __shared__ int2 s_ent[kIterThreads];
   const int it = blockIdx.x;
   if (it >= a.n_iitems) return;
   const int i = a.iitem_int[it];
-  if (a.active[i] == 0) return;
+  const int k = *a.kbase + a.k;
+  if (a.active[i] == 0 || k > a.max_iter) return;
   const int p = a.iitem_ant[it];
   const int na = a.n_ant[i];
   const int64_t go = a.gain_off[i];
   const int tid = threadIdx.x;
   for (int x = tid; x < na * ND; x += blockDim.x)
     gs[x] = cx<float>(a.gains[2 * (go * ND + x)], a.gains[2 * (go * ND + x) + 1]);
-  __syncthreads();
   const int comp = tid % CS, lane = tid / CS;
-  double2 acc = make_double2(0.0, 0.0);
-  if (comp < NO && lane < LANES) {
-    const int tab = a.itab[i];
-    const int* aoff = a.ant_off + a.tab_aoff[tab];
-    const int e0 = aoff[p], e1 = aoff[p + 1];
-    const int bo = a.bl_off[i];
-    int c = 0, d = 0;
-    if (comp < NU) upper_cd(ND, comp, c, d);
-    else c = comp - NU;
-    float sx = 0.f, sxc = 0.f, sy = 0.f, syc = 0.f;
-    const float2* mom = a.moments + a.mom_off[i];
-    // entries e0 + lane, + LANES, ... in that order; four at a time so that their dependent loads
-    // (entry -> baseline, antenna -> moment) are in flight together
-    constexpr int U = 4;
-    for (int e = e0 + lane; e < e1; e += U * LANES) {
-      int q[U];
-      float2 v[U];
-      bool ok[U];
+  const bool worker = comp < NO && lane < LANES;
+  int c = 0, d = 0;
+  if (comp < NU) upper_cd(ND, comp, c, d);
+  else c = comp - NU;
+  float sx = 0.f, sxc = 0.f, sy = 0.f, syc = 0.f;
+  const float2* mom = a.moments + a.mom_off[i];
+  const int e0 = a.iitem_e0[it], e1 = a.iitem_e1[it];
+  // the antenna's entries, kIterThreads at a time, staged in shared memory so that every moment
+  // load's address is known at once; each lane takes entries lane, lane + LANES, ... in order
+  for (int base = e0; base < e1; base += kIterThreads) {
+    const int n = min(kIterThreads, e1 - base);
+    if (tid < n) s_ent[tid] = make_int2(a.ent[base + tid], a.entq[base + tid]);
+    __syncthreads();
+    if (worker) {
+      constexpr int U = 8;
+      for (int j = lane; j < n; j += U * LANES) {
+        float2 v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int idx = e + u * LANES;
-        ok[u] = idx < e1;
-        const int en = ok[u] ? a.ent[idx] : 0;
-        const int b = en >> 1, side = en & 1;
-        q[u] = ok[u] ? (side ? a.ant1[bo + b] : a.ant2[bo + b]) : 0;
-        v[u] = ok[u] ? mom[(int64_t)b * NO + comp] : make_float2(0.f, 0.f);
-        if (side) v[u].y = -v[u].y;                 // conjugate baseline: conj(X), conj(B)
-      }
+        for (int u = 0; u < U; ++u) {
+          const int idx = j + u * LANES;
+          const int en = idx < n ? s_ent[idx].x : 0;
+          v[u] = idx < n ? mom[(int64_t)(en >> 1) * NO + comp] : make_float2(0.f, 0.f);
+          if (en & 1) v[u].y = -v[u].y;  // conjugate baseline: conj(X), conj(B)
+        }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (!ok[u]) continue;
-        Cx<float> t;
-        if (comp < NU) t = mul_(mulc_(gs[q[u] * ND + c], gs[q[u] * ND + d]), cx<float>(v[u].x, v[u].y));
-        else t = mul_(gs[q[u] * ND + c], cx<float>(v[u].x, v[u].y));
-        kahan_add(sx, sxc, t.x);
-        kahan_add(sy, syc, t.y);
+        for (int u = 0; u < U; ++u) {
+          const int idx = j + u * LANES;
+          if (idx >= n) continue;
+          const int q = s_ent[idx].y;
+          Cx<float> t;
+          if (comp < NU) t = mul_(mulc_(gs[q * ND + c], gs[q * ND + d]), cx<float>(v[u].x, v[u].y));
+          else t = mul_(gs[q * ND + c], cx<float>(v[u].x, v[u].y));
+          kahan_add(sx, sxc, t.x);
+          kahan_add(sy, syc, t.y);
+        }
       }
     }
-    acc = make_double2((double)sx - (double)sxc, (double)sy - (double)syc);
-    red[lane * NO + comp] = acc;
+    __syncthreads();  // before the next chunk replaces the staged entries
   }
+  if (e1 <= e0) __syncthreads();  // the gains are staged even for an antenna without baselines
+  if (worker) red[lane * NO + comp] = make_float4(sx, -sxc, sy, -syc);  // Kahan: the sum is s - c
   __syncthreads();
   if (tid < NO) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int l = 0; l < LANES; ++l) { s.x += red[l * NO + tid].x; s.y += red[l * NO + tid].y; }
-    if (tid < NU) Aup[tid] = s;
-    else bv[tid - NU] = s;
+    FF re{0.f, 0.f}, im{0.f, 0.f};
+    for (int l = 0; l < LANES; ++l) {
+      const float4 v = red[l * NO + tid];
+      re = ff_add(re, ff_two_sum(v.x, v.y));
+      im = ff_add(im, ff_two_sum(v.z, v.w));
+    }
+    if (tid < NU) { Ah[tid] = cx<float>(re.hi, im.hi); Al[tid] = cx<float>(re.lo, im.lo); }
+    else { bh[tid - NU] = cx<float>(re.hi, im.hi); bl[tid - NU] = cx<float>(re.lo, im.lo); }
   }
   __syncthreads();
   if (tid < 32) {
-    __shared__ double2 Am[ND * ND];
-    __shared__ double dinv[ND];
+    __shared__ Cx<float> Ls[ND * ND];
     __shared__ int s_ok;
-    const bool ok = chol_solve_warp<ND>(Aup, bv, xs, Am, dinv, &s_ok);
+    bool ok = chol_solve_warp_mixed<ND>(Ah, Al, bh, bl, xs, Ls);
+    if (!ok) {  // rare: the block is not positive definite in FP32; FP64 decides
+      __shared__ double2 Ad[NU], bd[ND], xd[ND], Am[ND * ND];
+      __shared__ double dinv[ND];
+      for (int u = tid; u < NU; u += 32)
+        Ad[u] = make_double2((double)Ah[u].x + (double)Al[u].x, (double)Ah[u].y + (double)Al[u].y);
+      for (int r = tid; r < ND; r += 32)
+        bd[r] = make_double2((double)bh[r].x + (double)bl[r].x, (double)bh[r].y + (double)bl[r].y);
+      __syncwarp();
+      ok = chol_solve_warp<ND>(Ad, bd, xd, Am, dinv, &s_ok);
+      for (int r = tid; r < ND; r += 32) xs[r] = cx<float>((float)xd[r].x, (float)xd[r].y);
+      __syncwarp();
+    }
     if (tid == 0) s_sing = ok ? 0 : 1;
   }
   __syncthreads();
   if (tid < ND) {
-    Cx<float> g = s_sing ? gs[p * ND + tid] : cx<float>((float)xs[tid].x, (float)xs[tid].y);
+    Cx<float> g = s_sing ? gs[p * ND + tid] : xs[tid];
     a.gnew[2 * ((go + p) * ND + tid)] = g.x;
     a.gnew[2 * ((go + p) * ND + tid) + 1] = g.y;
   }
@@ -317,7 +504,7 @@ __global__ void __launch_bounds__(kIterThreads) dd_iter_kernel(const DDArgs a) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const bool gn_step = (a.schedule == GC_SCHED_GN) || (a.k & 1);
+  const bool gn_step = (a.schedule == GC_SCHED_GN) || (k & 1);
   float d2 = 0.f, n2 = 0.f;
   int nonfin = 0, sing = 0;
   for (int x = tid; x < na * ND; x += blockDim.x) {
@@ -344,10 +531,10 @@ __global__ void __launch_bounds__(kIterThreads) dd_iter_kernel(const DDArgs a) {
     int st = -1;
     if (nonfin) st = GC_ST_NONFINITE;
     else if (D2 <= a.tol * a.tol * N2) st = GC_ST_OK;
-    else if (a.k >= a.max_iter) st = GC_ST_NOT_CONVERGED;
+    else if (k >= a.max_iter) st = GC_ST_NOT_CONVERGED;
     if (st >= 0) {
       a.active[i] = 0;
-      a.iters[i] = a.k;
+      a.iters[i] = k;
       a.status[i] = st | (sing ? GC_ST_SINGULAR_FLAG : 0);
       atomicSub(a.n_active, 1);
     }
@@ -395,7 +582,7 @@ __global__ void dd_chi2_final(const int32_t* first, const int32_t* count, const 
 
 __global__ void dd_init_kernel(DDArgs a, int n_int, int n_active0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *a.n_active = n_active0;
+  if (i == 0) { *a.n_active = n_active0; *a.kbase = 0; }
   if (i < n_int) {
     const int64_t rows = (int64_t)a.n_samp[i] * a.n_bl[i];
     a.active[i] = rows > 0 ? 1 : 0;
@@ -420,6 +607,9 @@ struct DDPlan {
   DDArgs args{};
   int n_int = 0, n_active0 = 0, nd = 1;
   int64_t n_mom = 0;
+  cudaGraphExec_t gexec = nullptr;  // the captured iteration segment
+  DDArgs gargs{};
+  int gS = 0, gnd = 0;
   int32_t* chi2_first = nullptr;
   int32_t* chi2_count = nullptr;
   double* chi2_items = nullptr;
@@ -437,7 +627,7 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
   const int n = L->n_intervals, nd = L->n_dir;
   const int NO = nd * (nd + 1) / 2 + nd;
   std::vector<int64_t> mom_off(n);
-  std::vector<int> mint, mtile, iint, iant, itab(n), tab_aoff, ant_off, ent, cfirst(n), ccount(n);
+  std::vector<int> mint, mtile, iint, iant, itab(n), tab_aoff, ant_off, ent, entq, cfirst(n), ccount(n);
   std::map<std::pair<int, int>, int> tabs;
   int64_t mo = 0;
   int n_active0 = 0, na_max = 1;
@@ -466,15 +656,16 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
       nat = L->ant1[key.first + b] + 1 > nat ? L->ant1[key.first + b] + 1 : nat;
       nat = L->ant2[key.first + b] + 1 > nat ? L->ant2[key.first + b] + 1 : nat;
     }
-    std::vector<std::vector<int>> lists(nat);
+    std::vector<std::vector<std::pair<int, int>>> lists(nat);  // (baseline * 2 + side, other antenna)
     for (int b = 0; b < nb; ++b) {
-      lists[L->ant1[key.first + b]].push_back(b * 2);
-      lists[L->ant2[key.first + b]].push_back(b * 2 + 1);
+      const int p1 = L->ant1[key.first + b], p2 = L->ant2[key.first + b];
+      lists[p1].push_back({b * 2, p2});
+      lists[p2].push_back({b * 2 + 1, p1});
     }
     tab_aoff.push_back((int)ant_off.size());
     for (int p = 0; p < nat; ++p) {
       ant_off.push_back((int)ent.size());
-      ent.insert(ent.end(), lists[p].begin(), lists[p].end());
+      for (auto& e : lists[p]) { ent.push_back(e.first); entq.push_back(e.second); }
     }
     ant_off.push_back((int)ent.size());
   }
@@ -486,7 +677,14 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
     const int nat = next - tab_aoff[tid] - 1;
     if (nat < L->n_ant[i]) return GC_ERR_LAYOUT;
   }
-  if (ent.empty()) ent.push_back(0);
+  std::vector<int> ie0(iint.size()), ie1(iint.size());  // each iteration item's entry range
+  for (size_t j = 0; j < iint.size(); ++j) {
+    const int o = tab_aoff[itab[iint[j]]] + iant[j];
+    ie0[j] = ant_off[o];
+    ie1[j] = ant_off[o + 1];
+  }
+  if (ent.empty()) { ent.push_back(0); entq.push_back(0); }
+  if (ie0.empty()) { ie0.push_back(0); ie1.push_back(0); }
   if (mint.empty()) { mint.push_back(0); mtile.push_back(0); }
   if (iint.empty()) { iint.push_back(0); iant.push_back(0); }
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -507,10 +705,10 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
   const size_t p_mtile = add(mtile.data(), mtile.size() * 4);
   const size_t p_iint = add(iint.data(), iint.size() * 4);
   const size_t p_iant = add(iant.data(), iant.size() * 4);
-  const size_t p_itab = add(itab.data(), itab.size() * 4);
-  const size_t p_taoff = add(tab_aoff.data(), tab_aoff.size() * 4);
-  const size_t p_aoff = add(ant_off.data(), ant_off.size() * 4);
+  const size_t p_ie0 = add(ie0.data(), ie0.size() * 4);
+  const size_t p_ie1 = add(ie1.data(), ie1.size() * 4);
   const size_t p_ent = add(ent.data(), ent.size() * 4);
+  const size_t p_entq = add(entq.data(), entq.size() * 4);
   const size_t p_cfirst = add(cfirst.data(), cfirst.size() * 4);
   const size_t p_ccount = add(ccount.data(), ccount.size() * 4);
   const size_t p_active = add(nullptr, (size_t)n * 4);
@@ -549,15 +747,16 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
   a.iitem_int = (const int32_t*)at(p_iint);
   a.iitem_ant = (const int32_t*)at(p_iant);
   a.n_iitems = (int)(n_active0 > 0 ? iint.size() : 0);
-  a.itab = (const int32_t*)at(p_itab);
-  a.tab_aoff = (const int32_t*)at(p_taoff);
-  a.ant_off = (const int32_t*)at(p_aoff);
+  a.iitem_e0 = (const int32_t*)at(p_ie0);
+  a.iitem_e1 = (const int32_t*)at(p_ie1);
   a.ent = (const int32_t*)at(p_ent);
+  a.entq = (const int32_t*)at(p_entq);
   a.active = (int32_t*)at(p_active);
   a.iters = (int32_t*)at(p_iters);
   a.status = (int32_t*)at(p_status);
   a.counters = (int32_t*)at(p_counters);
   a.n_active = (int32_t*)at(p_misc);
+  a.kbase = a.n_active + 1;
   a.sing = (int32_t*)at(p_sing);
   a.na_max = na_max;
   P.chi2_first = (int32_t*)at(p_cfirst);
@@ -614,15 +813,15 @@ static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag
   constexpr int CS = (NO + 31) / 32 * 32;
   constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
   DDArgs& a = P.args;
-  const size_t msmem = (size_t)kMomLanes * kMomBl * NO * sizeof(float2);
-  const size_t ismem = (size_t)a.na_max * ND * sizeof(Cx<float>) + (size_t)LANES * NO * sizeof(double2) + 16;
+  const size_t msmem = dd_moment_smem<ND>();
+  const size_t ismem = (size_t)a.na_max * ND * sizeof(Cx<float>) + (size_t)LANES * NO * sizeof(float4) + 16;
   DD_CUDA(cudaFuncSetAttribute(dd_moment_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
   DD_CUDA(cudaFuncSetAttribute(dd_iter_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
   dd_init_kernel<<<(P.n_int + 255) / 256, 256, 0, s>>>(a, P.n_int, P.n_active0);
   g_launches++;
   const char* ce = getenv("GAINCAL_CHECK_EVERY");
-  const int check_every = ce && atoi(ce) > 0 ? atoi(ce) : 8;
-  DDTimer mt(opt->profile != 0, 1), it(opt->profile != 0, check_every);
+  const int S = ce && atoi(ce) > 0 ? atoi(ce) : 8;
+  DDTimer mt(opt->profile != 0, 1), it(opt->profile != 0, 1);
   if (a.n_mitems > 0) {
     mt.before(s);
     dd_moment_kernel<ND><<<a.n_mitems, kMomBl * kMomLanes, msmem, s>>>(a);
@@ -630,16 +829,45 @@ static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag
     g_launches++;
   }
   DD_CUDA(cudaGetLastError());
-  int k_done = 0;
-  for (int k = 1; k <= opt->max_iter && a.n_iitems > 0; ++k) {
-    a.k = k;
-    it.before(s);
-    dd_iter_kernel<ND><<<a.n_iitems, kIterThreads, ismem, s>>>(a);
-    it.after(s);
-    g_launches++;
-    k_done = k;
-    DD_CUDA(cudaGetLastError());
-    if (k % check_every == 0 || k == opt->max_iter) {
+  if (a.n_iitems > 0) {
+    // One segment = S iteration launches (iterations *kbase + 1 .. *kbase + S) and the advance of
+    // *kbase, captured once per argument set and relaunched until no interval is active.  A block
+    // of a converged interval, or of an iteration past max_iter, returns at once.
+    DDArgs ga = a;
+    ga.k = 0;
+    ga.vis = ga.model = nullptr;  // the iterations read only the moments
+    if (!P.gexec || P.gS != S || P.gnd != ND || memcmp(&P.gargs, &ga, sizeof(DDArgs)) != 0) {
+      if (P.gexec) { cudaGraphExecDestroy(P.gexec); P.gexec = nullptr; }
+      cudaStream_t cs = nullptr;
+      DD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaError_t ce2 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      int crc = ce2 == cudaSuccess ? 0 : (int)ce2;
+      for (int j = 1; j <= S && !crc; ++j) {
+        DDArgs x = ga;
+        x.k = j;
+        dd_iter_kernel<ND><<<a.n_iitems, kIterThreads, ismem, cs>>>(x);
+        crc = (int)cudaGetLastError();
+      }
+      if (!crc) crc = di_launch_advance(a.kbase, S, cs);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ee = ce2 == cudaSuccess ? cudaStreamEndCapture(cs, &g) : ce2;
+      cudaStreamDestroy(cs);
+      cudaError_t ie = cudaSuccess;
+      if (!crc && ee == cudaSuccess) ie = cudaGraphInstantiate(&P.gexec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (crc || ee != cudaSuccess || ie != cudaSuccess) {
+        if (P.gexec) { cudaGraphExecDestroy(P.gexec); P.gexec = nullptr; }
+        return set_cuda_error(crc ? (cudaError_t)crc : (ee != cudaSuccess ? ee : ie), "capture of the DD iteration segment");
+      }
+      P.gargs = ga;
+      P.gS = S;
+      P.gnd = ND;
+    }
+    for (int k0 = 0; k0 < opt->max_iter; k0 += S) {
+      it.before(s);
+      DD_CUDA(cudaGraphLaunch(P.gexec, s));
+      it.after(s);
+      g_launches += S + 1;
       DD_CUDA(cudaMemcpyAsync(flag, a.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
       DD_CUDA(cudaStreamSynchronize(s));
       if (it.on) it.drain();
@@ -651,10 +879,9 @@ static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag
     it.drain();
     mt.drain();
     prof_ms[0] = it.ms;
-    prof_ms[1] = (double)it.launches;
+    prof_ms[1] = (double)it.launches * S;  // iteration launches (segments x S)
     prof_ms[2] = mt.ms;
   }
-  (void)k_done;
   if (opt->compute_chi2 && a.n_mitems > 0) {
     dd_chi2_kernel<ND><<<a.n_mitems, 256, 0, s>>>(a, P.chi2_items);
     dd_chi2_final<<<(P.n_int + 255) / 256, 256, 0, s>>>(P.chi2_first, P.chi2_count, P.chi2_items, P.chi2_out,
@@ -666,6 +893,7 @@ static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag
 }
 
 void dd_release() {
+  if (g_dd.gexec) cudaGraphExecDestroy(g_dd.gexec);
   if (g_dd.dev) cudaFree(g_dd.dev);
   g_dd = DDPlan{};
 }
@@ -694,17 +922,21 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
   const int nd = L->n_dir;
   const size_t vb = (size_t)L->n_rows * 8, mb = (size_t)L->n_rows * nd * 8, gb = (size_t)L->n_gain * nd * 8;
   DDArgs& a = P.args;
+  // the iterations work on a copy of the gains in the workspace, so that the captured iteration
+  // segment stays valid from call to call
+  void* dg = nullptr;
+  if ((rc = ws_get("dd_gains", gb > 0 ? gb : 8, &dg))) return rc;
   if (opt->host_buffers) {
-    void *dv, *dm, *dg;
-    if ((rc = ws_get("dd_h_vis", vb, &dv)) || (rc = ws_get("dd_h_model", mb, &dm)) || (rc = ws_get("dd_h_gains", gb, &dg)))
-      return rc;
+    void *dv, *dm;
+    if ((rc = ws_get("dd_h_vis", vb, &dv)) || (rc = ws_get("dd_h_model", mb, &dm))) return rc;
     if (vb) DD_CUDA(cudaMemcpyAsync(dv, vis, vb, cudaMemcpyHostToDevice, s));
     if (mb) DD_CUDA(cudaMemcpyAsync(dm, model, mb, cudaMemcpyHostToDevice, s));
-    DD_CUDA(cudaMemcpyAsync(dg, gains, gb, cudaMemcpyHostToDevice, s));
-    a.vis = (const float*)dv; a.model = (const float*)dm; a.gains = (float*)dg;
+    a.vis = (const float*)dv; a.model = (const float*)dm;
   } else {
-    a.vis = (const float*)vis; a.model = (const float*)model; a.gains = (float*)gains;
+    a.vis = (const float*)vis; a.model = (const float*)model;
   }
+  if (gb) DD_CUDA(cudaMemcpyAsync(dg, gains, gb, opt->host_buffers ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  a.gains = (float*)dg;
   void *mom, *gnew;
   if ((rc = ws_get("dd_moments", (size_t)(P.n_mom > 0 ? P.n_mom : 1) * sizeof(float2), &mom))) return rc;
   if ((rc = ws_get("dd_gnew", gb > 0 ? gb : 8, &gnew))) return rc;
@@ -731,7 +963,7 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
   }
   if (rc) return rc;
   const cudaMemcpyKind dk = opt->host_buffers ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (opt->host_buffers) DD_CUDA(cudaMemcpyAsync(gains, a.gains, gb, dk, s));
+  if (gb) DD_CUDA(cudaMemcpyAsync(gains, a.gains, gb, dk, s));
   if (iters_out) DD_CUDA(cudaMemcpyAsync(iters_out, a.iters, (size_t)P.n_int * 4, dk, s));
   if (status_out) DD_CUDA(cudaMemcpyAsync(status_out, a.status, (size_t)P.n_int * 4, dk, s));
   if (chi2_out && opt->compute_chi2) DD_CUDA(cudaMemcpyAsync(chi2_out, P.chi2_out, (size_t)P.n_int * 8, dk, s));

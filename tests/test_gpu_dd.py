@@ -1,7 +1,9 @@
 """GPU parity of CohJones (direction-dependent scalar gains) against the FP64 oracle.
 
 The GPU sums samples once per interval into FP32 moments (compensated across sample lanes),
-accumulates the N_d x N_d antenna blocks in FP32 with compensated sums and solves them in FP64.
+accumulates the N_d x N_d antenna blocks in FP32 with compensated sums, factors them in FP32 and
+refines the solution once against a float-float residual (FP64 only where the FP32 factorisation
+fails).
 Tolerance: gains after per-direction phase alignment, max ||dg|| / ||g|| <= 1e-5 for iterates and
 converged solutions (the FP32 target), chi^2 within 1e-4 relative.
 """
@@ -67,6 +69,29 @@ def test_cohjones_full_size_sampled(gpu_lib):
         assert gauge.rel_error('dd', gg[iv['gain_slice']], gr) < 1e-5
         ref = diagonal.chi2_interval('dd', gg[iv['gain_slice']], iv['vis'], iv['model'], iv['ant1'], iv['ant2'])
         assert abs(float(chi2[i]) - ref) <= 1e-4 * ref
+
+
+def test_cohjones_antenna_without_signal_is_singular(gpu_lib):
+    """An antenna whose baselines carry no model in one interval has A_p = 0: both precisions of
+    the factorisation fail, the antenna keeps its gains and its interval reports SINGULAR; every
+    other gain follows the oracle's iterates."""
+    b = synth.make_config(3, small=True)
+    i, p = 1, 3
+    nb, ns, bo, r0 = int(b.n_bl[i]), int(b.n_samp[i]), int(b.bl_off[i]), int(b.row_off[i])
+    sel = np.nonzero((b.ant1[bo:bo + nb] == p) | (b.ant2[bo:bo + nb] == p))[0]
+    assert sel.size > 0
+    for s in range(ns):
+        b.model[:, r0 + s * nb + sel] = 0
+    vis, model, g0, lay = device_batch(b)
+    g, iters, _, st = api.calibrate_dd_cohjones(vis, model, lay, g0.clone(), tol=0.0, max_iter=3)
+    gr, _, _ = diagonal.solve_batch(b, tol=0.0, max_iter=3)
+    gg = g.cpu().numpy()
+    assert per_slot_relerr(gg, gr) < 1e-5
+    slot = int(b.gain_off[i]) + p
+    np.testing.assert_array_equal(gg[slot], g0.cpu().numpy()[slot])
+    st = st.cpu().numpy()
+    flag = 16  # GC_ST_SINGULAR_FLAG
+    assert st[i] & flag and not np.delete(st & flag, i).any()
 
 
 def test_dd_host_buffers(gpu_lib):
