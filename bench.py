@@ -476,7 +476,7 @@ def run_gpu(args):
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"],
                     "traffic": (tpb * acc_bi / max(acc_n, 1)) if tpb is not None else None,
-                    "kernel": "di_macc_kernel<JonesMom> (moment-space J^H D / diag J^H J per 256-baseline tile)",
+                    "kernel": "di_macc_bulk_kernel<JonesMom> (moment-space J^H D / diag J^H J per 256-baseline tile, bulk copies into a two-stage shared-memory ring)",
                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6, "launches": acc_n,
                     "timed": "every accumulate launch of one full solve, CUDA events on the call's stream",
                     "peak_source": which}

@@ -155,7 +155,9 @@ uint64_t layout_hash(const gc_layout* L, uint64_t salt) {
 // override both (for experiments).
 struct Tune {
   int red_chunks = 1;     // moment path: per-antenna slot lists summed in 1 or 4 chunks
-  int prefetch = 1;       // moment path: 0 none, 1 next tile's moments into registers while reducing this one, 2 staged in shared memory
+  int prefetch = 3;       // moment path: 0 none, 1 next tile's moments into registers while reducing this one,
+                          // 2 staged in shared memory by cp.async, 3 bulk copies into a two-stage ring (2x2;
+                          // scalar moments take 1)
   int bps = 0;            // CTAs per SM of the persistent grid (0 = as many as fit)
   int check_every = 16;   // iterations per graph segment / between host checks of the active count
   int target_rows = 0;    // raw-row path: rows per work item (0 = default)
@@ -197,6 +199,7 @@ static Tune effective_tune(int kind, int dtype, int mode, const gc_layout* L) {
   }
   t.red_chunks = env_int("GAINCAL_RED_CHUNKS", t.red_chunks);
   t.prefetch = env_int("GAINCAL_ACC_PREFETCH", t.prefetch);
+  if (t.prefetch == 3 && (kind != 1 || mode != 1)) t.prefetch = 1;  // the bulk-copy kernel: 2x2 moments only
   t.bps = env_int("GAINCAL_BLOCKS_PER_SM", t.bps);
   t.check_every = std::max(1, env_int("GAINCAL_CHECK_EVERY", t.check_every));
   t.target_rows = env_int(kind == 0 ? "GAINCAL_TARGET_ROWS_SCALAR" : "GAINCAL_TARGET_ROWS_JONES", t.target_rows);
@@ -259,6 +262,10 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   // baseline tables
   std::map<std::pair<int, int>, int> tabs;
   std::vector<int> itab(n), tab_base, tab_nant, csr_off, csr_ent;
+  std::vector<int> tblk;                                   // bulk-copy accumulate: static tile blocks
+  std::vector<std::vector<std::pair<int, int>>> tblk_at;   // per table and tile: (offset, length) in ints
+  int tblk_max = 4;
+  auto pad4 = [](int x) { return (x + 3) & ~3; };
   for (int i = 0; i < n; ++i) {
     auto key = std::make_pair((int)L->bl_off[i], (int)L->n_bl[i]);
     auto f = tabs.find(key);
@@ -274,6 +281,7 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
     }
     tab_base.push_back((int)csr_off.size());
     tab_nant.push_back(nat);
+    tblk_at.emplace_back();
     const int ntiles = (nb + TB - 1) / TB;
     for (int tile = 0; tile < ntiles; ++tile) {
       std::vector<std::vector<int>> lists(nat);
@@ -291,6 +299,27 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
         csr_ent.insert(csr_ent.end(), lists[a].begin(), lists[a].end());
       }
       csr_off.push_back((int)csr_ent.size());
+      if (mode == 1) {
+        const int o = (int)tblk.size();
+        tblk.resize(o + 2 * TB, -1);
+        for (int s = 0; s < TB && tile * TB + s < nb; ++s) {
+          tblk[o + s] = L->ant1[bo + tile * TB + s];
+          tblk[o + TB + s] = L->ant2[bo + tile * TB + s];
+        }
+        const int oo = (int)tblk.size();
+        tblk.resize(oo + pad4(nat + 1), 0);
+        int ne = 0;
+        for (int a = 0; a < nat; ++a) { tblk[oo + a] = ne; ne += (int)lists[a].size(); }
+        tblk[oo + nat] = ne;
+        const int eo = (int)tblk.size();
+        tblk.resize(eo + pad4(ne), 0);
+        int e = eo;
+        for (int a = 0; a < nat; ++a)
+          for (int v : lists[a]) tblk[e++] = v;
+        const int len = (int)tblk.size() - o;
+        tblk_at[t].push_back({o, len});
+        tblk_max = len > tblk_max ? len : tblk_max;
+      }
     }
   }
   if (csr_off.empty()) csr_off.push_back(0);
@@ -336,6 +365,21 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
     }
   }
   const int n_items = (int)item_int.size();
+  std::vector<int4> idesc;  // bulk-copy accumulate descriptors, three per item
+  if (mode == 1) {
+    const int nm = kind == 0 ? 4 : 48;
+    for (int it = 0; it < n_items; ++it) {
+      const int i = item_int[it], t = item_s0[it];
+      const int64_t mom = (mom_off[i] + (int64_t)t * TB) * nm, sc = item_scr[it];
+      const int nbt = std::min(TB, L->n_bl[i] - t * TB);
+      const std::pair<int, int> blk = tblk_at[itab[i]][t];
+      idesc.push_back(make_int4((int)(mom & 0xffffffff), (int)(mom >> 32), nbt, blk.first));
+      idesc.push_back(make_int4(blk.second, tab_nant[itab[i]], L->gain_off[i], L->n_ant[i]));
+      idesc.push_back(make_int4((int)(sc & 0xffffffff), (int)(sc >> 32), 0, 0));
+    }
+  }
+  if (tblk.empty()) tblk.assign(4, 0);
+  if (idesc.empty()) idesc.assign(3, make_int4(0, 0, 0, 0));
   // pack into one device buffer: int64 arrays first
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   struct Part { const void* src; size_t bytes; size_t off; };
@@ -361,6 +405,8 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   const size_t p_item_s1 = add(item_s1.data(), item_s1.size() * 4);
   const size_t p_n_chunks = add(n_chunks.data(), n_chunks.size() * 4);
   const size_t p_first_item = add(first_item.data(), first_item.size() * 4);
+  const size_t p_tblk = add(tblk.data(), tblk.size() * 4);
+  const size_t p_idesc = add(idesc.data(), idesc.size() * sizeof(int4));
   if (mint.empty()) { mint.push_back(0); mtile.push_back(0); }
   const size_t p_mom_off = add(mom_off.data(), mom_off.size() * 8);
   const size_t p_mint = add(mint.data(), mint.size() * 4);
@@ -416,6 +462,10 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   a.n_active = (int32_t*)at(p_misc);
   a.qhead = (int32_t*)at(p_misc) + 4;
   a.kbase = (int32_t*)at(p_misc) + 8;
+  a.err = (int32_t*)at(p_misc) + 12;
+  a.tblk = (const int32_t*)at(p_tblk);
+  a.item_desc = (const int4*)at(p_idesc);
+  a.tblk_max = tblk_max;
   a.n_items = n_items;
   a.na_max = na_max;
   a.mom_off = (const int64_t*)at(p_mom_off);
@@ -442,16 +492,20 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   GC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   GC_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (P.smem > max_smem) return GC_ERR_LIMIT;
+  Tune tn = tune;
+  // the bulk-copy kernel's ring must fit; otherwise the register-prefetch kernel takes its place
+  if (mode == 1 && tn.prefetch == 3 && di_macc_bulk_smem(kind, na_max, tblk_max) > max_smem) tn.prefetch = 1;
   if (mode == 1) {
-    P.smem = di_macc_smem(kind, na_max, tune.red_chunks, tune.prefetch);
+    P.smem = tn.prefetch == 3 ? di_macc_bulk_smem(kind, na_max, tblk_max)
+                              : di_macc_smem(kind, na_max, tn.red_chunks, tn.prefetch);
     if (P.smem > max_smem) return GC_ERR_LIMIT;
-    GC_CUDA_I(di_macc_max_blocks_per_sm(kind, P.smem, tune.red_chunks, tune.prefetch, &per_sm));
+    GC_CUDA_I(di_macc_max_blocks_per_sm(kind, P.smem, tn.red_chunks, tn.prefetch, &per_sm));
   } else {
     GC_CUDA_I(di_max_blocks_per_sm(kind, dtype, acc_only, P.smem, &per_sm));
   }
   if (per_sm < 1) return GC_ERR_LIMIT;
   if (tune.bps > 0 && tune.bps < per_sm) per_sm = tune.bps;
-  P.tune = tune;
+  P.tune = tn;
   P.grid = nsm * per_sm;
   if (P.grid > n_items) P.grid = n_items > 0 ? n_items : 1;
   if (mode == 1) {
@@ -910,7 +964,9 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   std::vector<int32_t> stv(P->n_int), itv(P->n_int);
   GC_CUDA(cudaMemcpyAsync(stv.data(), a.status, (size_t)P->n_int * 4, cudaMemcpyDeviceToHost, s));
   if (opt->profile) GC_CUDA(cudaMemcpyAsync(itv.data(), a.iters, (size_t)P->n_int * 4, cudaMemcpyDeviceToHost, s));
+  if (mode == 1) GC_CUDA(cudaMemcpyAsync(flag + 5, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   GC_CUDA(cudaStreamSynchronize(s));
+  if (mode == 1 && flag[5]) return cuda_fail(cudaErrorLaunchTimeout, "a bulk copy of an accumulate tile did not complete");
   int bad = 0;
   for (int i = 0; i < P->n_int; ++i) bad += (stv[i] & 15) != GC_ST_OK;
   if (opt->profile) {
@@ -1124,7 +1180,11 @@ static int run_wavefront(const void* vis, const void* model, const gc_layout* L,
     GC_CUDA(cudaMemcpyAsync(chi2_out, P->chi2_out, (size_t)n_int * 8, cudaMemcpyDeviceToDevice, s));
   std::vector<int32_t> stv(n_int);
   GC_CUDA(cudaMemcpyAsync(stv.data(), a.status, (size_t)n_int * 4, cudaMemcpyDeviceToHost, s));
+  int* berr = nullptr;
+  if ((rc = pinned_flag(&berr))) return rc;
+  GC_CUDA(cudaMemcpyAsync(berr + 5, a.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   GC_CUDA(cudaStreamSynchronize(s));
+  if (berr[5]) return cuda_fail(cudaErrorLaunchTimeout, "a bulk copy of an accumulate tile did not complete");
   int bad = 0;
   for (int i = 0; i < n_int; ++i) bad += (stv[i] & 15) != GC_ST_OK;
   if (next < n_waves) return GC_ERR_LIMIT;  // the segment bound ran out before every wave joined
@@ -1202,9 +1262,10 @@ static int autotune_di(int kind, const void* vis, const void* model, const gc_la
   std::vector<Tune> cands;
   if (mode == 1) {
     for (int ch : {1, 4})
-      for (int pf : {0, 1, 2})
+      for (int pf : {0, 1, 2, 3})
         for (int bps : {0, 2}) {
-          if (pf == 2 && ch != 1) continue;  // the staged kernel reduces in one chunk
+          if ((pf == 2 || pf == 3) && ch != 1) continue;  // the staged and bulk kernels reduce in one chunk
+          if (pf == 3 && (kind != 1 || bps != 0)) continue;  // bulk: 2x2 only, two CTAs per SM by construction
           Tune t;
           t.red_chunks = ch;
           t.prefetch = pf;

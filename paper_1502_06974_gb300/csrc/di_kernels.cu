@@ -19,6 +19,8 @@
 // therefore bitwise reproducible run to run.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -557,6 +559,191 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_staged_kernel(const DIA
   cp_async_wait<0>();
 }
 
+// ------------------------------------------------------------------------------------ bulk-copy accumulate
+// di_macc_bulk_kernel: the accumulate launch fed by bulk asynchronous copies (cp.async.bulk, the
+// one-dimensional form of the tensor memory accelerator) into a two-stage shared-memory ring per
+// CTA.  Per tile, one thread copies four contiguous blocks whose addresses come from the item's
+// descriptor alone: the tile's moments (48 KB for 2x2), its static block (the antenna pair of each
+// slot and the slot lists of the reduction), and the interval's gains and auxiliaries; an mbarrier
+// per stage counts the bytes in.  The next tile is in flight while the current one is computed and
+// reduced from shared memory, so the only global loads on a tile's dependency chain are the
+// work-list entry and the descriptor, which the copying thread fetches a tile further ahead.  Same
+// arithmetic and reduction order as di_macc_kernel with CH = 1 (identical results).
+constexpr int kBulkSpins = 1 << 22;  // bounded mbarrier waits: each try_wait also suspends briefly
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned addr = smem_u32(bar);
+  for (int n = 0; n < kBulkSpins; ++n) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+template <class MK>
+struct BulkShape {
+  using K = typename MK::K;
+  static constexpr int PS = 2 * K::NC + 1;
+  static constexpr int MW = MK::NM > PS ? MK::NM : PS;  // floats per slot in a stage's first region
+  static_assert(MK::NM % 4 == 0 && K::GW % 4 == 0 && MK::AW % 4 == 0, "bulk copies move 16-byte units");
+  // a stage: [MW][TB] moments (then [TB][PS] partials) | static block | gains | auxiliaries
+  __host__ __device__ static size_t stage_floats(int na_max, int tblk_max) {
+    return (size_t)MW * kDIThreads + (size_t)tblk_max + (size_t)na_max * (K::GW + MK::AW);
+  }
+};
+
+template <class MK>
+__global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArgs a) {
+  using K = typename MK::K;
+  using Sh = BulkShape<MK>;
+  constexpr int NC = K::NC, GW = K::GW, NM = MK::NM, NG = NM / 4, AW = MK::AW, TB = kDIThreads, PS = Sh::PS,
+                MW = Sh::MW;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ int4 hdr[2][2];  // per stage: {baselines, table antennas, scratch lo, hi}, {first gain, ...}
+  const int tid = threadIdx.x;
+  const int na_max = a.na_max, tbm = a.tblk_max;
+  const size_t sf = Sh::stage_floats(na_max, tbm);
+  const int k = a.k + (a.kbase ? *a.kbase : 0);
+  const int cur = k % 3;
+  const bool fixed = a.xcount > 0;
+  const int* list = a.ilist + (size_t)cur * a.n_items;
+  const int n_list = fixed ? a.xcount : a.icount[cur];
+  if (!fixed && blockIdx.x == 0 && tid == 0) a.icount[(k + 2) % 3] = 0;
+  const int G = gridDim.x;
+  if ((int)blockIdx.x >= n_list) return;  // the whole CTA: no tile for it
+  const float* gains = static_cast<const float*>(a.gains);
+  const bool gal = (reinterpret_cast<uintptr_t>(gains) & 15) == 0;  // gains copied in bulk when 16-byte aligned
+  float* const stage0 = reinterpret_cast<float*>(smem_raw);
+  // descriptor of the item at `slot` (thread 0)
+  auto desc = [&](int slot, int4* d) {
+    const int it = fixed ? a.xbegin + slot : list[slot];
+    const int4* p = a.item_desc + (size_t)it * 3;
+    d[0] = p[0];
+    d[1] = p[1];
+    d[2] = p[2];
+  };
+  // copies of one tile into stage s (thread 0)
+  auto issue = [&](int s, const int4* d) {
+    float* st = stage0 + (size_t)s * sf;
+    const int64_t mom = (int64_t)(((uint64_t)(unsigned)d[0].y << 32) | (unsigned)d[0].x);
+    const int go = d[1].z, na = d[1].w;
+    hdr[s][0] = make_int4(d[0].z, d[1].y, d[2].x, d[2].y);
+    hdr[s][1] = make_int4(go, 0, 0, 0);
+    const unsigned mb = (unsigned)(NM * TB * sizeof(float)), tb = (unsigned)d[1].x * 4u;
+    const unsigned gb = gal ? (unsigned)(na * GW * sizeof(float)) : 0u, ab = (unsigned)(na * AW * sizeof(float));
+    mbar_expect_tx(&full[s], mb + tb + gb + ab);
+    bulk_g2s(st, a.moments + mom, mb, &full[s]);
+    bulk_g2s(st + MW * TB, a.tblk + d[0].w, tb, &full[s]);
+    if (gb) bulk_g2s(st + MW * TB + tbm, gains + (size_t)go * GW, gb, &full[s]);
+    bulk_g2s(st + MW * TB + tbm + (size_t)na_max * GW, a.aux + (size_t)go * AW, ab, &full[s]);
+  };
+  int4 nd[3];          // thread 0: descriptor of the slot after the two in flight
+  bool pend[2] = {false, false};
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int4 d[3];
+    desc(blockIdx.x, d);
+    issue(0, d);
+    pend[0] = true;
+    if ((int)blockIdx.x + G < n_list) {
+      desc(blockIdx.x + G, d);
+      issue(1, d);
+      pend[1] = true;
+    }
+    if ((int)blockIdx.x + 2 * G < n_list) desc(blockIdx.x + 2 * G, nd);
+  }
+  int j = 0;
+  for (int slot = blockIdx.x; slot < n_list; slot += G, ++j) {
+    const int s = j & 1;
+    const bool ok = mbar_wait(&full[s], (unsigned)(j >> 1) & 1u);
+    float* st = stage0 + (size_t)s * sf;
+    const int4 h = hdr[s][0];
+    const int nbt = h.x, nat = h.y, go = hdr[s][1].x;
+    const int* tbk = reinterpret_cast<const int*>(st + MW * TB);
+    const float* sg = st + MW * TB + tbm;
+    const float* sa = sg + (size_t)na_max * GW;
+    float pp[NC], pq[NC];
+    int p = -1;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pp[c] = pq[c] = 0.f;
+    if (ok && tid < nbt) {
+      p = tbk[tid];
+      const int q = tbk[TB + tid];
+      float m[NM];
+      const float4* mine = reinterpret_cast<const float4*>(st) + tid;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const float4 v = mine[g * TB];
+        m[4 * g] = v.x; m[4 * g + 1] = v.y; m[4 * g + 2] = v.z; m[4 * g + 3] = v.w;
+      }
+      const typename K::G gp = gal ? K::ld_gain(sg + p * GW) : K::ld_gain(gains + ((int64_t)go + p) * GW);
+      const typename K::G gq = gal ? K::ld_gain(sg + q * GW) : K::ld_gain(gains + ((int64_t)go + q) * GW);
+      MK::partials(m, gp, gq, sa + p * AW, sa + q * AW, pp, pq);
+    }
+    warp_run_scan<NC>(p, pp);
+    // every thread has its moments in registers: the stage's first region takes the partials.  A
+    // copy that never landed ends the CTA (all threads agree), after a bounded wait for the rest.
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(a.err, 1);
+        for (int t = 0; t < 2; ++t)
+          if (pend[t] && t != s) mbar_wait(&full[t], (unsigned)((j + 1) >> 1) & 1u);
+      }
+      return;
+    }
+    if (tid == 0) pend[s] = false;
+    float* part = st;  // [TB][PS]
+    if (tid < nbt) {
+      float* my = part + tid * PS;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) { my[c] = pp[c]; my[NC + c] = pq[c]; }
+    }
+    __syncthreads();
+    const int* off = tbk + 2 * TB;
+    const int* ent = off + ((nat + 1 + 3) & ~3);
+    float* scr = static_cast<float*>(a.scratch) + (int64_t)(((uint64_t)(unsigned)h.w << 32) | (unsigned)h.z);
+    for (int x = tid; x < nat * NC; x += TB) {
+      const int an = x / NC, c = x - an * NC;
+      const int e1 = off[an + 1];
+      float sum = 0.f;
+      for (int e = off[an]; e < e1; ++e) sum += part[ent[e] + c];
+      scr[x] = sum;
+    }
+    __syncthreads();  // the stage is free
+    if (tid == 0 && slot + 2 * G < n_list) {
+      // the stage was read and written through the generic proxy: order that before the copy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(s, nd);
+      pend[s] = true;
+      if (slot + 3 * G < n_list) desc(slot + 3 * G, nd);
+    }
+  }
+}
+
 template <class MK>
 __global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, int n_int) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -823,6 +1010,7 @@ __global__ void di_init_kernel(const DIArgs a, int n_int, int n_active0) {
   if (i == 0) {
     *a.n_active = n_active0;
     if (a.kbase) *a.kbase = 0;
+    if (a.err) *a.err = 0;
     a.qhead[0] = 0;
     a.qhead[1] = 0;
     if (a.icount) {
@@ -900,6 +1088,9 @@ static void* pick(int kind, int dtype, int acc_only) {
 template <class MK>
 static const void* pick_acc_k(int red_chunks, int prefetch) {
   const bool c4 = red_chunks == kRedChunks;
+  if constexpr (std::is_same<MK, JonesMom>::value) {
+    if (prefetch == 3) return (const void*)&di_macc_bulk_kernel<MK>;
+  }
   if (prefetch == 2) return (const void*)&di_macc_staged_kernel<MK>;
   if (prefetch) return c4 ? (const void*)&di_macc_kernel<MK, kRedChunks, true> : (const void*)&di_macc_kernel<MK, 1, true>;
   return c4 ? (const void*)&di_macc_kernel<MK, kRedChunks, false> : (const void*)&di_macc_kernel<MK, 1, false>;
@@ -917,6 +1108,11 @@ int di_macc_smem(int kind, int na_max, int red_chunks, int prefetch) {
   }
   const int ch = red_chunks == kRedChunks ? kRedChunks : 1;
   return (int)(sizeof(float) * ((size_t)kDIThreads * (2 * nc + 1) + (size_t)na_max * nc * ch + (size_t)na_max * nc));
+}
+
+int di_macc_bulk_smem(int kind, int na_max, int tblk_max) {
+  if (kind != 1) return 1 << 30;
+  return (int)(2 * sizeof(float) * BulkShape<JonesMom>::stage_floats(na_max, tblk_max));
 }
 
 int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, int* out) {

@@ -79,6 +79,17 @@ struct DIArgs {
   // the init launch fills (0 = list 1, the two-launch scheme's first list)
   int32_t* flag;
   int32_t first_list;
+  // bulk-copy accumulate (di_macc_bulk_kernel): per item three int4 descriptors
+  //   {moment float index lo, hi, baselines in the tile, static block offset (ints)},
+  //   {static block length (ints), antennas of the table, first gain, antennas of the interval},
+  //   {scratch offset lo, hi, 0, 0};
+  // per (table, tile) one static block of ints, 16-byte aligned: ant1 and ant2 of the tile's slots
+  // [kDIThreads each], the reduction offsets [tab_nant + 1, padded to 4] and slot entries [padded
+  // to 4]; tblk_max the longest block; err set when a copy's wait gives up.
+  const int4* item_desc;
+  const int32_t* tblk;
+  int32_t tblk_max;
+  int32_t* err;
 };
 
 // Launchers implemented in di_kernels.cu.  kind: 0 scalar, 1 jones.  Return cudaError_t as int.
@@ -87,6 +98,7 @@ int di_max_blocks_per_sm(int kind, int dtype, int acc_only, int smem, int* out);
 int di_launch_iter(int kind, int dtype, int acc_only, const DIArgs& a, int grid, int smem, void* stream);
 int di_launch_init(const DIArgs& a, int n_int, int n_active0, void* stream);
 int di_macc_smem(int kind, int na_max, int red_chunks, int prefetch);
+int di_macc_bulk_smem(int kind, int na_max, int tblk_max);
 int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, int* out);
 // one iteration: the accumulate launch, then the solve launch
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,

@@ -276,11 +276,13 @@ def test_graph_and_plain_loops_agree(gpu_lib, monkeypatch, path):
     out = []
     # (graph, persistent loop): one launch per iteration, graph segments, and (moment path) the
     # persistent cooperative loop kernel with grid barriers between the two phases
-    # and (moment path) the accumulate kernel with register prefetch or shared-memory staging, and
-    # one cooperative launch per iteration (update of k - 1, then accumulate of k) vs two launches
+    # and (moment path) the accumulate kernel with register prefetch, shared-memory staging or bulk
+    # copies into a two-stage ring, and one cooperative launch per iteration (update of k - 1, then
+    # accumulate of k) vs two launches
     modes = [("0", "0", "0", "0"), ("1", "0", "0", "0")]
     if path == N.GC_PATH_MOMENTS:
         modes += [("0", "1", "0", "0"), ("1", "0", "1", "0"), ("1", "0", "2", "0"), ("0", "0", "2", "0"),
+                  ("1", "0", "3", "0"), ("0", "0", "3", "0"),
                   ("1", "0", "1", "1"), ("0", "0", "1", "1"), ("1", "0", "0", "1")]
     for graph, loop, pf, step1 in modes:
         monkeypatch.setenv("GAINCAL_GRAPH", graph)
@@ -300,6 +302,24 @@ def test_graph_and_plain_loops_agree(gpu_lib, monkeypatch, path):
     for o in out[1:]:
         assert torch.equal(out[0][0], o[0]) and torch.equal(out[0][1], o[1]) and torch.equal(out[0][2], o[2])
     assert (out[0][1].numpy() <= 37).all()
+
+
+def test_bulk_accumulate_with_unaligned_gains(gpu_lib, monkeypatch):
+    """The bulk-copy accumulate copies the gains with the tile only when they start on a 16-byte
+    boundary; gains 8 bytes off it are read from global memory instead, with identical results."""
+    b = synth.make_config(2, small=True)
+    vis, model, g0, lay = device_batch(b)
+    monkeypatch.setenv("GAINCAL_ACC_PREFETCH", "3")
+    ga, ia, _, sa = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=40)
+    flat = torch.zeros(g0.numel() + 1, dtype=g0.dtype, device=g0.device)
+    gu = flat[1:].view(g0.shape)
+    gu.copy_(g0)
+    assert gu.data_ptr() % 16 == 8
+    gu, iu, _, su = api.calibrate_di_jones2x2(vis, model, lay, gu, tol=1e-6, max_iter=40)
+    assert torch.equal(ga, gu) and torch.equal(ia, iu) and torch.equal(sa, su)
+    monkeypatch.setenv("GAINCAL_ACC_PREFETCH", "1")
+    g1, i1, _, s1 = api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=1e-6, max_iter=40)
+    assert torch.equal(ga, g1) and torch.equal(ia, i1)
 
 
 def test_autotune_then_parity(gpu_lib):
