@@ -232,6 +232,7 @@ struct DIPlan {
   // moment-stream mode: moment-pass items (interval, 32 baselines), per-item chi^2 bookkeeping
   int mode = 0;
   int n_mitems = 0;
+  int ns_max = 0;  // most samples per baseline of any interval
   int64_t n_mom_bl = 0;
   const int32_t* mitem_int = nullptr;
   const int32_t* mitem_tile = nullptr;
@@ -474,6 +475,8 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
   P.mode = mode;
   P.n_mitems = n_active0 > 0 ? (int)mint.size() : 0;
   P.n_mom_bl = mo;
+  P.ns_max = 0;
+  for (int i = 0; i < n; ++i) P.ns_max = std::max(P.ns_max, (int)L->n_samp[i]);
   P.mitem_int = (const int32_t*)at(p_mint);
   P.mitem_tile = (const int32_t*)at(p_mtile);
   P.mfirst = (const int32_t*)at(p_mfirst);
@@ -813,7 +816,7 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
       GC_CUDA(cudaEventRecord(m0, s));
     }
     GC_CUDA_I(moment_pass(kind, (const float*)st.vis, (const float*)st.model, (float*)mom, a.row_off, a.mom_off,
-                          a.n_samp, a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, stream));
+                          a.n_samp, a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, P->ns_max, stream));
     void *aux = nullptr, *gnew = nullptr;
     if ((rc = ws_get("di_aux", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 4 * sizeof(float), &aux))) return rc;
     if ((rc = ws_get("di_gnew", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 8 * sizeof(float), &gnew))) return rc;
@@ -1045,7 +1048,7 @@ static int run_wavefront(const void* vis, const void* model, const gc_layout* L,
   float* g = (float*)gains;
   GC_CUDA_I(di_launch_init(a, n_int, P->n_active0, stream));
   GC_CUDA_I(moment_pass(1, (const float*)vis, (const float*)model, (float*)mom, a.row_off, a.mom_off, a.n_samp,
-                        a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, stream));
+                        a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, P->ns_max, stream));
   const int n_waves = (wf->n_t + lag - 1) / lag;
   auto wave_lo = [&](int w) { return std::min(w * lag, wf->n_t) * nfb; };
   int n0_active = 0;

@@ -249,20 +249,26 @@ __device__ __forceinline__ typename K::G ld_gain_c(const float* g) {
 }
 
 // An interval's tile partials summed in tile order with compensation, all (antenna, component)
-// pairs in parallel; antennas the baseline table does not reach get zeros.
+// pairs in parallel; antennas the baseline table does not reach get zeros.  The interval's items
+// are consecutive and so are their scratch blocks (nat * NC floats each), so every tile's address
+// is known without loading it: eight tiles' loads are in flight at once.
 template <int NC>
 __device__ __forceinline__ void combine_tiles(const DIArgs& a, const float* scr, int na, int nat, int nch, int fi,
                                               float* tot) {
+  const float* base = scr + a.item_scr[fi];
+  const int64_t stride = (int64_t)nat * NC;
   for (int x = threadIdx.x; x < na * NC; x += blockDim.x) {
     float s = 0.f, cc = 0.f;
     if (x < nat * NC) {
       int j = 0;
-      for (; j + 4 <= nch; j += 4) {
-        const float v0 = __ldcg(scr + a.item_scr[fi + j] + x), v1 = __ldcg(scr + a.item_scr[fi + j + 1] + x);
-        const float v2 = __ldcg(scr + a.item_scr[fi + j + 2] + x), v3 = __ldcg(scr + a.item_scr[fi + j + 3] + x);
-        kahan_add(s, cc, v0); kahan_add(s, cc, v1); kahan_add(s, cc, v2); kahan_add(s, cc, v3);
+      for (; j + 8 <= nch; j += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(base + (j + u) * stride + x);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) kahan_add(s, cc, v[u]);
       }
-      for (; j < nch; ++j) kahan_add(s, cc, __ldcg(scr + a.item_scr[fi + j] + x));
+      for (; j < nch; ++j) kahan_add(s, cc, __ldcg(base + j * stride + x));
     }
     tot[x] = s - cc;
   }

@@ -125,10 +125,12 @@ int di_launch_msum(int kind, const DIArgs& a, int i_lo, int n, float* tot_out, d
 int di_launch_wf_hold(const DIArgs& a, int n_int, int i_hold, int n_active0, void* stream);
 int di_launch_wf_activate(const DIArgs& a, int i_lo, int n, void* stream);
 int di_launch_maux(int kind, const float* gains, float* aux, int n_gain, void* stream);
-// moment pass (resident.cu): per-baseline moments of every interval; items are (interval, 32 baselines)
+// moment pass (resident.cu): per-baseline moments of every interval; items are (interval, 32 baselines);
+// ns_max, the most samples of any interval, picks one thread per baseline (few samples) or sample
+// lanes with a compensated shared-memory reduction
 int moment_pass(int kind, const float* vis, const float* model, float* moments, const int64_t* row_off,
                 const int64_t* mom_off, const int32_t* n_samp, const int32_t* n_bl, const int32_t* item_int,
-                const int32_t* item_tile, int n_items, void* stream);
+                const int32_t* item_tile, int n_items, int ns_max, void* stream);
 int moment_chi2(int kind, const float* vis, const float* model, const float* gains, const int64_t* row_off,
                 const int32_t* n_samp, const int32_t* n_bl, const int32_t* bl_off, const int32_t* gain_off,
                 const int32_t* ant1, const int32_t* ant2, const int32_t* item_int, const int32_t* item_tile,

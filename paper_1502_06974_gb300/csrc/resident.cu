@@ -91,6 +91,33 @@ __global__ void __launch_bounds__(kMomBl2 * kMomLanes2) di_moment_kernel(const M
   }
 }
 
+// di_moment_direct_kernel: the same moments for intervals with few samples per baseline (at most
+// kDirectSamp): one warp per 32-baseline item, one thread per baseline summing its samples in
+// order (plain FP32 sums of at most kDirectSamp terms), written straight into the tiled layout.
+// With 8 sample lanes and a shared-memory reduction, a 4-sample interval would leave half the
+// threads idle and spend most of its time in the reduction.
+constexpr int kDirectSamp = 16;
+template <class MK>
+__global__ void __launch_bounds__(256, 3) di_moment_direct_kernel(const MomArgs a) {
+  constexpr int NM = MK::NM;
+  const int it = blockIdx.x * 8 + (int)(threadIdx.x >> 5);
+  if (it >= a.n_items) return;
+  const int i = a.item_int[it], tile = a.item_tile[it];
+  const int nb = a.n_bl[i], ns = a.n_samp[i];
+  const int b = tile * kMomBl2 + (int)(threadIdx.x & 31);
+  if (b >= nb) return;
+  float m[NM];
+#pragma unroll
+  for (int c = 0; c < NM; ++c) m[c] = 0.f;
+  const int64_t r0 = a.row_off[i] + b;
+#pragma unroll 2
+  for (int s = 0; s < ns; ++s) MK::accum(a.vis, a.model, r0 + (int64_t)s * nb, m);
+  float4* out = reinterpret_cast<float4*>(a.moments);
+#pragma unroll
+  for (int g = 0; g < NM / 4; ++g)
+    out[mom_index(a.mom_off[i], b, 4 * g, NM) / 4] = make_float4(m[4 * g], m[4 * g + 1], m[4 * g + 2], m[4 * g + 3]);
+}
+
 // ------------------------------------------------------------------------------------ resident
 struct ResArgs {
   const float* moments;
@@ -597,11 +624,15 @@ static int res_run(ResPlan& P, const void* vis, const void* model, void* gains, 
 
 int moment_pass(int kind, const float* vis, const float* model, float* moments, const int64_t* row_off,
                 const int64_t* mom_off, const int32_t* n_samp, const int32_t* n_bl, const int32_t* item_int,
-                const int32_t* item_tile, int n_items, void* stream) {
+                const int32_t* item_tile, int n_items, int ns_max, void* stream) {
   if (n_items <= 0) return 0;
   MomArgs m{vis, model, moments, row_off, mom_off, n_samp, n_bl, item_int, item_tile, n_items};
   cudaStream_t s = (cudaStream_t)stream;
-  if (kind == 0) {
+  if (ns_max <= kDirectSamp) {
+    const int grid = (n_items + 7) / 8;
+    if (kind == 0) di_moment_direct_kernel<ScalarMom><<<grid, 256, 0, s>>>(m);
+    else di_moment_direct_kernel<JonesMom><<<grid, 256, 0, s>>>(m);
+  } else if (kind == 0) {
     const int sm = (int)(sizeof(float) * kMomLanes2 * kMomBl2 * ScalarMom::NM);
     di_moment_kernel<ScalarMom><<<n_items, kMomBl2 * kMomLanes2, sm, s>>>(m);
   } else {
