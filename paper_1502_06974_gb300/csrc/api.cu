@@ -1267,8 +1267,8 @@ static int autotune_di(int kind, const void* vis, const void* model, const gc_la
     for (int ch : {1, 4})
       for (int pf : {0, 1, 2, 3})
         for (int bps : {0, 2}) {
-          if ((pf == 2 || pf == 3) && ch != 1) continue;  // the staged and bulk kernels reduce in one chunk
-          if (pf == 3 && (kind != 1 || bps != 0)) continue;  // bulk: 2x2 only, two CTAs per SM by construction
+          if (pf >= 2 && ch != 1) continue;  // the staged and bulk-copy kernels reduce in one chunk
+          if (pf == 3 && (kind != 1 || bps != 0)) continue;  // the bulk-copy kernel: 2x2 only
           Tune t;
           t.red_chunks = ch;
           t.prefetch = pf;

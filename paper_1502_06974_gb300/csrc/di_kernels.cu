@@ -639,9 +639,10 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
   const float* gains = static_cast<const float*>(a.gains);
   const bool gal = (reinterpret_cast<uintptr_t>(gains) & 15) == 0;  // gains copied in bulk when 16-byte aligned
   float* const stage0 = reinterpret_cast<float*>(smem_raw);
-  // descriptor of the item at `slot` (thread 0)
-  auto desc = [&](int slot, int4* d) {
-    const int it = fixed ? a.xbegin + slot : list[slot];
+  // work-list entry and descriptor of a slot (thread 0); they are fetched a tile apart so that
+  // neither load waits for the other
+  auto item = [&](int slot) { return fixed ? a.xbegin + slot : list[slot]; };
+  auto desc = [&](int it, int4* d) {
     const int4* p = a.item_desc + (size_t)it * 3;
     d[0] = p[0];
     d[1] = p[1];
@@ -663,6 +664,7 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
     bulk_g2s(st + MW * TB + tbm + (size_t)na_max * GW, a.aux + (size_t)go * AW, ab, &full[s]);
   };
   int4 nd[3];          // thread 0: descriptor of the slot after the two in flight
+  int nit = 0;         // thread 0: work-list entry of the slot after that
   bool pend[2] = {false, false};
   if (tid == 0) {
     mbar_init(&full[0], 1);
@@ -672,15 +674,16 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
   __syncthreads();
   if (tid == 0) {
     int4 d[3];
-    desc(blockIdx.x, d);
+    desc(item(blockIdx.x), d);
     issue(0, d);
     pend[0] = true;
     if ((int)blockIdx.x + G < n_list) {
-      desc(blockIdx.x + G, d);
+      desc(item(blockIdx.x + G), d);
       issue(1, d);
       pend[1] = true;
     }
-    if ((int)blockIdx.x + 2 * G < n_list) desc(blockIdx.x + 2 * G, nd);
+    if ((int)blockIdx.x + 2 * G < n_list) desc(item(blockIdx.x + 2 * G), nd);
+    if ((int)blockIdx.x + 3 * G < n_list) nit = item(blockIdx.x + 3 * G);
   }
   int j = 0;
   for (int slot = blockIdx.x; slot < n_list; slot += G, ++j) {
@@ -745,7 +748,8 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(s, nd);
       pend[s] = true;
-      if (slot + 3 * G < n_list) desc(slot + 3 * G, nd);
+      if (slot + 3 * G < n_list) desc(nit, nd);
+      if (slot + 4 * G < n_list) nit = item(slot + 4 * G);
     }
   }
 }
