@@ -152,30 +152,62 @@ GC_DEV int block_or(int v, int* red) {
   return r;
 }
 
-// Fused end-of-update reduction over the block: sums of d2 and n2 (double) and OR of two flags,
-// two barriers.  Every thread gets the totals (warp totals summed in the same order everywhere).
-// `red` holds >= 96 doubles.
-GC_DEV void block_reduce_step(double& d2, double& n2, int& f1, int& f2, double* red) {
+// Float-float ("double-float") arithmetic on the FP32 pipe: an unevaluated sum hi + lo with
+// |lo| <= ulp(hi) / 2.  Knuth's TwoSum gives a sum's rounding error exactly; an FMA gives a
+// product's (the TwoProduct of Ogita, Rump and Oishi).  GB300 runs FP32 many times faster than
+// FP64, so sums that want more than FP32 precision are kept in these pairs instead of in doubles.
+struct FF {
+  float hi, lo;
+};
+// (the _rn intrinsics are never contracted into FMAs, which would break the exact error terms)
+GC_DEV FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+GC_DEV FF ff_add(FF x, FF y) {
+  const FF s = ff_two_sum(x.hi, y.hi);
+  const float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  const float hi = __fadd_rn(s.hi, lo);  // renormalise (fast TwoSum, |s.hi| >= |lo|)
+  return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+// x - a * b, with the product's rounding error carried into lo
+GC_DEV FF ff_sub_prod(FF x, float a, float b) {
+  const float p = __fmul_rn(a, b), e = __fmaf_rn(a, b, -p);
+  const FF s = ff_two_sum(x.hi, -p);
+  const float lo = __fadd_rn(s.lo, __fsub_rn(x.lo, e));
+  const float hi = __fadd_rn(s.hi, lo);
+  return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+
+GC_DEV FF ff_add_f(FF x, float v) { return ff_add(x, FF{v, 0.f}); }
+GC_DEV double ff_value(FF x) { return (double)x.hi + (double)x.lo; }
+
+// End-of-update reduction over the block with the two sums in float-float: every thread gets the
+// block totals of d2 and n2 (warp butterflies, then the warps in order) and the OR of the two
+// flags; two barriers.  `red` holds >= 160 floats.
+GC_DEV void block_reduce_step_ff(FF& d2, FF& n2, int& f1, int& f2, float* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   int fl = (f1 ? 1 : 0) | (f2 ? 2 : 0);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-    n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    d2 = ff_add(d2, FF{__shfl_xor_sync(0xffffffffu, d2.hi, o), __shfl_xor_sync(0xffffffffu, d2.lo, o)});
+    n2 = ff_add(n2, FF{__shfl_xor_sync(0xffffffffu, n2.hi, o), __shfl_xor_sync(0xffffffffu, n2.lo, o)});
     fl |= __shfl_xor_sync(0xffffffffu, fl, o);
   }
   if (lane == 0) {
-    red[warp] = d2;
-    red[32 + warp] = n2;
-    red[64 + warp] = (double)fl;
+    red[warp] = d2.hi;
+    red[32 + warp] = d2.lo;
+    red[64 + warp] = n2.hi;
+    red[96 + warp] = n2.lo;
+    red[128 + warp] = __int_as_float(fl);
   }
   __syncthreads();
-  double a = 0.0, b = 0.0;
+  FF a{0.f, 0.f}, b{0.f, 0.f};
   int f = 0;
   for (int w = 0; w < nw; ++w) {
-    a += red[w];
-    b += red[32 + w];
-    f |= (int)red[64 + w];
+    a = ff_add(a, FF{red[w], red[32 + w]});
+    b = ff_add(b, FF{red[64 + w], red[96 + w]});
+    f |= __float_as_int(red[128 + w]);
   }
   __syncthreads();
   d2 = a;
@@ -183,6 +215,7 @@ GC_DEV void block_reduce_step(double& d2, double& n2, int& f1, int& f2, double* 
   f1 = f & 1;
   f2 = (f >> 1) & 1;
 }
+
 
 // Fixed-order reduction of one tile's per-slot partial sums into per-antenna sums.  `off`/`ent`
 // give, per antenna, the list of partial-sum slots (float offsets into `part`).  Each list is cut

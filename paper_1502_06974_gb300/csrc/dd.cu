@@ -273,33 +273,6 @@ __device__ bool chol_solve_warp(const double2* Aup, const double2* b, double2* x
   return true;
 }
 
-// Float-float ("double-float") arithmetic on the FP32 pipe: an unevaluated sum hi + lo with
-// |lo| <= ulp(hi) / 2.  Knuth's TwoSum gives a sum's rounding error exactly; an FMA gives a
-// product's (the TwoProduct of Ogita, Rump and Oishi).  GB300 runs FP32 many times faster than
-// FP64, so the iteration keeps its extra precision in these pairs instead of in doubles.
-struct FF {
-  float hi, lo;
-};
-// (the _rn intrinsics are never contracted into FMAs, which would break the exact error terms)
-__device__ __forceinline__ FF ff_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
-  return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ FF ff_add(FF x, FF y) {
-  const FF s = ff_two_sum(x.hi, y.hi);
-  const float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
-  const float hi = __fadd_rn(s.hi, lo);  // renormalise (fast TwoSum, |s.hi| >= |lo|)
-  return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
-}
-// x - a * b, with the product's rounding error carried into lo
-__device__ __forceinline__ FF ff_sub_prod(FF x, float a, float b) {
-  const float p = __fmul_rn(a, b), e = __fmaf_rn(a, b, -p);
-  const FF s = ff_two_sum(x.hi, -p);
-  const float lo = __fadd_rn(s.lo, __fsub_rn(x.lo, e));
-  const float hi = __fadd_rn(s.hi, lo);
-  return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
-}
-
 // The factorisation in FP32 followed by one step of iterative refinement (Moler's
 // mixed-precision scheme): the residual r = b - A x0 in float-float against the float-float
 // block, then the correction solved with the FP32 factor; one step takes the error from about

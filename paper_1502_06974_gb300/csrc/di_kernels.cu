@@ -292,7 +292,7 @@ __device__ __forceinline__ void solve_interval(const DIArgs& a, int k, int i, fl
   const int nch = a.n_chunks[i], fi = a.first_item[i];
   combine_tiles<NC>(a, scr, na, nat, nch, fi, tot);
   __syncthreads();
-  double d2 = 0.0, n2 = 0.0;
+  FF d2{0.f, 0.f}, n2{0.f, 0.f};  // float-float sums (the FP64 pipe of GB300 is narrow)
   int sing = 0, nonfin = 0;
   const int kl = k - (a.k0 ? ldc<COH>(a.k0 + i) : 0);  // the interval's own iteration number
   const bool gn_step = (a.schedule == GC_SCHED_GN) || (kl & 1);
@@ -301,12 +301,12 @@ __device__ __forceinline__ void solve_interval(const DIArgs& a, int k, int i, fl
     G g;
     if (!K::solve(tot + an * NC, old, g)) sing = 1;
     const G nw = gn_step ? g : K::avg(old, g);
-    d2 += (double)K::dist2(nw, old);
-    n2 += (double)K::norm2(nw);
+    d2 = ff_add_f(d2, K::dist2(nw, old));
+    n2 = ff_add_f(n2, K::norm2(nw));
     if (!K::finite(nw)) nonfin = 1;
     K::st_gain(a.gnew + (go + an) * GW, nw);   // staged until the interval's decision is known
   }
-  block_reduce_step(d2, n2, sing, nonfin, red);
+  block_reduce_step_ff(d2, n2, sing, nonfin, reinterpret_cast<float*>(red));
   if (!nonfin)
     for (int an = tid; an < na; an += TB) {
       const G nw = K::ld_gain(a.gnew + (go + an) * GW);
@@ -314,11 +314,12 @@ __device__ __forceinline__ void solve_interval(const DIArgs& a, int k, int i, fl
       MK::aux(nw, a.aux + (go + an) * AW);
     }
   if (tid == 0) {
+    const double D2 = ff_value(d2), N2 = ff_value(n2);
     int st = -1;
     if (nonfin) st = GC_ST_NONFINITE;
-    else if (d2 <= a.tol * a.tol * n2) st = GC_ST_OK;
+    else if (D2 <= a.tol * a.tol * N2) st = GC_ST_OK;
     else if (kl >= a.max_iter) st = GC_ST_NOT_CONVERGED;
-    if (a.gate && a.gate[i] == 0 && (st >= 0 || d2 <= a.gate_tol * a.gate_tol * n2)) a.gate[i] = kl;
+    if (a.gate && a.gate[i] == 0 && (st >= 0 || D2 <= a.gate_tol * a.gate_tol * N2)) a.gate[i] = kl;
     if (st >= 0) {
       a.active[i] = 0;
       a.iters[i] = kl;
@@ -755,7 +756,7 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
 }
 
 template <class MK>
-__global__ void __launch_bounds__(kDIThreads) di_msolve_kernel(const DIArgs a, int n_int) {
+__global__ void __launch_bounds__(kDIThreads, 8) di_msolve_kernel(const DIArgs a, int n_int) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[96];
   msolve_phase<MK, false>(a, a.k + (a.kbase ? *a.kbase : 0), n_int, reinterpret_cast<float*>(smem_raw), red);

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kResThreads, 1) di_resident_kernel(const ResAr
       cluster.sync();
       // (C) totals in rank order, update, schedule, convergence -- identical in every CTA
       const bool gn_step = (a.schedule == GC_SCHED_GN) || (k & 1);
-      double d2 = 0.0, n2 = 0.0;
+      FF d2{0.f, 0.f}, n2{0.f, 0.f};
       int sg = 0, nonfin = 0;
       float* gn_out = gsb + (cur ^ 1) * a.na_max * GW;
       float* ax_out = axb + (cur ^ 1) * a.na_max * AW;
@@ -261,17 +261,17 @@ __global__ void __launch_bounds__(kResThreads, 1) di_resident_kernel(const ResAr
         G g;
         if (!K::solve(v, old, g)) sg = 1;
         const G nw = gn_step ? g : K::avg(old, g);
-        d2 += (double)K::dist2(nw, old);
-        n2 += (double)K::norm2(nw);
+        d2 = ff_add_f(d2, K::dist2(nw, old));
+        n2 = ff_add_f(n2, K::norm2(nw));
         if (!K::finite(nw)) nonfin = 1;
         K::st_gain(gn_out + an * GW, nw);
         MK::aux(nw, ax_out + an * AW);
       }
-      block_reduce_step(d2, n2, sg, nonfin, red);
+      block_reduce_step_ff(d2, n2, sg, nonfin, reinterpret_cast<float*>(red));
       sing = sg;
       if (nonfin) { st = GC_ST_NONFINITE; break; }
       cur ^= 1;
-      if (d2 <= a.tol * a.tol * n2) { st = GC_ST_OK; break; }
+      if (ff_value(d2) <= a.tol * a.tol * ff_value(n2)) { st = GC_ST_OK; break; }
       if (k >= a.max_iter) { st = GC_ST_NOT_CONVERGED; break; }
     }
     if (rank == 0) {
