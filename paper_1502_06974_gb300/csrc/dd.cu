@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
   float4* red = reinterpret_cast<float4*>(gs + a.na_max * ND);       // [LANES][NO] float-float (re, im)
   __shared__ Cx<float> Ah[NU], Al[NU], bh[ND], bl[ND], xs[ND];
   __shared__ int s_last, s_sing;
-  __shared__ double s_red[64];
+  __shared__ double s_red[80];  // >= 160 floats for the end-of-update reduction
   __shared__ int2 s_ent[kIterThreads];
   const int it = blockIdx.x;
   if (it >= a.n_iitems) return;
@@ -478,22 +478,20 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
   if (!s_last) return;
   __threadfence();
   const bool gn_step = (a.schedule == GC_SCHED_GN) || (k & 1);
-  float d2 = 0.f, n2 = 0.f;
+  FF d2{0.f, 0.f}, n2{0.f, 0.f};  // float-float sums (the FP64 pipe of GB300 is narrow)
   int nonfin = 0, sing = 0;
   for (int x = tid; x < na * ND; x += blockDim.x) {
     const Cx<float> old = gs[x];
     const Cx<float> gn = cx<float>(__ldcg(a.gnew + 2 * (go * ND + x)), __ldcg(a.gnew + 2 * (go * ND + x) + 1));
     const Cx<float> nw = gn_step ? gn : cx<float>(0.5f * (old.x + gn.x), 0.5f * (old.y + gn.y));
-    d2 += abs2_(sub_(nw, old));
-    n2 += abs2_(nw);
+    d2 = ff_add_f(d2, abs2_(sub_(nw, old)));
+    n2 = ff_add_f(n2, abs2_(nw));
     if (!isfinite(nw.x) || !isfinite(nw.y)) nonfin = 1;
     gs[x] = nw;  // stage; written below unless non-finite
   }
   for (int x = tid; x < na; x += blockDim.x) sing |= __ldcg(a.sing + go + x);
-  const double D2 = block_sum<double>((double)d2, s_red);
-  const double N2 = block_sum<double>((double)n2, s_red);
-  nonfin = block_or(nonfin, reinterpret_cast<int*>(s_red));
-  sing = block_or(sing, reinterpret_cast<int*>(s_red));
+  block_reduce_step_ff(d2, n2, nonfin, sing, reinterpret_cast<float*>(s_red));
+  const double D2 = ff_value(d2), N2 = ff_value(n2);
   if (!nonfin)
     for (int x = tid; x < na * ND; x += blockDim.x) {
       a.gains[2 * (go * ND + x)] = gs[x].x;
