@@ -159,7 +159,7 @@ struct Tune {
                           // 2 staged in shared memory by cp.async, 3 bulk copies into a two-stage ring (2x2;
                           // scalar moments take 1)
   int bps = 0;            // CTAs per SM of the persistent grid (0 = as many as fit)
-  int check_every = 16;   // iterations per graph segment / between host checks of the active count
+  int check_every = 64;   // iterations per graph segment / between host checks of the active count
   int target_rows = 0;    // raw-row path: rows per work item (0 = default)
   int graph = 1;          // capture iteration segments in a CUDA graph
   int step1 = 0;          // moment path: one cooperative launch per iteration (update + accumulate)

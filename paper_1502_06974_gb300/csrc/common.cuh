@@ -7,6 +7,13 @@
 
 #define GC_DEV __device__ __forceinline__
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may start
+// before the previous kernel in the stream has finished.  pdl_launch_dependents lets the next
+// kernel be scheduled early; pdl_wait blocks until every prerequisite grid has completed and its
+// memory is visible (a no-op for a kernel launched without the attribute).
+GC_DEV void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+GC_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename T>
 struct Cx {
   T x, y;  // re, im

@@ -19,6 +19,7 @@
 // therefore bitwise reproducible run to run.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <type_traits>
 
 #include <algorithm>
@@ -466,6 +467,8 @@ __device__ __forceinline__ void macc_phase(const DIArgs& a, int k, float* smem) 
 template <class MK, int CH, bool PF>
 __global__ void __launch_bounds__(kDIThreads, PF ? 3 : 4) di_macc_kernel(const DIArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_launch_dependents();
+  pdl_wait();  // gains, lists and the iteration base come from the previous launch
   macc_phase<MK, CH, PF, false>(a, a.k + (a.kbase ? *a.kbase : 0), reinterpret_cast<float*>(smem_raw));
 }
 
@@ -485,6 +488,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <class MK>
 __global__ void __launch_bounds__(kDIThreads, 2) di_macc_staged_kernel(const DIArgs a) {
+  pdl_launch_dependents();
+  pdl_wait();  // gains, lists and the iteration base come from the previous launch
   using K = typename MK::K;
   constexpr int NC = K::NC, GW = K::GW, NM = MK::NM, NG = NM / 4, AW = MK::AW, TB = kDIThreads, PS = 2 * NC + 1;
   // a stage holds a tile's moments ([NG][TB] float4) and, after they are read, its partials
@@ -619,11 +624,13 @@ struct BulkShape {
 
 template <class MK>
 __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArgs a) {
+  pdl_launch_dependents();
+  pdl_wait();  // gains, lists and the iteration base come from the previous launch
   using K = typename MK::K;
   using Sh = BulkShape<MK>;
   constexpr int NC = K::NC, GW = K::GW, NM = MK::NM, NG = NM / 4, AW = MK::AW, TB = kDIThreads, PS = Sh::PS,
                 MW = Sh::MW;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[2];
   __shared__ int4 hdr[2][2];  // per stage: {baselines, table antennas, scratch lo, hi}, {first gain, ...}
   const int tid = threadIdx.x;
@@ -758,6 +765,8 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
 template <class MK>
 __global__ void __launch_bounds__(kDIThreads, 8) di_msolve_kernel(const DIArgs a, int n_int) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_launch_dependents();
+  pdl_wait();  // the tile partials come from the accumulate launch
   __shared__ double red[96];
   msolve_phase<MK, false>(a, a.k + (a.kbase ? *a.kbase : 0), n_int, reinterpret_cast<float*>(smem_raw), red);
 }
@@ -1213,33 +1222,56 @@ int di_launch_mstep1(int kind, const DIArgs& a, int grid, int smem, int n_int, i
   return (int)cudaLaunchKernelExC(&cfg, pick_step1(kind, red_chunks, prefetch), args);
 }
 
-int di_launch_msolve(int kind, const DIArgs& a, int n_int, void* stream) {
-  cudaStream_t s = (cudaStream_t)stream;
-  const int g2 = n_int < kSolveGrid ? n_int : kSolveGrid;
+// The accumulate and solve launches of an iteration go out with programmatic stream serialization
+// (each kernel waits for its predecessor with griddepcontrol.wait before touching its data), so a
+// launch is scheduled while the previous one drains.  GAINCAL_PDL=0 turns it off.
+static bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("GAINCAL_PDL");
+    return !(v && atoi(v) == 0);
+  }();
+  return on;
+}
+
+static cudaError_t launch_dep(const void* f, int grid, size_t smem, cudaStream_t s, void** args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kDIThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelExC(&cfg, f, args);
+}
+
+static cudaError_t launch_msolve(int kind, const DIArgs& a, int n_int, cudaStream_t s) {
+  int n = n_int;
+  void* args[] = {const_cast<DIArgs*>(&a), &n};
+  const int g2 = n_int < kSolveGrid ? n_int : kSolveGrid;  // CTAs loop over the intervals
   const size_t sm2 = sizeof(float) * (size_t)a.na_max * (kind == 0 ? 3 : 12);
-  if (kind == 0) di_msolve_kernel<ScalarMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
-  else di_msolve_kernel<JonesMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
-  return (int)cudaGetLastError();
+  const void* f = kind == 0 ? (const void*)&di_msolve_kernel<ScalarMom> : (const void*)&di_msolve_kernel<JonesMom>;
+  return launch_dep(f, g2, sm2, s, args);
+}
+
+int di_launch_msolve(int kind, const DIArgs& a, int n_int, void* stream) {
+  return (int)launch_msolve(kind, a, n_int, (cudaStream_t)stream);
 }
 
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,
                     void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   void* args[] = {const_cast<DIArgs*>(&a)};
-  cudaError_t e = cudaLaunchKernel(pick_acc(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args,
-                                   (size_t)smem, s);
+  cudaError_t e = launch_dep(pick_acc(kind, red_chunks, prefetch), grid, (size_t)smem, s, args);
   if (e != cudaSuccess) return (int)e;
-  const int g2 = n_int < kSolveGrid ? n_int : kSolveGrid;  // CTAs loop over the intervals
-  const size_t sm2 = sizeof(float) * (size_t)a.na_max * (kind == 0 ? 3 : 12);
-  if (kind == 0) di_msolve_kernel<ScalarMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
-  else di_msolve_kernel<JonesMom><<<g2, kDIThreads, sm2, s>>>(a, n_int);
-  return (int)cudaGetLastError();
+  return (int)launch_msolve(kind, a, n_int, s);
 }
 
 int di_launch_macc(int kind, const DIArgs& a, int grid, int smem, int red_chunks, int prefetch, void* stream) {
   void* args[] = {const_cast<DIArgs*>(&a)};
-  return (int)cudaLaunchKernel(pick_acc(kind, red_chunks, prefetch), dim3(grid), dim3(kDIThreads), args,
-                               (size_t)smem, (cudaStream_t)stream);
+  return (int)launch_dep(pick_acc(kind, red_chunks, prefetch), grid, (size_t)smem, (cudaStream_t)stream, args);
 }
 
 int di_launch_msum(int kind, const DIArgs& a, int i_lo, int n, float* tot_out, double* e_out, void* stream) {
