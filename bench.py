@@ -221,6 +221,7 @@ def run_reference(args):
 
 
 WARM_LAG = 32           # wave length (time steps) of the learned wavefront
+WARM_GATE = 1e-5        # pipelined wavefront: a wave joins once its history's relative steps fall below this
 WARM_WORKLOAD = ("di_jones2x2 warm start: 64 ant (2016 bl), 720 t x 64 ch, intervals 1 t x 8 ch (5760), GP gains "
                  "(30 min / 50 MHz correlation, amplitude 0.1, phase 1 rad), tol 1e-6")
 
@@ -228,9 +229,10 @@ WARM_WORKLOAD = ("di_jones2x2 warm start: 64 ant (2016 bl), 720 t x 64 ch, inter
 def warm_start_block(dev, args):
     """Learned warm start + batched path vs the plain batched solver on the GP-gain workload.
 
-    The network is trained first (its own observation, another seed), then three solves of the
-    same 5760 intervals are timed with the data resident: plain (all intervals from unit gains in
-    one call), previous-solution wavefront and learned wavefront (one call per wave of 32 times)."""
+    The network is trained first (its own observation, another seed), then the same 5760 intervals
+    are solved with the data resident: plain (all intervals from unit gains in one call); the
+    previous-solution and learned starts in waves of 32 times, one call per wave; and the same two
+    starts pipelined in one call (a wave joins once its history has settled to WARM_GATE)."""
     import torch
     from paper_1502_06974_gb300 import api, synth, warmstart
     t0 = time.perf_counter()
@@ -265,6 +267,11 @@ def warm_start_block(dev, args):
     (gp, itp, stp), ms_plain = timed(lambda: warmstart.solve_plain(ve, me, ge, TOL, MAX_ITER))
     prev, ms_prev = timed(lambda: warmstart.solve_wavefront(ve, me, ge, WARM_LAG, None, TOL, MAX_ITER))
     lrn, ms_lrn = timed(lambda: warmstart.solve_wavefront(ve, me, ge, WARM_LAG, res.net, TOL, MAX_ITER))
+    # the same two starts in one library call, waves joining the running iteration (pipelined)
+    pprev, ms_pprev = timed(lambda: warmstart.solve_pipelined(ve, me, ge, WARM_LAG, None, TOL, MAX_ITER,
+                                                              gate_tol=WARM_GATE))
+    plrn, ms_plrn = timed(lambda: warmstart.solve_pipelined(ve, me, ge, WARM_LAG, res.net, TOL, MAX_ITER,
+                                                            gate_tol=WARM_GATE))
     itp = itp.cpu().numpy()
     rows = ge.rows * n_int
     g_true = be.g_true
@@ -294,8 +301,18 @@ def warm_start_block(dev, args):
                              {"proposals_taken": float(np.mean(lrn.used[np.repeat(np.arange(ge.n_t), ge.n_fb)
                                                                        >= WARM_LAG])),
                               "max_err_vs_truth": err_truth(lrn.gains)}),
+            "pipelined": {
+                "schedule": f"one gc_calibrate_di_jones2x2_wavefront call: a wave of lag x 8 intervals joins the "
+                            f"running iteration once the 4 times before it have finished or taken a relative step "
+                            f"below {WARM_GATE:g}",
+                "previous_solution": entry(ms_pprev, pprev.iters, pprev.status,
+                                           {"max_err_vs_truth": err_truth(pprev.gains)}),
+                "learned": entry(ms_plrn, plrn.iters, plrn.status, {"max_err_vs_truth": err_truth(plrn.gains)}),
+                "speedup_learned_vs_plain": ms_plain / ms_plrn,
+                "speedup_learned_vs_previous_solution": ms_pprev / ms_plrn},
             "speedup_learned_vs_plain": ms_plain / ms_lrn,
             "speedup_learned_vs_previous_solution": ms_prev / ms_lrn,
+            "speedup_best_learned_vs_plain": ms_plain / min(ms_lrn, ms_plrn),
             "training": {"trajectories": 50000, "observation": "160 t x 64 ch of the same array, another seed",
                          "adam_steps": res.steps, "train_s": res.seconds, "prep_s": prep_s,
                          "val_mse": res.val_mse, "val_mse_previous_solution": res.val_mse_zero}}
