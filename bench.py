@@ -506,7 +506,8 @@ def run_gpu(args):
             mom_bytes = (b.n_rows * BYTES_PER_ROW + b.n_int * int(b.n_bl[0]) * MOMENT_BYTES) * args.steps
             roof_mom = {"bound": "hbm", "achieved": mom_bytes / (kmom / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
                         "unit": "GB/s", "frac": mom_bytes / (kmom / 1e3) / 1e9 / peaks["hbm_gbs"],
-                        "kernel": "di_moment_kernel<JonesMom>", "ms_per_step": kmom / args.steps,
+                        "kernel": ("di_moment_direct_kernel<JonesMom>" if int(np.max(b.n_samp)) <= 16
+                                   else "di_moment_kernel<JonesMom>"), "ms_per_step": kmom / args.steps,
                         "peak_source": which}
         else:
             avg_launch_s = (kms / 1e3) / max(kl, 1)
