@@ -743,12 +743,23 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
     const int* off = tbk + 2 * TB;
     const int* ent = off + ((nat + 1 + 3) & ~3);
     float* scr = static_cast<float*>(a.scratch) + (int64_t)(((uint64_t)(unsigned)h.w << 32) | (unsigned)h.z);
-    for (int x = tid; x < nat * NC; x += TB) {
-      const int an = x / NC, c = x - an * NC;
+    // a thread takes one antenna and CG consecutive components: the slot list is read once for
+    // them and their sums (each in list order, as in the other variants) proceed side by side
+    constexpr int CG = 3, NG3 = NC / CG;
+    static_assert(NC % CG == 0, "components come in groups of CG");
+    for (int x = tid; x < nat * NG3; x += TB) {
+      const int an = x / NG3, c0 = (x - an * NG3) * CG;
       const int e1 = off[an + 1];
-      float sum = 0.f;
-      for (int e = off[an]; e < e1; ++e) sum += part[ent[e] + c];
-      scr[x] = sum;
+      float sum[CG];
+#pragma unroll
+      for (int u = 0; u < CG; ++u) sum[u] = 0.f;
+      for (int e = off[an]; e < e1; ++e) {
+        const float* pe = part + ent[e] + c0;
+#pragma unroll
+        for (int u = 0; u < CG; ++u) sum[u] += pe[u];
+      }
+#pragma unroll
+      for (int u = 0; u < CG; ++u) scr[an * NC + c0 + u] = sum[u];
     }
     __syncthreads();  // the stage is free
     if (tid == 0 && slot + 2 * G < n_list) {
