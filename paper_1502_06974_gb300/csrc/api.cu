@@ -312,11 +312,16 @@ static int build_di_plan(int mode, int kind, int dtype, int acc_only, const gc_l
         int ne = 0;
         for (int a = 0; a < nat; ++a) { tblk[oo + a] = ne; ne += (int)lists[a].size(); }
         tblk[oo + nat] = ne;
+        // entries address the partials as the bulk-copy kernel stores them: slot s's components
+        // c in float4 groups over the tile's moment area, [c / 4][TB][4] (q side from group nc / 4)
         const int eo = (int)tblk.size();
         tblk.resize(eo + pad4(ne), 0);
         int e = eo;
         for (int a = 0; a < nat; ++a)
-          for (int v : lists[a]) tblk[e++] = v;
+          for (int v : lists[a]) {
+            const int slot = v / (2 * nc + 1), q_side = v % (2 * nc + 1) == nc;
+            tblk[e++] = slot * 4 + (q_side ? (nc / 4) * TB * 4 : 0);
+          }
         const int len = (int)tblk.size() - o;
         tblk_at[t].push_back({o, len});
         tblk_max = len > tblk_max ? len : tblk_max;

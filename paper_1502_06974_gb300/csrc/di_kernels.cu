@@ -722,8 +722,18 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
       MK::partials(m, gp, gq, sa + p * AW, sa + q * AW, pp, pq);
     }
     warp_run_scan<NC>(p, pp);
-    // every thread has its moments in registers: the stage's first region takes the partials.  A
-    // copy that never landed ends the CTA (all threads agree), after a bounded wait for the rest.
+    // the partials go over this thread's own moment slots (it alone read them), component c of
+    // side h at float4 group (h NC + c) / 4: no barrier is needed before the stores
+    static_assert(NC % 4 == 0 && 2 * NC / 4 <= NG, "partials fit the thread's moment slots");
+    float4* my4 = reinterpret_cast<float4*>(st) + tid;
+    if (tid < nbt) {
+#pragma unroll
+      for (int r = 0; r < NC / 4; ++r) {
+        my4[r * TB] = make_float4(pp[4 * r], pp[4 * r + 1], pp[4 * r + 2], pp[4 * r + 3]);
+        my4[(NC / 4 + r) * TB] = make_float4(pq[4 * r], pq[4 * r + 1], pq[4 * r + 2], pq[4 * r + 3]);
+      }
+    }
+    // a copy that never landed ends the CTA (all threads agree), after a bounded wait for the rest
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicExch(a.err, 1);
@@ -733,13 +743,7 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
       return;
     }
     if (tid == 0) pend[s] = false;
-    float* part = st;  // [TB][PS]
-    if (tid < nbt) {
-      float* my = part + tid * PS;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) { my[c] = pp[c]; my[NC + c] = pq[c]; }
-    }
-    __syncthreads();
+    const float* part = st;  // slot s, component c of side h: [(h NC + c) / 4][TB][4]
     const int* off = tbk + 2 * TB;
     const int* ent = off + ((nat + 1 + 3) & ~3);
     float* scr = static_cast<float*>(a.scratch) + (int64_t)(((uint64_t)(unsigned)h.w << 32) | (unsigned)h.z);
@@ -753,10 +757,13 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
       float sum[CG];
 #pragma unroll
       for (int u = 0; u < CG; ++u) sum[u] = 0.f;
-      for (int e = off[an]; e < e1; ++e) {
-        const float* pe = part + ent[e] + c0;
+      int co[CG];  // offset of component c0 + u from its slot's first component
 #pragma unroll
-        for (int u = 0; u < CG; ++u) sum[u] += pe[u];
+      for (int u = 0; u < CG; ++u) co[u] = ((c0 + u) >> 2) * TB * 4 + ((c0 + u) & 3);
+      for (int e = off[an]; e < e1; ++e) {
+        const float* pe = part + ent[e];
+#pragma unroll
+        for (int u = 0; u < CG; ++u) sum[u] += pe[co[u]];
       }
 #pragma unroll
       for (int u = 0; u < CG; ++u) scr[an * NC + c0 + u] = sum[u];
