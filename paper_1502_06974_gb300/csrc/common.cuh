@@ -191,17 +191,21 @@ GC_DEV double ff_value(FF x) { return (double)x.hi + (double)x.lo; }
 
 // End-of-update reduction over the block with the two sums in float-float: every thread gets the
 // block totals of d2 and n2 (warp butterflies, then the warps in order) and the OR of the two
-// flags; two barriers.  `red` holds >= 160 floats.
-GC_DEV void block_reduce_step_ff(FF& d2, FF& n2, int& f1, int& f2, float* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+// flags; two barriers.  Only the first n_live threads may hold nonzero values or set flags: the
+// warps past them skip the butterfly and are left out of the totals.  `red` holds >= 160 floats.
+GC_DEV void block_reduce_step_ff(FF& d2, FF& n2, int& f1, int& f2, float* red, int n_live) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (min(n_live, (int)blockDim.x) + 31) >> 5;
   int fl = (f1 ? 1 : 0) | (f2 ? 2 : 0);
+  if (warp < nw) {  // warp-uniform
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    d2 = ff_add(d2, FF{__shfl_xor_sync(0xffffffffu, d2.hi, o), __shfl_xor_sync(0xffffffffu, d2.lo, o)});
-    n2 = ff_add(n2, FF{__shfl_xor_sync(0xffffffffu, n2.hi, o), __shfl_xor_sync(0xffffffffu, n2.lo, o)});
-    fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      d2 = ff_add(d2, FF{__shfl_xor_sync(0xffffffffu, d2.hi, o), __shfl_xor_sync(0xffffffffu, d2.lo, o)});
+      n2 = ff_add(n2, FF{__shfl_xor_sync(0xffffffffu, n2.hi, o), __shfl_xor_sync(0xffffffffu, n2.lo, o)});
+      fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    }
   }
-  if (lane == 0) {
+  if (lane == 0 && warp < nw) {
     red[warp] = d2.hi;
     red[32 + warp] = d2.lo;
     red[64 + warp] = n2.hi;

@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
     gs[x] = nw;  // stage; written below unless non-finite
   }
   for (int x = tid; x < na; x += blockDim.x) sing |= __ldcg(a.sing + go + x);
-  block_reduce_step_ff(d2, n2, nonfin, sing, reinterpret_cast<float*>(s_red));
+  block_reduce_step_ff(d2, n2, nonfin, sing, reinterpret_cast<float*>(s_red), (int)blockDim.x);
   const double D2 = ff_value(d2), N2 = ff_value(n2);
   if (!nonfin)
     for (int x = tid; x < na * ND; x += blockDim.x) {

@@ -307,7 +307,7 @@ __device__ __forceinline__ void solve_interval(const DIArgs& a, int k, int i, fl
     if (!K::finite(nw)) nonfin = 1;
     K::st_gain(a.gnew + (go + an) * GW, nw);   // staged until the interval's decision is known
   }
-  block_reduce_step_ff(d2, n2, sing, nonfin, reinterpret_cast<float*>(red));
+  block_reduce_step_ff(d2, n2, sing, nonfin, reinterpret_cast<float*>(red), na);  // antennas tid < na only
   if (!nonfin)
     for (int an = tid; an < na; an += TB) {
       const G nw = K::ld_gain(a.gnew + (go + an) * GW);

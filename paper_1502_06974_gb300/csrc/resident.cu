@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kResThreads, 1) di_resident_kernel(const ResAr
         K::st_gain(gn_out + an * GW, nw);
         MK::aux(nw, ax_out + an * AW);
       }
-      block_reduce_step_ff(d2, n2, sg, nonfin, reinterpret_cast<float*>(red));
+      block_reduce_step_ff(d2, n2, sg, nonfin, reinterpret_cast<float*>(red), (int)blockDim.x);
       sing = sg;
       if (nonfin) { st = GC_ST_NONFINITE; break; }
       cur ^= 1;
