@@ -161,8 +161,11 @@ int gc_calibrate_di_jones2x2(const void* vis, const void* model, const gc_layout
 /*
  * Direction-dependent scalar gains: CohJones (Sect. 3.2.2).  Per antenna p the N_d x N_d
  * block A_p[c][d] = sum_{q,s} conj(y^(c)) y^(d), y^(d) = m^(d) conj(g_q^(d)) (eq. JHJ:DD:unpol)
- * is solved against J^H d (eq. JHR:DD:unpol, data form of eq. ghat) by an FP64 Cholesky
- * factorisation.  The sums over samples are first reduced to per-baseline moments
+ * is solved against J^H d (eq. JHR:DD:unpol, data form of eq. ghat) by a Cholesky factorisation
+ * in FP32 refined once against a float-float residual; when an FP32 pivot is not positive the
+ * block is factored in FP64, and a block FP64 cannot factor keeps the antenna's gains and sets
+ * GC_ST_SINGULAR_FLAG in its interval's status.  The sums over samples are first reduced to
+ * per-baseline moments
  * X^(cd)_pq = sum_s conj(m^(c)) m^(d) and b^(c)_pq = sum_s conj(m^(c)) d (Sect. 3.2.1, the
  * gains factor out of the sample sum), read once per interval.
  *   vis    [n_rows] complex64; model [n_dir][n_rows] complex64; gains [n_gain][n_dir] complex64.
@@ -220,8 +223,10 @@ int gc_jhj_jhr_di_jones2x2_noalloc(const void* vis, const void* model, const gc_
 /*
  * Autotuner for the direction-independent solvers (launch shapes only; results are the same up to
  * FP32 summation order).  Runs `iters` iterations (tol 0) of gc_calibrate_di_scalar (kind 0) or
- * gc_calibrate_di_jones2x2 (kind 1) with each candidate shape -- reduction split, prefetch, CTAs
- * per SM for the moment path; rows per work item and CTAs per SM for the raw-row path -- on the
+ * gc_calibrate_di_jones2x2 (kind 1) with each candidate shape -- reduction split, how the next
+ * tile is brought in (none, registers, per-thread copies, or bulk copies into a shared-memory
+ * ring), CTAs per SM for the moment path; rows per work item and CTAs per SM for the raw-row
+ * path -- on the
  * caller's data, and records the fastest for the layout's shape bucket (kind, dtype, path, and
  * the powers of two of the interval count, largest baseline count and mean samples per interval).
  * Later calls with a layout in that bucket use it.  vis, model and gains are device pointers;
