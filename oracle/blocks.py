@@ -105,3 +105,83 @@ def dd_blocks(g, vis, model, a1, a2, n_ant):
         c[p] = np.conj(Yp).T @ r[sel]
         cd[p] = np.conj(Yp).T @ d[sel]
     return dict(A=A, c=c, cd=cd)
+
+
+# ----------------------------------------------------------------------------- full J^H J (exact GN / LM)
+
+def op_R4(A):
+    """W R_A of App. B eq. RA4x4: the 4x4 matrix of X -> X A acting on vec X (stacked columns)."""
+    A = np.asarray(A, np.complex128)
+    W = np.zeros(A.shape[:-2] + (4, 4), np.complex128)
+    W[..., 0, 0] = A[..., 0, 0]; W[..., 0, 2] = A[..., 1, 0]
+    W[..., 1, 1] = A[..., 0, 0]; W[..., 1, 3] = A[..., 1, 0]
+    W[..., 2, 0] = A[..., 0, 1]; W[..., 2, 2] = A[..., 1, 1]
+    W[..., 3, 1] = A[..., 0, 1]; W[..., 3, 3] = A[..., 1, 1]
+    return W
+
+
+def op_L4(A):
+    """W L_A of App. B eq. LA4x4: the 4x4 matrix of X -> A X acting on vec X."""
+    A = np.asarray(A, np.complex128)
+    W = np.zeros(A.shape[:-2] + (4, 4), np.complex128)
+    W[..., 0:2, 0:2] = A
+    W[..., 2:4, 2:4] = A
+    return W
+
+
+def _vec(X):
+    return np.stack([X[..., 0, 0], X[..., 1, 0], X[..., 0, 1], X[..., 1, 1]], axis=-1)
+
+
+def jones_jhj_full(G, vis, model, a1, a2, n_ant):
+    """The whole J^H J and J^H R of the 2x2 DI problem, off-diagonal antenna blocks included.
+
+    Sect. 4.2 eq. JHJ:pol with the 4x4 operator forms of App. B, over the directed rows [pq],
+    p != q (eq. JJ:pol) and the samples of the interval (Sect. 2.3).  The augmented parameter
+    vector is eq. GGvec, [vec G_1 .. vec G_n, vec G_1^H .. vec G_n^H]; with Y_ij = M_ij G_j^H:
+      top-left  (i, i)   sum_{q != i} R_{Y_iq Y_iq^H}        (zero for i != j)
+      top-right (i, j)   sum R_{Y_ij^H} L_{Y_ji^H}, i != j   (zero for i == j)
+      bottom-left (i, j) sum L_{Y_ij} R_{Y_ji}, i != j
+      bottom-right (i,i) sum_{q != i} L_{Y_iq Y_iq^H}
+    J^H R: top vec(sum_q R_iq Y_iq^H) (the product order read from R_A X = X A), bottom
+    vec((sum_q R_iq Y_iq^H)^H).
+    Returns (JHJ [8n, 8n], JHR [8n]) as complex128.
+    """
+    G = np.asarray(G, np.complex128)
+    i, j, D, M = directed_rows(vis, model, a1, a2, 'jones')
+    half = i.shape[0] // 2
+    mirror = np.concatenate([np.arange(half, 2 * half), np.arange(0, half)])   # row (j, i) of row (i, j)
+    Y = M @ np.conj(np.swapaxes(G[j], -1, -2))
+    YH = np.conj(np.swapaxes(Y, -1, -2))
+    R = D - G[i] @ Y
+    n = int(n_ant)
+    TL = np.zeros((n, 4, 4), np.complex128)
+    BR = np.zeros((n, 4, 4), np.complex128)
+    TR = np.zeros((n, n, 4, 4), np.complex128)
+    BL = np.zeros((n, n, 4, 4), np.complex128)
+    np.add.at(TL, i, op_R4(Y @ YH))
+    np.add.at(BR, i, op_L4(Y @ YH))
+    np.add.at(TR, (i, j), op_R4(YH) @ op_L4(YH[mirror]))
+    np.add.at(BL, (i, j), op_L4(Y) @ op_R4(Y[mirror]))
+    C = np.zeros((n, 2, 2), np.complex128)
+    np.add.at(C, i, R @ YH)
+    H = np.zeros((8 * n, 8 * n), np.complex128)
+    for p in range(n):
+        H[4 * p:4 * p + 4, 4 * p:4 * p + 4] = TL[p]
+        H[4 * n + 4 * p:4 * n + 4 * p + 4, 4 * n + 4 * p:4 * n + 4 * p + 4] = BR[p]
+        for q in range(n):
+            H[4 * p:4 * p + 4, 4 * n + 4 * q:4 * n + 4 * q + 4] = TR[p, q]
+            H[4 * n + 4 * p:4 * n + 4 * p + 4, 4 * q:4 * q + 4] = BL[p, q]
+    b = np.concatenate([_vec(C).reshape(-1), _vec(np.conj(np.swapaxes(C, -1, -2))).reshape(-1)])
+    return H, b
+
+
+def scalar_jhj_full(g, vis, model, a1, a2, n_ant):
+    """The whole J^H J and J^H r of the scalar DI problem (eq. JHJ:DI:ABCD / eq. JHJ:DI with the
+    sample sums of eq. JHJ:DI:tf, and eq. JHR:DI), ordering [g; conj g].  Returns (JHJ [2n, 2n],
+    JHR [2n])."""
+    blk = scalar_blocks(g, vis, model, a1, a2, n_ant)
+    A = np.diag(blk['A']).astype(np.complex128)
+    B = blk['B']
+    H = np.block([[A, B], [np.conj(B), A]])
+    return H, np.concatenate([blk['c'], np.conj(blk['c'])])

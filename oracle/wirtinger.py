@@ -215,15 +215,33 @@ def gauss_newton(prob: Problem, g0, tol=1e-12, max_iter=100):
     return prob.from_z(z), max_iter, hist
 
 
-def lm_step(H, b, lam):
-    """eq. LM: (J^H J + lambda D)^-1 J^H r_aug with D = diag(J^H J)."""
+def gauge_direction(z):
+    """Unit augmented vector of the phase gauge, u = [i z; -i conj z] / ||.||: the change of
+    [z; conj z] under z -> z e^{i phi} (chi^2 does not depend on phi, Sect. 2.1)."""
+    u = np.concatenate([1j * z, -1j * np.conj(z)])
+    return u / np.linalg.norm(u)
+
+
+def lm_step(H, b, lam, gauge=None):
+    """eq. LM: (J^H J + lambda D)^-1 J^H r_aug with D = diag(J^H J).
+
+    With ``gauge`` (a unit vector u spanning the phase-gauge null direction of J^H J), the step
+    is taken in the complement of u: J^H r_aug is projected off u and mu u u^H, mu the mean of
+    diag(J^H J), is added to the matrix.  For lambda = 0 this is the minimum-norm GN step; for
+    lambda > 0 it keeps the damped matrix well conditioned along u however small lambda gets.
+    """
     D = np.diag(np.real(np.diag(H)))
-    return min_norm_solve(H + lam * D, b)
+    A = H + lam * D
+    if gauge is not None:
+        b = b - gauge * np.vdot(gauge, b)
+        A = A + np.mean(np.real(np.diag(H))) * np.outer(gauge, np.conj(gauge))
+    return min_norm_solve(A, b)
 
 
-def levenberg_marquardt(prob: Problem, g0, tol=1e-12, max_iter=200, lam0=1.0, K=10.0):
+def levenberg_marquardt(prob: Problem, g0, tol=1e-12, max_iter=200, lam0=1.0, K=10.0, gauge=False):
     """Algorithm LM (App. C): accept a step only if chi^2 decreases; lambda /= K on success,
     lambda *= K and retry from the previous point on failure.  chi^2 = ||r||^2.
+    ``gauge``: take each step in the complement of the phase-gauge direction (see lm_step).
 
     Returns (g, accepted-iterations, chi2 history of accepted points).
     """
@@ -235,7 +253,7 @@ def levenberg_marquardt(prob: Problem, g0, tol=1e-12, max_iter=200, lam0=1.0, K=
     it = 0
     for _ in range(max_iter):
         H, b = prob.normal_equations(prob.from_z(z))
-        dz = lm_step(H, b, lam)[:n]
+        dz = lm_step(H, b, lam, gauge_direction(z) if gauge else None)[:n]
         z_new = z + dz
         chi_new = prob.chi2(prob.from_z(z_new))
         if chi_new < chi:
@@ -256,3 +274,33 @@ def steepest_descent_direction(prob: Problem, g):
     """Algorithm SD direction (App. C): J^H r_aug (top half)."""
     _, b = prob.normal_equations(g)
     return b[: b.shape[0] // 2]
+
+
+# ----------------------------------------------------------------------------- closed-form normal equations
+
+class ClosedFormProblem(Problem):
+    """A scalar or 2x2 DI interval whose normal equations come from the closed forms of the whole
+    J^H J (eq. JHJ:DI for scalar, eq. JHJ:pol for 2x2, blocks.scalar_jhj_full /
+    blocks.jones_jhj_full) instead of the explicit J, so that intervals of 64 antennas stay cheap.
+    Same interface and ordering ([z; conj z]) as Problem."""
+
+    def __init__(self, kind, vis, model, a1, a2, n_ant):
+        assert kind in ('scalar', 'jones')
+        super().__init__(kind, vis, model, a1, a2, n_ant)
+
+    def normal_equations(self, g):
+        from . import blocks
+        if self.kind == 'scalar':
+            return blocks.scalar_jhj_full(g, self.vis, self.model, self.a1, self.a2, self.n_ant)
+        H, b = blocks.jones_jhj_full(g, self.vis, self.model, self.a1, self.a2, self.n_ant)
+        T = paper_to_wirtinger_order(self.n_ant)
+        return T.T @ H @ T, T.T @ b
+
+
+def paper_to_wirtinger_order(n_ant):
+    """Permutation T with [vec G; vec G^H] (eq. GGvec) = T [vec G; vec conj G]: vec(G^H) = K vec(conj G)."""
+    n4 = 4 * int(n_ant)
+    T = np.zeros((2 * n4, 2 * n4))
+    T[:n4, :n4] = np.eye(n4)
+    T[n4:, n4:] = np.kron(np.eye(int(n_ant)), np.real(COMMUTATION_2x2))
+    return T

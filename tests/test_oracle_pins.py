@@ -403,3 +403,92 @@ def test_generator_is_seeded_and_noise_has_stated_sigma():
     res = iv['vis'] - v
     s = np.std(np.concatenate([res.real.ravel(), res.imag.ravel()]))
     assert abs(s - 0.01) < 0.001
+
+
+# ------------------------------------------------------------------------------------ whole J^H J (exact LM)
+
+def test_full_jones_jhj_equals_explicit_product():
+    """eq. JHJ:pol in operator form (App. B 4x4 matrices), off-diagonal antenna blocks included,
+    equals J^H J and J^H R of the explicit Jacobian after reordering [z; conj z] -> eq. GGvec."""
+    d, m, a1, a2, g = _tiny('jones', n_ant=4, n_samp=2, noise=0.1)
+    g0 = _perturbed_start('jones', g)
+    prob = wirtinger.Problem('jones', d, m, a1, a2, 4)
+    H, b = prob.normal_equations(g0)
+    Hc, bc = blocks.jones_jhj_full(g0, d, m, a1, a2, 4)
+    T = wirtinger.paper_to_wirtinger_order(4)
+    np.testing.assert_allclose(Hc, T @ H @ T.T, atol=1e-11)
+    np.testing.assert_allclose(bc, T @ b, atol=1e-11)
+    # structure of eq. JHJ:pol: top-left block-diagonal, top-right zero on the antenna diagonal
+    for p in range(4):
+        for q in range(4):
+            tl = Hc[4 * p:4 * p + 4, 4 * q:4 * q + 4]
+            tr = Hc[4 * p:4 * p + 4, 16 + 4 * q:16 + 4 * q + 4]
+            if p != q:
+                assert np.all(tl == 0)
+            else:
+                assert np.all(tr == 0)
+    # the top-left diagonal block is the polarized StefCal block R_H, H = sum Y Y^H
+    cf = blocks.jones_blocks(g0, d, m, a1, a2, 4)
+    for p in range(4):
+        np.testing.assert_allclose(Hc[4 * p:4 * p + 4, 4 * p:4 * p + 4], blocks.op_R4(cf['H'][p]), atol=1e-12)
+
+
+def test_full_scalar_jhj_equals_explicit_product():
+    """eq. JHJ:DI (A, B, conj B, A) over the interval's samples equals the explicit J^H J."""
+    d, m, a1, a2, g = _tiny('scalar', n_ant=5, n_samp=3, noise=0.1)
+    g0 = _perturbed_start('scalar', g)
+    H, b = wirtinger.Problem('scalar', d, m, a1, a2, 5).normal_equations(g0)
+    Hc, bc = blocks.scalar_jhj_full(g0, d, m, a1, a2, 5)
+    np.testing.assert_allclose(Hc, H, atol=1e-11)
+    np.testing.assert_allclose(bc, b, atol=1e-11)
+
+
+def test_gauge_step_is_minimum_norm_gn_at_zero_damping():
+    """lm_step with the gauge direction and lambda = 0 is the minimum-norm GN step (eq. GN): the
+    added mu u u^H only acts on the null direction of J^H J, which J^H r does not reach."""
+    d, m, a1, a2, g = _tiny('jones', n_ant=4, n_samp=3, noise=0.05)
+    g0 = _perturbed_start('jones', g, eps=0.05)
+    prob = wirtinger.Problem('jones', d, m, a1, a2, 4)
+    H, b = prob.normal_equations(g0)
+    z = prob.to_z(g0)
+    u = wirtinger.gauge_direction(z)
+    assert np.linalg.norm(H @ u) < 1e-10 * np.linalg.norm(H)
+    np.testing.assert_allclose(wirtinger.lm_step(H, b, 0.0, u), wirtinger.min_norm_solve(H, b), atol=1e-9)
+    # with damping the step still lowers chi^2 from a perturbed start
+    dz = wirtinger.lm_step(H, b, 1e-2, u)[: z.shape[0]]
+    assert prob.chi2(prob.from_z(z + dz)) < prob.chi2(g0)
+
+
+@pytest.mark.parametrize("kind", ['scalar', 'jones'])
+def test_closed_form_lm_recovers_noiseless_gains(kind):
+    """App. C LM on the closed-form normal equations, from a perturbed start, recovers the true
+    gains up to the phase gauge on noiseless data (zero residual is the global minimum)."""
+    from oracle import gauge as gauge_mod
+    d, m, a1, a2, g = _tiny(kind, n_ant=5, n_samp=3)
+    prob = wirtinger.ClosedFormProblem(kind, d, m, a1, a2, 5)
+    for gauge in (False, True):
+        gs, it, hist = wirtinger.levenberg_marquardt(prob, _perturbed_start(kind, g, eps=0.2), tol=1e-13,
+                                                     lam0=1e-2, K=10.0, gauge=gauge)
+        assert gauge_mod.rel_error(kind, gs, g) < 1e-10
+        assert all(h1 < h0 for h0, h1 in zip(hist, hist[1:]))
+
+
+def test_closed_form_lm_stationary_point_and_explicit_agreement():
+    """On noisy 2x2 data the closed-form LM stops where the chi^2 gradient vanishes (finite
+    differences, Sect. 1: d chi^2 / d conj z = -J^H r) and where the explicit-J LM stops."""
+    from oracle import gauge as gauge_mod
+    d, m, a1, a2, g = _tiny('jones', n_ant=5, n_samp=2, noise=0.05)
+    start = _perturbed_start('jones', g, eps=0.05)
+    pc = wirtinger.ClosedFormProblem('jones', d, m, a1, a2, 5)
+    pe = wirtinger.Problem('jones', d, m, a1, a2, 5)
+    gc_, _, _ = wirtinger.levenberg_marquardt(pc, start, tol=1e-13, lam0=1e-2, gauge=True)
+    ge_, _, _ = wirtinger.levenberg_marquardt(pe, start, tol=1e-13, lam0=1e-2)
+    assert gauge_mod.rel_error('jones', gc_, ge_) < 1e-9
+    h = 1e-6
+    c0 = pc.chi2(gc_)
+    for p in range(5):
+        for (u, v) in ((0, 0), (0, 1), (1, 0), (1, 1)):
+            e = np.zeros_like(gc_); e[p, u, v] = h
+            dx = (pc.chi2(gc_ + e) - pc.chi2(gc_ - e)) / (2 * h)
+            dy = (pc.chi2(gc_ + 1j * e) - pc.chi2(gc_ - 1j * e)) / (2 * h)
+            assert abs(dx) + abs(dy) < 1e-6 * c0 + 1e-7
