@@ -84,6 +84,14 @@ extern "C" {
 
 #define GC_SCHED_STEFCAL 0  /* odd k: GN step; even k: LM step with lambda = 1 = average (Sect. 3.1) */
 #define GC_SCHED_GN 1       /* GN step every iteration                                        */
+#define GC_SCHED_LM 2       /* opt->lm_after StefCal iterations, then Levenberg-Marquardt with the whole
+                               J^H J (App. C, Algorithm LM; Sect. 1, eq. LM): see gc_options     */
+
+/* Levenberg-Marquardt (GC_SCHED_LM) limits and defaults */
+#define GC_LM_MAX_UNKNOWNS 512       /* real unknowns per interval: 8 x antennas (2x2), 2 x antennas (scalar) */
+#define GC_LM_DEFAULT_AFTER 20       /* StefCal iterations before the first LM step                 */
+#define GC_LM_DEFAULT_LAMBDA0 1e-2   /* initial damping                                             */
+#define GC_LM_DEFAULT_K 10.0         /* damping factor K of App. C                                   */
 
 #define GC_MAX_ANT 1024      /* antennas per interval                                          */
 #define GC_MAX_DIR 10        /* directions for the DD entry point                              */
@@ -117,6 +125,24 @@ typedef struct gc_options {
                                read the totals with gc_profile_last / gc_profile_detail        */
   int32_t path;             /* DI entry points: GC_PATH_AUTO / _STREAM / _MOMENTS / _RESIDENT     */
   int32_t reserved;         /* must be 0                                                      */
+  /* GC_SCHED_LM only (DI entry points, complex64, moment path):
+   *   The first lm_after iterations are StefCal's (GN / average alternation, no stopping), from
+   *   the given gains.  Then every interval takes App. C's LM iterations: the whole J^H J of
+   *   eq. JHJ:pol (2x2) or eq. JHJ:DI (scalar), off-diagonal antenna blocks included, and J^H R
+   *   are formed at the current gains from the per-baseline moments; the step solves
+   *       (J^H J + lambda diag(J^H J) + mu v v^T) dz = (I - v v^T) J^H R             (eq. LM)
+   *   with v the unit phase-gauge direction i G (J^H J is singular along it, Sect. 2.1) and mu the
+   *   mean of diag(J^H J) -- the LM step in the complement of the gauge direction; the matrix is
+   *   factored in FP32 (Cholesky).  chi^2 at the trial gains is evaluated in FP64; a step that
+   *   lowers it is kept and lambda /= lm_K, otherwise the gains are kept and lambda *= lm_K.  An
+   *   interval stops (GC_ST_OK) after a step with ||dz|| <= tol ||G|| (App. C, first criterion),
+   *   or at max_iter (every LM iteration, kept or not, counts as one iteration).
+   *   Intervals with more than GC_LM_MAX_UNKNOWNS real unknowns: GC_ERR_LIMIT.           */
+  int32_t lm_after;         /* StefCal iterations before LM, >= 0 (0: LM from the given gains;
+                               GC_LM_DEFAULT_AFTER suits a start far from the solution)          */
+  int32_t lm_reserved;      /* must be 0                                                      */
+  double lm_lambda0;        /* initial lambda; 0 selects GC_LM_DEFAULT_LAMBDA0                   */
+  double lm_K;              /* lambda factor, > 1; 0 selects GC_LM_DEFAULT_K                     */
 } gc_options;
 
 /* Execution paths of the direction-independent solvers (same results up to FP32 rounding order):
@@ -370,6 +396,15 @@ int gc_calibrate_di_jones2x2_wavefront(const void* vis, const void* model, const
  * Synchronous.
  */
 int gc_gauge_fix_di(int32_t kind, void* gains, const gc_layout* layout, int32_t dtype, void* stream);
+
+/*
+ * Totals of the Levenberg-Marquardt phase (GC_SCHED_LM) of the last DI calibration made with
+ * opt->profile != 0: summed device time of its iteration launches (ms, CUDA events on the call's
+ * stream), their number, and the algorithmic floating-point operations of the FP32 Cholesky
+ * factorisations and triangular solves they performed (2 (n^3/3 + 2 n^2) per interval and
+ * iteration, n real unknowns).  Any pointer may be NULL.
+ */
+int gc_profile_lm(double* lm_ms, int64_t* launches, double* flop);
 
 /* Text for a GC_ERR_* return code or a GC_ST_* status. */
 const char* gc_error_string(int code);

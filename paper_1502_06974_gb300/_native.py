@@ -16,7 +16,8 @@ GC_ERR = {-1: 'GC_ERR_ARG', -2: 'GC_ERR_LAYOUT', -3: 'GC_ERR_ANTENNA', -4: 'GC_E
 GC_ERR_LIMIT = -6
 GC_ST_OK, GC_ST_NOT_CONVERGED, GC_ST_NONFINITE, GC_ST_NODATA, GC_ST_SINGULAR_FLAG = 0, 1, 2, 3, 16
 GC_DTYPE_C64, GC_DTYPE_C128 = 0, 1
-GC_SCHED_STEFCAL, GC_SCHED_GN = 0, 1
+GC_SCHED_STEFCAL, GC_SCHED_GN, GC_SCHED_LM = 0, 1, 2
+GC_LM_MAX_UNKNOWNS, GC_LM_DEFAULT_AFTER, GC_LM_DEFAULT_LAMBDA0, GC_LM_DEFAULT_K = 512, 20, 1e-2, 10.0
 GC_PATH_AUTO, GC_PATH_STREAM, GC_PATH_RESIDENT, GC_PATH_MOMENTS = 0, 1, 2, 3
 GC_MAX_ANT, GC_MAX_DIR = 1024, 10
 
@@ -27,7 +28,7 @@ EXPORTS = [
     'gc_chi2_di_jones2x2', 'gc_mlp_work_floats', 'gc_mlp_forward_f32', 'gc_mlp_grad_f32', 'gc_mlp_train_step',
     'gc_mlp_infer_bf16', 'gc_ws_features_jones', 'gc_ws_target_jones', 'gc_calibrate_di_jones2x2_warm',
     'gc_calibrate_di_jones2x2_wavefront', 'gc_gauge_fix_di',
-    'gc_autotune_di', 'gc_profile_last', 'gc_profile_detail', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
+    'gc_autotune_di', 'gc_profile_last', 'gc_profile_detail', 'gc_profile_lm', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
 ]
 
 _p = C.c_void_p
@@ -45,7 +46,8 @@ class GcLayout(C.Structure):
 class GcOptions(C.Structure):
     _fields_ = [('tol', C.c_double), ('max_iter', C.c_int32), ('schedule', C.c_int32), ('dtype', C.c_int32),
                 ('host_buffers', C.c_int32), ('compute_chi2', C.c_int32), ('profile', C.c_int32),
-                ('path', C.c_int32), ('reserved', C.c_int32)]
+                ('path', C.c_int32), ('reserved', C.c_int32), ('lm_after', C.c_int32), ('lm_reserved', C.c_int32),
+                ('lm_lambda0', C.c_double), ('lm_K', C.c_double)]
 
 
 class GcMlp(C.Structure):
@@ -127,6 +129,8 @@ def lib() -> C.CDLL:
         L.gc_autotune_di.restype = C.c_int
         L.gc_profile_detail.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.gc_profile_detail.restype = C.c_int
+        L.gc_profile_lm.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+        L.gc_profile_lm.restype = C.c_int
         L.gc_release.argtypes = []
         L.gc_release.restype = C.c_int
         _lib = L

@@ -77,8 +77,14 @@ def _check_tensor(t, name, host):
         raise ValueError(f"{name} must be a CUDA tensor")
 
 
+def _schedule_code(schedule):
+    if isinstance(schedule, str):
+        return {'stefcal': N.GC_SCHED_STEFCAL, 'gn': N.GC_SCHED_GN, 'lm': N.GC_SCHED_LM}[schedule]
+    return int(schedule)
+
+
 def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedule, compute_chi2, host_buffers,
-               want_outputs=True, profile=False, path=N.GC_PATH_AUTO):
+               want_outputs=True, profile=False, path=N.GC_PATH_AUTO, lm_after=None, lm_lambda0=0.0, lm_K=0.0):
     host = bool(host_buffers)
     for t, n in ((vis, 'vis'), (model, 'model'), (gains, 'gains')):
         _check_tensor(t, n, host)
@@ -97,8 +103,9 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
         status = torch.zeros(n, dtype=torch.int32, device=dev) if want_outputs else None
         chi2 = torch.zeros(n, dtype=torch.float64, device=dev) if (want_outputs and compute_chi2) else None
         stream = _stream_ptr(dev)
-    opt = N.GcOptions(float(tol), int(max_iter), int(schedule), dt, 1 if host else 0, 1 if compute_chi2 else 0,
-                      int(profile), int(path))
+    opt = N.GcOptions(float(tol), int(max_iter), _schedule_code(schedule), dt, 1 if host else 0,
+                      1 if compute_chi2 else 0, int(profile), int(path), 0,
+                      N.GC_LM_DEFAULT_AFTER if lm_after is None else int(lm_after), 0, float(lm_lambda0), float(lm_K))
     lay = layout.c()
     rc = getattr(N.lib(), fn_name)(_ptr(vis), _ptr(model), C.byref(lay), _ptr(gains), C.byref(opt), _ptr(iters),
                                    _ptr(chi2), _ptr(status), stream)
@@ -107,22 +114,36 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
 
 
 def calibrate_di_scalar(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
-                        compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO):
+                        compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO, lm_after=None,
+                        lm_lambda0=0.0, lm_K=0.0):
     """StefCal on scalar DI gains (gc_calibrate_di_scalar); gains are updated in place.
 
+    schedule: GC_SCHED_STEFCAL / GC_SCHED_GN / GC_SCHED_LM, or 'stefcal' / 'gn' / 'lm'; with 'lm',
+    lm_after StefCal iterations (None: GC_LM_DEFAULT_AFTER; 0: none) are followed by
+    Levenberg-Marquardt with the whole J^H J (lm_lambda0, lm_K: 0 selects the library defaults; see
+    include/gaincal.h).
     path: GC_PATH_AUTO (default), GC_PATH_STREAM or GC_PATH_RESIDENT (see include/gaincal.h).
     profile: 0 off, 1 (or True) time the iteration launches, 2 time the accumulate launches alone.
     Returns (gains, iters[n_int] int32, chi2[n_int] float64 or None, status[n_int] int32).
     """
     return _calibrate('gc_calibrate_di_scalar', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers, profile=profile, path=path)
+                      host_buffers, profile=profile, path=path, lm_after=lm_after, lm_lambda0=lm_lambda0, lm_K=lm_K)
 
 
 def calibrate_di_jones2x2(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
-                          compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO):
-    """Polarized StefCal on 2x2 DI gains (gc_calibrate_di_jones2x2); vis/model [rows,2,2], gains [n_gain,2,2]."""
+                          compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO, lm_after=None,
+                          lm_lambda0=0.0, lm_K=0.0):
+    """Polarized StefCal (or, with schedule 'lm', StefCal then Levenberg-Marquardt with the whole
+    J^H J) on 2x2 DI gains (gc_calibrate_di_jones2x2); vis/model [rows,2,2], gains [n_gain,2,2]."""
     return _calibrate('gc_calibrate_di_jones2x2', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers, profile=profile, path=path)
+                      host_buffers, profile=profile, path=path, lm_after=lm_after, lm_lambda0=lm_lambda0, lm_K=lm_K)
+
+
+def profile_lm():
+    """(ms, launches, flop) of the Levenberg-Marquardt phase of the last profiled DI calibration."""
+    ms, n, fl = C.c_double(0.0), C.c_int64(0), C.c_double(0.0)
+    N.check(N.lib().gc_profile_lm(C.byref(ms), C.byref(n), C.byref(fl)), 'gc_profile_lm')
+    return ms.value, n.value, fl.value
 
 
 def calibrate_dd_cohjones(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,

@@ -731,14 +731,21 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
                   const gc_warm* warm = nullptr) {
   if (!opt || !L) return GC_ERR_ARG;
   if (opt->dtype != GC_DTYPE_C64 && opt->dtype != GC_DTYPE_C128) return GC_ERR_DTYPE;
-  if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
+  if (opt->max_iter < 1 || !(opt->tol >= 0.0) ||
+      (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN && opt->schedule != GC_SCHED_LM))
     return GC_ERR_ARG;
   if (opt->host_buffers != 0 && opt->host_buffers != 1) return GC_ERR_ARG;
   if (opt->reserved || opt->path < GC_PATH_AUTO || opt->path > GC_PATH_MOMENTS) return GC_ERR_ARG;
   if (opt->profile < 0 || opt->profile > 2) return GC_ERR_ARG;
+  const bool lm = opt->schedule == GC_SCHED_LM;
+  if (opt->lm_reserved || opt->lm_after < 0 || !(opt->lm_lambda0 >= 0.0) || !(opt->lm_K == 0.0 || opt->lm_K > 1.0))
+    return GC_ERR_ARG;
+  if (lm && (opt->dtype != GC_DTYPE_C64)) return GC_ERR_DTYPE;
+  if (lm && (opt->path == GC_PATH_STREAM || opt->path == GC_PATH_RESIDENT)) return GC_ERR_ARG;
   int rc = validate_layout(L, 1);
   if (rc != GC_OK) return rc;
   if (L->n_intervals == 0) return GC_OK;
+  if (lm && !lm_limit_ok(kind, L)) return GC_ERR_LIMIT;
   if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && !gains)) return GC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const bool can_res = opt->dtype == GC_DTYPE_C64 && res_supported(kind, L);
@@ -790,6 +797,13 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   a.tol = opt->tol;
   a.max_iter = opt->max_iter;
   a.schedule = opt->schedule;
+  // LM schedule: a fixed number of StefCal iterations first (no stopping), then lm_run
+  const int lm_after = lm ? std::min(opt->max_iter, opt->lm_after) : 0;
+  if (lm) {
+    a.tol = 0.0;
+    a.max_iter = lm_after;
+    a.schedule = GC_SCHED_STEFCAL;
+  }
   if (P->scr_elems > 0) {
     void* scr = nullptr;
     if ((rc = ws_get("di_scratch", (size_t)P->scr_elems * (opt->dtype == GC_DTYPE_C64 ? 4 : 8), &scr))) return rc;
@@ -846,7 +860,7 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   const int S = tn.check_every;
   const int per_iter = mode == 1 && !s1 ? 2 : 1;
   // the single-launch scheme updates iteration k in launch k + 1: one more launch at the end
-  const int last_k = opt->max_iter + (s1 ? 1 : 0);
+  const int last_k = (lm ? lm_after : opt->max_iter) + (s1 ? 1 : 0);
   auto launch_iter = [&](const DIArgs& x, cudaStream_t st) -> int {
     if (s1) return di_launch_mstep1(kind, x, P->sgrid, P->ssmem, P->n_int, tn.red_chunks, tn.prefetch, s1err, st);
     return mode == 1 ? di_launch_mstep(kind, x, P->grid, P->smem, P->n_int, tn.red_chunks, tn.prefetch, st)
@@ -953,6 +967,10 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
         if (*flag <= 0) break;
       }
     }
+  }
+  if (lm && opt->max_iter > lm_after) {
+    rc = lm_run(kind, L, a.moments, a.mom_off, a.ant1, a.ant2, (float*)st.gains, a.iters, a.status, opt, stream);
+    if (rc != GC_OK) return rc;
   }
   if (opt->compute_chi2) {
     if (mode == 1)
@@ -1443,6 +1461,8 @@ int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row
 }
 
 int64_t gc_launch_count(void) { return (int64_t)gc::g_launches.load(); }
+
+int gc_profile_lm(double* lm_ms, int64_t* launches, double* flop) { return gc::lm_profile(lm_ms, launches, flop); }
 
 int gc_release(void) {
   for (auto& kv : gc::g_ws) {

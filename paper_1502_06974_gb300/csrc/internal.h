@@ -153,4 +153,14 @@ int ws_choose(const float* g1, const double* e_prev, const double* e_prop, const
 int gauge_fix(int kind, int dtype, void* gains, const int32_t* gain_off, const int32_t* n_ant, int n_int,
               void* stream);
 
+// Levenberg-Marquardt polish with the whole J^H J (lm.cu), run after the diagonal iterations of the
+// moment path: moments / mom_off / ant1 / ant2 are the caller's plan, gains / iters / status its
+// device state.  lm_limit_ok: every interval has at most GC_LM_MAX_UNKNOWNS real unknowns.
+int lm_limit_ok(int kind, const gc_layout* L);
+int lm_run(int kind, const gc_layout* L, const float* moments, const int64_t* mom_off, const int32_t* ant1,
+           const int32_t* ant2, float* gains, int32_t* iters, int32_t* status, const gc_options* opt, void* stream);
+// time of the last profiled polish's iteration launches (CUDA events), their count, and the
+// algorithmic flops of its factorisations and triangular solves
+int lm_profile(double* ms, int64_t* launches, double* flop);
+
 }  // namespace gc

@@ -46,14 +46,16 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / 'sz.c'
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gaincal.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(gc_layout), sizeof(gc_options),'
-                   ' offsetof(gc_layout, n_rows), offsetof(gc_options, reserved), offsetof(gc_layout, n_dir));'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gc_layout), sizeof(gc_options),'
+                   ' offsetof(gc_layout, n_rows), offsetof(gc_options, reserved), offsetof(gc_layout, n_dir),'
+                   ' offsetof(gc_options, lm_after), offsetof(gc_options, lm_lambda0), offsetof(gc_options, lm_K));'
                    'return 0;}\n')
     exe = tmp_path / 'sz'
     subprocess.run(['gcc', '-I', os.path.join(ROOT, 'include'), str(src), '-o', str(exe)], check=True)
     vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [C.sizeof(N.GcLayout), C.sizeof(N.GcOptions), N.GcLayout.n_rows.offset,
-                    N.GcOptions.reserved.offset, N.GcLayout.n_dir.offset]
+                    N.GcOptions.reserved.offset, N.GcLayout.n_dir.offset, N.GcOptions.lm_after.offset,
+                    N.GcOptions.lm_lambda0.offset, N.GcOptions.lm_K.offset]
 
 
 def _call(lib, fn, lay, opt, vis=1, model=1, gains=1):
@@ -94,6 +96,15 @@ def test_validation_errors_are_return_codes(lib, fn):
     assert _call(lib, fn, good, _opt(schedule=5)) == -1
     assert _call(lib, fn, good, _opt(dtype=7)) == -4
     assert _call(lib, fn, good, _opt(), vis=0) == -1
+    # Levenberg-Marquardt schedule: options checked, complex64 moment path only, size limit
+    assert _call(lib, fn, good, _opt(schedule=2, lm_K=0.5)) == -1
+    assert _call(lib, fn, good, _opt(schedule=2, lm_lambda0=-1.0)) == -1
+    assert _call(lib, fn, good, _opt(schedule=2, lm_reserved=1)) == -1
+    assert _call(lib, fn, good, _opt(schedule=2, dtype=1)) == -4
+    assert _call(lib, fn, good, _opt(schedule=2, path=1)) == -1
+    big = Layout(**lay.__dict__); big.n_ant = np.full_like(big.n_ant, 300); big.n_gain = 600
+    big.gain_off = np.array([0, 300], np.int32)
+    assert _call(lib, fn, big.c(), _opt(schedule=2)) == -6               # above GC_LM_MAX_UNKNOWNS
     keep.clear()
 
 
