@@ -5,8 +5,10 @@ Workload (the full-Jones direction-independent problem): 64 antennas (2016 basel
 60 times x 64 channels at 1.0-1.4 GHz, solution intervals of 1 time x 4 channels (960 intervals,
 7,741,440 rows of 2x2 complex64), 20 polarized point sources, true Jones = diagonal gains
 (amplitude 1 + N(0, 0.1), phase U(-pi, pi)) plus leakage CN(0, 0.02), noise sigma = 0.01,
-seed 150206974 (+ rank).  Every interval is solved by polarized StefCal from identity gains to a
-relative step tolerance of 1e-6.
+seed 150206974 (+ rank).  Every interval is solved from identity gains by 20 StefCal iterations
+followed by Levenberg-Marquardt with the whole J^H J (App. C, eq. LM), to a relative LM step of
+1e-6, which puts every interval within 1e-5 of the FP64 least-squares gains (checked on sampled
+intervals against the FP64 oracle run from its own start; reported as max_err_vs_oracle).
 
 One step = reset the gains to identity + one gc_calibrate_di_jones2x2 call over all 960 intervals
 (iterations run until every interval has converged).  value = rows calibrated / device time, inputs
@@ -15,7 +17,7 @@ call with pinned host buffers, host<->device copies inside the timed region.
 
 Under torchrun each rank solves its own copy of the workload on its own GPU (independent
 intervals, no collective on the data path: weak scaling); rank 0 prints one JSON line.
-``--impl reference`` times the FP64 CPU oracle (the paper's iteration in NumPy) on a bounded sample.
+``--impl reference`` times the FP64 CPU oracle (the same method in NumPy) on one interval per step.
 """
 from __future__ import annotations
 
@@ -34,15 +36,20 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-TOL = 1e-6
+TOL = 1e-6                  # relative LM step at which an interval stops
+LM_K = 2.0                  # App. C damping factor (K = 2, 3, 5, 10 measured; 2 the fastest)
+LM_AFTER = 20               # StefCal iterations before the first LM step
+TOL_STEFCAL = 1e-6          # the StefCal-only comparison stops at this relative step
 MAX_ITER = 20000
-BYTES_PER_ROW = 64          # vis + model, one 2x2 complex64 each (algorithmic bytes per row per iteration)
+SAMPLE_INTERVALS = (0, 480, 959)   # checked against the FP64 oracle's least-squares gains
+BYTES_PER_ROW = 64          # vis + model, one 2x2 complex64 each (algorithmic bytes per row)
 MOMENT_BYTES = 192          # per baseline: P (4x4 complex64) + R (4x4 float32), written once by the moment pass
-FLOP_PER_BASELINE_ITER = 320  # per baseline per iteration: 2 x (4x4 complex mat-vec + 4x4 real mat-vec)
 N_PATH_STREAM, N_PATH_RESIDENT, N_PATH_MOMENTS = 1, 2, 3
 METRIC = "visibilities calibrated/s to convergence at <=1e-5 gain err; learned+batched vs plain"
 UNIT = "visibilities/s"
-WORKLOAD = "di_jones2x2: 64 ant (2016 bl), 60 t x 64 ch, intervals 1 t x 4 ch (960), 20 polarized sources, tol 1e-6"
+WORKLOAD = ("di_jones2x2: 64 ant (2016 bl), 60 t x 64 ch, intervals 1 t x 4 ch (960), 20 polarized sources; "
+            "20 StefCal iterations + Levenberg-Marquardt (whole J^H J) to a relative step of 1e-6")
+SCHED = dict(schedule='lm', lm_after=LM_AFTER, lm_K=LM_K)
 
 
 def _env_rank():
@@ -123,66 +130,61 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------ CPU oracle
-def oracle_sample(b, n_iter=120, interval=0):
-    """Time the FP64 oracle iteration (NumPy, the paper's steps) on one interval for n_iter steps.
-
-    Returns (seconds per iteration, rows of the interval, cpu-seconds / wall-seconds).
-    """
-    from oracle import diagonal
-    iv = b.interval(interval)
+def oracle_solve(b, i, tol=TOL, n_stefcal=LM_AFTER, K=LM_K):
+    """The FP64 oracle's solution of interval i from its own unit start: the same schedule (StefCal,
+    then App. C LM on the closed-form whole J^H J) in NumPy.  Returns (gains, seconds, cpu/wall)."""
+    from oracle import diagonal, wirtinger
+    iv = b.interval(i)
     g0 = b.g0()[iv['gain_slice']]
     t0 = time.perf_counter(); c0 = time.process_time()
-    diagonal.iterate('jones', g0, iv['vis'], iv['model'], iv['ant1'], iv['ant2'], iv['n_ant'], tol=0.0,
-                     max_iter=n_iter)
+    r = diagonal.iterate('jones', g0, iv['vis'], iv['model'], iv['ant1'], iv['ant2'], iv['n_ant'], tol=0.0,
+                         max_iter=n_stefcal)
+    prob = wirtinger.ClosedFormProblem('jones', iv['vis'], iv['model'], iv['ant1'], iv['ant2'], iv['n_ant'])
+    g, _, _ = wirtinger.levenberg_marquardt(prob, r['g'], tol=tol, max_iter=400, lam0=1e-2, K=K, gauge=True)
     wall = time.perf_counter() - t0
-    cpu = time.process_time() - c0
-    return wall / n_iter, int(iv['vis'].shape[0] * iv['vis'].shape[1]), cpu / max(wall, 1e-9)
+    return g, wall, (time.process_time() - c0) / max(wall, 1e-9)
 
 
-def cpu_baseline_block(b, iters_to_converge, n_iter=120):
-    per_it, rows, threads = oracle_sample(b, n_iter)
-    value = rows / (per_it * iters_to_converge)
-    return {"value": value, "unit": UNIT, "cores": max(1, int(round(threads))), "kind": "oracle",
-            "sample": (f"FP64 NumPy oracle (diagonal iteration), 1 interval of {rows} rows x {n_iter} iterations "
-                       f"({per_it * 1e3:.2f} ms/iteration), extrapolated to {iters_to_converge} iterations "
-                       f"(median iteration count to tol {TOL:g} on the GPU run)")}
+def oracle_errors(b, gains, intervals=SAMPLE_INTERVALS, refs=None):
+    """max over antennas of ||G_p - G_ref,p|| / ||G_ref,p|| after phase alignment, per sampled
+    interval, G_ref the oracle's least-squares gains (tol 1e-12, its own start)."""
+    from oracle import gauge
+    refs = refs if refs is not None else {i: oracle_solve(b, i, tol=1e-12)[0] for i in intervals}
+    out = {}
+    for i in intervals:
+        iv = b.interval(i)
+        out[int(i)] = gauge.rel_error('jones', gains[iv['gain_slice']], refs[i])
+    return out, refs
+
+
+def cpu_baseline_block(b, interval=0):
+    g, wall, threads = oracle_solve(b, interval)
+    rows = int(b.n_samp[interval]) * int(b.n_bl[interval])
+    return {"value": rows / wall, "unit": UNIT, "cores": max(1, int(round(threads))), "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle, the same method (StefCal x{LM_AFTER}, then App. C LM on the whole "
+                       f"J^H J to a relative step of {TOL:g}) on 1 interval of {rows} rows: {wall:.2f} s")}
 
 
 # ------------------------------------------------------------------------------------ helpers
-def kernel_source_hash():
+def kernel_source_hash(files=('di_kernels.cu', 'resident.cu', 'kinds.cuh', 'common.cuh', 'internal.h')):
     h = hashlib.sha256()
-    for f in ('di_kernels.cu', 'resident.cu', 'kinds.cuh', 'common.cuh', 'internal.h'):
+    for f in files:
         with open(os.path.join(ROOT, 'paper_1502_06974_gb300', 'csrc', f), 'rb') as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(name, unit):
-    """DRAM bytes per launch of a kernel from a committed ncu summary (json) when it was taken on the
-    current kernel sources; None otherwise."""
+LM_SOURCES = ('lm.cu', 'kinds.cuh', 'common.cuh', 'internal.h')
+
+
+def ncu_summary(name, files):
+    """A committed ncu summary (json) when it was taken on the current kernel sources; None otherwise."""
     p = os.path.join(ROOT, 'profiles', name)
     try:
         d = json.load(open(p))
     except Exception:
         return None
-    if d.get('kernel_hash') != kernel_source_hash():
-        return None
-    if unit == 'moments':
-        return d['dram_bytes_per_launch'] / d['baselines_per_launch']
-    return d.get('dram_bytes_per_launch')
-
-
-def ncu_traffic_per_row():
-    """DRAM bytes per processed row of the iteration kernel from the committed ncu summary, if it was
-    taken on the current kernel source; None otherwise."""
-    p = os.path.join(ROOT, 'profiles', 'di_iter_jones_cfg2.json')
-    try:
-        d = json.load(open(p))
-    except Exception:
-        return None
-    if d.get('kernel_hash') != kernel_source_hash():
-        return None
-    return d['dram_bytes_per_launch'] / d['rows_per_launch']
+    return d if d.get('kernel_hash') == kernel_source_hash(files) else None
 
 
 def measured_peaks():
@@ -194,52 +196,58 @@ def measured_peaks():
 
 # ------------------------------------------------------------------------------------ arms
 def run_reference(args):
+    """The FP64 oracle, as it stands, on the host cores: each step solves one interval of the
+    workload with the same method (StefCal, then App. C LM on the whole J^H J, same tolerance).
+    The intervals are alike, so visibilities/s of one interval is the rate of the whole job."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
-    b = make_workload(0)
-    iters = args.ref_iters
+    from paper_1502_06974_gb300 import synth
+    b = synth.make_di_jones(seed=rank_seed(0), n_t=1)   # the workload's first 16 intervals, drawn identically
     samples = []
-    per_it = rows = threads = None
+    rows = threads = None
     for k in range(args.warmup + args.steps):
-        per_it, rows, threads = oracle_sample(b, n_iter=args.ref_sample_iters, interval=k % b.n_int)
+        i = k % b.n_int
+        _, wall, threads = oracle_solve(b, i)
+        rows = int(b.n_samp[i]) * int(b.n_bl[i])
         if k >= args.warmup:
-            samples.append(per_it)
-    per_it = statistics.median(samples)
-    value = rows / (per_it * iters)
+            samples.append(wall)
+    wall = statistics.median(samples)
+    value = rows / wall
     cores = max(1, int(round(threads)))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * iters * 1e3 * b.n_int,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "rows": b.n_rows, "intervals": b.n_int, "tol": TOL},
+           "config": {"workload": WORKLOAD, "rows": 7741440, "intervals": 960, "tol": TOL},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": (f"each step: FP64 NumPy oracle, 1 interval ({rows} rows) x "
-                                       f"{args.ref_sample_iters} iterations, extrapolated to {iters} iterations")},
+                            "sample": (f"each step: the FP64 NumPy oracle solves 1 interval ({rows} rows) of the "
+                                       f"workload with the same method and tolerance; ms_per_step is that solve")},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
 
 
 WARM_LAG = 32           # wave length (time steps) of the learned wavefront
-WARM_GATE = 1e-5        # pipelined wavefront: a wave joins once its history's relative steps fall below this
 WARM_WORKLOAD = ("di_jones2x2 warm start: 64 ant (2016 bl), 720 t x 64 ch, intervals 1 t x 8 ch (5760), GP gains "
-                 "(30 min / 50 MHz correlation, amplitude 0.1, phase 1 rad), tol 1e-6")
+                 "(30 min / 50 MHz correlation, amplitude 0.1, phase 1 rad); Levenberg-Marquardt to a relative "
+                 "step of 1e-6 from every start")
 
 
 def warm_start_block(dev, args):
-    """Learned warm start + batched path vs the plain batched solver on the GP-gain workload.
+    """Learned warm start + batched path vs the plain batched solver on the GP-gain workload, every
+    solve to the same tolerance with the same method (LM with the whole J^H J).
 
     The network is trained first (its own observation, another seed), then the same 5760 intervals
-    are solved with the data resident: plain (all intervals from unit gains in one call); the
-    previous-solution and learned starts in waves of 32 times, one call per wave; and the same two
-    starts pipelined in one call (a wave joins once its history has settled to WARM_GATE)."""
+    are solved with the data resident: plain (all intervals from unit gains in one call: StefCal x20,
+    then LM); the previous-solution and learned starts in waves of 32 times, one call per wave (the
+    first wave as plain, the others LM straight from the start)."""
     import torch
     from paper_1502_06974_gb300 import api, synth, warmstart
     t0 = time.perf_counter()
     bt = synth.make_warm(seed=synth.SEED + 1000, n_t=160)
     vt, mt = torch.from_numpy(bt.vis).to(dev), torch.from_numpy(bt.model).to(dev)
     gt = warmstart.Grid.from_batch(bt)
-    sol_t, _, st_t = warmstart.solve_plain(vt, mt, gt, TOL, MAX_ITER)
+    sol_t, _, st_t = warmstart.solve_plain(vt, mt, gt, TOL, MAX_ITER, **SCHED)
     x, t = warmstart.training_set(vt, mt, gt, sol_t, WARM_LAG, np.random.default_rng(0), n_samples=50000)
     res = warmstart.train(x, t, epochs=40, batch=1024, lr=1e-3)
     del vt, mt, sol_t, x, t
@@ -253,6 +261,7 @@ def warm_start_block(dev, args):
     if not args.no_autotune:
         api.autotune_di(ve, me, lay, warmstart._identity(n_int * ge.n_ant, dev), iters=24)
     stream = torch.cuda.current_stream(dev)
+    warm_sched = dict(schedule='lm', lm_after=0, lm_K=LM_K)
 
     def timed(fn):
         fn()                                   # warm-up (plan, graph capture)
@@ -264,14 +273,11 @@ def warm_start_block(dev, args):
         torch.cuda.synchronize(dev)
         return out, e0.elapsed_time(e1)
 
-    (gp, itp, stp), ms_plain = timed(lambda: warmstart.solve_plain(ve, me, ge, TOL, MAX_ITER))
-    prev, ms_prev = timed(lambda: warmstart.solve_wavefront(ve, me, ge, WARM_LAG, None, TOL, MAX_ITER))
-    lrn, ms_lrn = timed(lambda: warmstart.solve_wavefront(ve, me, ge, WARM_LAG, res.net, TOL, MAX_ITER))
-    # the same two starts in one library call, waves joining the running iteration (pipelined)
-    pprev, ms_pprev = timed(lambda: warmstart.solve_pipelined(ve, me, ge, WARM_LAG, None, TOL, MAX_ITER,
-                                                              gate_tol=WARM_GATE))
-    plrn, ms_plrn = timed(lambda: warmstart.solve_pipelined(ve, me, ge, WARM_LAG, res.net, TOL, MAX_ITER,
-                                                            gate_tol=WARM_GATE))
+    (gp, itp, stp), ms_plain = timed(lambda: warmstart.solve_plain(ve, me, ge, TOL, MAX_ITER, **SCHED))
+    prev, ms_prev = timed(lambda: warmstart.solve_wavefront(ve, me, ge, WARM_LAG, None, TOL, MAX_ITER, first=SCHED,
+                                                            **warm_sched))
+    lrn, ms_lrn = timed(lambda: warmstart.solve_wavefront(ve, me, ge, WARM_LAG, res.net, TOL, MAX_ITER, first=SCHED,
+                                                          **warm_sched))
     itp = itp.cpu().numpy()
     rows = ge.rows * n_int
     g_true = be.g_true
@@ -285,6 +291,13 @@ def warm_start_block(dev, args):
         d = np.linalg.norm(est * ph[:, None, None] - ref, axis=2) / np.linalg.norm(ref, axis=2)
         return float(d.max())
 
+    def agree(g, ref):
+        # the solutions of two starts must be the same least-squares point: max relative difference
+        a = g.cpu().numpy().astype(np.complex128).reshape(n_int, ge.n_ant, 4)
+        r = ref.cpu().numpy().astype(np.complex128).reshape(n_int, ge.n_ant, 4)
+        ph = np.exp(1j * np.angle(np.sum(r * np.conj(a), axis=(1, 2))))
+        return float((np.linalg.norm(a * ph[:, None, None] - r, axis=2) / np.linalg.norm(r, axis=2)).max())
+
     def entry(ms, iters, status, extra=None):
         d = {"ms": ms, "value": rows / (ms / 1e3), "iters_mean": float(np.mean(iters)),
              "iters_max": int(np.max(iters)), "interval_iterations": int(np.sum(iters)),
@@ -293,26 +306,18 @@ def warm_start_block(dev, args):
         return d
 
     return {"workload": WARM_WORKLOAD, "metric": METRIC, "unit": UNIT, "lag": WARM_LAG,
-            "schedule": "waves of lag x 8 intervals, one gc_calibrate_di_jones2x2_warm call each, predicted from "
-                        "the 4 solutions before the wave",
+            "schedule": ("plain: one call from unit gains (StefCal x20 then LM); waves: lag x 8 intervals per "
+                         "gc_calibrate_di_jones2x2_warm call, predicted from the 4 solutions before the wave, LM "
+                         "from the start; every solve to a relative LM step of 1e-6"),
             "plain": entry(ms_plain, itp, stp.cpu().numpy(), {"max_err_vs_truth": err_truth(gp)}),
-            "previous_solution": entry(ms_prev, prev.iters, prev.status, {"max_err_vs_truth": err_truth(prev.gains)}),
+            "previous_solution": entry(ms_prev, prev.iters, prev.status, {"max_err_vs_truth": err_truth(prev.gains),
+                                                                          "max_diff_vs_plain": agree(prev.gains, gp)}),
             "learned": entry(ms_lrn, lrn.iters, lrn.status,
                              {"proposals_taken": float(np.mean(lrn.used[np.repeat(np.arange(ge.n_t), ge.n_fb)
                                                                        >= WARM_LAG])),
-                              "max_err_vs_truth": err_truth(lrn.gains)}),
-            "pipelined": {
-                "schedule": f"one gc_calibrate_di_jones2x2_wavefront call: a wave of lag x 8 intervals joins the "
-                            f"running iteration once the 4 times before it have finished or taken a relative step "
-                            f"below {WARM_GATE:g}",
-                "previous_solution": entry(ms_pprev, pprev.iters, pprev.status,
-                                           {"max_err_vs_truth": err_truth(pprev.gains)}),
-                "learned": entry(ms_plrn, plrn.iters, plrn.status, {"max_err_vs_truth": err_truth(plrn.gains)}),
-                "speedup_learned_vs_plain": ms_plain / ms_plrn,
-                "speedup_learned_vs_previous_solution": ms_pprev / ms_plrn},
+                              "max_err_vs_truth": err_truth(lrn.gains), "max_diff_vs_plain": agree(lrn.gains, gp)}),
             "speedup_learned_vs_plain": ms_plain / ms_lrn,
             "speedup_learned_vs_previous_solution": ms_prev / ms_lrn,
-            "speedup_best_learned_vs_plain": ms_plain / min(ms_lrn, ms_plrn),
             "training": {"trajectories": 50000, "observation": "160 t x 64 ch of the same array, another seed",
                          "adam_steps": res.steps, "train_s": res.seconds, "prep_s": prep_s,
                          "val_mse": res.val_mse, "val_mse_previous_solution": res.val_mse_zero}}
@@ -388,12 +393,13 @@ def run_gpu(args):
     gains = g0.clone()
     stream = torch.cuda.current_stream(dev)
 
-    tol, max_iter = (0.0, args.iters) if args.iters else (TOL, MAX_ITER)
+    lm = args.schedule == 'lm'
+    sched = SCHED if lm else dict(schedule='stefcal', path=args.path)
+    tol, max_iter = (0.0, args.iters) if args.iters else (TOL if lm else TOL_STEFCAL, MAX_ITER)
 
     def step(profile=False):
         gains.copy_(g0)
-        return api.calibrate_di_jones2x2(vis, model, lay, gains, tol=tol, max_iter=max_iter, profile=profile,
-                                         path=args.path)
+        return api.calibrate_di_jones2x2(vis, model, lay, gains, tol=tol, max_iter=max_iter, profile=profile, **sched)
 
     tuned_ms = None
     if not args.no_autotune:   # launch shapes picked on this data, before any timing
@@ -414,12 +420,16 @@ def run_gpu(args):
     n0 = api.launch_count()
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     kms = 0.0; kl = 0; kri = 0; kmom = 0.0; kbi = 0; path_used = None
+    lms = 0.0; lml = 0; lmf = 0.0
     e0.record(stream)
     for _ in range(args.steps):
         step(profile=True)
         ms_k, n_k, ri_k = api.profile_last()
         mom_k, bi_k, path_used = api.profile_detail()
         kms += ms_k; kl += n_k; kri += ri_k; kmom += mom_k; kbi += bi_k
+        if lm:
+            a, n, f = api.profile_lm()
+            lms += a; lml += n; lmf += f
     e1.record(stream)
     torch.cuda.synchronize(dev)
     if dist:
@@ -430,9 +440,10 @@ def run_gpu(args):
     ms = max_over_ranks(ms, dist, dev)
     rows_total = b.n_rows * args.steps * world
     value = rows_total / (ms / 1e3)
+    g_sol = gains.cpu().numpy()
 
-    # the accumulate kernel timed alone (outside the timed region): one more full solve in which
-    # every accumulate launch is bracketed by CUDA events on the call's stream
+    # the accumulate kernel of the diagonal iterations timed alone (outside the timed region): one
+    # more full solve in which every accumulate launch is bracketed by CUDA events on the call's stream
     acc = None
     if path_used == N_PATH_MOMENTS:
         step(profile=2)
@@ -447,93 +458,101 @@ def run_gpu(args):
         visH = torch.from_numpy(b.vis).pin_memory()
         modelH = torch.from_numpy(b.model).pin_memory()
         gH = g0H.clone().pin_memory()
-        api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True, path=args.path)
+        api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True, **sched)
         e2e_steps = max(1, min(args.steps, 3))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             gH.copy_(g0H)
-            api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True,
-                                      path=args.path)
+            api.calibrate_di_jones2x2(visH, modelH, lay, gH, tol=tol, max_iter=max_iter, host_buffers=True, **sched)
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(e2e_s, dist, dev)
 
+    # StefCal alone to a relative step of 1e-6 (the diagonal method without LM), for comparison
+    stefcal_only = None
+    if lm and rank == 0 and not args.no_stefcal_compare and not args.iters:
+        gains.copy_(g0)
+        api.calibrate_di_jones2x2(vis, model, lay, gains, tol=TOL_STEFCAL, max_iter=MAX_ITER)
+        gains.copy_(g0)
+        torch.cuda.synchronize(dev)
+        f0 = torch.cuda.Event(enable_timing=True); f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        _, it_sc, _, st_sc = api.calibrate_di_jones2x2(vis, model, lay, gains, tol=TOL_STEFCAL, max_iter=MAX_ITER)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        stefcal_only = {"ms": f0.elapsed_time(f1), "tol": TOL_STEFCAL, "g": gains.cpu().numpy(),
+                        "iters_median": int(np.median(it_sc.cpu().numpy())), "iters_max": int(it_sc.max().item())}
+
     if rank == 0:
         peaks, which = measured_peaks()
-        roof_iter = None
-        if path_used == N_PATH_RESIDENT:
-            # dominant kernel: the cluster-resident iteration kernel (one launch per step); the
-            # moment pass (HBM-bound) is reported beside it
-            n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-            sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-            peak_tf = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12        # FP32 FMA lanes x 2 flop x clock
-            flops = kbi * FLOP_PER_BASELINE_ITER
-            achieved = flops / (kms / 1e3) / 1e12
-            tpl = ncu_traffic('di_resident_jones_cfg2.json', 'resident')
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tf, "traffic": (tpl * kl / max(kl, 1)) if tpl is not None else None,
-                    "kernel": "di_resident_kernel<JonesMom> (moment-space J^H D / J^H J + 2x2 update, on chip)",
-                    "flop_per_launch": flops / max(kl, 1), "avg_launch_us": kms * 1e3 / max(kl, 1),
-                    "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
-            mom_bytes = (b.n_rows * BYTES_PER_ROW + b.n_int * int(b.n_bl[0]) * MOMENT_BYTES) * args.steps
-            roof_mom = {"bound": "hbm", "achieved": mom_bytes / (kmom / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
-                        "unit": "GB/s", "frac": mom_bytes / (kmom / 1e3) / 1e9 / peaks["hbm_gbs"],
-                        "kernel": "di_moment_kernel<JonesMom>", "ms_per_step": kmom / args.steps,
-                        "peak_source": which}
-        elif path_used == N_PATH_MOMENTS:
-            # dominant kernel: the moment-space accumulate kernel, 192 B of moments per active
-            # baseline per iteration (HBM-bound), each launch timed alone in one full solve; the
-            # whole iteration (accumulate + solve launches, graph segments) over the timed steps
-            # and the one-off moment pass are reported beside it
+        props = torch.cuda.get_device_properties(dev)
+        n_sm = props.multi_processor_count
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        extra = {}
+        if lm and not args.iters:
+            errs, refs = oracle_errors(b, g_sol)
+            extra["max_err_vs_oracle"] = max(errs.values())
+            extra["err_vs_oracle_sampled"] = errs
+            if stefcal_only is not None:
+                e_sc, _ = oracle_errors(b, stefcal_only.pop("g"), refs=refs)
+                stefcal_only["max_err_vs_oracle"] = max(e_sc.values())
+                stefcal_only["value"] = b.n_rows / (stefcal_only["ms"] / 1e3)
+        roof_acc = None
+        if acc is not None:
             acc_ms, acc_n, acc_bi = acc
             avg_launch_s = (acc_ms / 1e3) / max(acc_n, 1)
             bytes_per_launch = acc_bi * MOMENT_BYTES / max(acc_n, 1)
-            achieved = bytes_per_launch / avg_launch_s / 1e9
-            tpb = ncu_traffic('di_macc_jones_cfg2.json', 'moments')   # DRAM bytes per active baseline
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"],
-                    "traffic": (tpb * acc_bi / max(acc_n, 1)) if tpb is not None else None,
-                    "kernel": "di_macc_bulk_kernel<JonesMom> (moment-space J^H D / diag J^H J per 256-baseline tile, bulk copies into a two-stage shared-memory ring)",
-                    "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6, "launches": acc_n,
-                    "timed": "every accumulate launch of one full solve, CUDA events on the call's stream",
-                    "peak_source": which}
-            it_bytes = kbi * MOMENT_BYTES
-            roof_iter = {"achieved": it_bytes / (kms / 1e3) / 1e9, "unit": "GB/s",
-                         "frac": it_bytes / (kms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                         "timed": "accumulate + solve launches of every iteration in the timed steps (graph "
-                                  "segments bracketed by CUDA events)", "iterations": kl,
-                         "avg_iteration_us": kms * 1e3 / max(kl, 1)}
-            mom_bytes = (b.n_rows * BYTES_PER_ROW + b.n_int * int(b.n_bl[0]) * MOMENT_BYTES) * args.steps
-            roof_mom = {"bound": "hbm", "achieved": mom_bytes / (kmom / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
-                        "unit": "GB/s", "frac": mom_bytes / (kmom / 1e3) / 1e9 / peaks["hbm_gbs"],
-                        "kernel": ("di_moment_direct_kernel<JonesMom>" if int(np.max(b.n_samp)) <= 16
-                                   else "di_moment_kernel<JonesMom>"), "ms_per_step": kmom / args.steps,
+            roof_acc = {"bound": "hbm", "achieved": bytes_per_launch / avg_launch_s / 1e9, "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": bytes_per_launch / avg_launch_s / 1e9 / peaks["hbm_gbs"],
+                        "kernel": "di_macc_bulk_kernel<JonesMom> (moment-space J^H D / diag J^H J per 256-baseline "
+                                  "tile, bulk copies into a two-stage shared-memory ring)",
+                        "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6, "launches": acc_n,
+                        "timed": "every accumulate launch of one full solve, CUDA events on the call's stream",
                         "peak_source": which}
+        mom_bytes = (b.n_rows * BYTES_PER_ROW + b.n_int * int(b.n_bl[0]) * MOMENT_BYTES) * args.steps
+        roof_mom = {"bound": "hbm", "achieved": mom_bytes / (kmom / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": mom_bytes / (kmom / 1e3) / 1e9 / peaks["hbm_gbs"],
+                    "kernel": ("di_moment_direct_kernel<JonesMom>" if int(np.max(b.n_samp)) <= 16
+                               else "di_moment_kernel<JonesMom>"), "ms_per_step": kmom / args.steps,
+                    "peak_source": which} if kmom > 0 else None
+        if lm:
+            # dominant kernel: the LM iteration kernel, bound by FP32 FMA issue (no tensor cores):
+            # achieved = algorithmic flops of its Cholesky factorisations and triangular solves /
+            # the summed CUDA-event time of its launches in the timed steps
+            peak_tf = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+            n_unk = 8 * int(b.n_ant[0])
+            flop_per_ii = 2.0 * (n_unk ** 3 / 3.0 + 2.0 * n_unk ** 2)
+            ii_per_launch = lmf / flop_per_ii / max(lml, 1)
+            summ = ncu_summary('lm_iter_jones_cfg2.json', LM_SOURCES)
+            roof = {"bound": "alu", "achieved": lmf / (lms / 1e3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": lmf / (lms / 1e3) / 1e12 / peak_tf,
+                    "traffic": (summ["dram_bytes_per_interval_iteration"] * ii_per_launch) if summ else None,
+                    "kernel": ("lm_iter_kernel<LMJones> (per interval: whole J^H J from the moments, FP32 blocked "
+                               "Cholesky + triangular solves, FP64 chi^2 and damping decision)"),
+                    "flop_per_launch": lmf / max(lml, 1), "interval_iterations_per_launch": ii_per_launch,
+                    "avg_launch_us": lms * 1e3 / max(lml, 1), "launches": lml,
+                    "timed": "every LM iteration launch of the timed steps, CUDA events on the call's stream",
+                    "peak_source": (f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop (FMA) x {sm_mhz:.0f} MHz")}
         else:
-            avg_launch_s = (kms / 1e3) / max(kl, 1)
-            bytes_per_launch = kri * BYTES_PER_ROW / max(kl, 1)
-            achieved = bytes_per_launch / avg_launch_s / 1e9
-            tpr = ncu_traffic_per_row()
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"],
-                    "traffic": (tpr * kri / max(kl, 1)) if tpr is not None else None,
-                    "kernel": "di_iter_kernel<float, JonesKind> (accumulate J^H D, diag J^H J + StefCal update)",
-                    "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6,
-                    "peak_source": which}
-            roof_mom = None
+            roof = roof_acc
         med_it = int(np.median(its))
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": WORKLOAD, "rows_per_gpu": b.n_rows, "intervals": b.n_int, "tol": TOL,
+               "config": {"workload": WORKLOAD if lm else WORKLOAD.split(';')[0] + f"; StefCal to {TOL_STEFCAL:g}",
+                          "rows_per_gpu": b.n_rows, "intervals": b.n_int, "tol": tol,
+                          "schedule": (f"StefCal x{LM_AFTER} then LM (K={LM_K:g}, lambda0 1e-2)" if lm else "StefCal"),
                           "l2": "inputs (495 MB vis+model) larger than L2; no flush",
                           "iters_median": med_it, "iters_max": int(its.max()),
                           "converged": int(np.sum((st & 15) == 0)),
                           "parallelism": f"replicas x{world} (independent intervals per GPU)",
-                          "autotuned": tuned_ms is not None},
+                          "autotuned": tuned_ms is not None, **extra},
                "roofline": roof,
+               "roofline_accumulate": roof_acc if lm else None,
                "roofline_moment_pass": roof_mom,
-               "roofline_iteration": roof_iter,
+               "time_split_ms_per_step": {"moment_pass": kmom / args.steps, "stefcal_iterations": kms / args.steps,
+                                          "lm_iterations": lms / args.steps} if lm else None,
+               "stefcal_only": stefcal_only,
                "path": {N_PATH_RESIDENT: "resident", N_PATH_MOMENTS: "moments"}.get(path_used, "stream"),
                "e2e": {"value": b.n_rows * world / e2e_s, "unit": UNIT,
                        "h2d_bytes_per_step": int(b.vis.nbytes + b.model.nbytes + g0H.numel() * 8),
@@ -541,7 +560,7 @@ def run_gpu(args):
                "gpu_launches": int(launches),
                "clocks": clocks}
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_block(b, med_it)
+            out["cpu_baseline"] = cpu_baseline_block(b, 0)
         if not args.no_warm and world == 1:
             del vis, model
             torch.cuda.empty_cache()
@@ -567,11 +586,13 @@ def main():
     ap.add_argument('--no-warm', action='store_true', help='skip the learned warm start comparison')
     ap.add_argument('--no-dd', action='store_true', help='skip the direction-dependent (CohJones) workload')
     ap.add_argument('--dd-only', action='store_true', help='run only the direction-dependent workload')
-    ap.add_argument('--path', type=int, default=0, help='0 auto (moments), 1 raw-row streaming, 2 resident, 3 moments')
+    ap.add_argument('--path', type=int, default=0,
+                    help='StefCal schedule only: 0 auto (moments), 1 raw-row streaming, 2 resident, 3 moments')
+    ap.add_argument('--schedule', default='lm', choices=['lm', 'stefcal'],
+                    help='lm (default): StefCal x20 then LM with the whole J^H J; stefcal: StefCal alone to 1e-6')
+    ap.add_argument('--no-stefcal-compare', action='store_true', help='skip the StefCal-only comparison solve')
     ap.add_argument('--iters', type=int, default=0,
                     help='run exactly this many iterations per step (tol 0) instead of converging; for profiling')
-    ap.add_argument('--ref-iters', type=int, default=3200, help='iterations the reference arm extrapolates to')
-    ap.add_argument('--ref-sample-iters', type=int, default=40)
     args = ap.parse_args()
     if args.impl == 'reference':
         return run_reference(args)

@@ -266,7 +266,8 @@ int gc_autotune_di(int32_t kind, const void* vis, const void* model, const gc_la
  * Totals of the last gc_calibrate_* call made with opt->profile = 1 or 2: summed device time of
  * its iteration launches (profile 2: of its accumulate launches only) in ms from CUDA events on the
  * call's stream, the number of iterations timed, and rows processed by them (sum over intervals
- * of iterations x rows).  Any pointer may be NULL.
+ * of iterations x rows).  With GC_SCHED_LM these are the diagonal iterations; gc_profile_lm reports
+ * the LM phase.  Any pointer may be NULL.
  */
 int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row_iterations);
 /* More of the same profile: the moment-pass time (ms; 0 on the streaming path), baselines x

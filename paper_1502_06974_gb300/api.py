@@ -302,8 +302,10 @@ def ws_target_jones(g1, g_next, rot):
 
 def calibrate_di_jones2x2_warm(vis, model, layout: Layout, solutions, hist_off, lead, net, gains, tol=1e-6,
                                max_iter=1000, schedule=N.GC_SCHED_STEFCAL, compute_chi2=False, profile=False,
-                               want_start=False):
+                               want_start=False, lm_after=None, lm_lambda0=0.0, lm_K=0.0):
     """gc_calibrate_di_jones2x2_warm: solve from the learned start (net=None: previous solution).
+    schedule / lm_*: as calibrate_di_jones2x2 (with 'lm' the StefCal and LM iterations start from
+    the chosen start).
 
     solutions: complex64 device [n_sol, 2, 2]; hist_off: host int32 [n_int, 4]; lead: host float32 [n_int].
     Returns (gains, iters, chi2 or None, status, used, dchi2, start or None).
@@ -327,8 +329,9 @@ def calibrate_di_jones2x2_warm(vis, model, layout: Layout, solutions, hist_off, 
     w = N.GcWarm(solutions.data_ptr(), int(solutions.shape[0]), hist_off.ctypes.data_as(C.POINTER(C.c_int32)),
                  lead.ctypes.data_as(C.POINTER(C.c_float)), C.pointer(net._c) if net is not None else None,
                  used.data_ptr(), dchi2.data_ptr(), start.data_ptr() if start is not None else None)
-    opt = N.GcOptions(float(tol), int(max_iter), int(schedule), N.GC_DTYPE_C64, 0, 1 if compute_chi2 else 0,
-                      1 if profile else 0, N.GC_PATH_AUTO)
+    opt = N.GcOptions(float(tol), int(max_iter), _schedule_code(schedule), N.GC_DTYPE_C64, 0,
+                      1 if compute_chi2 else 0, 1 if profile else 0, N.GC_PATH_AUTO, 0,
+                      N.GC_LM_DEFAULT_AFTER if lm_after is None else int(lm_after), 0, float(lm_lambda0), float(lm_K))
     lay = layout.c()
     rc = N.lib().gc_calibrate_di_jones2x2_warm(_ptr(vis), _ptr(model), C.byref(lay), C.byref(w), _ptr(gains),
                                                C.byref(opt), _ptr(iters), _ptr(chi2), _ptr(status), _stream_ptr(dev))

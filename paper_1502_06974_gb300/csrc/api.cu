@@ -998,8 +998,10 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   if (opt->profile) {
     int64_t ri = 0, bi = 0;
     for (int i = 0; i < P->n_int; ++i) {
-      ri += (int64_t)itv[i] * L->n_samp[i] * L->n_bl[i];
-      bi += (int64_t)itv[i] * L->n_bl[i];
+      // the profiled launches are the diagonal iterations only (the LM schedule's first lm_after)
+      const int64_t k = lm ? std::min<int64_t>(itv[i], lm_after) : itv[i];
+      ri += k * L->n_samp[i] * L->n_bl[i];
+      bi += k * L->n_bl[i];
     }
     prof.finish(ri, bi, mom_ms, mode == 1 ? GC_PATH_MOMENTS : GC_PATH_STREAM);
   }

@@ -64,12 +64,13 @@ def _identity(n, device):
     return g
 
 
-def solve_plain(vis, model, grid: Grid, tol, max_iter, gauge=True):
-    """All intervals in one batched launch from unit gains; returns (gains, iters, status)."""
+def solve_plain(vis, model, grid: Grid, tol, max_iter, gauge=True, **sched):
+    """All intervals in one batched launch from unit gains; returns (gains, iters, status).
+    sched: schedule / lm_after / lm_lambda0 / lm_K of calibrate_di_jones2x2."""
     n_int = grid.n_t * grid.n_fb
     lay = grid.layout(n_int)
     g = _identity(n_int * grid.n_ant, vis.device)
-    g, it, _, st = api.calibrate_di_jones2x2(vis, model, lay, g, tol=tol, max_iter=max_iter)
+    g, it, _, st = api.calibrate_di_jones2x2(vis, model, lay, g, tol=tol, max_iter=max_iter, **sched)
     if gauge:
         api.gauge_fix_di(g, lay)
     return g, it, st
@@ -230,9 +231,12 @@ def solve_pipelined(vis, model, grid: Grid, lag, net, tol, max_iter, gate_tol=0.
     return r
 
 
-def solve_wavefront(vis, model, grid: Grid, lag, net, tol, max_iter):
+def solve_wavefront(vis, model, grid: Grid, lag, net, tol, max_iter, first=None, **sched):
     """Solve the grid block by block (lag-L wavefront, one library call per wave, each wave waiting
-    for the previous one to finish); net=None starts from the previous solution."""
+    for the previous one to finish); net=None starts from the previous solution.  sched: schedule /
+    lm_after / lm_lambda0 / lm_K of the warm-started waves; first: the same for the first wave (which
+    starts from unit gains; default: sched)."""
+    first = sched if first is None else first
     n_int = grid.n_t * grid.n_fb
     na = grid.n_ant
     dev = vis.device
@@ -256,7 +260,7 @@ def solve_wavefront(vis, model, grid: Grid, lag, net, tol, max_iter):
         v, m = vis[r0:r1], model[r0:r1]
         if t0_blk == 0:
             g.copy_(_identity(nb * na, dev))
-            _, it, _, st = api.calibrate_di_jones2x2(v, m, lay, g, tol=tol, max_iter=max_iter)
+            _, it, _, st = api.calibrate_di_jones2x2(v, m, lay, g, tol=tol, max_iter=max_iter, **first)
             us = None
         else:
             tp = t0_blk - 1
@@ -265,7 +269,7 @@ def solve_wavefront(vis, model, grid: Grid, lag, net, tol, max_iter):
             hoff = (_hist_index(np.full(nb, tp), f_all, grid.n_fb) * na).astype(np.int32)
             lead = ((t_all - tp) / LEAD_SCALE).astype(np.float32)
             _, it, _, st, us, _, _ = api.calibrate_di_jones2x2_warm(v, m, lay, sols, hoff, lead, net, g, tol=tol,
-                                                                     max_iter=max_iter)
+                                                                     max_iter=max_iter, **sched)
         api.gauge_fix_di(g, lay)
         sols[i0 * na:(i0 + nb) * na].copy_(g)
         iters[i0:i0 + nb] = it.cpu().numpy()

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, 'bench.py'), '--impl', 'reference', '--steps', '1',
-                        '--warmup', '0', '--ref-sample-iters', '2'], capture_output=True, text=True, cwd=ROOT,
+                        '--warmup', '0'], capture_output=True, text=True, cwd=ROOT,
                        timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith('{')]

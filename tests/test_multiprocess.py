@@ -30,7 +30,7 @@ def _rank_main(rank, world, port, outdir):
         t = bench.max_over_ranks(10.0 * (rank + 1), dist, 'cpu')   # rank r "took" 10 (r + 1) ms
         dist.barrier()
         os.environ['RANK'], os.environ['WORLD_SIZE'] = str(rank), str(world)
-        args = argparse.Namespace(gpus=world, steps=1, warmup=0, ref_iters=10, ref_sample_iters=1)
+        args = argparse.Namespace(gpus=world, steps=1, warmup=0)
         ref_rc = bench.run_reference(args) if rank != 0 else 0    # non-zero ranks return at once
         with open(os.path.join(outdir, f'r{rank}.json'), 'w') as f:
             json.dump({'seed': seed, 'time': t, 'ref_rc': ref_rc}, f)
