@@ -406,6 +406,12 @@ int gc_gauge_fix_di(int32_t kind, void* gains, const gc_layout* layout, int32_t 
  * iteration, n real unknowns).  Any pointer may be NULL.
  */
 int gc_profile_lm(double* lm_ms, int64_t* launches, double* flop);
+/* SM clock cycles the same LM phase spent, summed over interval iterations, in its parts: [0] the
+ * per-antenna J^H J blocks and J^H R, [1] the damped matrix, [2] the Cholesky factorisation with
+ * the forward substitution, [3] the back substitution, [4] trial gains, chi^2 and the damping
+ * decision; and within [2]: [5] panel loads, [6] panel solves, [7] trailing updates with the
+ * look-ahead factor of the next diagonal block.  Writes min(n, 8) values; returns 8 (or GC_ERR_ARG). */
+int gc_profile_lm_phases(double* cycles, int32_t n);
 
 /* Text for a GC_ERR_* return code or a GC_ST_* status. */
 const char* gc_error_string(int code);

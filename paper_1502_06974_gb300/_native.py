@@ -28,7 +28,7 @@ EXPORTS = [
     'gc_chi2_di_jones2x2', 'gc_mlp_work_floats', 'gc_mlp_forward_f32', 'gc_mlp_grad_f32', 'gc_mlp_train_step',
     'gc_mlp_infer_bf16', 'gc_ws_features_jones', 'gc_ws_target_jones', 'gc_calibrate_di_jones2x2_warm',
     'gc_calibrate_di_jones2x2_wavefront', 'gc_gauge_fix_di',
-    'gc_autotune_di', 'gc_profile_last', 'gc_profile_detail', 'gc_profile_lm', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
+    'gc_autotune_di', 'gc_profile_last', 'gc_profile_detail', 'gc_profile_lm', 'gc_profile_lm_phases', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
 ]
 
 _p = C.c_void_p
@@ -131,6 +131,8 @@ def lib() -> C.CDLL:
         L.gc_profile_detail.restype = C.c_int
         L.gc_profile_lm.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)]
         L.gc_profile_lm.restype = C.c_int
+        L.gc_profile_lm_phases.argtypes = [C.POINTER(C.c_double), C.c_int32]
+        L.gc_profile_lm_phases.restype = C.c_int
         L.gc_release.argtypes = []
         L.gc_release.restype = C.c_int
         _lib = L

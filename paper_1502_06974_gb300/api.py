@@ -146,6 +146,17 @@ def profile_lm():
     return ms.value, n.value, fl.value
 
 
+LM_PHASES = ('blocks_and_gradient', 'matrix', 'factor_forward', 'back_substitution', 'trial_chi2_decision',
+             'factor.panel_load', 'factor.panel_solve', 'factor.trailing_update')
+
+
+def profile_lm_phases():
+    """{phase: SM cycles} of the same LM phase (see gc_profile_lm_phases)."""
+    buf = (C.c_double * len(LM_PHASES))()
+    N.check(N.lib().gc_profile_lm_phases(buf, len(LM_PHASES)), 'gc_profile_lm_phases')
+    return dict(zip(LM_PHASES, list(buf)))
+
+
 def calibrate_dd_cohjones(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
                           compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO):
     """CohJones on DD scalar gains (gc_calibrate_dd_cohjones); model [n_dir, rows], gains [n_gain, n_dir]."""

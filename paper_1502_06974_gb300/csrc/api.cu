@@ -969,7 +969,8 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     }
   }
   if (lm && opt->max_iter > lm_after) {
-    rc = lm_run(kind, L, a.moments, a.mom_off, a.ant1, a.ant2, (float*)st.gains, a.iters, a.status, opt, stream);
+    rc = lm_run(kind, L, (const float*)st.vis, (const float*)st.model, a.row_off, a.n_samp, a.moments, a.mom_off,
+                a.ant1, a.ant2, (float*)st.gains, a.iters, a.status, opt, stream);
     if (rc != GC_OK) return rc;
   }
   if (opt->compute_chi2) {
@@ -1465,6 +1466,11 @@ int gc_profile_last(double* iter_kernel_ms, int64_t* iter_launches, int64_t* row
 int64_t gc_launch_count(void) { return (int64_t)gc::g_launches.load(); }
 
 int gc_profile_lm(double* lm_ms, int64_t* launches, double* flop) { return gc::lm_profile(lm_ms, launches, flop); }
+
+int gc_profile_lm_phases(double* cycles, int32_t n) {
+  if (!cycles || n < 0) return GC_ERR_ARG;
+  return gc::lm_profile_phases(cycles, n);
+}
 
 int gc_release(void) {
   for (auto& kv : gc::g_ws) {

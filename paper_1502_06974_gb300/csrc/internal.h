@@ -154,13 +154,17 @@ int gauge_fix(int kind, int dtype, void* gains, const int32_t* gain_off, const i
               void* stream);
 
 // Levenberg-Marquardt polish with the whole J^H J (lm.cu), run after the diagonal iterations of the
-// moment path: moments / mom_off / ant1 / ant2 are the caller's plan, gains / iters / status its
-// device state.  lm_limit_ok: every interval has at most GC_LM_MAX_UNKNOWNS real unknowns.
+// moment path: vis / model the rows, row_off / n_samp / moments / mom_off / ant1 / ant2 the caller's
+// plan, gains / iters / status its device state.  lm_limit_ok: every interval has at most GC_LM_MAX_UNKNOWNS real unknowns.
 int lm_limit_ok(int kind, const gc_layout* L);
-int lm_run(int kind, const gc_layout* L, const float* moments, const int64_t* mom_off, const int32_t* ant1,
+int lm_run(int kind, const gc_layout* L, const float* vis, const float* model, const int64_t* row_off,
+           const int32_t* n_samp, const float* moments, const int64_t* mom_off, const int32_t* ant1,
            const int32_t* ant2, float* gains, int32_t* iters, int32_t* status, const gc_options* opt, void* stream);
 // time of the last profiled polish's iteration launches (CUDA events), their count, and the
 // algorithmic flops of its factorisations and triangular solves
 int lm_profile(double* ms, int64_t* launches, double* flop);
+// SM cycles the last profiled polish spent per phase (summed over interval iterations); returns the
+// number of phases
+int lm_profile_phases(double* cycles, int n);
 
 }  // namespace gc

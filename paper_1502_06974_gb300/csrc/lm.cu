@@ -23,11 +23,10 @@
 // Sect. 2.1, so J^H J is singular along v) and mu the mean of diag(H): the step is taken in the
 // complement of the gauge direction, and the matrix stays well conditioned however small lambda
 // gets.  The factorisation is an FP32 blocked Cholesky in global memory (panels of 32 columns in
-// shared memory, warp-tiled rank-32 trailing updates); chi^2 at the trial gains is evaluated from
-// the moments in FP64 (the damping decision compares two values that agree to ~1e-10 relative
-// near convergence); lambda is updated in FP64: divided by K after a step that lowered chi^2,
-// multiplied by K (gains kept) after one that did not.  An interval stops when a step is below
-// tol ||G|| (App. C, first criterion).
+// shared memory, warp-tiled rank-32 trailing updates); chi^2 at the trial gains is summed in FP64
+// from the FP32 residuals of the interval's rows; lambda is updated in FP64: divided by K after a
+// step that lowered chi^2, multiplied by K (gains kept) after one that did not.  An interval stops
+// when a step is below tol ||G|| (App. C, first criterion).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -52,6 +51,10 @@ constexpr int kLMThreads = 256;
 constexpr int kNB = 32;  // Cholesky panel width
 
 struct LMArgs {
+  const float* vis;         // the rows (complex64; 2x2 row-major for the 2x2 kind)
+  const float* model;
+  const int64_t* row_off;   // [n_int] first row of the interval
+  const int32_t* n_samp;    // [n_int] samples per baseline
   const float* moments;
   const int64_t* mom_off;   // [n_int] baseline slot of the interval's first moment tile
   float* gains;
@@ -64,7 +67,7 @@ struct LMArgs {
   const int32_t* ant_off;   // per table and antenna: offsets into ant_ent
   const int32_t* ant_ent;   // baseline * 2 + (1 if the antenna is the baseline's second)
   double* lam;              // [n_int] damping
-  double* chi;              // [n_int] chi^2 - sum |D|^2 at the current gains
+  double* chi;              // [n_int] chi^2 at the current gains
   int32_t* iters;
   int32_t* status;
   int32_t* list;            // [3][n_int] active intervals: iteration k reads list k % 3, appends to (k+1) % 3
@@ -78,13 +81,28 @@ struct LMArgs {
   int32_t k;
   int32_t n_int;
   double* flop;             // optional: algorithmic flops of the factorisations and solves, summed
+  unsigned long long* phase;  // optional [kLMPhases]: SM cycles per phase, summed over intervals
 };
+
+// Phases of one LM iteration of an interval (profile only): per-antenna sums, the matrix, the
+// factorisation with the forward substitution, the back substitution, trial gains and chi^2; then,
+// inside the factorisation, the panel loads, the panel solves and the trailing updates.
+constexpr int kLMPhases = 8;
+
+GC_DEV void lm_mark(unsigned long long* phase, int ph, long long& t0) {
+  if (phase && threadIdx.x == 0) {
+    const long long t = clock64();
+    atomicAdd(phase + ph, (unsigned long long)(t - t0));
+    t0 = t;
+  }
+}
 
 // ------------------------------------------------------------------------------------------
 // Per-kind pieces.  Gains: GW floats per antenna, (re, im) pairs in storage order.
 // ------------------------------------------------------------------------------------------
 struct LMJones {
   static constexpr int GW = 8, NM = 48, AW = 4;
+  using RK = JonesKind<float>;
   static GC_DEV void ld_mom(const float* mom, int64_t moff, int b, float* m) {
 #pragma unroll
     for (int c = 0; c < NM; c += 4) {
@@ -100,15 +118,6 @@ struct LMJones {
     a[2] = g[0] * g[2] + g[1] * g[3] + g[4] * g[6] + g[5] * g[7];
     a[3] = g[0] * g[3] - g[1] * g[2] + g[4] * g[7] - g[5] * g[6];
   }
-  static GC_DEV void aux64(const float* g, double* a) {
-    double d[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) d[c] = g[c];
-    a[0] = d[0] * d[0] + d[1] * d[1] + d[4] * d[4] + d[5] * d[5];
-    a[1] = d[2] * d[2] + d[3] * d[3] + d[6] * d[6] + d[7] * d[7];
-    a[2] = d[0] * d[2] + d[1] * d[3] + d[4] * d[6] + d[5] * d[7];
-    a[3] = d[0] * d[3] - d[1] * d[2] + d[4] * d[7] - d[5] * d[6];
-  }
   static GC_DEV float diag_sum(const float* A) { return 4.f * (A[0] + A[1]); }
   static GC_DEV bool no_data(const float* A) { return !(A[0] + A[1] > 0.f); }
 
@@ -117,7 +126,7 @@ struct LMJones {
   //   side 0 (me first):  C = unvec(P vec G_o),   Hb = R a_o
   //   side 1 (me second): C = unvec(P^H vec G_o), Hb = R' a_o, R' = W^-1 R^T W, W = diag(1, 1, 2, 2)
   static GC_DEV void side(const float* m, const float* gme, const float* go, const float* ao, int sd, float* A,
-                          double* gr) {
+                          float* gr, float* gc) {
     const Cx<float> vo[4] = {cx<float>(go[0], go[1]), cx<float>(go[4], go[5]), cx<float>(go[2], go[3]),
                              cx<float>(go[6], go[7])};
     Cx<float> c[4];
@@ -161,10 +170,10 @@ struct LMJones {
     Cx<float> t01 = scale_(gb, h[1]); fma_(t01, ga, h01);
     Cx<float> t10 = scale_(gc_, h[0]); fma_(t10, gd, h10);
     Cx<float> t11 = scale_(gd, h[1]); fma_(t11, gc_, h01);
-    gr[0] += (double)(c[0].x - t00.x); gr[1] += (double)(c[0].y - t00.y);
-    gr[2] += (double)(c[2].x - t01.x); gr[3] += (double)(c[2].y - t01.y);
-    gr[4] += (double)(c[1].x - t10.x); gr[5] += (double)(c[1].y - t10.y);
-    gr[6] += (double)(c[3].x - t11.x); gr[7] += (double)(c[3].y - t11.y);
+    const float d[8] = {c[0].x - t00.x, c[0].y - t00.y, c[2].x - t01.x, c[2].y - t01.y,
+                        c[1].x - t10.x, c[1].y - t10.y, c[3].x - t11.x, c[3].y - t11.y};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) kahan_add(gr[e], gc[e], d[e]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) A[i] += h[i];
   }
@@ -237,56 +246,26 @@ struct LMJones {
 #pragma unroll
       for (int c = 0; c < 8; ++c) blk[r * 8 + c] = ((r >> 2) == (c >> 2)) ? T[(r & 3) * 4 + (c & 3)] : 0.f;
   }
-
-  // chi^2 of the baseline minus sum |D|^2: -2 Re (vec G_p)^H P vec G_q + a_p^T W R a_q (FP64)
-  static GC_DEV double chi_term(const float* m, const float* gp, const float* gq, const double* ap,
-                                const double* aq) {
-    const double vq[8] = {gq[0], gq[1], gq[4], gq[5], gq[2], gq[3], gq[6], gq[7]};
-    const double vp[8] = {gp[0], gp[1], gp[4], gp[5], gp[2], gp[3], gp[6], gp[7]};
-    double t2 = 0.0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      double cr = 0.0, ci = 0.0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const double pr = m[2 * (r * 4 + k)], pi = m[2 * (r * 4 + k) + 1];
-        cr = fma(pr, vq[2 * k], fma(-pi, vq[2 * k + 1], cr));
-        ci = fma(pr, vq[2 * k + 1], fma(pi, vq[2 * k], ci));
-      }
-      t2 = fma(vp[2 * r], cr, fma(vp[2 * r + 1], ci, t2));
-    }
-    const float* R = m + 32;
-    const double w[4] = {1.0, 1.0, 2.0, 2.0};
-    double t3 = 0.0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) s = fma((double)R[i * 4 + j], aq[j], s);
-      t3 = fma(w[i] * ap[i], s, t3);
-    }
-    return t3 - 2.0 * t2;
-  }
 };
 
 struct LMScalar {
   static constexpr int GW = 2, NM = 4, AW = 1;
+  using RK = ScalarKind<float>;
   static GC_DEV void ld_mom(const float* mom, int64_t moff, int b, float* m) {
     const float4 v = *reinterpret_cast<const float4*>(mom + mom_index(moff, b, 0, NM));
     m[0] = v.x; m[1] = v.y; m[2] = v.z; m[3] = v.w;
   }
   static GC_DEV void aux(const float* g, float* a) { a[0] = g[0] * g[0] + g[1] * g[1]; }
-  static GC_DEV void aux64(const float* g, double* a) { a[0] = (double)g[0] * g[0] + (double)g[1] * g[1]; }
   static GC_DEV float diag_sum(const float* A) { return 2.f * A[0]; }
   static GC_DEV bool no_data(const float* A) { return !(A[0] > 0.f); }
   // side 0: c = g_o B, side 1: c = g_o conj(B); Hb = |g_o|^2 Q; J^H r = c - g_me Hb
   static GC_DEV void side(const float* m, const float* gme, const float* go, const float* ao, int sd, float* A,
-                          double* gr) {
+                          float* gr, float* gc) {
     const Cx<float> B = cx<float>(m[0], sd ? -m[1] : m[1]);
     const Cx<float> c = mul_(cx<float>(go[0], go[1]), B);
     const float h = ao[0] * m[2];
-    gr[0] += (double)(c.x - gme[0] * h);
-    gr[1] += (double)(c.y - gme[1] * h);
+    kahan_add(gr[0], gc[0], c.x - gme[0] * h);
+    kahan_add(gr[1], gc[1], c.y - gme[1] * h);
     A[0] += h;
   }
   // d_s -> b conj(d_s), b = g_f g_s Q (eq. JHJ:DI B); the real 2x2 block is symmetric
@@ -297,13 +276,6 @@ struct LMScalar {
   static GC_DEV void diag(const float* A, float lam, float* blk) {
     blk[0] = A[0] * (1.f + lam); blk[1] = 0.f; blk[2] = 0.f; blk[3] = A[0] * (1.f + lam);
   }
-  // -2 Re(B conj(g_p) g_q) + |g_p|^2 |g_q|^2 Q
-  static GC_DEV double chi_term(const float* m, const float* gp, const float* gq, const double* ap,
-                                const double* aq) {
-    const double pr = gp[0], pi = gp[1], qr = gq[0], qi = gq[1];
-    const double xr = pr * qr + pi * qi, xi = pr * qi - pi * qr;  // conj(g_p) g_q
-    return ap[0] * aq[0] * (double)m[2] - 2.0 * ((double)m[0] * xr - (double)m[1] * xi);
-  }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -313,10 +285,8 @@ template <class T>
 struct LMSmem {
   static __host__ __device__ size_t union_bytes(int NP) {
     const size_t panel = (size_t)kNB * NP * 4;
-    const size_t pass1 = (size_t)kLMThreads * (4 * 4 + T::GW * 8);
-    const size_t chi = (size_t)(NP / T::GW) * 4 * 8;
+    const size_t pass1 = (size_t)kLMThreads * (4 * 4 + T::GW * 4);
     size_t u = panel > pass1 ? panel : pass1;
-    u = u > chi ? u : chi;
     u = u > (size_t)8 * 32 * 4 ? u : (size_t)8 * 32 * 4;
     return (u + 15) & ~(size_t)15;
   }
@@ -336,24 +306,46 @@ GC_DEV void lm_pair_decode(int idx, int& P, int& Q) {
 }
 
 // Rank-32 update of the trailing lower triangle: H[k0+32.., k0+32..] -= Lp Lp^T, Lp = panel rows
-// 32..m-1 (in Ps, column-major [32][m]).  Warp-tiled: each warp takes 32x32 blocks, each lane an
-// 8x4 tile (lanes 4 x 8), operands read from shared memory as float4, the block read and written once.
-GC_DEV void lm_syrk(float* H, int npad, int k0, int m, const float* Ps) {
+// 32..m-1 (in Ps, column-major [32][m]).  Warp-tiled: a warp takes one 32x32 block at a time from a
+// shared counter (warps that arrive late -- warp 0 after its look-ahead -- take fewer), each lane an
+// 8x4 tile (lanes 4 x 8), operands read from shared memory as float4; the next block's values are
+// loaded while the current one is computed.  Blocks from 1 on (block 0 is the next diagonal block,
+// which the look-ahead updates).  *next must be 0 before the first warp arrives.
+GC_DEV void lm_syrk(float* H, int npad, int k0, int m, const float* Ps, int* next) {
   const int t = m - kNB;
   if (t <= 0) return;
   const int T = t / 32;
   const int nblk = T * (T + 1) / 2;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int ly = lane >> 3, lx = lane & 7;
-  for (int bidx = warp; bidx < nblk; bidx += kLMThreads / 32) {
-    int bi, bj;
-    lm_pair_decode(bidx, bi, bj);
-    const int r0 = kNB + bi * 32 + ly * 8;
-    const int c0 = kNB + bj * 32 + lx * 4;
-    float4 cv[8];
+  const unsigned full = 0xffffffffu;
+  auto grab = [&]() {
+    int b = 0;
+    if (lane == 0) b = 1 + atomicAdd(next, 1);
+    return __shfl_sync(full, b, 0);
+  };
+  // block order: (1, 0), (2, 0), .. (T-1, 0) -- the next panel, which the next step loads first --
+  // then the rest, (1, 1), (2, 1), (2, 2), ..
+  auto decode = [&](int b, int& bi, int& bj) {
+    if (b < T) { bi = b; bj = 0; return; }
+    int p, q;
+    lm_pair_decode(b - T, p, q);       // (bi - 1, bj - 1) over the lower triangle of T - 1 blocks
+    bi = p + 1; bj = q + 1;
+  };
+  int bidx = grab();
+  if (bidx >= nblk) return;
+  int bi, bj;
+  decode(bidx, bi, bj);
+  float4 cv[8];
+  {
+    const int r0 = kNB + bi * 32 + ly * 8, c0 = kNB + bj * 32 + lx * 4;
 #pragma unroll
     for (int rr = 0; rr < 8; ++rr)
       cv[rr] = *reinterpret_cast<const float4*>(H + (int64_t)(k0 + r0 + rr) * npad + k0 + c0);
+  }
+  while (true) {
+    const int r0 = kNB + bi * 32 + ly * 8;
+    const int c0 = kNB + bj * 32 + lx * 4;
     float acc[8][4];
 #pragma unroll
     for (int rr = 0; rr < 8; ++rr)
@@ -378,20 +370,115 @@ GC_DEV void lm_syrk(float* H, int npad, int k0, int m, const float* Ps) {
       v.x -= acc[rr][0]; v.y -= acc[rr][1]; v.z -= acc[rr][2]; v.w -= acc[rr][3];
       *reinterpret_cast<float4*>(H + (int64_t)(k0 + r0 + rr) * npad + k0 + c0) = v;
     }
+    bidx = grab();
+    if (bidx >= nblk) break;
+    decode(bidx, bi, bj);
+    const int nr0 = kNB + bi * 32 + ly * 8, nc0 = kNB + bj * 32 + lx * 4;
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr)
+      cv[rr] = *reinterpret_cast<const float4*>(H + (int64_t)(k0 + nr0 + rr) * npad + k0 + nc0);
   }
 }
 
+// Factor of one 32 x 32 diagonal block, by one warp (lane r holds row r of the block in x): L_kk^-1
+// in Linv ([t][c] = L_kk^-1[c][t]) and in H in place of the block (rows / columns k0.., row-major,
+// zeros above the diagonal: only the inverse is needed afterwards), y_k = L_kk^-1 rhs_k in
+// rhs[k0..] and yk.  *fail is set when a pivot is not positive.
+GC_DEV void lm_diag_block(float (&x)[kNB], float* H, int npad, int k0, float* rhs, float* Linv, float* yk,
+                          float* stage, int* fail) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  int bad = 0;
+  float dl = 0.f;   // 1 / L[lane][lane] (kept apart: indexing x by the lane would move x to local memory)
+#pragma unroll
+  for (int j = 0; j < kNB; ++j) {
+    const float piv = __shfl_sync(full, x[j], j);
+    bad |= !(piv > 0.f);
+    const float d = sqrtf(fmaxf(piv, 1e-30f)), inv = 1.f / d;
+    if (lane == j) { x[j] = d; dl = inv; }
+    if (lane > j) x[j] *= inv;
+    const float lj = x[j];
+#pragma unroll
+    for (int c = 1; c < kNB; ++c) {
+      if (c > j) {   // a fixed trip count keeps every index a compile-time constant after unrolling
+        const float lc = __shfl_sync(full, x[j], c);
+        if (lane >= c) x[c] = fmaf(-lj, lc, x[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) stage[c * kNB + lane] = c <= lane ? x[c] : 0.f;
+  __syncwarp();
+  // row `lane` of L_kk^-1: row t is final once divided by L[t][t]; it then updates the rows below
+  float w[kNB];
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) w[c] = c == lane ? 1.f : 0.f;
+#pragma unroll
+  for (int t = 0; t < kNB; ++t) {
+    if (lane == t) {
+#pragma unroll
+      for (int c = 0; c <= t; ++c) w[c] *= dl;
+    }
+    const float lrt = stage[t * kNB + lane];
+#pragma unroll
+    for (int c = 0; c <= t; ++c) {
+      const float v = __shfl_sync(full, w[c], t);
+      if (lane > t) w[c] = fmaf(-lrt, v, w[c]);
+    }
+  }
+  const float tr = rhs[k0 + lane];
+  float y = 0.f;
+  float* row = H + (int64_t)(k0 + lane) * npad + k0;   // row `lane` of L_kk^-1 replaces L_kk in H
+#pragma unroll
+  for (int c = 0; c < kNB; c += 4)
+    *reinterpret_cast<float4*>(row + c) = make_float4(c <= lane ? w[c] : 0.f, c + 1 <= lane ? w[c + 1] : 0.f,
+                                                      c + 2 <= lane ? w[c + 2] : 0.f, c + 3 <= lane ? w[c + 3] : 0.f);
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) {
+    Linv[c * kNB + lane] = c <= lane ? w[c] : 0.f;
+    y = fmaf(w[c], __shfl_sync(full, tr, c), y);
+  }
+  rhs[k0 + lane] = y;
+  yk[lane] = y;
+  if (lane == 0 && bad) *fail = 1;
+}
+
 // In-place blocked Cholesky H = L L^T (lower triangle of the row-major npad x npad matrix) with the
-// forward substitution L y = rhs carried along; then L^T x = y.  rhs holds x on return.  Returns 1
-// when a pivot is not positive (nothing more is computed then).
-GC_DEV int lm_cholesky_solve(float* H, int npad, float* rhs, float* Ps, float* dinv, int* fail) {
+// forward substitution L y = rhs carried along (rhs holds y on return).  Per panel of 32 columns,
+// its diagonal block already factored (L_kk^-1 in Linv, y_k in yk):
+//   (a) the panel rows below the diagonal block into shared memory (Ps, column-major [32][m]);
+//   (c) those rows solve x L_kk^T = a as the product x = a L_kk^-T (a warp-tiled 32-column GEMM,
+//       no dependent chain per row) and update rhs_r -= x . y_k;
+//   (d) the panel goes back to H;
+//   (e) look-ahead: warp 0 applies the rank-32 update to the next diagonal block and factors it
+//       (lm_diag_block) while the other warps apply it to the rest of the trailing matrix; warp 0
+//       then takes its share of what remains.
+// Returns 1 when a pivot is not positive (nothing more is computed then).  Linv, stage: 32 x 32
+// floats of shared memory; yk: 32 floats.
+GC_DEV int lm_cholesky_solve(float* H, int npad, float* rhs, float* Ps, float* Linv, float* yk, float* stage,
+                             int* fail, int* next, unsigned long long* phase) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned full = 0xffffffffu;
+  long long tc = phase ? clock64() : 0;
+  if (warp == 0) {
+    float x[kNB];
+    const float* row = H + (int64_t)lane * npad;
+#pragma unroll
+    for (int c = 0; c < kNB; c += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(row + c);
+      x[c] = v.x; x[c + 1] = v.y; x[c + 2] = v.z; x[c + 3] = v.w;
+    }
+    lm_diag_block(x, H, npad, 0, rhs, Linv, yk, stage, fail);
+  }
+  __syncthreads();
+  if (*fail) return 1;
   for (int k0 = 0; k0 < npad; k0 += kNB) {
     const int m = npad - k0;
-    // (a) panel rows k0.., columns k0..k0+31 into Ps[c * m + r]; a warp takes 32 consecutive rows
-    for (int idx = tid; idx < m * 8; idx += kLMThreads) {
-      const int cg = idx / m, r = idx - cg * m;
+    if (m == kNB) break;
+    // (a) rows 32..m-1; a warp takes 32 consecutive rows of one 4-column group
+    const int mr = m - kNB;
+    for (int idx = tid; idx < mr * 8; idx += kLMThreads) {
+      const int cg = idx / mr, r = kNB + idx - cg * mr;
       const float4 v = *reinterpret_cast<const float4*>(H + (int64_t)(k0 + r) * npad + k0 + 4 * cg);
       Ps[(4 * cg + 0) * m + r] = v.x;
       Ps[(4 * cg + 1) * m + r] = v.y;
@@ -399,70 +486,61 @@ GC_DEV int lm_cholesky_solve(float* H, int npad, float* rhs, float* Ps, float* d
       Ps[(4 * cg + 3) * m + r] = v.w;
     }
     __syncthreads();
-    // (b) the 32 x 32 diagonal block by warp 0, lane r holding row r; forward substitution of its
-    // part of the right-hand side along the way
-    if (warp == 0) {
-      float x[kNB];
+    lm_mark(phase, 5, tc);
+    // (c) warp w takes 32-row blocks of the rows below; lane (ly, lx) an 8 x 4 tile
+    {
+      const int ly = lane >> 3, lx = lane & 7;
+      const int nbr = mr / 32;
+      for (int bi = warp; bi < nbr; bi += kLMThreads / 32) {
+        const int r0 = kNB + bi * 32 + ly * 8, c0 = lx * 4;
+        float acc[8][4];
 #pragma unroll
-      for (int c = 0; c < kNB; ++c) x[c] = Ps[c * m + lane];
-      float t = rhs[k0 + lane];
-      int bad = 0;
+        for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
-      for (int j = 0; j < kNB; ++j) {
-        const float piv = __shfl_sync(full, x[j], j);
-        bad |= !(piv > 0.f);
-        const float d = sqrtf(fmaxf(piv, 1e-30f)), inv = 1.f / d;
-        if (lane == j) x[j] = d;
-        if (lane > j) x[j] *= inv;
-        const float yj = __shfl_sync(full, t, j) * inv;
-        if (lane == j) t = yj;
-        const float lj = x[j];
-        if (lane > j) t = fmaf(-lj, yj, t);
+          for (int cc = 0; cc < 4; ++cc) acc[rr][cc] = 0.f;
+#pragma unroll 4
+        for (int t = 0; t < kNB; ++t) {
+          const float4 a0 = *reinterpret_cast<const float4*>(Ps + t * m + r0);
+          const float4 a1 = *reinterpret_cast<const float4*>(Ps + t * m + r0 + 4);
+          const float4 b = *reinterpret_cast<const float4*>(Linv + t * kNB + c0);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int c = j + 1; c < kNB; ++c) {
-          const float lc = __shfl_sync(full, x[j], c);
-          if (lane >= c) x[c] = fmaf(-lj, lc, x[c]);
+          for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) acc[rr][cc] = fmaf(av[rr], bv[cc], acc[rr][cc]);
+        }
+        __syncwarp();   // every lane of the warp has read its 32 rows before any is overwritten
+        float part[8];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+          part[rr] = 0.f;
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) part[rr] = fmaf(acc[rr][cc], yk[c0 + cc], part[rr]);
+        }
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          *reinterpret_cast<float4*>(Ps + (c0 + cc) * m + r0) =
+              make_float4(acc[0][cc], acc[1][cc], acc[2][cc], acc[3][cc]);
+          *reinterpret_cast<float4*>(Ps + (c0 + cc) * m + r0 + 4) =
+              make_float4(acc[4][cc], acc[5][cc], acc[6][cc], acc[7][cc]);
+        }
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+#pragma unroll
+          for (int o = 1; o < 8; o <<= 1) part[rr] += __shfl_xor_sync(full, part[rr], o);
+        }
+        if (lx == 0) {
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr) rhs[k0 + r0 + rr] -= part[rr];
         }
       }
-#pragma unroll
-      for (int c = 0; c < kNB; ++c) Ps[c * m + lane] = c <= lane ? x[c] : 0.f;
-      dinv[lane] = 1.f / x[lane];
-      rhs[k0 + lane] = t;
-      if (lane == 0 && bad) *fail = 1;
     }
     __syncthreads();
-    if (*fail) return 1;
-    // (c) rows below the diagonal block: x L_kk^T = a (right-looking over the 32 columns, the
-    // column of L_kk read as float4), and the right-hand side update rhs_r -= x . y
-    for (int r = kNB + tid; r < m; r += kLMThreads) {
-      float x[kNB];
-#pragma unroll
-      for (int c = 0; c < kNB; ++c) x[c] = Ps[c * m + r];
-#pragma unroll
-      for (int t = 0; t < kNB; ++t) {
-        x[t] *= dinv[t];
-        const float* col = Ps + t * m;   // L[c][t] = col[c], c > t
-#pragma unroll
-        for (int c4 = (t + 1) & ~3; c4 < kNB; c4 += 4) {
-          const float4 l = *reinterpret_cast<const float4*>(col + c4);
-          const float lv[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (c4 + e > t) x[c4 + e] = fmaf(-x[t], lv[e], x[c4 + e]);
-        }
-      }
-      float acc = rhs[k0 + r];
-#pragma unroll
-      for (int c = 0; c < kNB; ++c) {
-        Ps[c * m + r] = x[c];
-        acc = fmaf(-x[c], rhs[k0 + c], acc);
-      }
-      rhs[k0 + r] = acc;
-    }
-    __syncthreads();
-    // (d) the factored panel back to H (the back substitution reads it), (e) trailing update
-    for (int idx = tid; idx < m * 8; idx += kLMThreads) {
-      const int cg = idx / m, r = idx - cg * m;
+    lm_mark(phase, 6, tc);
+    // (d) the solved rows back to H (the back substitution reads them)
+    for (int idx = tid; idx < mr * 8; idx += kLMThreads) {
+      const int cg = idx / mr, r = kNB + idx - cg * mr;
       float4 v;
       v.x = Ps[(4 * cg + 0) * m + r];
       v.y = Ps[(4 * cg + 1) * m + r];
@@ -470,52 +548,102 @@ GC_DEV int lm_cholesky_solve(float* H, int npad, float* rhs, float* Ps, float* d
       v.w = Ps[(4 * cg + 3) * m + r];
       *reinterpret_cast<float4*>(H + (int64_t)(k0 + r) * npad + k0 + 4 * cg) = v;
     }
-    lm_syrk(H, npad, k0, m, Ps);
-    __syncthreads();
-  }
-  // L^T x = y, last block first: s_c = sum_{r >= k0+32} L[r][k0+c] x_r over 8 warps, then the
-  // 32 x 32 upper-triangular solve by warp 0 (lane c holds column c of L_kk)
-  float* red = Ps;
-  for (int k0 = npad - kNB; k0 >= 0; k0 -= kNB) {
-    float s = 0.f;
-    for (int r = k0 + kNB + warp; r < npad; r += kLMThreads / 32) s = fmaf(H[(int64_t)r * npad + k0 + lane], rhs[r], s);
-    red[warp * 32 + lane] = s;
-    __syncthreads();
+    // (e) next diagonal block: rows / columns k0+32..k0+63 minus the panel's rank-32 update, then
+    // its factor (warp 0); the rest of the trailing matrix by warps 1..
     if (warp == 0) {
-      float b = rhs[k0 + lane];
+      const int kn = k0 + kNB;
+      float x[kNB];
+      const float* row = H + (int64_t)(kn + lane) * npad + kn;
 #pragma unroll
-      for (int w = 0; w < kLMThreads / 32; ++w) b -= red[w * 32 + lane];
-      float col[kNB];
-#pragma unroll
-      for (int i = 0; i < kNB; ++i) col[i] = H[(int64_t)(k0 + i) * npad + k0 + lane];
-#pragma unroll
-      for (int j = kNB - 1; j >= 0; --j) {
-        const float xj = __shfl_sync(full, b / col[j], j);
-        if (lane == j) b = xj;
-        if (lane < j) b = fmaf(-col[j], xj, b);
+      for (int c = 0; c < kNB; c += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + c);
+        x[c] = v.x; x[c + 1] = v.y; x[c + 2] = v.z; x[c + 3] = v.w;
       }
-      rhs[k0 + lane] = b;
+#pragma unroll 4
+      for (int t = 0; t < kNB; ++t) {
+        const float* col = Ps + t * m + kNB;
+        const float a = col[lane];
+#pragma unroll
+        for (int c = 0; c < kNB; c += 4) {
+          const float4 b = *reinterpret_cast<const float4*>(col + c);
+          x[c] = fmaf(-a, b.x, x[c]); x[c + 1] = fmaf(-a, b.y, x[c + 1]);
+          x[c + 2] = fmaf(-a, b.z, x[c + 2]); x[c + 3] = fmaf(-a, b.w, x[c + 3]);
+        }
+      }
+      lm_diag_block(x, H, npad, kn, rhs, Linv, yk, stage, fail);
     }
+    lm_syrk(H, npad, k0, m, Ps, next);
     __syncthreads();
+    if (tid == 0) *next = 0;
+    lm_mark(phase, 7, tc);
+    if (*fail) return 1;
   }
   return 0;
 }
 
-// chi^2 - sum |D|^2 of interval i at the gains in gs (shared memory), FP64; every thread returns it.
-template <class T>
-GC_DEV double lm_chi(const LMArgs& a, int64_t moff, int bo, int N, int nb, const float* gs, double* a64,
-                     double* red) {
-  const int tid = threadIdx.x;
-  for (int p = tid; p < N; p += kLMThreads) T::aux64(gs + T::GW * p, a64 + 4 * p);
-  __syncthreads();
-  double acc = 0.0;
-  float m[T::NM];
-  for (int b = tid; b < nb; b += kLMThreads) {
-    const int p = a.ant1[bo + b], q = a.ant2[bo + b];
-    T::ld_mom(a.moments, moff, b, m);
-    acc += T::chi_term(m, gs + T::GW * p, gs + T::GW * q, a64 + 4 * p, a64 + 4 * q);
+GC_DEV void lm_cp16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// L^T x = y for the factor left in H by lm_cholesky_solve (each diagonal block holding L_kk^-1);
+// rhs holds x on return.  Last block first: the slab of 32 rows below which x_k's contributions
+// are removed, H[k0..k0+31][0..k0), is copied to shared memory (cp.async, into `slab`) while warp 0
+// forms x_k = L_kk^-T b_k (lane r sums column r of L_kk^-1 against b); then every thread removes
+// x_k from its right-hand sides above, rhs_c -= sum_i L[k0+i][c] x_i.  `slab` holds 32 x (npad - 32)
+// floats.
+GC_DEV void lm_back_substitute(const float* H, int npad, float* rhs, float* slab) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned full = 0xffffffffu;
+  for (int k0 = npad - kNB; k0 >= 0; k0 -= kNB) {
+    const int q4 = k0 / 4;   // float4 groups per slab row
+    for (int idx = tid; idx < kNB * q4; idx += kLMThreads) {
+      const int i = idx / q4, c4 = idx - i * q4;
+      lm_cp16(slab + i * k0 + 4 * c4, H + (int64_t)(k0 + i) * npad + 4 * c4);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (warp == 0) {
+      float li[kNB];
+#pragma unroll
+      for (int c = 0; c < kNB; ++c) li[c] = H[(int64_t)(k0 + c) * npad + k0 + lane];   // L_kk^-1[c][lane]
+      const float b = rhs[k0 + lane];
+      float x = 0.f;
+#pragma unroll
+      for (int c = 0; c < kNB; ++c) x = fmaf(li[c], __shfl_sync(full, b, c), x);
+      rhs[k0 + lane] = x;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    for (int c = tid; c < k0; c += kLMThreads) {
+      float acc = 0.f;
+#pragma unroll 8
+      for (int i = 0; i < kNB; ++i) acc = fmaf(slab[i * k0 + c], rhs[k0 + i], acc);
+      rhs[c] -= acc;
+    }
+    __syncthreads();
   }
-  return block_sum(acc, red);
+}
+
+// chi^2 of interval i at the gains in gs (shared memory): sum over its rows of the squared residual
+// ||D - G_p M G_q^H||^2 (eq. cal:DI:pol / eq. cal:DI:tf), residuals in FP32, each thread's sum
+// compensated, the block total in FP64; every thread returns it.  Computing the residuals from the
+// rows keeps chi^2 free of the cancellation against sum |D|^2 that a moment-space form suffers:
+// near convergence chi^2 is ~1e-6 of sum |D|^2, and the damping decision compares two such values.
+template <class T>
+GC_DEV double lm_chi(const LMArgs& a, int i, int bo, int nb, const float* gs, double* red) {
+  using RK = typename T::RK;
+  const int tid = threadIdx.x;
+  const int64_t r0 = a.row_off[i];
+  const int ns = a.n_samp[i];
+  float sum = 0.f, comp = 0.f;
+  for (int b = tid; b < nb; b += kLMThreads) {
+    const typename RK::G gp = RK::ld_gain(gs + T::GW * a.ant1[bo + b]);
+    const typename RK::G gq = RK::ld_gain(gs + T::GW * a.ant2[bo + b]);
+#pragma unroll 4
+    for (int smp = 0; smp < ns; ++smp)
+      kahan_add(sum, comp, RK::resid2(a.vis, a.model, r0 + (int64_t)smp * nb + b, gp, gq));
+  }
+  return block_sum((double)sum - (double)comp, red);
 }
 
 // Start of the polish: chi^2 at the current gains, lambda = lambda0, every interval that has data
@@ -531,10 +659,9 @@ __global__ void __launch_bounds__(kLMThreads) lm_init_kernel(const LMArgs a) {
   const int st = a.status[i] & 15;
   if (st == GC_ST_NODATA || st == GC_ST_NONFINITE || nb == 0) return;
   float* gs = reinterpret_cast<float*>(smem);
-  double* a64 = reinterpret_cast<double*>(smem + (((size_t)T::GW * N * 4 + 15) & ~(size_t)15));
   for (int e = tid; e < T::GW * N; e += kLMThreads) gs[e] = a.gains[(int64_t)inf.z * T::GW + e];
   __syncthreads();
-  const double chi = lm_chi<T>(a, a.mom_off[i], tb.z, N, nb, gs, a64, red);
+  const double chi = lm_chi<T>(a, i, tb.z, nb, gs, red);
   if (tid == 0) {
     a.chi[i] = chi;
     a.lam[i] = a.lam0;
@@ -551,8 +678,10 @@ template <class T>
 __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, int NP) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
-  __shared__ float dinv[kNB];
-  __shared__ int s_i, s_fail, s_acc;
+  __shared__ __align__(16) float Linv[kNB * kNB];
+  __shared__ __align__(16) float stage[kNB * kNB];
+  __shared__ __align__(16) float yk[kNB];
+  __shared__ int s_i, s_fail, s_acc, s_next;
   const int tid = threadIdx.x;
   const int lin = a.k % 3, lout = (a.k + 1) % 3, lclr = (a.k + 2) % 3;
   if (blockIdx.x == 0 && tid == 0) { a.cnt[lclr] = 0; a.cnt[3 + lclr] = 0; }
@@ -568,10 +697,19 @@ __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, 
       const int idx = atomicAdd(&a.cnt[3 + lin], 1);
       s_i = idx < a.cnt[lin] ? a.list[lin * a.n_int + idx] : -1;
       s_fail = 0;
+      s_next = 0;
     }
     __syncthreads();
     const int i = s_i;
     if (i < 0) break;
+    long long tclk = a.phase ? clock64() : 0;
+    auto mark = [&](int ph) {
+      if (a.phase && threadIdx.x == 0) {
+        const long long t = clock64();
+        atomicAdd(a.phase + ph, (unsigned long long)(t - tclk));
+        tclk = t;
+      }
+    };
     const int4 inf = a.iinfo[i];
     const int4 tb = a.tinfo[inf.x];
     const int N = inf.y, nb = inf.w, bo = tb.z, nat = tb.w;
@@ -585,13 +723,13 @@ __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, 
     {
       const int S = N >= kLMThreads ? 1 : kLMThreads / N;
       float* pA = reinterpret_cast<float*>(U);
-      double* pg = reinterpret_cast<double*>(U + (size_t)kLMThreads * 16);
+      float* pg = pA + (size_t)kLMThreads * 4;
       for (int t = tid; t < N * S; t += kLMThreads) {
         const int p = t / S, part = t - p * S;
         float A[4] = {0.f, 0.f, 0.f, 0.f};
-        double g[T::GW];
+        float g[T::GW], gc[T::GW];   // compensated sums of J^H R
 #pragma unroll
-        for (int c = 0; c < T::GW; ++c) g[c] = 0.0;
+        for (int c = 0; c < T::GW; ++c) { g[c] = 0.f; gc[c] = 0.f; }
         if (p < nat) {
           const int e0 = a.ant_off[tb.y + p], e1 = a.ant_off[tb.y + p + 1];
           float m[T::NM];
@@ -599,28 +737,30 @@ __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, 
             const int ent = a.ant_ent[e], b = ent >> 1, sd = ent & 1;
             const int o = sd ? a.ant1[bo + b] : a.ant2[bo + b];
             T::ld_mom(a.moments, moff, b, m);
-            T::side(m, gs + T::GW * p, gs + T::GW * o, auxs + 4 * o, sd, A, g);
+            T::side(m, gs + T::GW * p, gs + T::GW * o, auxs + 4 * o, sd, A, g, gc);
           }
         }
         // N * S <= kLMThreads: slot t is this thread's own
 #pragma unroll
         for (int c = 0; c < 4; ++c) pA[4 * t + c] = A[c];
 #pragma unroll
-        for (int c = 0; c < T::GW; ++c) pg[T::GW * t + c] = g[c];
+        for (int c = 0; c < T::GW; ++c) pg[T::GW * t + c] = g[c] - gc[c];
       }
       __syncthreads();
       double dsum = 0.0, gn2 = 0.0;
       for (int p = tid; p < N; p += kLMThreads) {
         float A[4] = {0.f, 0.f, 0.f, 0.f};
-        double g[T::GW];
+        float g[T::GW], gc[T::GW];
 #pragma unroll
-        for (int c = 0; c < T::GW; ++c) g[c] = 0.0;
+        for (int c = 0; c < T::GW; ++c) { g[c] = 0.f; gc[c] = 0.f; }
         for (int part = 0; part < S; ++part) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) A[c] += pA[4 * (p * S + part) + c];
 #pragma unroll
-          for (int c = 0; c < T::GW; ++c) g[c] += pg[T::GW * (p * S + part) + c];
+          for (int c = 0; c < T::GW; ++c) kahan_add(g[c], gc[c], pg[T::GW * (p * S + part) + c]);
         }
+#pragma unroll
+        for (int c = 0; c < T::GW; ++c) g[c] -= gc[c];
         const bool nd = T::no_data(A);
 #pragma unroll
         for (int c = 0; c < 4; ++c) As[4 * p + c] = A[c];
@@ -648,6 +788,7 @@ __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, 
         finite = finite && isfinite(rhs[2 * e]) && isfinite(rhs[2 * e + 1]);
       }
       if (!finite) s_fail = 2;
+      mark(0);
       // ---- pass 2: the damped, gauge-fixed matrix, block (P, Q), P >= Q, one thread each
       const float lam = (float)a.lam[i];
       const float vs = (float)vnorm;
@@ -709,9 +850,14 @@ __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, 
       }
       __syncthreads();
     }
+    mark(1);
     // ---- factor and solve (skipped if the right-hand side is not finite)
-    if (s_fail == 0) lm_cholesky_solve(H, npad, rhs, reinterpret_cast<float*>(U), dinv, &s_fail);
+    if (s_fail == 0)
+      lm_cholesky_solve(H, npad, rhs, reinterpret_cast<float*>(U), Linv, yk, stage, &s_fail, &s_next, a.phase);
     __syncthreads();
+    mark(2);
+    if (s_fail == 0) lm_back_substitute(H, npad, rhs, reinterpret_cast<float*>(U));
+    mark(3);
     // ---- trial gains, their chi^2 (FP64), the damping decision (App. C)
     double dx2 = 0.0, gn2 = 0.0;
     const bool solved = s_fail == 0;
@@ -727,7 +873,7 @@ __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, 
     gn2 = block_sum(gn2, red);
     double chi = 0.0;
     const bool finite = solved && isfinite(dx2) && isfinite(gn2);
-    if (finite) chi = lm_chi<T>(a, moff, bo, N, nb, gs, reinterpret_cast<double*>(U), red);
+    if (finite) chi = lm_chi<T>(a, i, bo, nb, gs, red);
     if (tid == 0) {
       const double chi0 = a.chi[i];
       double lam = a.lam[i];
@@ -756,6 +902,7 @@ __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, 
     if (s_acc)
       for (int e = tid; e < n; e += kLMThreads) a.gains[(int64_t)inf.z * T::GW + e] = gs[e];
     __syncthreads();
+    mark(4);
   }
 }
 
@@ -867,12 +1014,13 @@ int lm_limit_ok(int kind, const gc_layout* L) {
 struct LMProfile {
   double ms = 0.0, flop = 0.0;
   int64_t launches = 0;
+  double phase[kLMPhases] = {};
 };
 static LMProfile g_lm_prof;
 
 template <class T>
 static int lm_launch_all(LMArgs& a, int n_int, int np_max, int max_lm, bool prof, cudaStream_t s) {
-  const size_t ish = (((size_t)T::GW * (np_max / T::GW) * 4 + 15) & ~(size_t)15) + (size_t)(np_max / T::GW) * 4 * 8;
+  const size_t ish = (size_t)np_max * 4;
   lm_init_kernel<T><<<n_int, kLMThreads, ish, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_cuda_error(e, "lm_init_kernel");
@@ -937,7 +1085,8 @@ static int lm_launch_all(LMArgs& a, int n_int, int np_max, int max_lm, bool prof
 // The polish after the diagonal iterations: gains, iters and status are device arrays of the
 // calling solver (iters already counts the diagonal iterations); ant1 / ant2 / mom_off are the
 // device copies of the baseline tables and moment offsets of the calling solver's plan.
-int lm_run(int kind, const gc_layout* L, const float* moments, const int64_t* mom_off, const int32_t* ant1,
+int lm_run(int kind, const gc_layout* L, const float* vis, const float* model, const int64_t* row_off,
+           const int32_t* n_samp, const float* moments, const int64_t* mom_off, const int32_t* ant1,
            const int32_t* ant2, float* gains, int32_t* iters, int32_t* status, const gc_options* opt, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int n = L->n_intervals;
@@ -953,9 +1102,14 @@ int lm_run(int kind, const gc_layout* L, const float* moments, const int64_t* mo
     P.key = key;
   }
   void* st = nullptr;
-  int rc = ws_get("lm_state", (size_t)n * 2 * sizeof(double) + (size_t)(3 * n + 8) * sizeof(int32_t) + 16, &st);
+  int rc = ws_get("lm_state", 2 * sizeof(double) + kLMPhases * sizeof(unsigned long long) + (size_t)n * 2 * sizeof(double) +
+                                  (size_t)(3 * n + 8) * sizeof(int32_t), &st);
   if (rc) return rc;
   LMArgs a{};
+  a.vis = vis;
+  a.model = model;
+  a.row_off = row_off;
+  a.n_samp = n_samp;
   a.moments = moments;
   a.mom_off = mom_off;
   a.gains = gains;
@@ -967,8 +1121,10 @@ int lm_run(int kind, const gc_layout* L, const float* moments, const int64_t* mo
   a.pair_ent = P.pair_ent;
   a.ant_off = P.ant_off;
   a.ant_ent = P.ant_ent;
-  double* flop_slot = static_cast<double*>(st);  // first 16 bytes: the profile's flop counter
-  a.lam = flop_slot + 2;
+  // state: [flop counter, 2 doubles][phase counters][lambda n][chi n][lists 3n ints][counters 8 ints]
+  double* flop_slot = static_cast<double*>(st);
+  unsigned long long* phase_slot = reinterpret_cast<unsigned long long*>(flop_slot + 2);
+  a.lam = reinterpret_cast<double*>(phase_slot + kLMPhases);
   a.chi = a.lam + n;
   a.list = reinterpret_cast<int32_t*>(a.chi + n);
   a.cnt = a.list + 3 * n;
@@ -985,15 +1141,25 @@ int lm_run(int kind, const gc_layout* L, const float* moments, const int64_t* mo
   g_lm_prof = LMProfile{};
   if (prof) {
     a.flop = flop_slot;
+    a.phase = phase_slot;
     e = cudaMemsetAsync(a.flop, 0, sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.phase, 0, kLMPhases * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return set_cuda_error(e, "LM profile counter");
   }
   rc = kind == 0 ? lm_launch_all<LMScalar>(a, n, P.np_max, opt->max_iter, prof, s)
                  : lm_launch_all<LMJones>(a, n, P.np_max, opt->max_iter, prof, s);
   if (rc != GC_OK || !prof) return rc;
+  unsigned long long ph[kLMPhases];
   e = cudaMemcpy(&g_lm_prof.flop, a.flop, sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(ph, a.phase, sizeof(ph), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return set_cuda_error(e, "LM profile counter");
+  for (int j = 0; j < kLMPhases; ++j) g_lm_prof.phase[j] = (double)ph[j];
   return GC_OK;
+}
+
+int lm_profile_phases(double* cycles, int n) {
+  for (int j = 0; j < n && j < kLMPhases; ++j) cycles[j] = g_lm_prof.phase[j];
+  return kLMPhases;
 }
 
 int lm_profile(double* ms, int64_t* launches, double* flop) {
