@@ -157,6 +157,23 @@ def oracle_errors(b, gains, intervals=SAMPLE_INTERVALS, refs=None):
     return out, refs
 
 
+def cpu_openmp_block(seed, n_t=4):
+    """The FP64 C++/OpenMP implementation of the same method (oracle/cpu_lm.cpp) on all host cores:
+    the workload's first n_t x 16 intervals (drawn identically), one interval per thread."""
+    from oracle import cpu
+    from paper_1502_06974_gb300 import synth
+    b = synth.make_di_jones(seed=seed, n_t=n_t)
+    cpu.calibrate_jones_lm(b, intervals=[0], tol=TOL, K=LM_K, lm_after=LM_AFTER)     # load / warm the library
+    t0 = time.perf_counter()
+    _, iters, status, used = cpu.calibrate_jones_lm(b, tol=TOL, K=LM_K, lm_after=LM_AFTER)
+    wall = time.perf_counter() - t0
+    return {"value": b.n_rows / wall, "unit": UNIT, "cores": int(used), "kind": "cpp_openmp_fp64",
+            "converged": int(np.sum(status == 0)),
+            "sample": (f"FP64 C++/OpenMP, the same method (StefCal x{LM_AFTER}, then LM on the whole J^H J, "
+                       f"K={LM_K:g}, relative step {TOL:g}), the workload's first {b.n_int} intervals "
+                       f"({b.n_rows} rows) on {used} threads: {wall:.2f} s")}
+
+
 def cpu_baseline_block(b, interval=0):
     g, wall, threads = oracle_solve(b, interval)
     rows = int(b.n_samp[interval]) * int(b.n_bl[interval])
@@ -552,7 +569,7 @@ def run_gpu(args):
             # the summed CUDA-event time of its launches in the timed steps
             peak_tf = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
             n_unk = 8 * int(b.n_ant[0])
-            flop_per_ii = 2.0 * (n_unk ** 3 / 3.0 + 2.0 * n_unk ** 2)
+            flop_per_ii = n_unk ** 3 / 3.0 + 2.0 * n_unk ** 2
             ii_per_launch = lmf / flop_per_ii / max(lml, 1)
             summ = ncu_summary('lm_iter_jones_cfg2.json', LM_SOURCES)
             roof = {"bound": "alu", "achieved": lmf / (lms / 1e3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
@@ -592,6 +609,7 @@ def run_gpu(args):
                "clocks": clocks}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_block(b, 0)
+            out["cpu_baseline_openmp"] = cpu_openmp_block(rank_seed(0))
         if not args.no_warm and world == 1:
             del vis, model
             torch.cuda.empty_cache()

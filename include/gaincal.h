@@ -402,8 +402,8 @@ int gc_gauge_fix_di(int32_t kind, void* gains, const gc_layout* layout, int32_t 
  * Totals of the Levenberg-Marquardt phase (GC_SCHED_LM) of the last DI calibration made with
  * opt->profile != 0: summed device time of its iteration launches (ms, CUDA events on the call's
  * stream), their number, and the algorithmic floating-point operations of the FP32 Cholesky
- * factorisations and triangular solves they performed (2 (n^3/3 + 2 n^2) per interval and
- * iteration, n real unknowns).  Any pointer may be NULL.
+ * factorisations and triangular solves they performed (n^3/3 + 2 n^2 per interval and iteration,
+ * n real unknowns).  Any pointer may be NULL.
  */
 int gc_profile_lm(double* lm_ms, int64_t* launches, double* flop);
 /* SM clock cycles the same LM phase spent, summed over interval iterations, in its parts: [0] the

@@ -895,8 +895,8 @@ __global__ void __launch_bounds__(kLMThreads, 2) lm_iter_kernel(const LMArgs a, 
         a.list[lout * a.n_int + at] = i;
       }
       s_acc = acc;
-      // algorithmic work of this interval's step: Cholesky n^3/3 + two triangular solves 2 n^2 (FMAs)
-      if (a.flop && s_fail != 2) atomicAdd(a.flop, 2.0 * ((double)n * n * n / 3.0 + 2.0 * (double)n * n));
+      // algorithmic work of this interval's step: Cholesky n^3/3 flops, two triangular solves n^2 each
+      if (a.flop && s_fail != 2) atomicAdd(a.flop, (double)n * n * n / 3.0 + 2.0 * (double)n * n);
     }
     __syncthreads();
     if (s_acc)

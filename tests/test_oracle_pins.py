@@ -492,3 +492,21 @@ def test_closed_form_lm_stationary_point_and_explicit_agreement():
             dx = (pc.chi2(gc_ + e) - pc.chi2(gc_ - e)) / (2 * h)
             dy = (pc.chi2(gc_ + 1j * e) - pc.chi2(gc_ - 1j * e)) / (2 * h)
             assert abs(dx) + abs(dy) < 1e-6 * c0 + 1e-7
+
+
+def test_cpu_openmp_lm_matches_oracle_least_squares():
+    """The FP64 C++/OpenMP implementation of the same method (the benchmark's all-core CPU comparator)
+    converges to the NumPy oracle's least-squares gains on a small 2x2 workload, every interval."""
+    from oracle import cpu
+    from paper_1502_06974_gb300 import synth as sy
+    b = sy.make_config(2, small=True)
+    g, iters, status, used = cpu.calibrate_jones_lm(b, tol=1e-10, max_iter=500, K=2.0, threads=2)
+    assert used >= 1 and (status == 0).all(), status
+    for i in range(b.n_int):
+        iv = b.interval(i)
+        prob = wirtinger.ClosedFormProblem('jones', iv['vis'], iv['model'], iv['ant1'], iv['ant2'], iv['n_ant'])
+        r = diagonal.iterate('jones', b.g0()[iv['gain_slice']], iv['vis'], iv['model'], iv['ant1'], iv['ant2'],
+                             iv['n_ant'], tol=0.0, max_iter=20)
+        ls, _, _ = wirtinger.levenberg_marquardt(prob, r['g'], tol=1e-12, lam0=1e-2, gauge=True)
+        # complex64 storage of the result limits the agreement to FP32 rounding
+        assert gauge.rel_error('jones', g[iv['gain_slice']], ls) < 1e-6, i
