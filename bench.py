@@ -371,6 +371,71 @@ def warm_start_block(dev, args):
                          "val_mse": res.val_mse, "val_mse_previous_solution": res.val_mse_zero}}
 
 
+UNEVEN_WORKLOAD = ("uneven: independent intervals, N_ant U{16,24,32,48,64}, 1-32 t x 1-16 ch, scalar or 2x2 "
+                   "(Bernoulli 1/2), 5 sources each, sigma 0.01; StefCal x20 then LM to a relative step of 1e-6; "
+                   "one call per kind, back to back on one stream")
+
+
+def oracle_ls_interval(kind, iv, tol=1e-12):
+    """The oracle's FP64 least-squares gains of one interval from its own unit start."""
+    from oracle import diagonal, wirtinger
+    na = iv['n_ant']
+    g0 = np.tile(np.eye(2, dtype=np.complex128), (na, 1, 1)) if kind == 'jones' else np.ones(na, np.complex128)
+    r = diagonal.iterate(kind, g0, iv['vis'], iv['model'], iv['ant1'], iv['ant2'], na, tol=0.0, max_iter=LM_AFTER)
+    prob = wirtinger.ClosedFormProblem(kind, iv['vis'], iv['model'], iv['ant1'], iv['ant2'], na)
+    return wirtinger.levenberg_marquardt(prob, r['g'], tol=tol, max_iter=400, lam0=1e-2, K=LM_K, gauge=True)[0]
+
+
+def uneven_block(dev, args):
+    """The uneven batched workload at full size (4096 intervals, ~0.46 G rows, ~18.5 GB of vis + model):
+    both kinds to convergence with the LM schedule, sampled intervals against the oracle."""
+    import torch
+    from oracle import gauge
+    from paper_1502_06974_gb300 import api, synth
+    t0 = time.perf_counter()
+    d = synth.make_uneven(n_intervals=args.uneven_intervals, workers=min(32, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": UNEVEN_WORKLOAD, "intervals": int(args.uneven_intervals), "metric": METRIC, "unit": UNIT,
+           "generation_s": gen_s}
+    tot_ms = 0.0
+    tot_rows = 0
+    errs = []
+    for kind, fn in (('scalar', api.calibrate_di_scalar), ('jones', api.calibrate_di_jones2x2)):
+        b = d[kind]
+        vis = torch.from_numpy(b.vis).to(dev)
+        model = torch.from_numpy(b.model).to(dev)
+        g0 = torch.from_numpy(b.g0()).to(dev)
+        lay = api.Layout.from_batch(b)
+        if not args.no_autotune:
+            api.autotune_di(vis, model, lay, g0.clone(), iters=24)
+        fn(vis, model, lay, g0.clone(), tol=TOL, max_iter=2000, **SCHED)           # warm-up (plans)
+        g = g0.clone()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        g, it, _, st = fn(vis, model, lay, g, tol=TOL, max_iter=2000, **SCHED)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        it = it.cpu().numpy(); st = st.cpu().numpy(); gh = g.cpu().numpy()
+        order = np.argsort(b.n_samp.astype(np.int64) * b.n_bl)
+        samp = [int(order[0]), int(order[len(order) // 2])]
+        e = [gauge.rel_error(kind, gh[b.interval(i)['gain_slice']], oracle_ls_interval(kind, b.interval(i)))
+             for i in samp]
+        errs += e
+        out[kind] = {"intervals": b.n_int, "rows": b.n_rows, "ms": ms, "value": b.n_rows / (ms / 1e3),
+                     "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+                     "converged": int(np.sum((st & 15) == 0)), "oracle_sampled_intervals": samp,
+                     "max_err_vs_oracle": max(e)}
+        tot_ms += ms
+        tot_rows += b.n_rows
+        del vis, model, g0, g
+        torch.cuda.empty_cache()
+    out.update({"rows": tot_rows, "ms": tot_ms, "value": tot_rows / (tot_ms / 1e3), "max_err_vs_oracle": max(errs)})
+    return out
+
+
 DD_WORKLOAD = ("dd_cohjones: 62 ant (1891 bl), 9 directions x 3 sources, 120 t x 16 ch, intervals 10 t x 16 ch "
                "(12), direction gains 1+N(0,0.2) x U(-pi,pi), sigma 0.02, tol 1e-6")
 
@@ -616,6 +681,8 @@ def run_gpu(args):
             out["warm_start"] = warm_start_block(dev, args)
         if not args.no_dd and world == 1:
             out["dd_cohjones"] = dd_block(dev, args, peaks, which)
+        if not args.no_uneven and world == 1:
+            out["uneven"] = uneven_block(dev, args)
         print(json.dumps(out))
     if dist:
         dist.barrier()
@@ -635,6 +702,8 @@ def main():
     ap.add_argument('--no-warm', action='store_true', help='skip the learned warm start comparison')
     ap.add_argument('--no-dd', action='store_true', help='skip the direction-dependent (CohJones) workload')
     ap.add_argument('--dd-only', action='store_true', help='run only the direction-dependent workload')
+    ap.add_argument('--no-uneven', action='store_true', help='skip the uneven batched workload')
+    ap.add_argument('--uneven-intervals', type=int, default=4096, help='intervals of the uneven workload')
     ap.add_argument('--path', type=int, default=0,
                     help='StefCal schedule only: 0 auto (moments), 1 raw-row streaming, 2 resident, 3 moments')
     ap.add_argument('--schedule', default='lm', choices=['lm', 'stefcal'],

@@ -304,12 +304,55 @@ def make_dd(seed=SEED, n_ant=62, n_dir=9, n_t=120, n_chan=16, t_per=10, f_per=16
                    g_l, dtype, n_dir=n_dir, meta=dict(sigma=sigma))
 
 
+def _uneven_interval(seed, i, kval, na, T, F, n_src, sigma, fmin, fmax):
+    """Model, visibilities and true gains of interval i of the uneven workload (its own stream)."""
+    r = rng_for(seed, 4, 1 + i)
+    a1, a2 = baseline_table(na)
+    xy = antenna_positions(r, na)
+    freqs = np.linspace(fmin, fmax, F) if F > 1 else np.array([0.5 * (fmin + fmax)])
+    if kval == 0:
+        flux, l, m = scalar_sky(r, n_src)
+        mf = np.einsum('fbs,s->fb', fringe(xy, a1, a2, l, m, freqs), flux)
+        mod = np.repeat(mf[None], T, axis=0).reshape(T * F, -1)
+        g = scalar_gains(r, na, 0.1)
+        v = simulate_scalar(g, mod, a1, a2) + complex_noise(r, mod.shape, sigma)
+    else:
+        B, l, m = polarized_sky(r, n_src)
+        mf = np.einsum('fbs,sij->fbij', fringe(xy, a1, a2, l, m, freqs), B)
+        mod = np.repeat(mf[None], T, axis=0).reshape(T * F, -1, 2, 2)
+        g = jones_gains(r, na, 0.1, 0.02)
+        v = simulate_jones(g, mod, a1, a2) + complex_noise(r, mod.shape, sigma)
+    return v, mod, g
+
+
+def _uneven_worker(job):
+    """Fill a share of the uneven workload's intervals into shared-memory arrays (process pool)."""
+    from multiprocessing import shared_memory
+    names, shapes, dtype, seed, jobs, n_src, sigma, fmin, fmax = job
+    shm = [shared_memory.SharedMemory(name=n) for n in names]
+    try:
+        vis = np.ndarray(shapes[0], dtype=dtype, buffer=shm[0].buf)
+        model = np.ndarray(shapes[0], dtype=dtype, buffer=shm[1].buf)
+        g_true = np.ndarray(shapes[1], dtype=np.complex128, buffer=shm[2].buf)
+        for (i, kval, na, T, F, r0, nr, g0) in jobs:
+            v, mod, g = _uneven_interval(seed, i, kval, na, T, F, n_src, sigma, fmin, fmax)
+            vis[r0:r0 + nr] = v.reshape((nr,) + tuple(shapes[0][1:]))
+            model[r0:r0 + nr] = mod.reshape((nr,) + tuple(shapes[0][1:]))
+            g_true[g0:g0 + na] = g
+        del vis, model, g_true
+    finally:
+        for m in shm:
+            m.close()
+    return len(jobs)
+
+
 def make_uneven(seed=SEED, n_intervals=4096, ant_choices=(16, 24, 32, 48, 64), t_max=32, f_max=16, n_src=5,
-                sigma=0.01, dtype=np.complex64, only: Optional[str] = None, fmin=1.0e9, fmax=1.4e9):
+                sigma=0.01, dtype=np.complex64, only: Optional[str] = None, fmin=1.0e9, fmax=1.4e9, workers=1):
     """Independent intervals of uneven size; half scalar, half 2x2 (a Bernoulli draw per interval).
 
     Returns {'scalar': Batch, 'jones': Batch} (each kind compacted into its own batch) and the
-    per-interval draw table under meta['draws'].
+    per-interval draw table under meta['draws'].  Every interval draws from its own stream; with
+    workers > 1 they are simulated by a process pool (spawn) into shared memory, with the same result.
     """
     rd = rng_for(seed, 4, 0)
     n_ant = rd.choice(np.asarray(ant_choices), n_intervals)
@@ -328,29 +371,49 @@ def make_uneven(seed=SEED, n_intervals=4096, ant_choices=(16, 24, 32, 48, 64), t
         for n in ant_choices:
             off[int(n)] = o
             a1_all.append(tables[int(n)][0]); a2_all.append(tables[int(n)][1]); o += len(tables[int(n)][0])
-        vis_l, mod_l, g_l, ns_l, nb_l, bo_l, na_l = [], [], [], [], [], [], []
-        for i in idx:
-            r = rng_for(seed, 4, 1 + int(i))
-            na = int(n_ant[i]); a1, a2 = tables[na]
-            xy = antenna_positions(r, na)
-            freqs = np.linspace(fmin, fmax, int(F[i])) if F[i] > 1 else np.array([0.5 * (fmin + fmax)])
-            if kval == 0:
-                flux, l, m = scalar_sky(r, n_src)
-                mf = np.einsum('fbs,s->fb', fringe(xy, a1, a2, l, m, freqs), flux)
-                mod = np.repeat(mf[None], int(T[i]), axis=0).reshape(int(T[i]) * int(F[i]), -1)
-                g = scalar_gains(r, na, 0.1)
-                vis = simulate_scalar(g, mod, a1, a2) + complex_noise(r, mod.shape, sigma)
-            else:
-                B, l, m = polarized_sky(r, n_src)
-                mf = np.einsum('fbs,sij->fbij', fringe(xy, a1, a2, l, m, freqs), B)
-                mod = np.repeat(mf[None], int(T[i]), axis=0).reshape(int(T[i]) * int(F[i]), -1, 2, 2)
-                g = jones_gains(r, na, 0.1, 0.02)
-                vis = simulate_jones(g, mod, a1, a2) + complex_noise(r, mod.shape, sigma)
-            vis_l.append(vis); mod_l.append(mod); g_l.append(g)
-            ns_l.append(int(T[i]) * int(F[i])); nb_l.append(len(a1)); bo_l.append(off[na]); na_l.append(na)
-        b = _finish(kname, vis_l, mod_l, np.concatenate(a1_all), np.concatenate(a2_all), ns_l, nb_l, bo_l, na_l,
-                    g_l, dtype, meta=dict(sigma=sigma, interval_ids=idx))
-        out[kname] = b
+        na_l = n_ant[idx].astype(np.int32)
+        nb_l = np.array([len(tables[int(n)][0]) for n in na_l], np.int32)
+        ns_l = (T[idx] * F[idx]).astype(np.int32)
+        bo_l = np.array([off[int(n)] for n in na_l], np.int32)
+        sizes = ns_l.astype(np.int64) * nb_l
+        row_off = np.zeros(len(idx), np.int64)
+        row_off[1:] = np.cumsum(sizes)[:-1]
+        gain_off = np.zeros(len(idx), np.int32)
+        gain_off[1:] = np.cumsum(na_l.astype(np.int64))[:-1]
+        shape = (int(sizes.sum()),) + (() if kval == 0 else (2, 2))
+        gshape = (int(na_l.sum()),) + (() if kval == 0 else (2, 2))
+        jobs = [(int(idx[j]), kval, int(na_l[j]), int(T[idx[j]]), int(F[idx[j]]), int(row_off[j]), int(sizes[j]),
+                 int(gain_off[j])) for j in range(len(idx))]
+        if workers <= 1:
+            vis = np.empty(shape, dtype)
+            model = np.empty(shape, dtype)
+            g_true = np.empty(gshape, np.complex128)
+            for (i, kv, na, tt, ff, r0, nr, g0) in jobs:
+                v, mod, g = _uneven_interval(seed, i, kv, na, tt, ff, n_src, sigma, fmin, fmax)
+                vis[r0:r0 + nr] = v.reshape((nr,) + shape[1:])
+                model[r0:r0 + nr] = mod.reshape((nr,) + shape[1:])
+                g_true[g0:g0 + na] = g
+        else:
+            import multiprocessing as mp
+            from multiprocessing import shared_memory
+            nbytes = [int(np.prod(shape)) * np.dtype(dtype).itemsize] * 2 + [int(np.prod(gshape)) * 16]
+            shm = [shared_memory.SharedMemory(create=True, size=max(n, 1)) for n in nbytes]
+            try:
+                chunks = [jobs[w::workers] for w in range(workers)]
+                args = [([m.name for m in shm], (shape, gshape), np.dtype(dtype).str, seed, c, n_src, sigma, fmin,
+                         fmax) for c in chunks if c]
+                with mp.get_context('spawn').Pool(len(args)) as pool:
+                    pool.map(_uneven_worker, args)
+                vis = np.ndarray(shape, dtype=dtype, buffer=shm[0].buf).copy()
+                model = np.ndarray(shape, dtype=dtype, buffer=shm[1].buf).copy()
+                g_true = np.ndarray(gshape, dtype=np.complex128, buffer=shm[2].buf).copy()
+            finally:
+                for m in shm:
+                    m.close()
+                    m.unlink()
+        out[kname] = Batch(kname, vis, model, np.concatenate(a1_all).astype(np.int32),
+                           np.concatenate(a2_all).astype(np.int32), row_off, ns_l, nb_l, bo_l, na_l, gain_off, g_true,
+                           1, dict(sigma=sigma, interval_ids=idx))
     out['draws'] = dict(n_ant=n_ant, T=T, F=F, kind=kind)
     return out
 
