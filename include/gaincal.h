@@ -327,6 +327,25 @@ int gc_ws_features_jones(const float* hist, int32_t hist_stride, const float* jh
 /* Training target [n][8] = e^{-i phi} (g_next - g1), the network output that would propose g_next. */
 int gc_ws_target_jones(const float* g1, const float* g_next, const float* rot, int32_t n, float* target,
                        void* stream);
+/* Training-set preparation for the network (device pointers, asynchronous on `stream`).
+ * gc_rows_gather_f32: dst[r][:] = src[index[r]][:] for r < n, rows of `width` floats (index int64,
+ *   device; every entry must address a row of src: not checked).
+ * gc_col_stats_f32: per column of x [.][width] over the rows index[0..n-1] (rows 0..n-1 when index
+ *   is NULL), the FP64 mean and population standard deviation (two passes); a column whose
+ *   deviation is below 1e-12 gets sd = 1 and, when zero_const_mean, mean = 0.  n >= 1.
+ * gc_standardize_f32: out = (x - mean) / sd per column in FP64, rounded to FP32 (mean may be NULL:
+ *   out = x / sd); out may equal x.
+ * gc_mlp_fold_standardization: rewrite the network in place so that it takes raw inputs and
+ *   returns raw outputs: with W1, b1 the first layer and W3, b3 the last, b1 -= (mean/sd) W1,
+ *   W1 /= sd (per input row), W3 *= tsd and b3 *= tsd (per output column), in FP64.  mean/sd
+ *   [in], tsd [out], device.
+ * Each returns GC_OK, GC_ERR_ARG (bad size or NULL), GC_ERR_LIMIT (network shape) or GC_ERR_CUDA. */
+int gc_rows_gather_f32(const float* src, int32_t width, const int64_t* index, int64_t n, float* dst, void* stream);
+int gc_col_stats_f32(const float* x, int32_t width, const int64_t* index, int64_t n, int32_t zero_const_mean,
+                     double* mean, double* sd, void* stream);
+int gc_standardize_f32(const float* x, int32_t width, int64_t n, const double* mean, const double* sd, float* out,
+                       void* stream);
+int gc_mlp_fold_standardization(gc_mlp* net, const double* mean, const double* sd, const double* tsd, void* stream);
 
 /* Inputs of a warm-started solve. */
 typedef struct gc_warm {
@@ -418,6 +437,15 @@ const char* gc_error_string(int code);
 const char* gc_status_string(int status);
 /* The last CUDA error string seen by the library ("" if none). */
 const char* gc_last_cuda_error(void);
+/* Bounded waits.  The 2x2 accumulate kernel of the moment path waits for each tile's bulk copies
+ * on an mbarrier, at most `tries` polls (each poll may also suspend the thread briefly); when the
+ * wait runs out the kernel first waits, with the default bound, for the copies it still has in
+ * flight, records the failure and ends, and the calling gc_calibrate_* returns GC_ERR_CUDA with
+ * gc_last_cuda_error() naming the incomplete copy.  The GPU context stays usable.  tries < 0
+ * restores the default bound (2^22 polls); 0 makes every such wait give up at once.  Applies to the
+ * current device and every later call on it; meant for testing the error path.  Returns GC_OK or
+ * GC_ERR_CUDA. */
+int gc_set_wait_limit(int32_t tries);
 /* Kernels launched by this process so far (a monotone counter, for launch accounting). */
 int64_t gc_launch_count(void);
 /* Free the cached device workspace (safe to call at any time no call is running). */

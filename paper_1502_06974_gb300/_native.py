@@ -28,7 +28,8 @@ EXPORTS = [
     'gc_chi2_di_jones2x2', 'gc_mlp_work_floats', 'gc_mlp_forward_f32', 'gc_mlp_grad_f32', 'gc_mlp_train_step',
     'gc_mlp_infer_bf16', 'gc_ws_features_jones', 'gc_ws_target_jones', 'gc_calibrate_di_jones2x2_warm',
     'gc_calibrate_di_jones2x2_wavefront', 'gc_gauge_fix_di',
-    'gc_autotune_di', 'gc_profile_last', 'gc_profile_detail', 'gc_profile_lm', 'gc_profile_lm_phases', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_launch_count', 'gc_release',
+    'gc_autotune_di', 'gc_profile_last', 'gc_profile_detail', 'gc_profile_lm', 'gc_profile_lm_phases', 'gc_error_string', 'gc_status_string', 'gc_last_cuda_error', 'gc_set_wait_limit', 'gc_rows_gather_f32', 'gc_col_stats_f32',
+    'gc_standardize_f32', 'gc_mlp_fold_standardization', 'gc_launch_count', 'gc_release',
 ]
 
 _p = C.c_void_p
@@ -95,6 +96,16 @@ def lib() -> C.CDLL:
         L.gc_status_string.restype = C.c_char_p
         L.gc_last_cuda_error.argtypes = []
         L.gc_last_cuda_error.restype = C.c_char_p
+        L.gc_rows_gather_f32.argtypes = [_p, C.c_int32, _p, C.c_int64, _p, _p]
+        L.gc_rows_gather_f32.restype = C.c_int
+        L.gc_col_stats_f32.argtypes = [_p, C.c_int32, _p, C.c_int64, C.c_int32, _p, _p, _p]
+        L.gc_col_stats_f32.restype = C.c_int
+        L.gc_standardize_f32.argtypes = [_p, C.c_int32, C.c_int64, _p, _p, _p, _p]
+        L.gc_standardize_f32.restype = C.c_int
+        L.gc_mlp_fold_standardization.argtypes = [C.POINTER(GcMlp), _p, _p, _p, _p]
+        L.gc_mlp_fold_standardization.restype = C.c_int
+        L.gc_set_wait_limit.argtypes = [C.c_int32]
+        L.gc_set_wait_limit.restype = C.c_int
         L.gc_launch_count.argtypes = []
         L.gc_launch_count.restype = C.c_int64
         L.gc_profile_last.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]

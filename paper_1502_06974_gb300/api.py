@@ -283,6 +283,57 @@ def mlp_infer_bf16(net: Mlp, x):
     return y
 
 
+def _i64_dev(index, device):
+    if isinstance(index, torch.Tensor):
+        if index.dtype != torch.int64 or index.device != device or not index.is_contiguous():
+            raise ValueError("index must be a contiguous int64 tensor on the data's device")
+        return index
+    return torch.from_numpy(np.ascontiguousarray(index, np.int64)).to(device)
+
+
+def rows_gather_f32(src, index):
+    """dst[r] = src[index[r]] for a float32 [m, w] CUDA tensor (gc_rows_gather_f32); index: host or device int64."""
+    src2 = src.reshape(src.shape[0], -1)
+    _f32(src2, 'src')
+    idx = _i64_dev(index, src.device)
+    n, w = int(idx.numel()), int(src2.shape[1])
+    dst = torch.empty((n, w), dtype=torch.float32, device=src.device)
+    N.check(N.lib().gc_rows_gather_f32(_ptr(src2), w, _ptr(idx), n, _ptr(dst), _stream_ptr(src.device)),
+            'gc_rows_gather_f32')
+    return dst
+
+
+def col_stats_f32(x, index=None, zero_const_mean=True):
+    """(mean, sd) float64 [w] device tensors of the columns of x over the rows `index` (all rows if None)."""
+    _f32(x, 'x')
+    w = int(x.shape[1])
+    idx = None if index is None else _i64_dev(index, x.device)
+    n = int(x.shape[0] if idx is None else idx.numel())
+    mean = torch.empty(w, dtype=torch.float64, device=x.device)
+    sd = torch.empty(w, dtype=torch.float64, device=x.device)
+    N.check(N.lib().gc_col_stats_f32(_ptr(x), w, None if idx is None else _ptr(idx), n, int(bool(zero_const_mean)),
+                                     _ptr(mean), _ptr(sd), _stream_ptr(x.device)), 'gc_col_stats_f32')
+    return mean, sd
+
+
+def standardize_f32(x, mean, sd):
+    """(x - mean) / sd per column (mean None: x / sd), float32 out (gc_standardize_f32)."""
+    _f32(x, 'x')
+    out = torch.empty_like(x)
+    N.check(N.lib().gc_standardize_f32(_ptr(x), int(x.shape[1]), int(x.shape[0]), None if mean is None else _ptr(mean),
+                                       _ptr(sd), _ptr(out), _stream_ptr(x.device)), 'gc_standardize_f32')
+    return out
+
+
+def mlp_fold_standardization(net: Mlp, mean, sd, tsd):
+    """Fold input standardisation and output scaling into the network in place."""
+    for t, nm in ((mean, 'mean'), (sd, 'sd'), (tsd, 'tsd')):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{nm} must be a contiguous float64 CUDA tensor")
+    N.check(N.lib().gc_mlp_fold_standardization(net.c(), _ptr(mean), _ptr(sd), _ptr(tsd),
+                                                _stream_ptr(net.params.device)), 'gc_mlp_fold_standardization')
+
+
 def _as_f32_view(g):
     """complex64 [n, 2, 2] -> float32 [n, 8] view (no copy)."""
     if g.dtype == torch.complex64:
@@ -414,3 +465,8 @@ def launch_count() -> int:
 
 def release():
     N.check(N.lib().gc_release(), 'gc_release')
+
+
+def set_wait_limit(tries: int):
+    """Polls of the 2x2 accumulate kernel's bounded copy wait on the current device (< 0: default)."""
+    N.check(N.lib().gc_set_wait_limit(int(tries)), 'gc_set_wait_limit')

@@ -1449,6 +1449,11 @@ const char* gc_status_string(int status) {
 
 const char* gc_last_cuda_error(void) { return gc::last_cuda_error(); }
 
+int gc_set_wait_limit(int32_t tries) {
+  GC_CUDA_I(gc::di_set_bulk_wait_tries(tries));
+  return GC_OK;
+}
+
 int gc_profile_detail(double* moment_pass_ms, int64_t* baseline_iterations, int32_t* path) {
   if (moment_pass_ms) *moment_pass_ms = gc::g_prof.moment_ms;
   if (baseline_iterations) *baseline_iterations = gc::g_prof.bl_iters;

@@ -582,6 +582,10 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_staged_kernel(const DIA
 // work-list entry and the descriptor, which the copying thread fetches a tile further ahead.  Same
 // arithmetic and reduction order as di_macc_kernel with CH = 1 (identical results).
 constexpr int kBulkSpins = 1 << 22;  // bounded mbarrier waits: each try_wait also suspends briefly
+// Tries of a tile's first wait (kBulkSpins unless di_set_bulk_wait_tries changed it).  Waits for
+// copies still in flight after a failed one always take the full kBulkSpins: a CTA leaves only once
+// its own copies have landed, or after that bound too.
+__device__ int g_bulk_wait_tries = kBulkSpins;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -590,9 +594,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int tries) {
   const unsigned addr = smem_u32(bar);
-  for (int n = 0; n < kBulkSpins; ++n) {
+  for (int n = 0; n < tries; ++n) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -636,6 +640,7 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
   const int tid = threadIdx.x;
   const int na_max = a.na_max, tbm = a.tblk_max;
   const size_t sf = Sh::stage_floats(na_max, tbm);
+  const int tries = g_bulk_wait_tries;
   const int k = a.k + (a.kbase ? *a.kbase : 0);
   const int cur = k % 3;
   const bool fixed = a.xcount > 0;
@@ -696,7 +701,7 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
   int j = 0;
   for (int slot = blockIdx.x; slot < n_list; slot += G, ++j) {
     const int s = j & 1;
-    const bool ok = mbar_wait(&full[s], (unsigned)(j >> 1) & 1u);
+    const bool ok = mbar_wait(&full[s], (unsigned)(j >> 1) & 1u, tries);
     float* st = stage0 + (size_t)s * sf;
     const int4 h = hdr[s][0];
     const int nbt = h.x, nat = h.y, go = hdr[s][1].x;
@@ -733,13 +738,15 @@ __global__ void __launch_bounds__(kDIThreads, 2) di_macc_bulk_kernel(const DIArg
         my4[(NC / 4 + r) * TB] = make_float4(pq[4 * r], pq[4 * r + 1], pq[4 * r + 2], pq[4 * r + 3]);
       }
     }
-    // a copy that never landed ends the CTA (all threads agree), after a bounded wait for the rest
+    // a copy that never landed ends the CTA (all threads agree), after a bounded wait for every
+    // copy it still has in flight (this tile's and the next one's)
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicExch(a.err, 1);
         for (int t = 0; t < 2; ++t)
-          if (pend[t] && t != s) mbar_wait(&full[t], (unsigned)((j + 1) >> 1) & 1u);
+          if (pend[t]) mbar_wait(&full[t], (unsigned)((t == s ? j : j + 1) >> 1) & 1u, kBulkSpins);
       }
+      __syncthreads();
       return;
     }
     if (tid == 0) pend[s] = false;
@@ -1151,6 +1158,11 @@ int di_macc_smem(int kind, int na_max, int red_chunks, int prefetch) {
 int di_macc_bulk_smem(int kind, int na_max, int tblk_max) {
   if (kind != 1) return 1 << 30;
   return (int)(2 * sizeof(float) * BulkShape<JonesMom>::stage_floats(na_max, tblk_max));
+}
+
+int di_set_bulk_wait_tries(int tries) {
+  const int v = tries < 0 ? kBulkSpins : tries;
+  return (int)cudaMemcpyToSymbol(g_bulk_wait_tries, &v, sizeof(int));
 }
 
 int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, int* out) {

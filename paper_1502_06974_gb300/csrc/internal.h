@@ -91,6 +91,10 @@ struct DIArgs {
   int32_t tblk_max;
   int32_t* err;
 };
+// DIArgs goes to the kernels by value: every translation unit, host and device pass, must agree on
+// its layout.  A field added here changes this size and must be added in the same build of every
+// object that uses it (the library build recompiles all of them together).
+static_assert(sizeof(DIArgs) == 416, "DIArgs layout changed: rebuild every translation unit and update this size");
 
 // Launchers implemented in di_kernels.cu.  kind: 0 scalar, 1 jones.  Return cudaError_t as int.
 int di_smem_bytes(int kind, int dtype, int na_max);
@@ -99,6 +103,9 @@ int di_launch_iter(int kind, int dtype, int acc_only, const DIArgs& a, int grid,
 int di_launch_init(const DIArgs& a, int n_int, int n_active0, void* stream);
 int di_macc_smem(int kind, int na_max, int red_chunks, int prefetch);
 int di_macc_bulk_smem(int kind, int na_max, int tblk_max);
+// Tries of the bulk-copy accumulate kernel's first wait per tile on the current device (< 0: the
+// default bound).  Returns cudaError_t as int.
+int di_set_bulk_wait_tries(int tries);
 int di_macc_max_blocks_per_sm(int kind, int smem, int red_chunks, int prefetch, int* out);
 // one iteration: the accumulate launch, then the solve launch
 int di_launch_mstep(int kind, const DIArgs& a, int grid, int smem, int n_int, int red_chunks, int prefetch,

@@ -123,6 +123,73 @@ __global__ void to_bf16_kernel(const float* p, __nv_bfloat16* q, size_t n) {
   if (i < n) q[i] = __float2bfloat16_rn(p[i]);
 }
 
+// dst[r][:] = src[index[r]][:], rows of w floats
+__global__ void rows_gather_kernel(const float* src, int w, const int64_t* index, int64_t n, float* dst) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * w) return;
+  const int64_t r = e / w;
+  dst[e] = src[index[r] * w + (e - r * w)];
+}
+
+// Per column c of x [.][w] over the rows index[0 .. n-1] (all rows 0 .. n-1 when index is NULL):
+// FP64 mean and population standard deviation, two passes (mean first, then the centred squares).
+// A column whose deviation is below 1e-12 gets sd 1 (and mean 0 when zero_const_mean).
+__global__ void col_stats_kernel(const float* x, int w, const int64_t* index, int64_t n, int zero_const_mean,
+                                 double* mean, double* sd) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  if (c >= w) return;
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s += (double)x[(index ? index[r] : r) * w + c];
+  const double mu = block_sum<double>(s, red) / (double)n;
+  double q = 0.0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double d = (double)x[(index ? index[r] : r) * w + c] - mu;
+    q = fma(d, d, q);
+  }
+  const double v = block_sum<double>(q, red) / (double)n;
+  if (threadIdx.x == 0) {
+    double sdv = sqrt(v), m = mu;
+    if (sdv < 1e-12) {
+      sdv = 1.0;
+      if (zero_const_mean) m = 0.0;
+    }
+    mean[c] = m;
+    sd[c] = sdv;
+  }
+}
+
+// out = (x - mean) / sd per column, in FP64, rounded to FP32 (mean may be NULL: no centring)
+__global__ void standardize_kernel(const float* x, int w, int64_t n, const double* mean, const double* sd, float* out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n * w) return;
+  const int c = (int)(e % w);
+  out[e] = (float)(((double)x[e] - (mean ? mean[c] : 0.0)) / sd[c]);
+}
+
+// Fold x -> (x - mean) / sd into the first layer and y -> y * tsd into the last, in place:
+// b1[h] -= sum_i (mean_i / sd_i) W1[i][h], W1[i][h] /= sd_i, W3[.][o] *= tsd_o, b3[o] *= tsd_o (FP64).
+// One thread per first-layer unit h (it alone touches column h of W1 and b1[h]) and, after them,
+// one per last-layer weight or bias.
+__global__ void fold_standardization_kernel(float* p, int in, int h1, int h2, int out, const double* mean,
+                                            const double* sd, const double* tsd) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < h1) {
+    double b = p[(size_t)in * h1 + t];
+    for (int i = 0; i < in; ++i) {
+      const double wv = p[(size_t)i * h1 + t];
+      b -= (mean[i] / sd[i]) * wv;
+      p[(size_t)i * h1 + t] = (float)(wv / sd[i]);
+    }
+    p[(size_t)in * h1 + t] = (float)b;
+    return;
+  }
+  const int u = t - h1;
+  const size_t o3 = (size_t)in * h1 + h1 + (size_t)h1 * h2 + h2;
+  if (u < h2 * out) p[o3 + u] = (float)((double)p[o3 + u] * tsd[u % out]);
+  else if (u < h2 * out + out) p[o3 + u] = (float)((double)p[o3 + u] * tsd[u - h2 * out]);
+}
+
 // BF16 inference: weights and activations in BF16, products accumulated in FP32.  One CTA holds
 // all weights in shared memory and runs rows in tiles of kRows; thread j owns hidden unit j.
 constexpr int kRows = 16;
@@ -513,6 +580,51 @@ int gc_ws_target_jones(const float* g1, const float* g_next, const float* rot, i
   g_launches++;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GC_OK : set_cuda_error(e, "target");
+}
+
+int gc_rows_gather_f32(const float* src, int32_t width, const int64_t* index, int64_t n, float* dst, void* stream) {
+  if (width < 1 || n < 0) return GC_ERR_ARG;
+  if (n == 0) return GC_OK;
+  if (!src || !index || !dst) return GC_ERR_ARG;
+  const int64_t ne = n * width;
+  rows_gather_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, (cudaStream_t)stream>>>(src, width, index, n, dst);
+  g_launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : set_cuda_error(e, "rows gather");
+}
+
+int gc_col_stats_f32(const float* x, int32_t width, const int64_t* index, int64_t n, int32_t zero_const_mean,
+                     double* mean, double* sd, void* stream) {
+  if (width < 1 || n < 1 || !x || !mean || !sd) return GC_ERR_ARG;
+  col_stats_kernel<<<width, 256, 0, (cudaStream_t)stream>>>(x, width, index, n, zero_const_mean, mean, sd);
+  g_launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : set_cuda_error(e, "column statistics");
+}
+
+int gc_standardize_f32(const float* x, int32_t width, int64_t n, const double* mean, const double* sd, float* out,
+                       void* stream) {
+  if (width < 1 || n < 0) return GC_ERR_ARG;
+  if (n == 0) return GC_OK;
+  if (!x || !sd || !out) return GC_ERR_ARG;
+  const int64_t ne = n * width;
+  standardize_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, width, n, mean, sd, out);
+  g_launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : set_cuda_error(e, "standardize");
+}
+
+int gc_mlp_fold_standardization(gc_mlp* net, const double* mean, const double* sd, const double* tsd, void* stream) {
+  if (!net || !net->params || !mean || !sd || !tsd) return GC_ERR_ARG;
+  const MlpDims d{net->in, net->h1, net->h2, net->out};
+  int rc = check_dims(d);
+  if (rc) return rc;
+  const int nt = d.h1 + d.h2 * d.out + d.out;
+  fold_standardization_kernel<<<(nt + 255) / 256, 256, 0, (cudaStream_t)stream>>>(net->params, d.in, d.h1, d.h2,
+                                                                                   d.out, mean, sd, tsd);
+  g_launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GC_OK : set_cuda_error(e, "fold standardization");
 }
 
 }  // extern "C"

@@ -22,6 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
+from . import _native as N
 from . import api
 
 LEAD_SCALE = 32.0        # lead (in intervals) is divided by this before it enters the network
@@ -100,9 +101,10 @@ def training_set(vis, model, grid: Grid, sols, lag, rng, n_samples=None):
     hidx = _hist_index(np.maximum(t_all - lead, 0), f_all, grid.n_fb)          # [n_int, 4]
     dev = vis.device
     rows = (hidx[:, :, None] * na + np.arange(na)[None, None, :])                # [n_int, 4, na]
-    rows = torch.from_numpy(np.transpose(rows, (0, 2, 1)).reshape(-1)).to(dev)   # [n_int*na*4]
-    hist = sols.index_select(0, rows).reshape(n_int * na, 4, 2, 2)
-    g1 = hist[:, 0].contiguous()
+    rows = np.transpose(rows, (0, 2, 1))                                         # [n_int, na, 4]
+    sol8 = torch.view_as_real(sols).reshape(sols.shape[0], 8)
+    hist = torch.view_as_complex(api.rows_gather_f32(sol8, rows.reshape(-1)).reshape(n_int * na, 4, 2, 2, 2))
+    g1 = torch.view_as_complex(api.rows_gather_f32(sol8, rows[:, :, 0].reshape(-1)).reshape(n_int * na, 2, 2, 2))
     lay = grid.layout(n_int)
     jhd, jhj = api.jhj_jhr_di_jones2x2(vis, model, lay, g1)
     lead_rows = torch.from_numpy(np.repeat(lead.astype(np.float32) / LEAD_SCALE, na)).to(dev)
@@ -111,8 +113,7 @@ def training_set(vis, model, grid: Grid, sols, lag, rng, n_samples=None):
     keep = np.nonzero(np.repeat(ok, na))[0]
     if n_samples is not None and n_samples < keep.size:
         keep = np.sort(rng.choice(keep, n_samples, replace=False))
-    k = torch.from_numpy(keep).to(dev)
-    return x.index_select(0, k).contiguous(), tgt.index_select(0, k).contiguous()
+    return api.rows_gather_f32(x, keep), api.rows_gather_f32(tgt, keep)
 
 
 def he_init(dims, rng):
@@ -132,22 +133,6 @@ class TrainResult:
     steps: int = 0
 
 
-def _fold(params, dims, mu, sd, tsd):
-    """Fold x -> (x - mu) / sd into layer 1 and y -> y * tsd into layer 3 (float64 on the host)."""
-    i, h1, h2, o = dims
-    p = params.astype(np.float64).copy()
-    W1 = p[:i * h1].reshape(i, h1)
-    b1 = p[i * h1:i * h1 + h1]
-    b1 -= (mu / sd) @ W1
-    W1 /= sd[:, None]
-    o3 = i * h1 + h1 + h1 * h2 + h2
-    W3 = p[o3:o3 + h2 * o].reshape(h2, o)
-    b3 = p[o3 + h2 * o:]
-    W3 *= tsd[None, :]
-    b3 *= tsd
-    return p.astype(np.float32)
-
-
 def train(x, t, epochs=40, batch=1024, lr=1e-3, seed=0, val_frac=0.1, dims=api.MLP_DIMS):
     """Adam on mean((y - t)^2) with standardised inputs and targets; returns a TrainResult whose
     network takes raw features and predicts raw deltas (the standardisation is folded in)."""
@@ -156,44 +141,43 @@ def train(x, t, epochs=40, batch=1024, lr=1e-3, seed=0, val_frac=0.1, dims=api.M
     perm = rng.permutation(m)
     n_val = max(1, int(m * val_frac))
     dev = x.device
-    xh = x.cpu().numpy().astype(np.float64)
-    th = t.cpu().numpy().astype(np.float64)
+    x, t = x.contiguous(), t.contiguous()
     tr = perm[n_val:]
-    mu = xh[tr].mean(axis=0)
-    sd = xh[tr].std(axis=0)
-    sd[sd < 1e-12] = 1.0
-    mu[sd == 1.0] = 0.0
-    tsd = th[tr].std(axis=0)
-    tsd[tsd < 1e-12] = 1.0
-    xs = torch.from_numpy(((xh - mu) / sd).astype(np.float32)).to(dev)
-    ts = torch.from_numpy((th / tsd).astype(np.float32)).to(dev)
+    tr_t = torch.from_numpy(np.ascontiguousarray(tr, np.int64)).to(dev)
+    mu, sd = api.col_stats_f32(x, tr_t, zero_const_mean=True)
+    _, tsd = api.col_stats_f32(t, tr_t, zero_const_mean=False)
+    xs = api.standardize_f32(x, mu, sd)
+    ts = api.standardize_f32(t, None, tsd)
     net = api.Mlp(he_init(dims, rng), dev, dims)
     res = TrainResult(net)
-    tr_t = torch.from_numpy(tr).to(dev)
     work = net.work(batch)
-    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    n_tr = tr.size
+    nb = max(0, (n_tr - batch) // batch + 1)
+    losses = torch.zeros((epochs, max(nb, 1)), dtype=torch.float32, device=dev)   # one slot per step
+    xb = torch.empty((batch, x.shape[1]), dtype=torch.float32, device=dev)
+    tb = torch.empty((batch, t.shape[1]), dtype=torch.float32, device=dev)
+    L = N.lib()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    n_tr = tr.size
     for ep in range(epochs):
-        order = tr_t[torch.from_numpy(rng.permutation(n_tr)).to(dev)]
-        ep_loss = torch.zeros(1, dtype=torch.float32, device=dev)
-        nb = 0
-        for b0 in range(0, n_tr - batch + 1, batch):
-            idx = order[b0:b0 + batch]
-            api.mlp_train_step(net, xs.index_select(0, idx), ts.index_select(0, idx), lr, work=work, loss=loss)
-            ep_loss += loss
-            nb += 1
-        res.losses.append(float(ep_loss.item()) / max(nb, 1))
+        order = torch.from_numpy(np.ascontiguousarray(tr[rng.permutation(n_tr)], np.int64)).to(dev)
+        st = api._stream_ptr(dev)
+        for j in range(nb):
+            idx = order[j * batch:(j + 1) * batch]
+            N.check(L.gc_rows_gather_f32(api._ptr(xs), xs.shape[1], api._ptr(idx), batch, api._ptr(xb), st),
+                    'gc_rows_gather_f32')
+            N.check(L.gc_rows_gather_f32(api._ptr(ts), ts.shape[1], api._ptr(idx), batch, api._ptr(tb), st),
+                    'gc_rows_gather_f32')
+            api.mlp_train_step(net, xb, tb, lr, work=work, loss=losses[ep, j:j + 1])
         res.steps += nb
     torch.cuda.synchronize(dev)
     res.seconds = time.perf_counter() - t0
-    folded = _fold(net.params.cpu().numpy(), dims, mu, sd, tsd)
-    net.params.copy_(torch.from_numpy(folded).to(dev))
-    vi = torch.from_numpy(perm[:n_val]).to(dev)
-    xv = x.index_select(0, vi).contiguous()
-    yv = api.mlp_forward_f32(net, xv).cpu().numpy().astype(np.float64)
-    tv = th[perm[:n_val]]
+    lh = losses.cpu().numpy().astype(np.float64)
+    res.losses = [float(lh[ep, :nb].mean()) if nb else 0.0 for ep in range(epochs)]
+    api.mlp_fold_standardization(net, mu, sd, tsd)
+    vidx = perm[:n_val]
+    yv = api.mlp_forward_f32(net, api.rows_gather_f32(x, vidx)).cpu().numpy().astype(np.float64)
+    tv = api.rows_gather_f32(t, vidx).cpu().numpy().astype(np.float64)
     res.val_mse = float(np.mean((yv - tv) ** 2))
     res.val_mse_zero = float(np.mean(tv ** 2))
     return res

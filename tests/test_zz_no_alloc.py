@@ -4,8 +4,11 @@ Some callers cannot let a library allocate device memory -- a pipeline that rese
 memory at start-up, or an application whose allocator owns the GPU.  For them the library offers
 one entry point whose scratch lives in a static device array instead of cudaMalloc'd memory.  These
 tests call it through the C ABI and check that it returns what the allocating entry point returns
-(within the accumulation tolerance of the other GPU tests, 2e-5 relative per antenna), on two calls
-in a row, with intervals split into several work items so the scratch partial sums are used.
+and what the FP64 oracle's closed-form blocks give (eq. JHJ:pol's diagonal blocks and J^H D, within
+the accumulation tolerance of the other GPU tests: 2e-5 relative per antenna for complex64, 1e-12
+for complex128), on two calls in a row, with intervals split into several work items so the
+scratch partial sums are used, and on a large layout followed by a smaller one of another dtype
+on the same stream (the static array's tables, items and scratch re-laid out between calls).
 
 This file is named to be collected last.
 """
@@ -16,6 +19,7 @@ import pytest
 import torch
 
 from helpers import device_batch, per_slot_relerr
+from oracle import blocks
 from paper_1502_06974_gb300 import _native as N
 from paper_1502_06974_gb300 import api, synth
 
@@ -48,6 +52,30 @@ def test_noalloc_matches_allocating_pass(gpu_lib, monkeypatch, dtype):
         torch.cuda.synchronize()
         assert per_slot_relerr(jhd.cpu().numpy(), ref_d.cpu().numpy()) < 2e-5
         assert per_slot_relerr(jhj.cpu().numpy(), ref_j.cpu().numpy()) < 2e-5
+
+
+def _oracle(b, g):
+    g = np.asarray(g, np.complex128)
+    ref = [blocks.jones_blocks(g[iv['gain_slice']], iv['vis'], iv['model'], iv['ant1'], iv['ant2'], iv['n_ant'])
+           for iv in (b.interval(i) for i in range(b.n_int))]
+    return np.concatenate([r['CD'] for r in ref]), np.concatenate([r['H'] for r in ref])
+
+
+def test_noalloc_large_then_small_layout_against_oracle(gpu_lib, monkeypatch):
+    """A 48-antenna complex64 layout of 8 intervals split into several items, then a 7-antenna
+    complex128 layout of 3 intervals in one item each, on one stream: each against the oracle."""
+    monkeypatch.setenv("GAINCAL_TARGET_ROWS_JONES", "2000")
+    cases = [(synth.make_di_jones(n_ant=48, n_t=4, n_chan=8, t_per=2, f_per=4, dtype=np.complex64), 2e-5),
+             (synth.make_di_jones(n_ant=7, n_t=3, n_chan=2, t_per=1, f_per=2, dtype=np.complex128), 1e-12)]
+    for n, (b, tol) in enumerate(cases):
+        vis, model, _, lay = device_batch(b)
+        gh = synth.jones_gains(synth.rng_for(23, n), b.n_gain, 0.1, 0.05).astype(b.vis.dtype)
+        rc, jhd, jhj = _noalloc(vis, model, lay, torch.from_numpy(gh).cuda())
+        assert rc == 0, N.lib().gc_last_cuda_error()
+        torch.cuda.synchronize()
+        CD, H = _oracle(b, gh)
+        assert per_slot_relerr(jhd.cpu().numpy(), CD) < tol, n
+        assert per_slot_relerr(jhj.cpu().numpy(), H) < tol, n
 
 
 def test_noalloc_rejects_beyond_its_limit(gpu_lib):
