@@ -29,6 +29,10 @@ def directed_rows(vis, model, a1, a2, kind):
     if kind == 'dd':
         d = vis.reshape(-1); m = model.reshape(model.shape[0], -1)
         return i, j, np.concatenate([d, np.conj(d)]), np.concatenate([m, np.conj(m)], axis=1)
+    if kind == 'dd_jones':
+        d = vis.reshape(-1, 2, 2); m = model.reshape(model.shape[0], -1, 2, 2)
+        dH = np.conj(np.swapaxes(d, -1, -2)); mH = np.conj(np.swapaxes(m, -1, -2))
+        return i, j, np.concatenate([d, dH]), np.concatenate([m, mH], axis=1)
     d = vis.reshape(-1); m = model.reshape(-1)
     return i, j, np.concatenate([d, np.conj(d)]), np.concatenate([m, np.conj(m)])
 
@@ -105,6 +109,33 @@ def dd_blocks(g, vis, model, a1, a2, n_ant):
         c[p] = np.conj(Yp).T @ r[sel]
         cd[p] = np.conj(Yp).T @ d[sel]
     return dict(A=A, c=c, cd=cd)
+
+
+def dd_jones_blocks(G, vis, model, a1, a2, n_ant):
+    """2x2 DD (Sect. 4.4, eqs. JHJ:DD:pol and JHR:DD:pol, product order as for the DI case):
+    Y^(d)_iqs = M^(d)_iqs G_q^(d)H, R_iqs = D_iqs - sum_d G_i^(d) Y^(d)_iqs.
+
+      H   [n, 2Nd, 2Nd]  block (c, d) = sum_{q,s} Y^(c) Y^(d)H: the operator form of the top-left
+                         antenna block is X -> X H (R_H of App. B), so the antenna's normal
+                         equations read [G^(1) .. G^(Nd)] H = [C^(1) .. C^(Nd)]
+      C   [n, 2, 2Nd]    [.. sum R Y^(d)H ..]  (J^H R, direction d in columns 2d, 2d+1)
+      CD  [n, 2, 2Nd]    [.. sum D Y^(d)H ..]  (J^H D)
+    """
+    G = np.asarray(G, np.complex128)
+    nd = G.shape[1]
+    i, j, D, M = directed_rows(vis, model, a1, a2, 'dd_jones')
+    Y = M @ np.conj(np.swapaxes(G[j], -1, -2)).transpose(1, 0, 2, 3)          # [Nd, rows, 2, 2]
+    V = np.sum(G[i].transpose(1, 0, 2, 3) @ Y, axis=0)
+    R = D - V
+    Ycat = np.concatenate(list(Y), axis=-2)                                     # [rows, 2Nd, 2]
+    YcatH = np.conj(np.swapaxes(Ycat, -1, -2))                                  # [rows, 2, 2Nd]
+    H = np.zeros((n_ant, 2 * nd, 2 * nd), np.complex128)
+    C = np.zeros((n_ant, 2, 2 * nd), np.complex128)
+    CD = np.zeros((n_ant, 2, 2 * nd), np.complex128)
+    np.add.at(H, i, Ycat @ YcatH)
+    np.add.at(C, i, R @ YcatH)
+    np.add.at(CD, i, D @ YcatH)
+    return dict(H=H, C=C, CD=CD)
 
 
 # ----------------------------------------------------------------------------- full J^H J (exact GN / LM)

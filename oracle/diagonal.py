@@ -2,6 +2,9 @@
 
 Test infrastructure only (see the package header).
 
+Methods: StefCal (scalar and 2x2 DI), CohJones (scalar and 2x2 DD: exact inverse of each
+antenna's direction block, data form), AllJones (scalar and 2x2 DD: diagonal J^H J, residual form).
+
 Schedule (Sect. 3.1): iterations are numbered k = 1, 2, ...; odd k take the GN step with the
 (block-)diagonal J^H J (eq. stefcal-matrix), even k take the LM step with lambda = 1, which for
 a (block-)diagonal approximation is the average of the current gains and the GN gains
@@ -15,7 +18,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .blocks import jones_blocks, scalar_blocks, dd_blocks
+from .blocks import dd_blocks, dd_jones_blocks, jones_blocks, scalar_blocks
 
 
 def _schedule_mix(k, g_old, g_gn, schedule):
@@ -61,16 +64,68 @@ def cohjones_step(g, vis, model, a1, a2, n_ant):
     return out, sing
 
 
-_STEPS = {'scalar': stefcal_scalar_step, 'jones': stefcal_jones_step, 'dd': cohjones_step}
+def alljones_step(g, vis, model, a1, a2, n_ant):
+    """One GN step of AllJones (Sect. 3.2.3, eq. stefcal:dd:unpol): the whole J^H J taken as its
+    diagonal, so the step goes through the residuals, g_p^(d) += c_p^(d) / A_p[d, d] with
+    c = sum conj(y^(d)) r.  A direction with no signal at an antenna (A_p[d, d] = 0) keeps its gain."""
+    b = dd_blocks(g, vis, model, a1, a2, n_ant)
+    a = np.real(np.diagonal(b['A'], axis1=1, axis2=2))           # [n, Nd]
+    sing = ~(a > 0)
+    out = np.where(sing, g, g + b['c'] / np.where(sing, 1.0, a))
+    return out, sing.any(axis=1)
+
+
+def cohjones_jones_step(G, vis, model, a1, a2, n_ant):
+    """One GN step of polarized CohJones (Sect. 4.4): per antenna [G^(1) .. G^(Nd)] = CD H^-1 with
+    the 2Nd x 2Nd H of blocks.dd_jones_blocks (the 4Nd x 4Nd operator block is R_H, whose inverse
+    is R_{H^-1}, App. B eq. RAB:LAB).  An antenna whose H is not positive definite keeps its gains."""
+    b = dd_jones_blocks(G, vis, model, a1, a2, n_ant)
+    nd = G.shape[1]
+    out = G.copy()
+    sing = np.zeros(n_ant, bool)
+    for p in range(n_ant):
+        try:
+            np.linalg.cholesky(b['H'][p])
+        except np.linalg.LinAlgError:
+            sing[p] = True
+            continue
+        X = np.linalg.solve(b['H'][p].T, b['CD'][p].T).T              # X H = CD
+        out[p] = np.stack([X[:, 2 * d:2 * d + 2] for d in range(nd)])
+    return out, sing
+
+
+def alljones_jones_step(G, vis, model, a1, a2, n_ant):
+    """One GN step of polarized AllJones (Sect. 4.4, eq. update:DD:diag:pol, product order as
+    [sum R Y^(d)H][sum Y^(d) Y^(d)H]^-1): dG_p^(d) = C^(d) H_p[d, d]^-1, per antenna and direction.
+    A (p, d) whose 2x2 block is singular keeps its gain."""
+    b = dd_jones_blocks(G, vis, model, a1, a2, n_ant)
+    nd = G.shape[1]
+    out = G.copy()
+    sing = np.zeros(n_ant, bool)
+    for p in range(n_ant):
+        for d in range(nd):
+            Hd = b['H'][p, 2 * d:2 * d + 2, 2 * d:2 * d + 2]
+            det = np.real(Hd[0, 0] * Hd[1, 1] - Hd[0, 1] * Hd[1, 0])
+            if not (det > 0 and np.real(Hd[0, 0]) > 0):
+                sing[p] = True
+                continue
+            out[p, d] = G[p, d] + b['C'][p][:, 2 * d:2 * d + 2] @ np.linalg.inv(Hd)
+    return out, sing
+
+
+_STEPS = {'scalar': stefcal_scalar_step, 'jones': stefcal_jones_step, 'dd': cohjones_step,
+          'dd_jones': cohjones_jones_step}
+_ALLJONES = {'dd': alljones_step, 'dd_jones': alljones_jones_step}
 
 
 def iterate(kind, g0, vis, model, a1, a2, n_ant, tol=1e-12, max_iter=1000, schedule='stefcal',
-            record=False):
-    """Run the diagonal iteration of ``kind`` on one interval.
+            record=False, method='cohjones'):
+    """Run the diagonal iteration of ``kind`` on one interval (for the DD kinds, ``method``
+    'cohjones' or 'alljones').
 
     Returns dict(g, iters, converged, singular, history(optional list of iterates)).
     """
-    step = _STEPS[kind]
+    step = _ALLJONES[kind] if method == 'alljones' else _STEPS[kind]
     g = np.asarray(g0, np.complex128).copy()
     hist = [g.copy()] if record else None
     sing = None
@@ -87,7 +142,7 @@ def iterate(kind, g0, vis, model, a1, a2, n_ant, tol=1e-12, max_iter=1000, sched
     return dict(g=g, iters=max_iter, converged=False, singular=sing, history=hist)
 
 
-def solve_batch(batch, tol=1e-12, max_iter=1000, schedule='stefcal', intervals=None, g0=None):
+def solve_batch(batch, tol=1e-12, max_iter=1000, schedule='stefcal', intervals=None, g0=None, method='cohjones'):
     """Diagonal iteration on every (or the listed) interval of a synth.Batch.
 
     Returns (gains like batch.g_true for the listed intervals, iters [k], converged [k]).
@@ -98,7 +153,7 @@ def solve_batch(batch, tol=1e-12, max_iter=1000, schedule='stefcal', intervals=N
     for i in idx:
         iv = batch.interval(int(i))
         r = iterate(batch.kind, start[iv['gain_slice']], iv['vis'], iv['model'], iv['ant1'], iv['ant2'],
-                    iv['n_ant'], tol=tol, max_iter=max_iter, schedule=schedule)
+                    iv['n_ant'], tol=tol, max_iter=max_iter, schedule=schedule, method=method)
         gs.append(r['g']); its.append(r['iters']); conv.append(r['converged'])
     return np.concatenate(gs), np.asarray(its), np.asarray(conv)
 
@@ -112,6 +167,9 @@ def chi2_interval(kind, g, vis, model, a1, a2):
         v = g[a1][None] * model * np.conj(g[a2])[None]
     elif kind == 'dd':
         v = np.einsum('bd,dsb,bd->sb', g[a1], model, np.conj(g[a2]))
+    elif kind == 'dd_jones':
+        v = sum(g[a1, d][None] @ model[d] @ np.conj(np.swapaxes(g[a2, d], -1, -2))[None]
+                for d in range(model.shape[0]))
     else:
         v = g[a1][None] @ model @ np.conj(np.swapaxes(g[a2], -1, -2))[None]
     r = vis - v

@@ -3,7 +3,7 @@
 Test infrastructure only (see the package header).
 
 chi^2 is unchanged by g_p -> g_p e^{i phi} for all p at once (Sect. 2.1, eq. cal:DI: the phase
-cancels in g_p m conj(g_q)); the DD problem has one such phase per direction and the 2x2 problem
+cancels in g_p m conj(g_q)); the DD problems (scalar and 2x2) have one such phase per direction and the 2x2 problem
 G_p -> G_p e^{i phi}.  Two solutions are compared after rotating the estimate onto the
 reference by the least-squares phase.
 """
@@ -18,6 +18,9 @@ def align(kind, g_est, g_ref):
     if kind == 'dd':
         ph = np.angle(np.sum(g_ref * np.conj(g_est), axis=0))       # [Nd]
         return g_est * np.exp(1j * ph)[None, :]
+    if kind == 'dd_jones':
+        ph = np.angle(np.sum(g_ref * np.conj(g_est), axis=(0, 2, 3)))   # [Nd]
+        return g_est * np.exp(1j * ph)[None, :, None, None]
     ph = np.angle(np.sum(g_ref * np.conj(g_est)))
     return g_est * np.exp(1j * ph)
 
@@ -39,6 +42,10 @@ def rel_error(kind, g_est, g_ref, n_ant=None, gain_off=None):
         r = g_ref[a:b].reshape(b - a, -1) if kind != 'dd' else g_ref[a:b]
         if kind == 'dd':
             e = np.abs(d) / np.abs(r)
+        elif kind == 'dd_jones':                 # per antenna and direction
+            nd = g_ref.shape[1]
+            e = (np.linalg.norm(d.reshape(b - a, nd, 4), axis=2)
+                 / np.linalg.norm(r.reshape(b - a, nd, 4), axis=2))
         else:
             e = np.linalg.norm(d, axis=1) / np.linalg.norm(r, axis=1)
         worst = max(worst, float(np.max(e)))

@@ -16,6 +16,7 @@ Parameter orderings:
   scalar DI      z = [g_1 .. g_n]
   scalar DD      z = [g_1^(1) .. g_1^(Nd), g_2^(1) ..]   (CAD ordering, Sect. 3.2)
   2x2 DI         z = [vec G_1, vec G_2, ..]  with vec stacking columns (App. B)
+  2x2 DD         z = [vec G_1^(1) .. vec G_1^(Nd), vec G_2^(1) ..]  (CAD ordering, Sect. 4.4)
 """
 from __future__ import annotations
 
@@ -37,6 +38,14 @@ def model_dd(g, m, a1, a2):
 def model_jones(G, M, a1, a2):
     """V = G_p M G_q^H (eq. RIME:pol); M [N_s, N_bl, 2, 2]."""
     return G[a1][None] @ M @ np.conj(np.swapaxes(G[a2], -1, -2))[None]
+
+
+def model_dd_jones(G, M, a1, a2):
+    """V = sum_d G_p^(d) M^(d) G_q^(d)H (Sect. 4.4); G [n_ant, Nd, 2, 2], M [Nd, N_s, N_bl, 2, 2]."""
+    V = 0
+    for d in range(M.shape[0]):
+        V = V + G[a1, d][None] @ M[d] @ np.conj(np.swapaxes(G[a2, d], -1, -2))[None]
+    return V
 
 
 def vec2(X):
@@ -116,6 +125,26 @@ def partials_jones(G, M, a1, a2):
     return Jk, Jc
 
 
+def partials_dd_jones(G, M, a1, a2):
+    """J_k, J_k* for 2x2 DD: each direction contributes the 2x2 DI blocks of ``partials_jones``
+    with its own model and gains; columns in CAD order ((j * Nd + d) * 4 + vec index)."""
+    nd, ns, nb = M.shape[:3]
+    n = G.shape[0]
+    I2 = np.eye(2, dtype=np.complex128)
+    Jk = np.zeros((ns * nb * 4, n * nd * 4), np.complex128)
+    Jc = np.zeros((ns * nb * 4, n * nd * 4), np.complex128)
+    for s in range(ns):
+        for b in range(nb):
+            p, q = int(a1[b]), int(a2[b])
+            r = (s * nb + b) * 4
+            for d in range(nd):
+                Y = M[d, s, b] @ np.conj(G[q, d]).T
+                cp, cq = 4 * (p * nd + d), 4 * (q * nd + d)
+                Jk[r:r + 4, cp:cp + 4] += np.kron(Y.T, I2)
+                Jc[r:r + 4, cq:cq + 4] += np.kron(I2, G[p, d] @ M[d, s, b]) @ COMMUTATION_2x2
+    return Jk, Jc
+
+
 def full_jacobian(Jk, Jc):
     """eq. JJ."""
     return np.block([[Jk, Jc], [np.conj(Jc), np.conj(Jk)]])
@@ -138,13 +167,15 @@ class Problem:
     # z <-> gains
     def to_z(self, g):
         g = np.asarray(g, np.complex128)
-        if self.kind == 'jones':
+        if self.kind in ('jones', 'dd_jones'):
             return vec2(g).reshape(-1)
         return g.reshape(-1)
 
     def from_z(self, z):
         if self.kind == 'jones':
             return unvec2(z.reshape(self.n_ant, 4))
+        if self.kind == 'dd_jones':
+            return unvec2(z.reshape(self.n_ant, self.n_dir, 4))
         if self.kind == 'dd':
             return z.reshape(self.n_ant, self.n_dir)
         return z.copy()
@@ -154,17 +185,21 @@ class Problem:
             return model_scalar(g, self.model, self.a1, self.a2)
         if self.kind == 'dd':
             return model_dd(g, self.model, self.a1, self.a2)
+        if self.kind == 'dd_jones':
+            return model_dd_jones(g, self.model, self.a1, self.a2)
         return model_jones(g, self.model, self.a1, self.a2)
 
     def residual_vec(self, g):
         r = self.vis - self.model_vis(g)
-        return vec2(r).reshape(-1) if self.kind == 'jones' else r.reshape(-1)
+        return vec2(r).reshape(-1) if self.kind in ('jones', 'dd_jones') else r.reshape(-1)
 
     def partials(self, g):
         if self.kind == 'scalar':
             return partials_scalar(g, self.model, self.a1, self.a2)
         if self.kind == 'dd':
             return partials_dd(g, self.model, self.a1, self.a2)
+        if self.kind == 'dd_jones':
+            return partials_dd_jones(g, self.model, self.a1, self.a2)
         return partials_jones(g, self.model, self.a1, self.a2)
 
     def jacobian(self, g):

@@ -273,8 +273,10 @@ def make_di_jones(seed=SEED, n_ant=64, n_t=60, n_chan=64, t_per=1, f_per=4, n_sr
 
 
 def make_dd(seed=SEED, n_ant=62, n_dir=9, n_t=120, n_chan=16, t_per=10, f_per=16, src_per_dir=3,
-            amp_sigma=0.2, sigma=0.02, grid_deg=1.0, cluster_deg=0.1, dtype=np.complex64, fmin=1.0e9, fmax=1.4e9):
-    """Direction-dependent scalar gains: n_dir clusters of point sources on a square grid."""
+            amp_sigma=0.2, sigma=0.02, grid_deg=1.0, cluster_deg=0.1, dtype=np.complex64, fmin=1.0e9, fmax=1.4e9,
+            log_flux=(-1.0, 1.0)):
+    """Direction-dependent scalar gains: n_dir clusters of point sources on a square grid, source
+    fluxes with log10 S uniform in ``log_flux``."""
     rng_sky = rng_for(seed, 3, 0)
     xy = antenna_positions(rng_sky, n_ant)
     a1, a2 = baseline_table(n_ant)
@@ -284,7 +286,7 @@ def make_dd(seed=SEED, n_ant=62, n_dir=9, n_t=120, n_chan=16, t_per=10, f_per=16
     freqs = np.linspace(fmin, fmax, n_chan)
     model_dirs = []
     for d in range(n_dir):
-        flux = 10.0 ** rng_sky.uniform(-1.0, 1.0, src_per_dir)
+        flux = 10.0 ** rng_sky.uniform(log_flux[0], log_flux[1], src_per_dir)
         l = cx[d] + rng_sky.uniform(-cluster_deg, cluster_deg, src_per_dir) * DEG
         m = cy[d] + rng_sky.uniform(-cluster_deg, cluster_deg, src_per_dir) * DEG
         model_dirs.append(np.einsum('fbs,s->fb', fringe(xy, a1, a2, l, m, freqs), flux))
