@@ -37,8 +37,18 @@ def directed_rows(vis, model, a1, a2, kind):
     return i, j, np.concatenate([d, np.conj(d)]), np.concatenate([m, np.conj(m)])
 
 
-def scalar_blocks(g, vis, model, a1, a2, n_ant):
-    """Scalar DI with intervals (eqs. JHJ:DI:tf, JHR:DI:tf) and the data form (eq. ghat).
+def directed_weights(weights, n_dir_rows):
+    """Per-row weights w_pqs (Sect. 2.4, a diagonal W in eq. LSmin:w) for the directed rows of
+    ``directed_rows``: a stored row and its conjugate row share one weight.  None: unit weights."""
+    if weights is None:
+        return np.ones(n_dir_rows)
+    w = np.asarray(weights, np.float64).reshape(-1)
+    return np.concatenate([w, w])
+
+
+def scalar_blocks(g, vis, model, a1, a2, n_ant, weights=None):
+    """Scalar DI with intervals (eqs. JHJ:DI:tf, JHR:DI:tf) and the data form (eq. ghat); with
+    per-row weights, eqs. JHJ:DI:tfw and JHR:DI:tfw (each sum over rows carries w_iqs).
 
     Returns dict with
       A    [n]      diag of the top-left block: sum_{q!=i,s} |y_iqs|^2, y_iqs = m_iqs conj(g_q)
@@ -48,22 +58,23 @@ def scalar_blocks(g, vis, model, a1, a2, n_ant):
     """
     g = np.asarray(g, np.complex128)
     i, j, d, m = directed_rows(vis, model, a1, a2, 'scalar')
+    w = directed_weights(weights, i.shape[0])
     y = m * np.conj(g[j])
     r = d - g[i] * y
     A = np.zeros(n_ant); c = np.zeros(n_ant, np.complex128); cd = np.zeros(n_ant, np.complex128)
-    np.add.at(A, i, np.abs(y) ** 2)
-    np.add.at(c, i, np.conj(y) * r)
-    np.add.at(cd, i, np.conj(y) * d)
+    np.add.at(A, i, w * np.abs(y) ** 2)
+    np.add.at(c, i, w * np.conj(y) * r)
+    np.add.at(cd, i, w * np.conj(y) * d)
     # off-diagonal block: pair each directed row ij s with its mirror ji s
     half = y.shape[0] // 2
     y_ij, y_ji = y[:half], y[half:]
     B = np.zeros((n_ant, n_ant), np.complex128)
-    np.add.at(B, (i[:half], j[:half]), np.conj(y_ij) * np.conj(y_ji))
-    np.add.at(B, (j[:half], i[:half]), np.conj(y_ij) * np.conj(y_ji))
+    np.add.at(B, (i[:half], j[:half]), w[:half] * np.conj(y_ij) * np.conj(y_ji))
+    np.add.at(B, (j[:half], i[:half]), w[:half] * np.conj(y_ij) * np.conj(y_ji))
     return dict(A=A, B=B, c=c, cd=cd)
 
 
-def jones_blocks(G, vis, model, a1, a2, n_ant):
+def jones_blocks(G, vis, model, a1, a2, n_ant, weights=None):
     """2x2 DI: the diagonal operator blocks of eq. JHJ:pol and the top half of J^H R.
 
     Y_iq = M_iq G_q^H, R_iq = D_iq - G_i Y_iq.
@@ -73,15 +84,16 @@ def jones_blocks(G, vis, model, a1, a2, n_ant):
     """
     G = np.asarray(G, np.complex128)
     i, j, D, M = directed_rows(vis, model, a1, a2, 'jones')
+    w = directed_weights(weights, i.shape[0])[:, None, None]
     Y = M @ np.conj(np.swapaxes(G[j], -1, -2))
     YH = np.conj(np.swapaxes(Y, -1, -2))
     R = D - G[i] @ Y
     H = np.zeros((n_ant, 2, 2), np.complex128)
     C = np.zeros((n_ant, 2, 2), np.complex128)
     CD = np.zeros((n_ant, 2, 2), np.complex128)
-    np.add.at(H, i, Y @ YH)
-    np.add.at(C, i, R @ YH)
-    np.add.at(CD, i, D @ YH)
+    np.add.at(H, i, w * (Y @ YH))
+    np.add.at(C, i, w * (R @ YH))
+    np.add.at(CD, i, w * (D @ YH))
     return dict(H=H, C=C, CD=CD)
 
 
@@ -127,14 +139,15 @@ def dd_jones_blocks(G, vis, model, a1, a2, n_ant):
     Y = M @ np.conj(np.swapaxes(G[j], -1, -2)).transpose(1, 0, 2, 3)          # [Nd, rows, 2, 2]
     V = np.sum(G[i].transpose(1, 0, 2, 3) @ Y, axis=0)
     R = D - V
-    Ycat = np.concatenate(list(Y), axis=-2)                                     # [rows, 2Nd, 2]
-    YcatH = np.conj(np.swapaxes(Ycat, -1, -2))                                  # [rows, 2, 2Nd]
     H = np.zeros((n_ant, 2 * nd, 2 * nd), np.complex128)
     C = np.zeros((n_ant, 2, 2 * nd), np.complex128)
     CD = np.zeros((n_ant, 2, 2 * nd), np.complex128)
-    np.add.at(H, i, Ycat @ YcatH)
-    np.add.at(C, i, R @ YcatH)
-    np.add.at(CD, i, D @ YcatH)
+    for p in range(n_ant):                    # rows whose first antenna is p, summed as one product
+        sel = i == p
+        A = Y[:, sel].transpose(0, 2, 1, 3).reshape(2 * nd, -1)   # [Y^(1); ..; Y^(Nd)] side by side over rows
+        H[p] = A @ A.conj().T
+        C[p] = R[sel].transpose(1, 0, 2).reshape(2, -1) @ A.conj().T
+        CD[p] = D[sel].transpose(1, 0, 2).reshape(2, -1) @ A.conj().T
     return dict(H=H, C=C, CD=CD)
 
 
@@ -164,7 +177,7 @@ def _vec(X):
     return np.stack([X[..., 0, 0], X[..., 1, 0], X[..., 0, 1], X[..., 1, 1]], axis=-1)
 
 
-def jones_jhj_full(G, vis, model, a1, a2, n_ant):
+def jones_jhj_full(G, vis, model, a1, a2, n_ant, weights=None):
     """The whole J^H J and J^H R of the 2x2 DI problem, off-diagonal antenna blocks included.
 
     Sect. 4.2 eq. JHJ:pol with the 4x4 operator forms of App. B, over the directed rows [pq],
@@ -175,11 +188,12 @@ def jones_jhj_full(G, vis, model, a1, a2, n_ant):
       bottom-left (i, j) sum L_{Y_ij} R_{Y_ji}, i != j
       bottom-right (i,i) sum_{q != i} L_{Y_iq Y_iq^H}
     J^H R: top vec(sum_q R_iq Y_iq^H) (the product order read from R_A X = X A), bottom
-    vec((sum_q R_iq Y_iq^H)^H).
+    vec((sum_q R_iq Y_iq^H)^H).  With per-row weights every sum carries w_iqs (J^H W J, J^H W R).
     Returns (JHJ [8n, 8n], JHR [8n]) as complex128.
     """
     G = np.asarray(G, np.complex128)
     i, j, D, M = directed_rows(vis, model, a1, a2, 'jones')
+    w = directed_weights(weights, i.shape[0])[:, None, None]
     half = i.shape[0] // 2
     mirror = np.concatenate([np.arange(half, 2 * half), np.arange(0, half)])   # row (j, i) of row (i, j)
     Y = M @ np.conj(np.swapaxes(G[j], -1, -2))
@@ -190,12 +204,12 @@ def jones_jhj_full(G, vis, model, a1, a2, n_ant):
     BR = np.zeros((n, 4, 4), np.complex128)
     TR = np.zeros((n, n, 4, 4), np.complex128)
     BL = np.zeros((n, n, 4, 4), np.complex128)
-    np.add.at(TL, i, op_R4(Y @ YH))
-    np.add.at(BR, i, op_L4(Y @ YH))
-    np.add.at(TR, (i, j), op_R4(YH) @ op_L4(YH[mirror]))
-    np.add.at(BL, (i, j), op_L4(Y) @ op_R4(Y[mirror]))
+    np.add.at(TL, i, w * op_R4(Y @ YH))
+    np.add.at(BR, i, w * op_L4(Y @ YH))
+    np.add.at(TR, (i, j), w * (op_R4(YH) @ op_L4(YH[mirror])))
+    np.add.at(BL, (i, j), w * (op_L4(Y) @ op_R4(Y[mirror])))
     C = np.zeros((n, 2, 2), np.complex128)
-    np.add.at(C, i, R @ YH)
+    np.add.at(C, i, w * (R @ YH))
     H = np.zeros((8 * n, 8 * n), np.complex128)
     for p in range(n):
         H[4 * p:4 * p + 4, 4 * p:4 * p + 4] = TL[p]
@@ -207,11 +221,11 @@ def jones_jhj_full(G, vis, model, a1, a2, n_ant):
     return H, b
 
 
-def scalar_jhj_full(g, vis, model, a1, a2, n_ant):
+def scalar_jhj_full(g, vis, model, a1, a2, n_ant, weights=None):
     """The whole J^H J and J^H r of the scalar DI problem (eq. JHJ:DI:ABCD / eq. JHJ:DI with the
     sample sums of eq. JHJ:DI:tf, and eq. JHR:DI), ordering [g; conj g].  Returns (JHJ [2n, 2n],
     JHR [2n])."""
-    blk = scalar_blocks(g, vis, model, a1, a2, n_ant)
+    blk = scalar_blocks(g, vis, model, a1, a2, n_ant, weights)
     A = np.diag(blk['A']).astype(np.complex128)
     B = blk['B']
     H = np.block([[A, B], [np.conj(B), A]])

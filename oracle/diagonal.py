@@ -27,20 +27,20 @@ def _schedule_mix(k, g_old, g_gn, schedule):
     return 0.5 * (g_old + g_gn)
 
 
-def stefcal_scalar_step(g, vis, model, a1, a2, n_ant):
+def stefcal_scalar_step(g, vis, model, a1, a2, n_ant, weights=None):
     """One GN step of eq. stefcal: g_p = (sum conj(y) y)^-1 sum conj(y) d.
 
     Antennas with no data (A_p = 0) keep their gain; returns (g_gn, singular mask).
     """
-    b = scalar_blocks(g, vis, model, a1, a2, n_ant)
+    b = scalar_blocks(g, vis, model, a1, a2, n_ant, weights)
     sing = ~(b['A'] > 0)
     g_gn = np.where(sing, g, b['cd'] / np.where(sing, 1.0, b['A']))
     return g_gn, sing
 
 
-def stefcal_jones_step(G, vis, model, a1, a2, n_ant):
+def stefcal_jones_step(G, vis, model, a1, a2, n_ant, weights=None):
     """One GN step of the polarized update (eq. update:DI:diag:pol, order [sum D Y^H][sum Y Y^H]^-1)."""
-    b = jones_blocks(G, vis, model, a1, a2, n_ant)
+    b = jones_blocks(G, vis, model, a1, a2, n_ant, weights)
     H = b['H']
     det = np.real(H[:, 0, 0] * H[:, 1, 1] - H[:, 0, 1] * H[:, 1, 0])
     sing = ~(det > 0)
@@ -119,9 +119,9 @@ _ALLJONES = {'dd': alljones_step, 'dd_jones': alljones_jones_step}
 
 
 def iterate(kind, g0, vis, model, a1, a2, n_ant, tol=1e-12, max_iter=1000, schedule='stefcal',
-            record=False, method='cohjones'):
+            record=False, method='cohjones', weights=None):
     """Run the diagonal iteration of ``kind`` on one interval (for the DD kinds, ``method``
-    'cohjones' or 'alljones').
+    'cohjones' or 'alljones'; per-row ``weights`` [N_s, N_bl] for the DI kinds, Sect. 2.4).
 
     Returns dict(g, iters, converged, singular, history(optional list of iterates)).
     """
@@ -130,7 +130,8 @@ def iterate(kind, g0, vis, model, a1, a2, n_ant, tol=1e-12, max_iter=1000, sched
     hist = [g.copy()] if record else None
     sing = None
     for k in range(1, max_iter + 1):
-        g_gn, sing = step(g, vis, model, a1, a2, n_ant)
+        g_gn, sing = (step(g, vis, model, a1, a2, n_ant) if weights is None
+                      else step(g, vis, model, a1, a2, n_ant, weights))
         g_new = _schedule_mix(k, g, g_gn, schedule)
         dn = np.linalg.norm((g_new - g).ravel())
         nn = np.linalg.norm(g_new.ravel())
@@ -153,13 +154,15 @@ def solve_batch(batch, tol=1e-12, max_iter=1000, schedule='stefcal', intervals=N
     for i in idx:
         iv = batch.interval(int(i))
         r = iterate(batch.kind, start[iv['gain_slice']], iv['vis'], iv['model'], iv['ant1'], iv['ant2'],
-                    iv['n_ant'], tol=tol, max_iter=max_iter, schedule=schedule, method=method)
+                    iv['n_ant'], tol=tol, max_iter=max_iter, schedule=schedule, method=method,
+                    weights=iv.get('weights'))
         gs.append(r['g']); its.append(r['iters']); conv.append(r['converged'])
     return np.concatenate(gs), np.asarray(its), np.asarray(conv)
 
 
-def chi2_interval(kind, g, vis, model, a1, a2):
-    """chi^2 = sum |r|^2 over the interval (eq. cal:DI:tf / cal:dd:unpol / cal:DI:pol, squared norm)."""
+def chi2_interval(kind, g, vis, model, a1, a2, weights=None):
+    """chi^2 = sum |r|^2 over the interval (eq. cal:DI:tf / cal:dd:unpol / cal:DI:pol, squared norm);
+    with per-row weights sum w |r|^2 (eq. LSmin:w with a diagonal W)."""
     g = np.asarray(g, np.complex128)
     vis = np.asarray(vis, np.complex128); model = np.asarray(model, np.complex128)
     a1 = np.asarray(a1, np.int64); a2 = np.asarray(a2, np.int64)
@@ -172,5 +175,7 @@ def chi2_interval(kind, g, vis, model, a1, a2):
                 for d in range(model.shape[0]))
     else:
         v = g[a1][None] @ model @ np.conj(np.swapaxes(g[a2], -1, -2))[None]
-    r = vis - v
-    return float(np.sum(np.abs(r) ** 2))
+    r = np.abs(vis - v) ** 2
+    if weights is not None:
+        r = r * np.asarray(weights, np.float64).reshape(r.shape[:2] + (1,) * (r.ndim - 2))
+    return float(np.sum(r))

@@ -155,8 +155,10 @@ def full_jacobian(Jk, Jc):
 class Problem:
     """One solution interval in a uniform interface for the explicit-Jacobian solvers."""
 
-    def __init__(self, kind, vis, model, a1, a2, n_ant, n_dir=1):
+    def __init__(self, kind, vis, model, a1, a2, n_ant, n_dir=1, weights=None):
         self.kind = kind
+        # per-row weights w_pqs [N_s, N_bl] (Sect. 2.4: a diagonal W in eq. LSmin:w); None: unit
+        self.weights = None if weights is None else np.asarray(weights, np.float64)
         self.a1 = np.asarray(a1, np.int64)
         self.a2 = np.asarray(a2, np.int64)
         self.n_ant = int(n_ant)
@@ -205,16 +207,28 @@ class Problem:
     def jacobian(self, g):
         return full_jacobian(*self.partials(g))
 
+    def row_weights(self):
+        """The diagonal of W over the entries of residual_vec (4 per row for the 2x2 kinds)."""
+        if self.weights is None:
+            return None
+        w = self.weights.reshape(-1)
+        return np.repeat(w, 4) if self.kind in ('jones', 'dd_jones') else w
+
     def chi2(self, g):
         r = self.residual_vec(g)
-        return float(np.real(np.vdot(r, r)))
+        w = self.row_weights()
+        return float(np.real(np.vdot(r, r if w is None else w * r)))
 
     def normal_equations(self, g):
-        """(J^H J, J^H r_aug) at g, eq. GN / eq. LM ingredients."""
+        """(J^H W J, J^H W r_aug) at g, eq. GN / eq. LM (eq. LM:W with weights) ingredients."""
         J = self.jacobian(g)
         r = self.residual_vec(g)
         raug = np.concatenate([r, np.conj(r)])
-        return J.conj().T @ J, J.conj().T @ raug
+        w = self.row_weights()
+        if w is None:
+            return J.conj().T @ J, J.conj().T @ raug
+        w2 = np.concatenate([w, w])
+        return J.conj().T @ (w2[:, None] * J), J.conj().T @ (w2 * raug)
 
 
 # ----------------------------------------------------------------------------- solvers (App. C)
@@ -319,15 +333,15 @@ class ClosedFormProblem(Problem):
     blocks.jones_jhj_full) instead of the explicit J, so that intervals of 64 antennas stay cheap.
     Same interface and ordering ([z; conj z]) as Problem."""
 
-    def __init__(self, kind, vis, model, a1, a2, n_ant):
+    def __init__(self, kind, vis, model, a1, a2, n_ant, weights=None):
         assert kind in ('scalar', 'jones')
-        super().__init__(kind, vis, model, a1, a2, n_ant)
+        super().__init__(kind, vis, model, a1, a2, n_ant, weights=weights)
 
     def normal_equations(self, g):
         from . import blocks
         if self.kind == 'scalar':
-            return blocks.scalar_jhj_full(g, self.vis, self.model, self.a1, self.a2, self.n_ant)
-        H, b = blocks.jones_jhj_full(g, self.vis, self.model, self.a1, self.a2, self.n_ant)
+            return blocks.scalar_jhj_full(g, self.vis, self.model, self.a1, self.a2, self.n_ant, self.weights)
+        H, b = blocks.jones_jhj_full(g, self.vis, self.model, self.a1, self.a2, self.n_ant, self.weights)
         T = paper_to_wirtinger_order(self.n_ant)
         return T.T @ H @ T, T.T @ b
 

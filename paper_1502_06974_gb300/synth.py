@@ -39,9 +39,10 @@ def rng_for(seed: int, *keys: int) -> np.random.Generator:
 @dataclass
 class Batch:
     """A set of independent solution intervals sharing one data layout."""
-    kind: str                      # 'scalar' | 'jones' | 'dd'
-    vis: np.ndarray                # scalar/dd: [rows]; jones: [rows, 2, 2]
-    model: np.ndarray              # scalar: [rows]; jones: [rows, 2, 2]; dd: [n_dir, rows]
+    kind: str                      # 'scalar' | 'jones' | 'dd' | 'dd_jones'
+    vis: np.ndarray                # scalar/dd: [rows]; jones/dd_jones: [rows, 2, 2]
+    model: np.ndarray              # scalar: [rows]; jones: [rows, 2, 2]; dd: [n_dir, rows];
+                                   # dd_jones: [n_dir, rows, 2, 2]
     ant1: np.ndarray               # int32 [n_bl_total]
     ant2: np.ndarray               # int32 [n_bl_total]
     row_off: np.ndarray            # int64 [n_int]
@@ -50,9 +51,11 @@ class Batch:
     bl_off: np.ndarray             # int32 [n_int]
     n_ant: np.ndarray              # int32 [n_int]
     gain_off: np.ndarray           # int32 [n_int]
-    g_true: np.ndarray             # scalar: [n_gain]; jones: [n_gain,2,2]; dd: [n_gain, n_dir]
+    g_true: np.ndarray             # scalar: [n_gain]; jones: [n_gain,2,2]; dd: [n_gain, n_dir];
+                                   # dd_jones: [n_gain, n_dir, 2, 2]
     n_dir: int = 1
     meta: dict = field(default_factory=dict)
+    weights: Optional[np.ndarray] = None   # per-row non-negative weights [rows] (None: unit)
 
     @property
     def n_int(self) -> int:
@@ -75,6 +78,11 @@ class Batch:
             return g
         if self.kind == 'dd':
             return np.ones((self.n_gain, self.n_dir), dtype=self.vis.dtype)
+        if self.kind == 'dd_jones':
+            g = np.zeros((self.n_gain, self.n_dir, 2, 2), dtype=self.vis.dtype)
+            g[..., 0, 0] = 1.0
+            g[..., 1, 1] = 1.0
+            return g
         return np.ones(self.n_gain, dtype=self.vis.dtype)
 
     def interval(self, i: int) -> dict:
@@ -84,11 +92,14 @@ class Batch:
         sl = slice(r0, r0 + ns * nb)
         if self.kind == 'dd':
             model = self.model[:, sl].reshape(self.n_dir, ns, nb)
+        elif self.kind == 'dd_jones':
+            model = self.model[:, sl].reshape(self.n_dir, ns, nb, 2, 2)
         else:
             model = self.model[sl].reshape((ns, nb) + self.model.shape[1:])
         return dict(vis=self.vis[sl].reshape((ns, nb) + self.vis.shape[1:]), model=model,
                     ant1=self.ant1[b0:b0 + nb], ant2=self.ant2[b0:b0 + nb], n_ant=na,
-                    g_true=self.g_true[g0:g0 + na], gain_slice=slice(g0, g0 + na))
+                    g_true=self.g_true[g0:g0 + na], gain_slice=slice(g0, g0 + na),
+                    weights=None if self.weights is None else self.weights[sl].reshape(ns, nb))
 
     def subset(self, idx) -> 'Batch':
         """A new batch holding only intervals ``idx`` (data copied, compacted)."""
@@ -110,12 +121,13 @@ class Batch:
                 bls.append(np.arange(key[0], key[0] + key[1])); nb_tot += key[1]
             bl_off.append(bl_map[key])
         rows = np.concatenate(rows); grows = np.concatenate(grows); bls = np.concatenate(bls)
-        model = self.model[:, rows] if self.kind == 'dd' else self.model[rows]
+        model = self.model[:, rows] if self.kind in ('dd', 'dd_jones') else self.model[rows]
         return Batch(self.kind, np.ascontiguousarray(self.vis[rows]), np.ascontiguousarray(model),
                      np.ascontiguousarray(self.ant1[bls]), np.ascontiguousarray(self.ant2[bls]),
                      np.asarray(row_off, np.int64), self.n_samp[idx].copy(), self.n_bl[idx].copy(),
                      np.asarray(bl_off, np.int32), self.n_ant[idx].copy(), np.asarray(gain_off, np.int32),
-                     np.ascontiguousarray(self.g_true[grows]), self.n_dir, dict(self.meta))
+                     np.ascontiguousarray(self.g_true[grows]), self.n_dir, dict(self.meta),
+                     None if self.weights is None else np.ascontiguousarray(self.weights[rows]))
 
 
 # ----------------------------------------------------------------------------- array and sky
@@ -154,6 +166,24 @@ def polarized_sky(rng, n_src, frac_sigma=0.05, lm_max_deg=2.0):
     l = rng.uniform(-lm_max_deg, lm_max_deg, n_src) * DEG
     m = rng.uniform(-lm_max_deg, lm_max_deg, n_src) * DEG
     B = np.empty((n_src, 2, 2), dtype=np.complex128)                  # linear-feed coherency
+    B[:, 0, 0] = I + Q
+    B[:, 0, 1] = U + 1j * V
+    B[:, 1, 0] = U - 1j * V
+    B[:, 1, 1] = I - Q
+    return B, l, m
+
+
+def polarized_sky_strong(rng, n_src, p_lo=0.3, p_hi=0.7, lm_max_deg=2.0):
+    """Strongly polarized point sources: fractional polarization p ~ U(p_lo, p_hi) along a direction
+    uniform on the Poincare sphere, (Q, U, V) = I p n; linear-feed coherencies as polarized_sky."""
+    I = 10.0 ** rng.uniform(-1.0, 1.0, n_src)
+    n = rng.normal(0.0, 1.0, (n_src, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    frac = rng.uniform(p_lo, p_hi, n_src)
+    Q, U, V = (I * frac * n[:, k] for k in range(3))
+    l = rng.uniform(-lm_max_deg, lm_max_deg, n_src) * DEG
+    m = rng.uniform(-lm_max_deg, lm_max_deg, n_src) * DEG
+    B = np.empty((n_src, 2, 2), dtype=np.complex128)
     B[:, 0, 0] = I + Q
     B[:, 0, 1] = U + 1j * V
     B[:, 1, 0] = U - 1j * V
@@ -211,6 +241,8 @@ def _finish(kind, vis_list, model_list, a1, a2, n_samp, n_bl, bl_off, n_ant, g_l
     vis = np.concatenate([v.reshape((-1,) + v.shape[2:]) for v in vis_list]).astype(dtype)
     if kind == 'dd':
         model = np.concatenate([m.reshape(m.shape[0], -1) for m in model_list], axis=1).astype(dtype)
+    elif kind == 'dd_jones':
+        model = np.concatenate([m.reshape((m.shape[0], -1, 2, 2)) for m in model_list], axis=1).astype(dtype)
     else:
         model = np.concatenate([m.reshape((-1,) + m.shape[2:]) for m in model_list]).astype(dtype)
     g_true = np.concatenate(g_list).astype(np.complex128)
@@ -303,6 +335,53 @@ def make_dd(seed=SEED, n_ant=62, n_dir=9, n_t=120, n_chan=16, t_per=10, f_per=16
             vis_l.append(vis); mod_l.append(mod); g_l.append(g)
     n = len(vis_l)
     return _finish('dd', vis_l, mod_l, a1, a2, [t_per * f_per] * n, [len(a1)] * n, [0] * n, [n_ant] * n,
+                   g_l, dtype, n_dir=n_dir, meta=dict(sigma=sigma))
+
+
+def simulate_dd_jones(G, model, a1, a2):
+    """V = sum_d G_p^(d) M^(d) G_q^(d)H; G [n_ant, n_dir, 2, 2], model [n_dir, n_samp, n_bl, 2, 2]."""
+    V = 0
+    for d in range(model.shape[0]):
+        V = V + G[a1, d] @ model[d] @ np.conj(np.swapaxes(G[a2, d], -1, -2))
+    return V
+
+
+def make_dd_jones(seed=SEED, n_ant=62, n_dir=9, n_t=120, n_chan=16, t_per=10, f_per=16, src_per_dir=3,
+                  amp_sigma=0.2, leak_sigma=0.02, pol_frac=(0.3, 0.7), sigma=0.02, grid_deg=1.0, cluster_deg=0.1,
+                  dtype=np.complex64, fmin=1.0e9, fmax=1.4e9, log_flux=(-0.5, 0.5)):
+    """Direction-dependent 2x2 gains: the geometry of make_dd (n_dir clusters on a square grid) with
+    strongly polarized sources (polarized_sky_strong, fractional polarization in pol_frac) and a
+    2x2 gain per antenna and direction (diagonal 1 + N(0, amp_sigma) amplitudes with uniform
+    phases, leakage CN(0, leak_sigma))."""
+    rng_sky = rng_for(seed, 6, 0)
+    xy = antenna_positions(rng_sky, n_ant)
+    a1, a2 = baseline_table(n_ant)
+    side = int(np.ceil(np.sqrt(n_dir)))
+    cx = (np.arange(n_dir) % side - (side - 1) / 2.0) * grid_deg * DEG
+    cy = (np.arange(n_dir) // side - (side - 1) / 2.0) * grid_deg * DEG
+    freqs = np.linspace(fmin, fmax, n_chan)
+    model_dirs = []
+    for d in range(n_dir):
+        B, _, _ = polarized_sky_strong(rng_sky, src_per_dir, pol_frac[0], pol_frac[1])
+        B *= (10.0 ** rng_sky.uniform(log_flux[0], log_flux[1], src_per_dir))[:, None, None] / np.real(
+            B[:, 0, 0] + B[:, 1, 1])[:, None, None] * 2.0
+        l = cx[d] + rng_sky.uniform(-cluster_deg, cluster_deg, src_per_dir) * DEG
+        m = cy[d] + rng_sky.uniform(-cluster_deg, cluster_deg, src_per_dir) * DEG
+        model_dirs.append(np.einsum('fbs,sij->fbij', fringe(xy, a1, a2, l, m, freqs), B))
+    model_f = np.stack(model_dirs)                                                  # [d, f, b, 2, 2]
+    vis_l, mod_l, g_l = [], [], []
+    n_tb, n_fb = n_t // t_per, n_chan // f_per
+    for it in range(n_tb):
+        for jf in range(n_fb):
+            i = it * n_fb + jf
+            r = rng_for(seed, 6, 1 + i)
+            g = np.stack([jones_gains(r, n_ant, amp_sigma, leak_sigma) for _ in range(n_dir)], axis=1)
+            mod = np.repeat(model_f[:, None, jf * f_per:(jf + 1) * f_per], t_per, axis=1).reshape(
+                n_dir, t_per * f_per, -1, 2, 2)
+            vis = simulate_dd_jones(g, mod, a1, a2) + complex_noise(r, mod.shape[1:], sigma)
+            vis_l.append(vis); mod_l.append(mod); g_l.append(g)
+    n = len(vis_l)
+    return _finish('dd_jones', vis_l, mod_l, a1, a2, [t_per * f_per] * n, [len(a1)] * n, [0] * n, [n_ant] * n,
                    g_l, dtype, n_dir=n_dir, meta=dict(sigma=sigma))
 
 
