@@ -202,6 +202,43 @@ int gc_calibrate_dd_cohjones(const void* vis, const void* model, const gc_layout
                              int32_t* status_out, void* stream);
 
 /*
+ * Direction-dependent scalar gains: AllJones (Sect. 3.2.3, eq. stefcal:dd:unpol).  The whole
+ * J^H J is taken as its diagonal, so the step goes through the residuals:
+ *   g_p^(d) += c_p^(d) / sum_{q,s} |y^(d)|^2,   c_p^(d) = sum_{q,s} conj(y^(d)) r_pqs,
+ * every antenna and direction independently.  c is formed from the same per-baseline moments as
+ * CohJones (c_p = b_p - A_p g_p, an identity of the residual sum), in float-float.  A direction
+ * with no signal at an antenna keeps its gain and sets GC_ST_SINGULAR_FLAG.  Same schedule
+ * (odd iterations the step, even ones its average with the current gains), layout, arguments and
+ * limits as gc_calibrate_dd_cohjones.
+ */
+int gc_calibrate_dd_alljones(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                             const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                             int32_t* status_out, void* stream);
+
+/*
+ * Direction-dependent 2x2 gains (Sect. 4.4, eqs. JHJ:DD:pol, JHR:DD:pol), with Y^(d) = M^(d) G_q^(d)H.
+ * Per antenna p, H (2Nd x 2Nd, 2x2 block (c, d) = sum_{q,s} Y^(c) Y^(d)H) and
+ * CD = [.. sum_{q,s} D Y^(d)H ..] (2 x 2Nd); the antenna's normal equations are
+ * [G^(1) .. G^(Nd)] H = CD (the 4Nd x 4Nd operator block R_H, inverted as R_{H^-1}).
+ *   gc_calibrate_dd_cohjones2x2: polarized CohJones, [G^(1) .. G^(Nd)] = CD H^-1 (data form), H
+ *     factored in FP32 and the solution refined once against a float-float residual; FP64 when an
+ *     FP32 pivot fails; an antenna FP64 cannot factor keeps its gains (GC_ST_SINGULAR_FLAG).
+ *   gc_calibrate_dd_alljones2x2: polarized AllJones (eq. update:DD:diag:pol),
+ *     G^(d) += [sum R Y^(d)H] [sum Y^(d) Y^(d)H]^-1 per antenna and direction (residual form).
+ * The sums over samples are taken once per interval as the Hermitian Gram matrix of each
+ * baseline's stacked row [D, M^(1) .. M^(Nd)] (16 (Nd + 1)(Nd + 2) / 2 complex values per baseline).
+ *   vis [n_rows][2][2] complex64 (row-major 2x2); model [n_dir][n_rows][2][2]; gains
+ *   [n_gain][n_dir][2][2].  vis and model 16-byte aligned (device buffers; GC_ERR_ARG otherwise).
+ * Same schedule, options, outputs and limits as gc_calibrate_dd_cohjones; only GC_DTYPE_C64.
+ */
+int gc_calibrate_dd_cohjones2x2(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                                const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                                int32_t* status_out, void* stream);
+int gc_calibrate_dd_alljones2x2(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                                const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                                int32_t* status_out, void* stream);
+
+/*
  * One accumulation pass, no update: for every gain slot p of every interval, the top half of
  * J^H d and the diagonal block of J^H J at the given gains (device pointers, work on `stream`,
  * asynchronous).

@@ -23,7 +23,8 @@ GC_MAX_ANT, GC_MAX_DIR = 1024, 10
 
 # Every symbol include/gaincal.h declares (checked by the CPU test suite).
 EXPORTS = [
-    'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones',
+    'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones', 'gc_calibrate_dd_alljones',
+    'gc_calibrate_dd_cohjones2x2', 'gc_calibrate_dd_alljones2x2',
     'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2', 'gc_jhj_jhr_di_jones2x2_noalloc',
     'gc_chi2_di_jones2x2', 'gc_mlp_work_floats', 'gc_mlp_forward_f32', 'gc_mlp_grad_f32', 'gc_mlp_train_step',
     'gc_mlp_infer_bf16', 'gc_ws_features_jones', 'gc_ws_target_jones', 'gc_calibrate_di_jones2x2_warm',
@@ -82,7 +83,8 @@ def lib() -> C.CDLL:
                                "(there is no CPU fallback)")
         L = C.CDLL(LIB_PATH)
         cal = [_p, _p, C.POINTER(GcLayout), _p, C.POINTER(GcOptions), _p, _p, _p, _p]
-        for name in ('gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones'):
+        for name in ('gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones',
+                     'gc_calibrate_dd_alljones', 'gc_calibrate_dd_cohjones2x2', 'gc_calibrate_dd_alljones2x2'):
             f = getattr(L, name)
             f.argtypes = cal
             f.restype = C.c_int

@@ -164,6 +164,28 @@ def calibrate_dd_cohjones(vis, model, layout, gains, tol=1e-6, max_iter=1000, sc
                       host_buffers, profile=profile, path=path)
 
 
+def calibrate_dd_alljones(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
+                          compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO):
+    """AllJones on DD scalar gains (gc_calibrate_dd_alljones); same layout as calibrate_dd_cohjones."""
+    return _calibrate('gc_calibrate_dd_alljones', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
+                      host_buffers, profile=profile, path=path)
+
+
+def calibrate_dd_cohjones2x2(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
+                             compute_chi2=False, host_buffers=False, profile=False):
+    """Polarized CohJones (gc_calibrate_dd_cohjones2x2); vis [rows, 2, 2], model [n_dir, rows, 2, 2],
+    gains [n_gain, n_dir, 2, 2], all complex64."""
+    return _calibrate('gc_calibrate_dd_cohjones2x2', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
+                      host_buffers, profile=profile)
+
+
+def calibrate_dd_alljones2x2(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
+                             compute_chi2=False, host_buffers=False, profile=False):
+    """Polarized AllJones (gc_calibrate_dd_alljones2x2); same layout as calibrate_dd_cohjones2x2."""
+    return _calibrate('gc_calibrate_dd_alljones2x2', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
+                      host_buffers, profile=profile)
+
+
 def _jhj_jhr(fn_name, vis, model, layout, gains, jones):
     for t, n in ((vis, 'vis'), (model, 'model'), (gains, 'gains')):
         _check_tensor(t, n, False)

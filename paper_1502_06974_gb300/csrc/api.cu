@@ -1491,6 +1491,7 @@ int gc_release(void) {
           c = gc::DIPlan{};
         }
   gc::dd_release();
+  gc::ddpol_release();
   gc::res_release();
   gc::g_tune.clear();
   if (gc::g_pinned_flag) { cudaFreeHost(gc::g_pinned_flag); gc::g_pinned_flag = nullptr; }

@@ -21,72 +21,19 @@
 #include <map>
 #include <vector>
 
-#include "common.cuh"
 #include "dd.h"
-#include "internal.h"
+#include "dd_common.cuh"
 
 namespace gc {
 
 constexpr int kMomBl = 32;      // baselines per moment CTA
 constexpr int kMomLanes = 8;    // sample lanes per baseline in the moment CTA
-constexpr int kIterThreads = 256;
-
-struct DDArgs {
-  const float* vis;
-  const float* model;  // [n_dir][n_rows] complex
-  float* gains;        // [n_gain][n_dir] complex
-  int64_t n_rows;
-  const int64_t* row_off;
-  const int32_t* n_samp;
-  const int32_t* n_bl;
-  const int32_t* bl_off;
-  const int32_t* n_ant;
-  const int32_t* gain_off;
-  const int32_t* ant1;
-  const int32_t* ant2;
-  const int64_t* mom_off;    // [n_int] first moment (complex index) of the interval
-  // moment items
-  const int32_t* mitem_int;
-  const int32_t* mitem_tile;
-  int32_t n_mitems;
-  // iteration items (interval, antenna) and per-table antenna -> (baseline, side) lists
-  const int32_t* iitem_int;
-  const int32_t* iitem_ant;
-  int32_t n_iitems;
-  const int32_t* ent;        // baseline * 2 + side (side 1: the antenna is ant2 of the stored pair)
-  const int32_t* entq;       // the other antenna of each entry's baseline
-  const int32_t* iitem_e0;   // per iteration item: its antenna's entries [e0, e1) in ent / entq
-  const int32_t* iitem_e1;
-  // state
-  float2* moments;
-  float* gnew;               // [n_gain][n_dir] complex GN gains of this iteration
-  int32_t* sing;             // [n_gain]
-  int32_t* active;
-  int32_t* iters;
-  int32_t* status;
-  int32_t* counters;
-  int32_t* n_active;
-  int32_t* kbase;            // iterations before this launch's segment (advanced on the device)
-  double tol;
-  int32_t max_iter;
-  int32_t schedule;
-  int32_t k;                 // position within the segment: the iteration is *kbase + k
-  int32_t na_max;
-};
 
 template <int ND>
 struct DDShape {
   static constexpr int NU = ND * (ND + 1) / 2;  // upper-triangle entries of X
   static constexpr int NO = NU + ND;            // moments per baseline
 };
-
-// Component index -> (c, d) for the upper triangle, row-major: (0,0) (0,1) .. (0,ND-1) (1,1) ..
-__host__ __device__ inline void upper_cd(int nd, int comp, int& c, int& d) {
-  int r = 0, base = 0;
-  while (comp >= base + (nd - r)) { base += nd - r; ++r; }
-  c = r;
-  d = r + (comp - base);
-}
 
 // ------------------------------------------------------------------------------------ moments
 // Rows reach shared memory by cp.async, NST samples ahead of the arithmetic, so that the bytes in
@@ -194,177 +141,43 @@ __global__ void __launch_bounds__(kMomBl * kMomLanes) dd_moment_kernel(const DDA
   }
 }
 
-// ------------------------------------------------------------------------------------ FP64 solve
-// Cholesky A = L L^H of the Hermitian ND x ND block (upper triangle given) and solve A x = b, in
-// FP64, by one warp (right-looking: at column k one lane takes the square root of the pivot, the
-// lanes scale the column below it and update the trailing lower triangle in parallel; then the
-// two triangular solves, column by column).  Am: [ND][ND] double2 and dinv: [ND] double of shared
-// memory.  Every lane of the warp calls it and gets the same result; false when a pivot is not
-// positive (the block is not numerically positive definite).
+// AllJones (Sect. 3.2.3, eq. stefcal:dd:unpol): J^H J taken as its diagonal, so the step goes
+// through the residuals.  For antenna p, c_p[r] = sum conj(y^(r)) r equals b_p[r] - sum_j A_p[r][j]
+// g_p^(j) exactly (the residual r = d - sum_j g_p^(j) y^(j) summed against conj(y^(r))), with A_p,
+// b_p the CohJones block and data sums built from the moments; g_p^(r) += c_p[r] / A_p[r][r].
+// c is formed in float-float against the float-float A and b (as the CohJones refinement
+// residual).  One warp, lane r takes direction r; a direction with A_p[r][r] <= 0 (no signal)
+// keeps its gain and sets *sing.
 template <int ND>
-__device__ bool chol_solve_warp(const double2* Aup, const double2* b, double2* x, double2* Am, double* dinv,
-                                int* ok_s) {
-  const int lane = threadIdx.x & 31;
-  auto au = [](int r, int c) { return r * ND - r * (r - 1) / 2 + (c - r); };  // upper entry (r <= c)
-  for (int e = lane; e < ND * ND; e += 32) {  // lower triangle of A (conjugates of the upper entries)
-    const int r = e / ND, c = e % ND;
-    if (c <= r) {
-      double2 v = Aup[au(c, r)];
-      v.y = -v.y;
-      Am[e] = v;
-    }
-  }
-  for (int r = lane; r < ND; r += 32) x[r] = b[r];
-  if (lane == 0) *ok_s = 1;
-  __syncwarp();
-  for (int k = 0; k < ND; ++k) {
-    if (lane == 0) {
-      const double akk = Am[k * ND + k].x;
-      if (!(akk > 0.0) || !isfinite(akk)) {
-        *ok_s = 0;
-      } else {
-        const double l = sqrt(akk);
-        Am[k * ND + k] = make_double2(l, 0.0);
-        dinv[k] = 1.0 / l;
-      }
-    }
-    __syncwarp();
-    if (!*ok_s) return false;
-    for (int i = k + 1 + lane; i < ND; i += 32) {
-      const double2 v = Am[i * ND + k];
-      Am[i * ND + k] = make_double2(v.x * dinv[k], v.y * dinv[k]);
-    }
-    __syncwarp();
-    // A[i][j] -= L[i][k] conj(L[j][k]) for k < j <= i
-    const int m = ND - 1 - k;
-    for (int t = lane; t < m * (m + 1) / 2; t += 32) {
-      int i = 0;
-      while ((i + 1) * (i + 2) / 2 <= t) ++i;
-      const int j = t - i * (i + 1) / 2;
-      const int ii = k + 1 + i, jj = k + 1 + j;
-      const double2 p = Am[ii * ND + k], q = Am[jj * ND + k];
-      double2 v = Am[ii * ND + jj];
-      v.x -= p.x * q.x + p.y * q.y;
-      v.y -= p.y * q.x - p.x * q.y;
-      Am[ii * ND + jj] = v;
-    }
-    __syncwarp();
-  }
-  for (int k = 0; k < ND; ++k) {  // L y = b (y in x)
-    if (lane == 0) x[k] = make_double2(x[k].x * dinv[k], x[k].y * dinv[k]);
-    __syncwarp();
-    for (int i = k + 1 + lane; i < ND; i += 32) {
-      const double2 p = Am[i * ND + k], q = x[k];
-      x[i].x -= p.x * q.x - p.y * q.y;
-      x[i].y -= p.x * q.y + p.y * q.x;
-    }
-    __syncwarp();
-  }
-  for (int k = ND - 1; k >= 0; --k) {  // L^H x = y
-    if (lane == 0) x[k] = make_double2(x[k].x * dinv[k], x[k].y * dinv[k]);
-    __syncwarp();
-    for (int i = lane; i < k; i += 32) {  // x[i] -= conj(L[k][i]) x[k]
-      const double2 p = Am[k * ND + i], q = x[k];
-      x[i].x -= p.x * q.x + p.y * q.y;
-      x[i].y -= p.x * q.y - p.y * q.x;
-    }
-    __syncwarp();
-  }
-  return true;
-}
-
-// The factorisation in FP32 followed by one step of iterative refinement (Moler's
-// mixed-precision scheme): the residual r = b - A x0 in float-float against the float-float
-// block, then the correction solved with the FP32 factor; one step takes the error from about
-// kappa(A) u_32 to about (kappa(A) u_32)^2.  Ah + Al is the upper triangle of A and bh + bl the
-// right-hand side, each an unevaluated float-float sum.  Called by one whole warp: lane r keeps
-// row r of the block in registers and the columns are factored right-looking with shuffles (lanes
-// r >= ND shadow row ND - 1 and store nothing).  False when an FP32 pivot is not positive: the
-// caller then runs the FP64 factorisation, which alone decides singularity.
-// Ls: [ND][ND] of shared memory (the factor, rows); the solution goes to x.
-template <int ND>
-__device__ bool chol_solve_warp_mixed(const Cx<float>* Ah, const Cx<float>* Al, const Cx<float>* bh,
-                                      const Cx<float>* bl, Cx<float>* x, Cx<float>* Ls) {
-  constexpr unsigned kAll = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int r = lane < ND ? lane : ND - 1;
+__device__ void alljones_update_warp(const Cx<float>* Ah, const Cx<float>* Al, const Cx<float>* bh,
+                                     const Cx<float>* bl, const Cx<float>* g, Cx<float>* x, int* sing) {
+  const int r = threadIdx.x & 31;
+  if (r >= ND) return;
   auto au = [](int i, int j) { return i * ND - i * (i - 1) / 2 + (j - i); };  // upper entry (i <= j)
-  auto shfl = [&](Cx<float> v, int src) {
-    return cx<float>(__shfl_sync(kAll, v.x, src), __shfl_sync(kAll, v.y, src));
-  };
-  float dinv[ND];
-  {
-    Cx<float> L[ND];  // row r: A[r][j], becoming L[r][j] for j <= r
-#pragma unroll
-    for (int j = 0; j < ND; ++j) L[j] = r <= j ? Ah[au(r, j)] : conj_(Ah[au(j, r)]);
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-      const float akk = __shfl_sync(kAll, L[k].x, k);
-      if (!(akk > 0.f) || !isfinite(akk)) return false;  // the same pivot in every lane
-      const float l = sqrtf(akk);
-      dinv[k] = __frcp_rn(l);
-      if (r == k) L[k] = cx<float>(l, 0.f);
-      else if (r > k) L[k] = scale_(L[k], dinv[k]);
-#pragma unroll
-      for (int j = k + 1; j < ND; ++j) {  // A[r][j] -= L[r][k] conj(L[j][k]) for j <= r
-        const Cx<float> ljk = shfl(L[k], j);
-        if (r >= j) L[j] = sub_(L[j], mulc_(L[k], ljk));
-      }
-    }
-    if (lane < ND) {
-#pragma unroll
-      for (int j = 0; j < ND; ++j)
-        if (j <= r) Ls[r * ND + j] = L[j];
-    }
-  }
-  __syncwarp();
-  // L L^H v = w for the w held by lane r: forward with row r of L, backward with column r
-  auto subst = [&](Cx<float> v) {
-    Cx<float> row[ND];
-#pragma unroll
-    for (int k = 0; k < ND; ++k) row[k] = k < r ? Ls[r * ND + k] : cx<float>(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < ND; ++k) {
-      if (r == k) v = scale_(v, dinv[k]);
-      const Cx<float> vk = shfl(v, k);
-      if (r > k) v = sub_(v, mul_(row[k], vk));
-    }
-    Cx<float> col[ND];
-#pragma unroll
-    for (int k = 0; k < ND; ++k) col[k] = k > r ? Ls[k * ND + r] : cx<float>(0.f, 0.f);
-#pragma unroll
-    for (int k = ND - 1; k >= 0; --k) {
-      if (r == k) v = scale_(v, dinv[k]);
-      const Cx<float> vk = shfl(v, k);
-      if (r < k) v = sub_(v, cmul_(col[k], vk));  // v_r -= conj(L[k][r]) v_k
-    }
-    return v;
-  };
-  const Cx<float> x0 = subst(bh[r]);
-  // residual in float-float: r_r = b_r - sum_j A[r][j] x0_j, two interleaved partial sums per part
-  FF rx0{bh[r].x, bl[r].x}, ry0{bh[r].y, bl[r].y}, rx1{0.f, 0.f}, ry1{0.f, 0.f};
+  FF rx{bh[r].x, bl[r].x}, ry{bh[r].y, bl[r].y};
   float lox = 0.f, loy = 0.f;
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
     const int u = r <= j ? au(r, j) : au(j, r);
     Cx<float> h = Ah[u], lo = Al[u];
     if (r > j) { h.y = -h.y; lo.y = -lo.y; }
-    const Cx<float> xj = shfl(x0, j);
-    FF& ax = (j & 1) ? rx1 : rx0;
-    FF& ay = (j & 1) ? ry1 : ry0;
-    ax = ff_sub_prod(ax, h.x, xj.x);
-    ax = ff_sub_prod(ax, -h.y, xj.y);
-    ay = ff_sub_prod(ay, h.x, xj.y);
-    ay = ff_sub_prod(ay, h.y, xj.x);
-    lox = fmaf(lo.x, xj.x, fmaf(-lo.y, xj.y, lox));
-    loy = fmaf(lo.x, xj.y, fmaf(lo.y, xj.x, loy));
+    const Cx<float> gj = g[j];
+    rx = ff_sub_prod(rx, h.x, gj.x);
+    rx = ff_sub_prod(rx, -h.y, gj.y);
+    ry = ff_sub_prod(ry, h.x, gj.y);
+    ry = ff_sub_prod(ry, h.y, gj.x);
+    lox = fmaf(lo.x, gj.x, fmaf(-lo.y, gj.y, lox));
+    loy = fmaf(lo.x, gj.y, fmaf(lo.y, gj.x, loy));
   }
-  const FF rx = ff_add(rx0, rx1), ry = ff_add(ry0, ry1);
-  const Cx<float> dres = cx<float>(rx.hi + (rx.lo - lox), ry.hi + (ry.lo - loy));
-  const Cx<float> d = subst(dres);
-  if (lane < ND) x[lane] = add_(x0, d);
-  __syncwarp();
-  return true;
+  const Cx<float> c = cx<float>(rx.hi + (rx.lo - lox), ry.hi + (ry.lo - loy));
+  const float arr = Ah[au(r, r)].x + Al[au(r, r)].x;
+  if (arr > 0.f) {
+    const float inv = 1.f / arr;
+    x[r] = cx<float>(g[r].x + c.x * inv, g[r].y + c.y * inv);
+  } else {
+    x[r] = g[r];
+    atomicOr(sing, 1);
+  }
 }
 
 // ------------------------------------------------------------------------------------ iteration
@@ -377,7 +190,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
   Cx<float>* gs = reinterpret_cast<Cx<float>*>(smem_raw);            // [n_ant][ND]
   float4* red = reinterpret_cast<float4*>(gs + a.na_max * ND);       // [LANES][NO] float-float (re, im)
   __shared__ Cx<float> Ah[NU], Al[NU], bh[ND], bl[ND], xs[ND];
-  __shared__ int s_last, s_sing;
+  __shared__ int s_last, s_sing, s_nf;
   __shared__ double s_red[80];  // >= 160 floats for the end-of-update reduction
   __shared__ int2 s_ent[kIterThreads];
   const int it = blockIdx.x;
@@ -433,6 +246,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
   }
   if (e1 <= e0) __syncthreads();  // the gains are staged even for an antenna without baselines
   if (worker) red[lane * NO + comp] = make_float4(sx, -sxc, sy, -syc);  // Kahan: the sum is s - c
+  if (tid == 0) s_nf = 0;
   __syncthreads();
   if (tid < NO) {
     FF re{0.f, 0.f}, im{0.f, 0.f};
@@ -443,9 +257,14 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
     }
     if (tid < NU) { Ah[tid] = cx<float>(re.hi, im.hi); Al[tid] = cx<float>(re.lo, im.lo); }
     else { bh[tid - NU] = cx<float>(re.hi, im.hi); bl[tid - NU] = cx<float>(re.lo, im.lo); }
+    if (!isfinite(re.hi) || !isfinite(im.hi)) atomicOr(&s_nf, 1);  // sums overflowed: the gains diverged
   }
   __syncthreads();
-  if (tid < 32) {
+  if (a.method == 1) {  // AllJones
+    if (tid == 0) s_sing = 0;
+    __syncthreads();
+    if (tid < 32) alljones_update_warp<ND>(Ah, Al, bh, bl, gs + p * ND, xs, &s_sing);
+  } else if (tid < 32) {
     __shared__ Cx<float> Ls[ND * ND];
     __shared__ int s_ok;
     bool ok = chol_solve_warp_mixed<ND>(Ah, Al, bh, bl, xs, Ls);
@@ -465,7 +284,8 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
   }
   __syncthreads();
   if (tid < ND) {
-    Cx<float> g = s_sing ? gs[p * ND + tid] : xs[tid];
+    Cx<float> g = (s_sing && a.method != 1) ? gs[p * ND + tid] : xs[tid];
+    if (s_nf) g = cx<float>(__int_as_float(0x7fc00000), 0.f);  // reported as non-finite gains
     a.gnew[2 * ((go + p) * ND + tid)] = g.x;
     a.gnew[2 * ((go + p) * ND + tid) + 1] = g.y;
   }
@@ -477,39 +297,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const bool gn_step = (a.schedule == GC_SCHED_GN) || (k & 1);
-  FF d2{0.f, 0.f}, n2{0.f, 0.f};  // float-float sums (the FP64 pipe of GB300 is narrow)
-  int nonfin = 0, sing = 0;
-  for (int x = tid; x < na * ND; x += blockDim.x) {
-    const Cx<float> old = gs[x];
-    const Cx<float> gn = cx<float>(__ldcg(a.gnew + 2 * (go * ND + x)), __ldcg(a.gnew + 2 * (go * ND + x) + 1));
-    const Cx<float> nw = gn_step ? gn : cx<float>(0.5f * (old.x + gn.x), 0.5f * (old.y + gn.y));
-    d2 = ff_add_f(d2, abs2_(sub_(nw, old)));
-    n2 = ff_add_f(n2, abs2_(nw));
-    if (!isfinite(nw.x) || !isfinite(nw.y)) nonfin = 1;
-    gs[x] = nw;  // stage; written below unless non-finite
-  }
-  for (int x = tid; x < na; x += blockDim.x) sing |= __ldcg(a.sing + go + x);
-  block_reduce_step_ff(d2, n2, nonfin, sing, reinterpret_cast<float*>(s_red), (int)blockDim.x);
-  const double D2 = ff_value(d2), N2 = ff_value(n2);
-  if (!nonfin)
-    for (int x = tid; x < na * ND; x += blockDim.x) {
-      a.gains[2 * (go * ND + x)] = gs[x].x;
-      a.gains[2 * (go * ND + x) + 1] = gs[x].y;
-    }
-  if (tid == 0) {
-    a.counters[i] = 0;
-    int st = -1;
-    if (nonfin) st = GC_ST_NONFINITE;
-    else if (D2 <= a.tol * a.tol * N2) st = GC_ST_OK;
-    else if (k >= a.max_iter) st = GC_ST_NOT_CONVERGED;
-    if (st >= 0) {
-      a.active[i] = 0;
-      a.iters[i] = k;
-      a.status[i] = st | (sing ? GC_ST_SINGULAR_FLAG : 0);
-      atomicSub(a.n_active, 1);
-    }
-  }
+  dd_interval_update(a, i, k, na, go, ND, gs, reinterpret_cast<float*>(s_red));
 }
 
 // chi^2 per moment item (interval, 32-baseline tile) over all its rows, then per interval.
@@ -551,52 +339,12 @@ __global__ void dd_chi2_final(const int32_t* first, const int32_t* count, const 
   out[i] = s;
 }
 
-__global__ void dd_init_kernel(DDArgs a, int n_int, int n_active0) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) { *a.n_active = n_active0; *a.kbase = 0; }
-  if (i < n_int) {
-    const int64_t rows = (int64_t)a.n_samp[i] * a.n_bl[i];
-    a.active[i] = rows > 0 ? 1 : 0;
-    a.iters[i] = 0;
-    a.status[i] = rows > 0 ? GC_ST_NOT_CONVERGED : GC_ST_NODATA;
-    a.counters[i] = 0;
-  }
-}
-
 // ------------------------------------------------------------------------------------ host side
-extern std::atomic<long long> g_launches;
-int ws_get(const char* name, size_t bytes, void** out);
-int pinned_flag(int** out);
-int validate_layout(const gc_layout* L, int n_dir_max);
-uint64_t layout_hash(const gc_layout* L, uint64_t salt);
-int set_cuda_error(cudaError_t e, const char* what);
-
-struct DDPlan {
-  uint64_t key = 0;
-  void* dev = nullptr;
-  size_t dev_bytes = 0;
-  DDArgs args{};
-  int n_int = 0, n_active0 = 0, nd = 1;
-  int64_t n_mom = 0;
-  cudaGraphExec_t gexec = nullptr;  // the captured iteration segment
-  DDArgs gargs{};
-  int gS = 0, gnd = 0;
-  int32_t* chi2_first = nullptr;
-  int32_t* chi2_count = nullptr;
-  double* chi2_items = nullptr;
-  double* chi2_out = nullptr;
-};
 static DDPlan g_dd;
 
-#define DD_CUDA(call)                                             \
-  do {                                                            \
-    cudaError_t e__ = (call);                                     \
-    if (e__ != cudaSuccess) return set_cuda_error(e__, #call);    \
-  } while (0)
-
-static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
+int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s, int64_t mom_per_bl, int mom_tile) {
   const int n = L->n_intervals, nd = L->n_dir;
-  const int NO = nd * (nd + 1) / 2 + nd;
+  const int64_t NO = mom_per_bl;
   std::vector<int64_t> mom_off(n);
   std::vector<int> mint, mtile, iint, iant, itab(n), tab_aoff, ant_off, ent, entq, cfirst(n), ccount(n);
   std::map<std::pair<int, int>, int> tabs;
@@ -611,7 +359,7 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
     const bool has = (int64_t)nb * ns > 0;
     n_active0 += has;
     if (has)
-      for (int t = 0; t < (nb + kMomBl - 1) / kMomBl; ++t) { mint.push_back(i); mtile.push_back(t); }
+      for (int t = 0; t < (nb + mom_tile - 1) / mom_tile; ++t) { mint.push_back(i); mtile.push_back(t); }
     ccount[i] = (int)mint.size() - cfirst[i];
     if (has)
       for (int p = 0; p < na; ++p) { iint.push_back(i); iant.push_back(p); }
@@ -741,43 +489,6 @@ static int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s) {
   return GC_OK;
 }
 
-void profile_record(double iter_ms, int64_t launches, int64_t row_iters, double moment_ms, int64_t bl_iters, int path);
-
-// opt->profile: the moment pass and every iteration launch bracketed by CUDA events on `s`
-struct DDTimer {
-  bool on;
-  std::vector<cudaEvent_t> ev;
-  int used = 0;
-  double ms = 0.0;
-  int64_t launches = 0;
-  explicit DDTimer(bool on_, int cap) : on(on_) {
-    if (on)
-      for (int i = 0; i < 2 * cap; ++i) {
-        cudaEvent_t e = nullptr;
-        cudaEventCreate(&e);
-        ev.push_back(e);
-      }
-  }
-  ~DDTimer() {
-    for (auto e : ev) cudaEventDestroy(e);
-  }
-  void before(cudaStream_t s) {
-    if (on) cudaEventRecord(ev[2 * used], s);
-  }
-  void after(cudaStream_t s) {
-    if (on) { cudaEventRecord(ev[2 * used + 1], s); ++used; }
-  }
-  void drain() {  // after a synchronize of the stream
-    for (int i = 0; i < used; ++i) {
-      float t = 0.f;
-      cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
-      ms += t;
-    }
-    launches += used;
-    used = 0;
-  }
-};
-
 template <int ND>
 static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag, double* prof_ms) {
   constexpr int NO = DDShape<ND>::NO;
@@ -870,7 +581,7 @@ void dd_release() {
 }
 
 int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, const gc_options* opt,
-           int32_t* iters_out, double* chi2_out, int32_t* status_out, void* stream) {
+           int32_t* iters_out, double* chi2_out, int32_t* status_out, void* stream, int method) {
   if (!opt || !L) return GC_ERR_ARG;
   if (opt->dtype != GC_DTYPE_C64) return GC_ERR_DTYPE;
   if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
@@ -886,7 +597,7 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
   const uint64_t key = layout_hash(L, 0xDDull ^ ((uint64_t)dev << 40));
   if (g_dd.key != key || !g_dd.dev) {
     g_dd.key = 0;
-    if ((rc = build_dd_plan(L, g_dd, s))) return rc;
+    if ((rc = build_dd_plan(L, g_dd, s, (int64_t)L->n_dir * (L->n_dir + 1) / 2 + L->n_dir, kMomBl))) return rc;
     g_dd.key = key;
   }
   DDPlan& P = g_dd;
@@ -916,6 +627,7 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
   a.tol = opt->tol;
   a.max_iter = opt->max_iter;
   a.schedule = opt->schedule;
+  a.method = method;
   int* flag = nullptr;
   if ((rc = pinned_flag(&flag))) return rc;
   double prof[3] = {0.0, 0.0, 0.0};
@@ -960,5 +672,10 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
 extern "C" int gc_calibrate_dd_cohjones(const void* vis, const void* model, const gc_layout* layout, void* gains,
                                         const gc_options* opt, int32_t* iters_out, double* chi2_out,
                                         int32_t* status_out, void* stream) {
-  return gc::run_dd(vis, model, layout, gains, opt, iters_out, chi2_out, status_out, stream);
+  return gc::run_dd(vis, model, layout, gains, opt, iters_out, chi2_out, status_out, stream, 0);
+}
+extern "C" int gc_calibrate_dd_alljones(const void* vis, const void* model, const gc_layout* layout, void* gains,
+                                        const gc_options* opt, int32_t* iters_out, double* chi2_out,
+                                        int32_t* status_out, void* stream) {
+  return gc::run_dd(vis, model, layout, gains, opt, iters_out, chi2_out, status_out, stream, 1);
 }

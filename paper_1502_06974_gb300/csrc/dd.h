@@ -1,6 +1,7 @@
-// Direction-dependent (CohJones) part of the library.
+// Direction-dependent part of the library (scalar and 2x2 gains).
 #pragma once
 
 namespace gc {
 void dd_release();
+void ddpol_release();
 }
