@@ -14,6 +14,9 @@ Modules
   diagonal     the paper's approximate-inverse iterations step by step: StefCal (eq. stefcal,
                eq. stefcal-lambda-average), polarized StefCal (eq. update:DI:diag:pol, read as
                [sum D Y^H][sum Y Y^H]^-1) and CohJones (Sect. 3.2.2).
+  smooth       smoothing in time and frequency (Sect. 3.4): per-sample gains from the ratio of two
+               kernel convolutions (eq. JHJ:diag:smooth), scalar and 2x2.
+  cpu_lm.cpp   the same StefCal + LM method in FP64 C++/OpenMP (the all-core CPU comparator).
   gauge        gauge alignment and the relative gain error used for parity.
 
 Every function works in complex128 / float64 whatever the input precision.
