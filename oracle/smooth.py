@@ -15,8 +15,20 @@ single tap, no smoothing).  The convolutions are the direct sums over the kernel
 clipped at the grid edges (the ratio does not depend on the kernel's normalisation).
 
 Schedule as for StefCal (odd iterations the GN gains, even ones their average with the current
-gains), and one convergence test over the whole grid: ||g_{k+1} - g_k|| <= tol ||g_{k+1}|| summed
-over every sample and antenna (the samples are coupled through the kernel).
+gains), with two phase conventions per sample.  Each sample's problem is unchanged by a common
+phase of its gains (Sect. 2.1), but the kernel couples neighbouring samples through their phases:
+  * the GN gains are first rotated by the common phase that best aligns them with the sample's
+    current gains (psi = arg sum_p conj(g_p) gn_p; 2x2: arg sum_p tr(G_p^H Gn_p)): they come back
+    rotated by a small per-sample phase even at the solution, and unaligned the iterates drift along
+    those phase modes at a constant step (the average of two vectors a phase apart also shrinks
+    them), never meeting the stopping rule;
+  * every new iterate is put in the canonical gauge (sum_p g_p, 2x2: sum_p tr G_p, real and
+    non-negative), so that neighbouring samples share one phase reference: with per-sample phase
+    offsets (from the start, say) the convolution averages unaligned gains and biases the solution.
+Without smoothing neither changes the solution: at a fixed point sum_p A_p conj(g_p) gn_p is real
+(the sum over both orientations of every baseline of conj(v) d), so the alignment is 0 (or pi), and
+the canonical rotation only picks the gauge.  One convergence test over the whole grid:
+||g_{k+1} - g_k|| <= tol ||g_{k+1}|| summed over every sample and antenna (the samples are coupled).
 """
 from __future__ import annotations
 
@@ -84,6 +96,22 @@ def smooth_step(kind, g, vis, model, a1, a2, n_ant, wt, wf):
     return np.where(sing[..., None, None], g, sa @ inv)
 
 
+def canonical_phase(kind, g):
+    """Rotate each sample's gains (axes 0, 1 of g) so that sum_p g_p (2x2: sum_p tr G_p) is real, >= 0."""
+    S = np.sum(g, axis=2) if kind == 'scalar' else np.sum(np.trace(g, axis1=-2, axis2=-1), axis=2)
+    ph = np.where(np.abs(S) > 0, np.exp(-1j * np.angle(S)), 1.0)
+    return g * (ph[:, :, None] if kind == 'scalar' else ph[:, :, None, None, None])
+
+
+def align_phase(kind, gn, g):
+    """gn rotated, per sample (axes 0, 1), by the common phase that best aligns it with g."""
+    if kind == 'scalar':
+        S = np.sum(np.conj(g) * gn, axis=2)
+        return gn * np.exp(-1j * np.angle(S))[:, :, None]
+    S = np.sum(np.conj(g) * gn, axis=(2, 3, 4))
+    return gn * np.exp(-1j * np.angle(S))[:, :, None, None, None]
+
+
 def iterate_smooth(kind, g0, vis, model, a1, a2, n_ant, sigma_t, sigma_f, tol=1e-10, max_iter=500,
                    schedule='stefcal', taps=None):
     """Returns dict(g [n_t, n_f, n_ant(, 2, 2)], iters, converged).  taps = (wt, wf) replaces the
@@ -93,7 +121,8 @@ def iterate_smooth(kind, g0, vis, model, a1, a2, n_ant, sigma_t, sigma_f, tol=1e
     vis = np.asarray(vis, np.complex128); model = np.asarray(model, np.complex128)
     for k in range(1, max_iter + 1):
         gn = smooth_step(kind, g, vis, model, a1, a2, n_ant, wt, wf)
-        new = gn if (schedule == 'gn' or k % 2 == 1) else 0.5 * (g + gn)
+        gn = align_phase(kind, gn, g)
+        new = canonical_phase(kind, gn if (schedule == 'gn' or k % 2 == 1) else 0.5 * (g + gn))
         dn = np.linalg.norm((new - g).ravel())
         nn = np.linalg.norm(new.ravel())
         g = new
