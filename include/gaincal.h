@@ -143,6 +143,13 @@ typedef struct gc_options {
   int32_t lm_reserved;      /* must be 0                                                      */
   double lm_lambda0;        /* initial lambda; 0 selects GC_LM_DEFAULT_LAMBDA0                   */
   double lm_K;              /* lambda factor, > 1; 0 selects GC_LM_DEFAULT_K                     */
+  /* Per-row weights (Sect. 2.4, eq. LSmin:w with a diagonal W; eqs. JHJ:DI:tfw, JHR:DI:tfw): NULL
+   * for unit weights, else [n_rows] non-negative reals (float for GC_DTYPE_C64, double for
+   * GC_DTYPE_C128; device memory, or host memory with host_buffers).  Row r's weight multiplies its
+   * terms in every sum over rows (J^H W J, J^H W R, J^H W D, chi^2); one weight serves the four
+   * correlations of a 2x2 row.  Taken by the DI entry points on the moment and streaming paths
+   * (and GC_SCHED_LM); GC_PATH_RESIDENT and the DD entry points return GC_ERR_ARG when it is set. */
+  const void* weights;
 } gc_options;
 
 /* Execution paths of the direction-independent solvers (same results up to FP32 rounding order):
@@ -237,6 +244,40 @@ int gc_calibrate_dd_cohjones2x2(const void* vis, const void* model, const gc_lay
 int gc_calibrate_dd_alljones2x2(const void* vis, const void* model, const gc_layout* layout, void* gains,
                                 const gc_options* opt, int32_t* iters_out, double* chi2_out,
                                 int32_t* status_out, void* stream);
+
+/*
+ * Smoothing in time and frequency (Sect. 3.4, eqs. cal:DI:smooth, stefcal:w, JHJ:diag:smooth).
+ * Every sample (t, f) of an n_t x n_f grid has its own gains; each iteration replaces the sums of
+ * StefCal's update by their convolutions with a separable Gaussian kernel over the grid,
+ *   scalar: g_p(t, f) = (w o alpha_p)(t, f) / (w o beta_p)(t, f),
+ *           alpha_p = sum_q conj(y_pq) d_pq, beta_p = sum_q |y_pq|^2 at each sample;
+ *   2x2:    G_p(t, f) = (w o C_p)(t, f) (w o H_p)(t, f)^-1, C_p = sum_q D Y^H, H_p = sum_q Y Y^H;
+ * w(dt, df) = exp(-dt^2 / 2 sigma_t^2) exp(-df^2 / 2 sigma_f^2) on the sample grid, cut at
+ * |dt| <= ceil(3 sigma_t), |df| <= ceil(3 sigma_f) and at the grid's edges (sigma = 0: no
+ * smoothing along that axis).  Odd iterations take these gains, even ones their average with the
+ * current ones (opt->schedule as for the DI solvers); the grid stops as a whole when
+ * ||g_{k+1} - g_k|| <= tol ||g_{k+1}|| over every sample and antenna.  A sample and antenna whose
+ * smoothed sum is singular keeps its gains (GC_ST_SINGULAR_FLAG).
+ *   vis, model [n_t][n_f][n_bl] rows (complex64; 2x2 row-major for the 2x2 entry point), device;
+ *   gains [n_t][n_f][n_ant] (2x2: [..][2][2]) in/out, device; ant1/ant2 host [n_bl].
+ *   iters_out, status_out: one value each (device); chi2_out: [n_t * n_f] per-sample chi^2 (device,
+ *   opt->compute_chi2).  Only GC_DTYPE_C64, device buffers, no weights.  Synchronous; returns 0
+ *   when the grid converged, 1 when not, or a GC_ERR_* code.
+ */
+typedef struct gc_smooth {
+  int32_t n_t, n_f;         /* sample grid (time-major)                                      */
+  int32_t n_bl;             /* baselines per sample                                          */
+  int32_t n_ant;            /* antennas                                                      */
+  const int32_t* ant1;      /* host [n_bl]                                                   */
+  const int32_t* ant2;      /* host [n_bl]                                                   */
+  double sigma_t, sigma_f;  /* kernel widths in samples, >= 0                                */
+} gc_smooth;
+int gc_calibrate_di_smooth_scalar(const void* vis, const void* model, const gc_smooth* sm, void* gains,
+                                  const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out,
+                                  void* stream);
+int gc_calibrate_di_smooth_jones2x2(const void* vis, const void* model, const gc_smooth* sm, void* gains,
+                                    const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out,
+                                    void* stream);
 
 /*
  * One accumulation pass, no update: for every gain slot p of every interval, the top half of

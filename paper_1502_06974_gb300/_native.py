@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, 'libgaincal.so')
 GC_OK = 0
 GC_ERR = {-1: 'GC_ERR_ARG', -2: 'GC_ERR_LAYOUT', -3: 'GC_ERR_ANTENNA', -4: 'GC_ERR_DTYPE', -5: 'GC_ERR_CUDA',
           -6: 'GC_ERR_LIMIT'}
-GC_ERR_LIMIT = -6
+GC_ERR_ARG, GC_ERR_LIMIT = -1, -6
 GC_ST_OK, GC_ST_NOT_CONVERGED, GC_ST_NONFINITE, GC_ST_NODATA, GC_ST_SINGULAR_FLAG = 0, 1, 2, 3, 16
 GC_DTYPE_C64, GC_DTYPE_C128 = 0, 1
 GC_SCHED_STEFCAL, GC_SCHED_GN, GC_SCHED_LM = 0, 1, 2
@@ -24,7 +24,8 @@ GC_MAX_ANT, GC_MAX_DIR = 1024, 10
 # Every symbol include/gaincal.h declares (checked by the CPU test suite).
 EXPORTS = [
     'gc_calibrate_di_scalar', 'gc_calibrate_di_jones2x2', 'gc_calibrate_dd_cohjones', 'gc_calibrate_dd_alljones',
-    'gc_calibrate_dd_cohjones2x2', 'gc_calibrate_dd_alljones2x2',
+    'gc_calibrate_dd_cohjones2x2', 'gc_calibrate_dd_alljones2x2', 'gc_calibrate_di_smooth_scalar',
+    'gc_calibrate_di_smooth_jones2x2',
     'gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2', 'gc_jhj_jhr_di_jones2x2_noalloc',
     'gc_chi2_di_jones2x2', 'gc_mlp_work_floats', 'gc_mlp_forward_f32', 'gc_mlp_grad_f32', 'gc_mlp_train_step',
     'gc_mlp_infer_bf16', 'gc_ws_features_jones', 'gc_ws_target_jones', 'gc_calibrate_di_jones2x2_warm',
@@ -49,7 +50,12 @@ class GcOptions(C.Structure):
     _fields_ = [('tol', C.c_double), ('max_iter', C.c_int32), ('schedule', C.c_int32), ('dtype', C.c_int32),
                 ('host_buffers', C.c_int32), ('compute_chi2', C.c_int32), ('profile', C.c_int32),
                 ('path', C.c_int32), ('reserved', C.c_int32), ('lm_after', C.c_int32), ('lm_reserved', C.c_int32),
-                ('lm_lambda0', C.c_double), ('lm_K', C.c_double)]
+                ('lm_lambda0', C.c_double), ('lm_K', C.c_double), ('weights', C.c_void_p)]
+
+
+class GcSmooth(C.Structure):
+    _fields_ = [('n_t', C.c_int32), ('n_f', C.c_int32), ('n_bl', C.c_int32), ('n_ant', C.c_int32),
+                ('ant1', _i32p), ('ant2', _i32p), ('sigma_t', C.c_double), ('sigma_f', C.c_double)]
 
 
 class GcMlp(C.Structure):
@@ -91,6 +97,10 @@ def lib() -> C.CDLL:
         for name in ('gc_jhj_jhr_di_scalar', 'gc_jhj_jhr_di_jones2x2', 'gc_jhj_jhr_di_jones2x2_noalloc'):
             f = getattr(L, name)
             f.argtypes = [_p, _p, C.POINTER(GcLayout), _p, C.c_int32, _p, _p, _p]
+            f.restype = C.c_int
+        for name in ('gc_calibrate_di_smooth_scalar', 'gc_calibrate_di_smooth_jones2x2'):
+            f = getattr(L, name)
+            f.argtypes = [_p, _p, C.POINTER(GcSmooth), _p, C.POINTER(GcOptions), _p, _p, _p, _p]
             f.restype = C.c_int
         L.gc_error_string.argtypes = [C.c_int]
         L.gc_error_string.restype = C.c_char_p

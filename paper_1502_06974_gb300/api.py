@@ -83,14 +83,27 @@ def _schedule_code(schedule):
     return int(schedule)
 
 
+def _check_weights(weights, vis, layout, host):
+    """Per-row weights: a contiguous real tensor [n_rows] of vis's precision, where vis is."""
+    if weights is None:
+        return None
+    want = torch.float32 if vis.dtype == torch.complex64 else torch.float64
+    if weights.dtype != want or weights.numel() != layout.n_rows:
+        raise TypeError(f"weights must be {want} with one value per row ({layout.n_rows})")
+    _check_tensor(weights, 'weights', host)
+    return weights
+
+
 def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedule, compute_chi2, host_buffers,
-               want_outputs=True, profile=False, path=N.GC_PATH_AUTO, lm_after=None, lm_lambda0=0.0, lm_K=0.0):
+               want_outputs=True, profile=False, path=N.GC_PATH_AUTO, lm_after=None, lm_lambda0=0.0, lm_K=0.0,
+               weights=None):
     host = bool(host_buffers)
     for t, n in ((vis, 'vis'), (model, 'model'), (gains, 'gains')):
         _check_tensor(t, n, host)
     dt = _dtype_code(vis)
     if model.dtype != vis.dtype or gains.dtype != vis.dtype:
         raise TypeError("vis, model and gains must share one dtype")
+    weights = _check_weights(weights, vis, layout, host)
     n = layout.n_intervals
     if host:
         iters = torch.zeros(n, dtype=torch.int32).pin_memory() if want_outputs else None
@@ -105,7 +118,8 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
         stream = _stream_ptr(dev)
     opt = N.GcOptions(float(tol), int(max_iter), _schedule_code(schedule), dt, 1 if host else 0,
                       1 if compute_chi2 else 0, int(profile), int(path), 0,
-                      N.GC_LM_DEFAULT_AFTER if lm_after is None else int(lm_after), 0, float(lm_lambda0), float(lm_K))
+                      N.GC_LM_DEFAULT_AFTER if lm_after is None else int(lm_after), 0, float(lm_lambda0), float(lm_K),
+                      None if weights is None else weights.data_ptr())
     lay = layout.c()
     rc = getattr(N.lib(), fn_name)(_ptr(vis), _ptr(model), C.byref(lay), _ptr(gains), C.byref(opt), _ptr(iters),
                                    _ptr(chi2), _ptr(status), stream)
@@ -115,7 +129,7 @@ def _calibrate(fn_name, vis, model, layout: Layout, gains, tol, max_iter, schedu
 
 def calibrate_di_scalar(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
                         compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO, lm_after=None,
-                        lm_lambda0=0.0, lm_K=0.0):
+                        lm_lambda0=0.0, lm_K=0.0, weights=None):
     """StefCal on scalar DI gains (gc_calibrate_di_scalar); gains are updated in place.
 
     schedule: GC_SCHED_STEFCAL / GC_SCHED_GN / GC_SCHED_LM, or 'stefcal' / 'gn' / 'lm'; with 'lm',
@@ -124,19 +138,23 @@ def calibrate_di_scalar(vis, model, layout, gains, tol=1e-6, max_iter=1000, sche
     include/gaincal.h).
     path: GC_PATH_AUTO (default), GC_PATH_STREAM or GC_PATH_RESIDENT (see include/gaincal.h).
     profile: 0 off, 1 (or True) time the iteration launches, 2 time the accumulate launches alone.
+    weights: None or per-row real weights [rows] (float32 for complex64 data, float64 for complex128).
     Returns (gains, iters[n_int] int32, chi2[n_int] float64 or None, status[n_int] int32).
     """
     return _calibrate('gc_calibrate_di_scalar', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers, profile=profile, path=path, lm_after=lm_after, lm_lambda0=lm_lambda0, lm_K=lm_K)
+                      host_buffers, profile=profile, path=path, lm_after=lm_after, lm_lambda0=lm_lambda0, lm_K=lm_K,
+                      weights=weights)
 
 
 def calibrate_di_jones2x2(vis, model, layout, gains, tol=1e-6, max_iter=1000, schedule=N.GC_SCHED_STEFCAL,
                           compute_chi2=False, host_buffers=False, profile=False, path=N.GC_PATH_AUTO, lm_after=None,
-                          lm_lambda0=0.0, lm_K=0.0):
+                          lm_lambda0=0.0, lm_K=0.0, weights=None):
     """Polarized StefCal (or, with schedule 'lm', StefCal then Levenberg-Marquardt with the whole
-    J^H J) on 2x2 DI gains (gc_calibrate_di_jones2x2); vis/model [rows,2,2], gains [n_gain,2,2]."""
+    J^H J) on 2x2 DI gains (gc_calibrate_di_jones2x2); vis/model [rows,2,2], gains [n_gain,2,2];
+    weights as for calibrate_di_scalar (one per 2x2 row)."""
     return _calibrate('gc_calibrate_di_jones2x2', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
-                      host_buffers, profile=profile, path=path, lm_after=lm_after, lm_lambda0=lm_lambda0, lm_K=lm_K)
+                      host_buffers, profile=profile, path=path, lm_after=lm_after, lm_lambda0=lm_lambda0, lm_K=lm_K,
+                      weights=weights)
 
 
 def profile_lm():
@@ -184,6 +202,33 @@ def calibrate_dd_alljones2x2(vis, model, layout, gains, tol=1e-6, max_iter=1000,
     """Polarized AllJones (gc_calibrate_dd_alljones2x2); same layout as calibrate_dd_cohjones2x2."""
     return _calibrate('gc_calibrate_dd_alljones2x2', vis, model, layout, gains, tol, max_iter, schedule, compute_chi2,
                       host_buffers, profile=profile)
+
+
+def calibrate_di_smooth(vis, model, n_t, n_f, ant1, ant2, n_ant, gains, sigma_t, sigma_f, tol=1e-6, max_iter=1000,
+                        schedule=N.GC_SCHED_STEFCAL, compute_chi2=False):
+    """Per-sample gains smoothed in time and frequency (gc_calibrate_di_smooth_scalar / _jones2x2,
+    Sect. 3.4).  vis/model [n_t * n_f * n_bl] complex64 (2x2: [.., 2, 2]), time-major then channel
+    then baseline; gains [n_t * n_f * n_ant] (2x2: [.., 2, 2]) updated in place; sigma_t / sigma_f
+    the Gaussian kernel widths in samples.  Returns (gains, iters[1], chi2[n_t * n_f] or None, status[1])."""
+    jones = vis.dim() == 3
+    for t, n in ((vis, 'vis'), (model, 'model'), (gains, 'gains')):
+        _check_tensor(t, n, False)
+        if t.dtype != torch.complex64:
+            raise TypeError(f"{n} must be complex64")
+    a1 = np.ascontiguousarray(ant1, np.int32)
+    a2 = np.ascontiguousarray(ant2, np.int32)
+    sm = N.GcSmooth(int(n_t), int(n_f), int(a1.shape[0]), int(n_ant), a1.ctypes.data_as(C.POINTER(C.c_int32)),
+                    a2.ctypes.data_as(C.POINTER(C.c_int32)), float(sigma_t), float(sigma_f))
+    dev = vis.device
+    iters = torch.zeros(1, dtype=torch.int32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    chi2 = torch.zeros(int(n_t) * int(n_f), dtype=torch.float64, device=dev) if compute_chi2 else None
+    opt = N.GcOptions(float(tol), int(max_iter), _schedule_code(schedule), N.GC_DTYPE_C64, 0, 1 if compute_chi2 else 0)
+    fn = 'gc_calibrate_di_smooth_jones2x2' if jones else 'gc_calibrate_di_smooth_scalar'
+    rc = getattr(N.lib(), fn)(_ptr(vis), _ptr(model), C.byref(sm), _ptr(gains), C.byref(opt), _ptr(iters), _ptr(chi2),
+                              _ptr(status), _stream_ptr(dev))
+    N.check(rc, fn)
+    return gains, iters, chi2, status
 
 
 def _jhj_jhr(fn_name, vis, model, layout, gains, jones):

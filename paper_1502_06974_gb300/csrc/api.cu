@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdlib>
 #include <string>
 #include <cstdio>
@@ -748,6 +749,7 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   if (lm && !lm_limit_ok(kind, L)) return GC_ERR_LIMIT;
   if ((L->n_rows > 0 && (!vis || !model)) || (L->n_gain > 0 && !gains)) return GC_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (opt->path == GC_PATH_RESIDENT && opt->weights) return GC_ERR_ARG;  // the resident path takes no weights
   const bool can_res = opt->dtype == GC_DTYPE_C64 && res_supported(kind, L);
   if (opt->path == GC_PATH_RESIDENT && !can_res) return GC_ERR_LIMIT;
   if (opt->path == GC_PATH_MOMENTS && opt->dtype != GC_DTYPE_C64) return GC_ERR_DTYPE;
@@ -772,6 +774,15 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
     GC_CUDA(cudaMemcpyAsync(dg, gains, (size_t)L->n_gain * eb, cudaMemcpyHostToDevice, s));
     st = Staged{dv, dm, dg};
   }
+  // per-row weights (Sect. 2.4): real, of the dtype's precision, [n_rows]
+  const void* wts = opt->weights;
+  if (wts && opt->host_buffers && L->n_rows) {
+    const size_t wb = (size_t)L->n_rows * (opt->dtype == GC_DTYPE_C64 ? 4 : 8);
+    void* dw = nullptr;
+    if ((rc = ws_get("h_weights", wb, &dw))) return rc;
+    GC_CUDA(cudaMemcpyAsync(dw, wts, wb, cudaMemcpyHostToDevice, s));
+    wts = dw;
+  }
   if (resident) {
     int32_t *it_d = nullptr, *st_d = nullptr;
     double* c2_d = nullptr;
@@ -794,6 +805,7 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   a.vis = st.vis;
   a.model = st.model;
   a.gains = st.gains;
+  a.weights = wts;
   a.tol = opt->tol;
   a.max_iter = opt->max_iter;
   a.schedule = opt->schedule;
@@ -835,7 +847,8 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
       GC_CUDA(cudaEventRecord(m0, s));
     }
     GC_CUDA_I(moment_pass(kind, (const float*)st.vis, (const float*)st.model, (float*)mom, a.row_off, a.mom_off,
-                          a.n_samp, a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, P->ns_max, stream));
+                          a.n_samp, a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, P->ns_max, stream,
+                          (const float*)wts));
     void *aux = nullptr, *gnew = nullptr;
     if ((rc = ws_get("di_aux", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 4 * sizeof(float), &aux))) return rc;
     if ((rc = ws_get("di_gnew", (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 8 * sizeof(float), &gnew))) return rc;
@@ -970,14 +983,15 @@ static int run_di(int kind, const void* vis, const void* model, const gc_layout*
   }
   if (lm && opt->max_iter > lm_after) {
     rc = lm_run(kind, L, (const float*)st.vis, (const float*)st.model, a.row_off, a.n_samp, a.moments, a.mom_off,
-                a.ant1, a.ant2, (float*)st.gains, a.iters, a.status, opt, stream);
+                a.ant1, a.ant2, (float*)st.gains, a.iters, a.status, opt, stream, (const float*)wts);
     if (rc != GC_OK) return rc;
   }
   if (opt->compute_chi2) {
     if (mode == 1)
       GC_CUDA_I(moment_chi2(kind, (const float*)st.vis, (const float*)st.model, (const float*)st.gains, a.row_off,
                             a.n_samp, a.n_bl, a.bl_off, a.gain_off, a.ant1, a.ant2, P->mitem_int, P->mitem_tile,
-                            P->n_mitems, P->mfirst, P->mcount, P->mchi2, P->chi2_out, P->n_int, stream));
+                            P->n_mitems, P->mfirst, P->mcount, P->mchi2, P->chi2_out, P->n_int, stream,
+                            (const float*)wts));
     else
       GC_CUDA_I(di_launch_chi2(kind, opt->dtype, a, P->chi2_items, P->chi2_out, P->n_int, P->grid, stream));
     g_launches += 2;
@@ -1073,8 +1087,10 @@ static int run_wavefront(const void* vis, const void* model, const gc_layout* L,
   a.gate_tol = wf->gate_tol;
   float* g = (float*)gains;
   GC_CUDA_I(di_launch_init(a, n_int, P->n_active0, stream));
+  a.weights = opt->weights;
   GC_CUDA_I(moment_pass(1, (const float*)vis, (const float*)model, (float*)mom, a.row_off, a.mom_off, a.n_samp,
-                        a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, P->ns_max, stream));
+                        a.n_bl, P->mitem_int, P->mitem_tile, P->n_mitems, P->ns_max, stream,
+                        (const float*)opt->weights));
   const int n_waves = (wf->n_t + lag - 1) / lag;
   auto wave_lo = [&](int w) { return std::min(w * lag, wf->n_t) * nfb; };
   int n0_active = 0;
@@ -1200,7 +1216,7 @@ static int run_wavefront(const void* vis, const void* model, const gc_layout* L,
   if (opt->compute_chi2) {
     GC_CUDA_I(moment_chi2(1, (const float*)vis, (const float*)model, g, a.row_off, a.n_samp, a.n_bl, a.bl_off,
                           a.gain_off, a.ant1, a.ant2, P->mitem_int, P->mitem_tile, P->n_mitems, P->mfirst, P->mcount,
-                          P->mchi2, P->chi2_out, n_int, stream));
+                          P->mchi2, P->chi2_out, n_int, stream, (const float*)opt->weights));
     g_launches += 2;
   }
   if (iters_out) GC_CUDA(cudaMemcpyAsync(iters_out, a.iters, (size_t)n_int * 4, cudaMemcpyDeviceToDevice, s));
@@ -1272,6 +1288,106 @@ static int run_chi2(int kind, const void* vis, const void* model, const gc_layou
   GC_CUDA_I(di_launch_chi2(kind, dtype, a, P->chi2_items, chi2_out, P->n_int, P->grid, stream));
   g_launches += 2;
   return GC_OK;
+}
+
+// Smoothing (Sect. 3.4): every sample of the grid is one solution interval of one sample for the
+// accumulation pass; its per-antenna sums are convolved along frequency, then time, and each
+// sample's gains updated from the smoothed sums.
+static int run_smooth(int kind, const void* vis, const void* model, const gc_smooth* sm, void* gains,
+                      const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out,
+                      void* stream) {
+  if (!sm || !opt) return GC_ERR_ARG;
+  if (opt->dtype != GC_DTYPE_C64) return GC_ERR_DTYPE;
+  if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
+    return GC_ERR_ARG;
+  if (opt->host_buffers || opt->reserved || opt->weights) return GC_ERR_ARG;
+  if (sm->n_t < 1 || sm->n_f < 1 || sm->n_bl < 1 || sm->n_ant < 2 || !sm->ant1 || !sm->ant2) return GC_ERR_ARG;
+  if (!(sm->sigma_t >= 0.0) || !(sm->sigma_f >= 0.0) || sm->sigma_t > 1e4 || sm->sigma_f > 1e4) return GC_ERR_ARG;
+  if (!vis || !model || !gains) return GC_ERR_ARG;
+  const int64_t n_s = (int64_t)sm->n_t * sm->n_f;
+  if (n_s > INT32_MAX || n_s * sm->n_ant > INT32_MAX) return GC_ERR_LIMIT;
+  const int n_int = (int)n_s;
+  // the grid as one-sample intervals sharing one baseline table
+  std::vector<int64_t> row_off(n_int);
+  std::vector<int32_t> n_samp(n_int, 1), n_bl(n_int, sm->n_bl), bl_off(n_int, 0), n_ant(n_int, sm->n_ant),
+      gain_off(n_int);
+  for (int i = 0; i < n_int; ++i) {
+    row_off[i] = (int64_t)i * sm->n_bl;
+    gain_off[i] = i * sm->n_ant;
+  }
+  gc_layout L{n_int, row_off.data(), n_samp.data(), n_bl.data(), bl_off.data(), n_ant.data(), gain_off.data(),
+              sm->n_bl, sm->ant1, sm->ant2, n_s * sm->n_bl, (int32_t)(n_s * sm->n_ant), 1};
+  int rc = validate_layout(&L, 1);
+  if (rc != GC_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  DIPlan* P = nullptr;
+  if ((rc = get_di_plan(0, kind, GC_DTYPE_C64, 1, &L, &P, stream))) return rc;
+  // Gaussian taps exp(-x^2 / 2 sigma^2), |x| <= ceil(3 sigma) (one tap of 1 for sigma = 0)
+  auto taps = [](double sigma, std::vector<float>& w) {
+    const int R = sigma > 0.0 ? (int)std::ceil(3.0 * sigma) : 0;
+    w.resize(2 * R + 1);
+    for (int x = -R; x <= R; ++x) w[x + R] = sigma > 0.0 ? (float)std::exp(-0.5 * (x / sigma) * (x / sigma)) : 1.f;
+    return R;
+  };
+  std::vector<float> wt, wf;
+  const int Rt = taps(sm->sigma_t, wt), Rf = taps(sm->sigma_f, wf);
+  const int64_t n_gain = n_s * sm->n_ant;
+  const int JD = kind == 0 ? 2 : 8, JJ = kind == 0 ? 1 : 8, GW = kind == 0 ? 2 : 8;
+  void *jd = nullptr, *jj = nullptr, *tmp = nullptr, *sjd = nullptr, *sjj = nullptr, *gnew = nullptr, *aux = nullptr;
+  const size_t tb = (wt.size() + wf.size()) * sizeof(float);
+  if ((rc = ws_get("sm_jd", (size_t)n_gain * JD * 4, &jd)) || (rc = ws_get("sm_jj", (size_t)n_gain * JJ * 4, &jj)) ||
+      (rc = ws_get("sm_tmp", (size_t)n_gain * 8 * 4, &tmp)) || (rc = ws_get("sm_sjd", (size_t)n_gain * JD * 4, &sjd)) ||
+      (rc = ws_get("sm_sjj", (size_t)n_gain * JJ * 4, &sjj)) || (rc = ws_get("sm_gnew", (size_t)n_gain * GW * 4, &gnew)) ||
+      (rc = ws_get("sm_aux", tb + 32 + (size_t)n_int * 3 * 8, &aux)))
+    return rc;
+  float* dtaps = (float*)aux;
+  int* state = (int*)((char*)aux + ((tb + 15) & ~(size_t)15));
+  double* partials = (double*)(state + 4);
+  GC_CUDA(cudaMemcpyAsync(dtaps, wt.data(), wt.size() * 4, cudaMemcpyHostToDevice, s));
+  GC_CUDA(cudaMemcpyAsync(dtaps + wt.size(), wf.data(), wf.size() * 4, cudaMemcpyHostToDevice, s));
+  GC_CUDA(cudaMemsetAsync(jd, 0, (size_t)n_gain * JD * 4, s));  // antennas without data stay zero
+  GC_CUDA(cudaMemsetAsync(jj, 0, (size_t)n_gain * JJ * 4, s));
+  GC_CUDA_I(sm_launch_init(state, stream));
+  DIArgs a = P->args;
+  a.kbase = nullptr;
+  a.vis = vis;
+  a.model = model;
+  a.gains = gains;
+  a.jhd_out = jd;
+  a.jhj_out = jj;
+  a.k = 1;
+  if (P->scr_elems > 0) {
+    void* scr = nullptr;
+    if ((rc = ws_get("di_scratch", (size_t)P->scr_elems * 4, &scr))) return rc;
+    a.scratch = scr;
+  }
+  int* flag = nullptr;
+  if ((rc = pinned_flag(&flag))) return rc;
+  const int64_t per_s = (int64_t)sm->n_ant;  // gain slots per sample
+  for (int k = 1; k <= opt->max_iter; ++k) {
+    GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
+    GC_CUDA_I(di_launch_iter(kind, GC_DTYPE_C64, 1, a, P->grid, P->smem, stream));
+    // frequency, then time: [n_t][n_f][n_ant * W] with W floats per slot
+    GC_CUDA_I(sm_launch_conv((const float*)jd, (float*)tmp, sm->n_t, sm->n_f, per_s * JD, dtaps + wt.size(), Rf, stream));
+    GC_CUDA_I(sm_launch_conv((const float*)tmp, (float*)sjd, 1, sm->n_t, (int64_t)sm->n_f * per_s * JD, dtaps, Rt, stream));
+    GC_CUDA_I(sm_launch_conv((const float*)jj, (float*)tmp, sm->n_t, sm->n_f, per_s * JJ, dtaps + wt.size(), Rf, stream));
+    GC_CUDA_I(sm_launch_conv((const float*)tmp, (float*)sjj, 1, sm->n_t, (int64_t)sm->n_f * per_s * JJ, dtaps, Rt, stream));
+    GC_CUDA_I(sm_launch_update(kind, (const float*)sjd, (const float*)sjj, (const float*)gains, (float*)gnew, n_int,
+                               sm->n_ant, k, opt->schedule, opt->max_iter, opt->tol, state, partials, stream));
+    g_launches += 9;
+    GC_CUDA(cudaMemcpyAsync(flag, state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if (flag[0]) break;
+  }
+  if (iters_out) GC_CUDA(cudaMemcpyAsync(iters_out, state + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  if (status_out) GC_CUDA(cudaMemcpyAsync(status_out, state + 2, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  if (chi2_out && opt->compute_chi2) {
+    a.gains = gains;
+    GC_CUDA_I(di_launch_chi2(kind, GC_DTYPE_C64, a, P->chi2_items, chi2_out, P->n_int, P->grid, stream));
+    g_launches += 2;
+  }
+  GC_CUDA(cudaStreamSynchronize(s));
+  return (flag[2] & 15) == GC_ST_OK ? 0 : 1;
 }
 
 // Time candidate launch shapes on the caller's data and record the fastest for this shape bucket.
@@ -1412,6 +1528,18 @@ int gc_jhj_jhr_di_scalar(const void* vis, const void* model, const gc_layout* la
 int gc_jhj_jhr_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,
                            int32_t dtype, void* jhd_out, void* jhj_out, void* stream) {
   return run_di_acc(1, vis, model, layout, gains, dtype, jhd_out, jhj_out, stream);
+}
+
+int gc_calibrate_di_smooth_scalar(const void* vis, const void* model, const gc_smooth* sm, void* gains,
+                                  const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out,
+                                  void* stream) {
+  return run_smooth(0, vis, model, sm, gains, opt, iters_out, chi2_out, status_out, stream);
+}
+
+int gc_calibrate_di_smooth_jones2x2(const void* vis, const void* model, const gc_smooth* sm, void* gains,
+                                    const gc_options* opt, int32_t* iters_out, double* chi2_out, int32_t* status_out,
+                                    void* stream) {
+  return run_smooth(1, vis, model, sm, gains, opt, iters_out, chi2_out, status_out, stream);
 }
 
 int gc_chi2_di_jones2x2(const void* vis, const void* model, const gc_layout* layout, const void* gains,

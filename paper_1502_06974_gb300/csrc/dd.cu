@@ -586,7 +586,7 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
   if (opt->dtype != GC_DTYPE_C64) return GC_ERR_DTYPE;
   if (opt->max_iter < 1 || !(opt->tol >= 0.0) || (opt->schedule != GC_SCHED_STEFCAL && opt->schedule != GC_SCHED_GN))
     return GC_ERR_ARG;
-  if ((opt->host_buffers != 0 && opt->host_buffers != 1) || opt->reserved) return GC_ERR_ARG;
+  if ((opt->host_buffers != 0 && opt->host_buffers != 1) || opt->reserved || opt->weights) return GC_ERR_ARG;
   int rc = validate_layout(L, GC_MAX_DIR);
   if (rc != GC_OK) return rc;
   if (L->n_intervals == 0) return GC_OK;

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kDIThreads) di_iter_kernel(const DIArgs a) {
   const int k = a.k + (a.kbase ? *a.kbase : 0);
   const T* vis = static_cast<const T*>(a.vis);
   const T* mod = static_cast<const T*>(a.model);
+  const T* wts = static_cast<const T*>(a.weights);
   T* gains = static_cast<T*>(a.gains);
 
   if (blockIdx.x == 0 && tid == 0) a.qhead[(k + 1) & 1] = 0;  // next launch's queue head
@@ -101,7 +102,10 @@ __global__ void __launch_bounds__(kDIThreads) di_iter_kernel(const DIArgs a) {
         if (have) {
           const int64_t rb = r0 + b;
 #pragma unroll 4
-          for (int s = sc; s < se; ++s) K::row(vis, mod, rb + (int64_t)s * nb, gp, gq, pp, pq);
+          for (int s = sc; s < se; ++s) {
+            const int64_t r = rb + (int64_t)s * nb;
+            K::row(vis, mod, r, gp, gq, pp, pq, row_sw(wts, r));
+          }
         }
         T* my = part + tid * PS;
 #pragma unroll
@@ -1083,6 +1087,7 @@ __global__ void __launch_bounds__(kDIThreads) di_chi2_kernel(const DIArgs a, dou
   __shared__ double red[64];
   const T* vis = static_cast<const T*>(a.vis);
   const T* mod = static_cast<const T*>(a.model);
+  const T* wts = static_cast<const T*>(a.weights);
   const T* gains = static_cast<const T*>(a.gains);
   for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
     const int i = a.item_int[it];
@@ -1096,7 +1101,8 @@ __global__ void __launch_bounds__(kDIThreads) di_chi2_kernel(const DIArgs a, dou
       const int p = a.ant1[bo + b], q = a.ant2[bo + b];
       const typename K::G gp = K::ld_gain(gains + (go + p) * GW);
       const typename K::G gq = K::ld_gain(gains + (go + q) * GW);
-      kahan_add(s, c, K::resid2(vis, mod, r0 + (int64_t)(s0 + sl) * nb + b, gp, gq));
+      const int64_t r = r0 + (int64_t)(s0 + sl) * nb + b;
+      kahan_add(s, c, row_w(wts, r) * K::resid2(vis, mod, r, gp, gq));
     }
     const double tot = block_sum<double>((double)s - (double)c, red);
     if (threadIdx.x == 0) item_chi2[it] = tot;

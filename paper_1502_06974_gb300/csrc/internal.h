@@ -90,11 +90,13 @@ struct DIArgs {
   const int32_t* tblk;
   int32_t tblk_max;
   int32_t* err;
+  // per-row weights (Sect. 2.4; T of the kernel's dtype, [n_rows]) or NULL for unit weights
+  const void* weights;
 };
 // DIArgs goes to the kernels by value: every translation unit, host and device pass, must agree on
 // its layout.  A field added here changes this size and must be added in the same build of every
 // object that uses it (the library build recompiles all of them together).
-static_assert(sizeof(DIArgs) == 416, "DIArgs layout changed: rebuild every translation unit and update this size");
+static_assert(sizeof(DIArgs) == 424, "DIArgs layout changed: rebuild every translation unit and update this size");
 
 // Launchers implemented in di_kernels.cu.  kind: 0 scalar, 1 jones.  Return cudaError_t as int.
 int di_smem_bytes(int kind, int dtype, int na_max);
@@ -103,6 +105,16 @@ int di_launch_iter(int kind, int dtype, int acc_only, const DIArgs& a, int grid,
 int di_launch_init(const DIArgs& a, int n_int, int n_active0, void* stream);
 int di_macc_smem(int kind, int na_max, int red_chunks, int prefetch);
 int di_macc_bulk_smem(int kind, int na_max, int tblk_max);
+// Smoothing in time and frequency (smooth.cu): separable convolution along one axis of a
+// [n_outer][n_axis][inner] float array with 2R + 1 taps; the update of every sample (phase
+// alignment, schedule, canonical gauge) and the grid-wide stopping rule (state [4] ints: done,
+// iterations, status, apply; partials 3 doubles per sample), then the staged gains copied over the
+// current ones when the step is kept.
+int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int64_t inner, const float* taps, int R,
+                   void* stream);
+int sm_launch_update(int kind, const float* jd, const float* jj, const float* gains, float* gnew, int n_s, int n_ant,
+                     int k, int schedule, int max_iter, double tol, int* state, double* partials, void* stream);
+int sm_launch_init(int* state, void* stream);
 // Tries of the bulk-copy accumulate kernel's first wait per tile on the current device (< 0: the
 // default bound).  Returns cudaError_t as int.
 int di_set_bulk_wait_tries(int tries);
@@ -137,12 +149,12 @@ int di_launch_maux(int kind, const float* gains, float* aux, int n_gain, void* s
 // lanes with a compensated shared-memory reduction
 int moment_pass(int kind, const float* vis, const float* model, float* moments, const int64_t* row_off,
                 const int64_t* mom_off, const int32_t* n_samp, const int32_t* n_bl, const int32_t* item_int,
-                const int32_t* item_tile, int n_items, int ns_max, void* stream);
+                const int32_t* item_tile, int n_items, int ns_max, void* stream, const float* weights);
 int moment_chi2(int kind, const float* vis, const float* model, const float* gains, const int64_t* row_off,
                 const int32_t* n_samp, const int32_t* n_bl, const int32_t* bl_off, const int32_t* gain_off,
                 const int32_t* ant1, const int32_t* ant2, const int32_t* item_int, const int32_t* item_tile,
                 int n_items, const int32_t* first, const int32_t* count, double* item_chi2, double* out, int n_int,
-                void* stream);
+                void* stream, const float* weights);
 int di_launch_chi2(int kind, int dtype, const DIArgs& a, double* item_chi2, double* chi2_out, int n_int,
                    int grid, void* stream);
 
@@ -166,7 +178,8 @@ int gauge_fix(int kind, int dtype, void* gains, const int32_t* gain_off, const i
 int lm_limit_ok(int kind, const gc_layout* L);
 int lm_run(int kind, const gc_layout* L, const float* vis, const float* model, const int64_t* row_off,
            const int32_t* n_samp, const float* moments, const int64_t* mom_off, const int32_t* ant1,
-           const int32_t* ant2, float* gains, int32_t* iters, int32_t* status, const gc_options* opt, void* stream);
+           const int32_t* ant2, float* gains, int32_t* iters, int32_t* status, const gc_options* opt, void* stream,
+           const float* weights);
 // time of the last profiled polish's iteration launches (CUDA events), their count, and the
 // algorithmic flops of its factorisations and triangular solves
 int lm_profile(double* ms, int64_t* launches, double* flop);

@@ -7,6 +7,15 @@
 
 namespace gc {
 
+template <typename T> GC_DEV M2<T> scale_m2(M2<T> x, T s) {
+  x.a = scale_(x.a, s); x.b = scale_(x.b, s); x.c = scale_(x.c, s); x.d = scale_(x.d, s);
+  return x;
+}
+// sqrt of row r's weight (Sect. 2.4, a diagonal W), 1 without weights
+template <typename T> GC_DEV T row_sw(const T* w, int64_t r) { return w ? sqrt(w[r]) : T(1); }
+// row r's weight, 1 without weights
+template <typename T> GC_DEV T row_w(const T* w, int64_t r) { return w ? w[r] : T(1); }
+
 // ------------------------------------------------------------------------------------------
 // Per-kind row arithmetic.  Partial-sum component order (per side):
 //   scalar: [Re c, Im c, A]                              c = sum conj(y) d, A = sum |y|^2
@@ -22,10 +31,11 @@ struct ScalarKind {
   static GC_DEV void st_gain(T* g, const G& v) { g[0] = v.x; g[1] = v.y; }
 
   // Row (p, q, s): y = m conj(g_q) feeds antenna p; the conjugate row (q, p) has
-  // y_qp = conj(m) conj(g_p) = conj(w) with w = g_p m and d_qp = conj(d).
-  static GC_DEV void row(const T* vis, const T* mod, int64_t r, const G& gp, const G& gq, T* pp, T* pq) {
-    const Cx<T> d = Vec<T>::ld1(vis + 2 * r);
-    const Cx<T> m = Vec<T>::ld1(mod + 2 * r);
+  // y_qp = conj(m) conj(g_p) = conj(w) with w = g_p m and d_qp = conj(d).  sw = sqrt of the row's
+  // weight (Sect. 2.4): d and m scaled by it make every sum below carry the weight once.
+  static GC_DEV void row(const T* vis, const T* mod, int64_t r, const G& gp, const G& gq, T* pp, T* pq, T sw) {
+    const Cx<T> d = scale_(Vec<T>::ld1(vis + 2 * r), sw);
+    const Cx<T> m = scale_(Vec<T>::ld1(mod + 2 * r), sw);
     const Cx<T> y = mulc_(m, gq);
     const Cx<T> w = mul_(gp, m);
     pp[0] = fma(y.x, d.x, fma(y.y, d.y, pp[0]));   // conj(y) d
@@ -83,10 +93,10 @@ struct JonesKind {
 
   // Row (p, q, s) with Y = M G_q^H feeds antenna p: C_p += D Y^H, H_p += Y Y^H.
   // Its conjugate row (q, p) has Y_qp = M^H G_p^H = W^H with W = G_p M and D_qp = D^H:
-  //   C_q += D^H W,  H_q += W^H W.
-  static GC_DEV void row(const T* vis, const T* mod, int64_t r, const G& gp, const G& gq, T* pp, T* pq) {
-    const M2<T> D = Vec<T>::ld4(vis + 8 * r);
-    const M2<T> M = Vec<T>::ld4(mod + 8 * r);
+  //   C_q += D^H W,  H_q += W^H W.  sw: sqrt of the row's weight, applied to D and M.
+  static GC_DEV void row(const T* vis, const T* mod, int64_t r, const G& gp, const G& gq, T* pp, T* pq, T sw) {
+    const M2<T> D = scale_m2(Vec<T>::ld4(vis + 8 * r), sw);
+    const M2<T> M = scale_m2(Vec<T>::ld4(mod + 8 * r), sw);
     const M2<T> Y = mmh_(M, gq);
     const M2<T> W = mm_(gp, M);
     // p side
@@ -186,8 +196,8 @@ struct ScalarMom {
   static constexpr int AW = 1;   // |g|^2
   static constexpr int BPT = 4;  // baselines per thread in the resident kernel
   using K = ScalarKind<float>;
-  static GC_DEV void accum(const float* vis, const float* mod, int64_t r, float* m) {
-    const Cx<float> d = Vec<float>::ld1(vis + 2 * r), mm = Vec<float>::ld1(mod + 2 * r);
+  static GC_DEV void accum(const float* vis, const float* mod, int64_t r, float* m, float sw) {
+    const Cx<float> d = scale_(Vec<float>::ld1(vis + 2 * r), sw), mm = scale_(Vec<float>::ld1(mod + 2 * r), sw);
     m[0] = fma(mm.x, d.x, fma(mm.y, d.y, m[0]));
     m[1] = fma(mm.x, d.y, fma(-mm.y, d.x, m[1]));
     m[2] = fma(mm.x, mm.x, fma(mm.y, mm.y, m[2]));
@@ -209,8 +219,8 @@ struct JonesMom {
   static constexpr int BPT = 1;
   using K = JonesKind<float>;
   // P[r][c] += conj(M[i1][j1]) D[i2][j2], r = 2 i1 + i2, c = 2 j1 + j2; R from M (see header).
-  static GC_DEV void accum(const float* vis, const float* mod, int64_t r, float* m) {
-    const M2<float> D = Vec<float>::ld4(vis + 8 * r), M = Vec<float>::ld4(mod + 8 * r);
+  static GC_DEV void accum(const float* vis, const float* mod, int64_t r, float* m, float sw) {
+    const M2<float> D = scale_m2(Vec<float>::ld4(vis + 8 * r), sw), M = scale_m2(Vec<float>::ld4(mod + 8 * r), sw);
     const Cx<float> Me[4] = {M.a, M.b, M.c, M.d};   // M[i][j] = Me[2 i + j]
     const Cx<float> De[4] = {D.a, D.b, D.c, D.d};
 #pragma unroll

@@ -53,6 +53,7 @@ constexpr int kNB = 32;  // Cholesky panel width
 struct LMArgs {
   const float* vis;         // the rows (complex64; 2x2 row-major for the 2x2 kind)
   const float* model;
+  const float* weights;     // per-row weights (Sect. 2.4) or NULL
   const int64_t* row_off;   // [n_int] first row of the interval
   const int32_t* n_samp;    // [n_int] samples per baseline
   const float* moments;
@@ -641,7 +642,8 @@ GC_DEV double lm_chi(const LMArgs& a, int i, int bo, int nb, const float* gs, do
     const typename RK::G gq = RK::ld_gain(gs + T::GW * a.ant2[bo + b]);
 #pragma unroll 4
     for (int smp = 0; smp < ns; ++smp)
-      kahan_add(sum, comp, RK::resid2(a.vis, a.model, r0 + (int64_t)smp * nb + b, gp, gq));
+      kahan_add(sum, comp, row_w(a.weights, r0 + (int64_t)smp * nb + b) *
+                               RK::resid2(a.vis, a.model, r0 + (int64_t)smp * nb + b, gp, gq));
   }
   return block_sum((double)sum - (double)comp, red);
 }
@@ -1087,7 +1089,8 @@ static int lm_launch_all(LMArgs& a, int n_int, int np_max, int max_lm, bool prof
 // device copies of the baseline tables and moment offsets of the calling solver's plan.
 int lm_run(int kind, const gc_layout* L, const float* vis, const float* model, const int64_t* row_off,
            const int32_t* n_samp, const float* moments, const int64_t* mom_off, const int32_t* ant1,
-           const int32_t* ant2, float* gains, int32_t* iters, int32_t* status, const gc_options* opt, void* stream) {
+           const int32_t* ant2, float* gains, int32_t* iters, int32_t* status, const gc_options* opt, void* stream,
+           const float* weights) {
   cudaStream_t s = (cudaStream_t)stream;
   const int n = L->n_intervals;
   if (n == 0) return GC_OK;
@@ -1108,6 +1111,7 @@ int lm_run(int kind, const gc_layout* L, const float* vis, const float* model, c
   LMArgs a{};
   a.vis = vis;
   a.model = model;
+  a.weights = weights;
   a.row_off = row_off;
   a.n_samp = n_samp;
   a.moments = moments;

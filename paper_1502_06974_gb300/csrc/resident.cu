@@ -55,6 +55,7 @@ struct MomArgs {
   const int32_t* item_int;
   const int32_t* item_tile;
   int32_t n_items;
+  const float* weights;  // per-row weights or NULL (Sect. 2.4)
 };
 
 template <class MK>
@@ -75,7 +76,10 @@ __global__ void __launch_bounds__(kMomBl2 * kMomLanes2) di_moment_kernel(const M
   for (int c = 0; c < NM; ++c) m[c] = 0.f;
   if (b < nb) {
     const int64_t r0 = a.row_off[i] + b;
-    for (int s = s0; s < s1; ++s) MK::accum(a.vis, a.model, r0 + (int64_t)s * nb, m);
+    for (int s = s0; s < s1; ++s) {
+      const int64_t r = r0 + (int64_t)s * nb;
+      MK::accum(a.vis, a.model, r, m, row_sw(a.weights, r));
+    }
   }
   float* my = part + ((size_t)lane * kMomBl2 + bl) * NM;
 #pragma unroll
@@ -111,7 +115,10 @@ __global__ void __launch_bounds__(256, 3) di_moment_direct_kernel(const MomArgs 
   for (int c = 0; c < NM; ++c) m[c] = 0.f;
   const int64_t r0 = a.row_off[i] + b;
 #pragma unroll 2
-  for (int s = 0; s < ns; ++s) MK::accum(a.vis, a.model, r0 + (int64_t)s * nb, m);
+  for (int s = 0; s < ns; ++s) {
+    const int64_t r = r0 + (int64_t)s * nb;
+    MK::accum(a.vis, a.model, r, m, row_sw(a.weights, r));
+  }
   float4* out = reinterpret_cast<float4*>(a.moments);
 #pragma unroll
   for (int g = 0; g < NM / 4; ++g)
@@ -293,7 +300,8 @@ __global__ void __launch_bounds__(256) di_res_chi2_kernel(const float* vis, cons
                                                           const int32_t* n_bl, const int32_t* bl_off,
                                                           const int32_t* gain_off, const int32_t* ant1,
                                                           const int32_t* ant2, const int32_t* item_int,
-                                                          const int32_t* item_tile, int n_items, double* item_chi2) {
+                                                          const int32_t* item_tile, int n_items, double* item_chi2,
+                                                          const float* weights) {
   using K = typename MK::K;
   __shared__ double red[64];
   const int it = blockIdx.x;
@@ -306,8 +314,9 @@ __global__ void __launch_bounds__(256) di_res_chi2_kernel(const float* vis, cons
   for (int u = threadIdx.x; u < nbt * ns; u += blockDim.x) {
     const int sl = u / nbt, b = tile * kMomBl2 + (u - sl * nbt);
     const int p = ant1[bo + b], q = ant2[bo + b];
-    kahan_add(s, c, K::resid2(vis, model, row_off[i] + (int64_t)sl * nb + b, K::ld_gain(gains + (go + p) * K::GW),
-                              K::ld_gain(gains + (go + q) * K::GW)));
+    const int64_t r = row_off[i] + (int64_t)sl * nb + b;
+    kahan_add(s, c, row_w(weights, r) * K::resid2(vis, model, r, K::ld_gain(gains + (go + p) * K::GW),
+                                                  K::ld_gain(gains + (go + q) * K::GW)));
   }
   const double tot = block_sum<double>((double)s - (double)c, red);
   if (threadIdx.x == 0) item_chi2[it] = tot;
@@ -596,7 +605,7 @@ static int res_run(ResPlan& P, const void* vis, const void* model, void* gains, 
   if (opt->compute_chi2 && P.m.n_items > 0) {
     di_res_chi2_kernel<MK><<<P.m.n_items, 256, 0, s>>>(
         (const float*)vis, (const float*)model, (const float*)gains, P.m.row_off, P.m.n_samp, P.m.n_bl, P.r.bl_off,
-        P.r.gain_off, P.r.ant1, P.r.ant2, P.m.item_int, P.m.item_tile, P.m.n_items, P.chi2_items);
+        P.r.gain_off, P.r.ant1, P.r.ant2, P.m.item_int, P.m.item_tile, P.m.n_items, P.chi2_items, nullptr);
     res_chi2_final<<<(P.n_int + 255) / 256, 256, 0, s>>>(P.chi2_first, P.chi2_count, P.chi2_items, P.chi2_out, P.n_int);
     RS_CUDA(cudaGetLastError());
     g_launches += 2;
@@ -624,9 +633,9 @@ static int res_run(ResPlan& P, const void* vis, const void* model, void* gains, 
 
 int moment_pass(int kind, const float* vis, const float* model, float* moments, const int64_t* row_off,
                 const int64_t* mom_off, const int32_t* n_samp, const int32_t* n_bl, const int32_t* item_int,
-                const int32_t* item_tile, int n_items, int ns_max, void* stream) {
+                const int32_t* item_tile, int n_items, int ns_max, void* stream, const float* weights) {
   if (n_items <= 0) return 0;
-  MomArgs m{vis, model, moments, row_off, mom_off, n_samp, n_bl, item_int, item_tile, n_items};
+  MomArgs m{vis, model, moments, row_off, mom_off, n_samp, n_bl, item_int, item_tile, n_items, weights};
   cudaStream_t s = (cudaStream_t)stream;
   if (ns_max <= kDirectSamp) {
     const int grid = (n_items + 7) / 8;
@@ -648,17 +657,17 @@ int moment_chi2(int kind, const float* vis, const float* model, const float* gai
                 const int32_t* n_samp, const int32_t* n_bl, const int32_t* bl_off, const int32_t* gain_off,
                 const int32_t* ant1, const int32_t* ant2, const int32_t* item_int, const int32_t* item_tile,
                 int n_items, const int32_t* first, const int32_t* count, double* item_chi2, double* out, int n_int,
-                void* stream) {
+                void* stream, const float* weights) {
   cudaStream_t s = (cudaStream_t)stream;
   if (n_items > 0) {
     if (kind == 0)
       di_res_chi2_kernel<ScalarMom><<<n_items, 256, 0, s>>>(vis, model, gains, row_off, n_samp, n_bl, bl_off,
                                                             gain_off, ant1, ant2, item_int, item_tile, n_items,
-                                                            item_chi2);
+                                                            item_chi2, weights);
     else
       di_res_chi2_kernel<JonesMom><<<n_items, 256, 0, s>>>(vis, model, gains, row_off, n_samp, n_bl, bl_off,
                                                            gain_off, ant1, ant2, item_int, item_tile, n_items,
-                                                           item_chi2);
+                                                           item_chi2, weights);
   }
   res_chi2_final<<<(n_int + 255) / 256, 256, 0, s>>>(first, count, item_chi2, out, n_int);
   return (int)cudaGetLastError();

@@ -581,6 +581,42 @@ def make_warm(seed=SEED, n_ant=64, n_t=720, n_chan=64, f_per=8, dt_s=10.0, t_cor
                  dict(sigma=sigma, n_t=n_t, n_fb=n_fb, n_src=n_src, dt_s=dt_s))
 
 
+def make_smooth(kind='jones', seed=SEED, n_ant=64, n_t=240, n_chan=64, dt_s=10.0, t_corr_s=1800.0,
+                f_corr_hz=50e6, amp_sigma=0.1, phase_sigma=1.0, n_src=20, sigma=0.2, dtype=np.complex64,
+                fmin=1.0e9, df_hz=6.25e6):
+    """Per-sample gains for smoothing (Sect. 3.4): every time x channel sample is one "interval" of
+    one sample (interval i = t * n_chan + f), with gains drawn from the separable Gaussian process
+    of make_warm at that sample.  2x2: make_warm with one channel per interval; scalar: the same
+    process for one amplitude and one phase per antenna, an unpolarized sky.  Channels are df_hz
+    apart from fmin (the 2x2 warm-start workload's spacing).  meta holds n_t, n_fb."""
+    fmax = fmin + df_hz * (n_chan - 1)
+    if kind == 'jones':
+        return make_warm(seed, n_ant=n_ant, n_t=n_t, n_chan=n_chan, f_per=1, dt_s=dt_s, t_corr_s=t_corr_s,
+                         f_corr_hz=f_corr_hz, amp_sigma=amp_sigma, phase_sigma=phase_sigma, n_src=n_src,
+                         sigma=sigma, dtype=dtype, fmin=fmin, fmax=fmax)
+    rng_sky = rng_for(seed, 7, 0)
+    xy = antenna_positions(rng_sky, n_ant)
+    a1, a2 = baseline_table(n_ant)
+    flux, l, m = scalar_sky(rng_sky, n_src)
+    freqs = fmin + df_hz * np.arange(n_chan)
+    model_f = np.einsum('fbs,s->fb', fringe(xy, a1, a2, l, m, freqs), flux)           # [f, b]
+    Lt = gp_sqrt(np.arange(n_t) * dt_s, t_corr_s)
+    Lf = gp_sqrt(freqs, f_corr_hz)
+    z = rng_for(seed, 7, 1).normal(0.0, 1.0, (2, n_ant, n_t, n_chan))
+    z = np.einsum('tu,kauv,fv->ktfa', Lt, z, Lf)                                      # [2, t, f, a]
+    g = (1.0 + amp_sigma * z[0]) * np.exp(1j * phase_sigma * z[1])                      # [t, f, a]
+    vis = g[:, :, a1] * model_f[None] * np.conj(g[:, :, a2])
+    vis = vis + complex_noise(rng_for(seed, 7, 2), vis.shape, sigma)
+    n_int, nb = n_t * n_chan, len(a1)
+    model = np.broadcast_to(model_f[None], (n_t, n_chan, nb))
+    return Batch('scalar', np.ascontiguousarray(vis.reshape(-1).astype(dtype)),
+                 np.ascontiguousarray(model.reshape(-1).astype(dtype)), a1, a2,
+                 np.arange(n_int, dtype=np.int64) * nb, np.ones(n_int, np.int32), np.full(n_int, nb, np.int32),
+                 np.zeros(n_int, np.int32), np.full(n_int, n_ant, np.int32),
+                 (np.arange(n_int) * n_ant).astype(np.int32), g.reshape(-1), 1,
+                 dict(sigma=sigma, n_t=n_t, n_fb=n_chan, dt_s=dt_s))
+
+
 def make_config(k: int, seed: int = SEED, small: bool = False):
     """Synthetic stand-ins for the five workloads (small=True: a reduced copy for CPU tests)."""
     if k == 1:

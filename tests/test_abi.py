@@ -46,16 +46,17 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / 'sz.c'
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gaincal.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gc_layout), sizeof(gc_options),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gc_layout), sizeof(gc_options),'
                    ' offsetof(gc_layout, n_rows), offsetof(gc_options, reserved), offsetof(gc_layout, n_dir),'
-                   ' offsetof(gc_options, lm_after), offsetof(gc_options, lm_lambda0), offsetof(gc_options, lm_K));'
+                   ' offsetof(gc_options, lm_after), offsetof(gc_options, lm_lambda0), offsetof(gc_options, lm_K),'
+                   ' offsetof(gc_options, weights));'
                    'return 0;}\n')
     exe = tmp_path / 'sz'
     subprocess.run(['gcc', '-I', os.path.join(ROOT, 'include'), str(src), '-o', str(exe)], check=True)
     vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [C.sizeof(N.GcLayout), C.sizeof(N.GcOptions), N.GcLayout.n_rows.offset,
                     N.GcOptions.reserved.offset, N.GcLayout.n_dir.offset, N.GcOptions.lm_after.offset,
-                    N.GcOptions.lm_lambda0.offset, N.GcOptions.lm_K.offset]
+                    N.GcOptions.lm_lambda0.offset, N.GcOptions.lm_K.offset, N.GcOptions.weights.offset]
 
 
 def _call(lib, fn, lay, opt, vis=1, model=1, gains=1):

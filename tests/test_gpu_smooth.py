@@ -1,0 +1,81 @@
+"""GPU parity of smoothing in time and frequency (Sect. 3.4, eq. JHJ:diag:smooth) against the FP64
+oracle (oracle/smooth.py).
+
+The GPU takes each sample's per-antenna sums from the accumulation pass, convolves them along
+frequency and then time with the Gaussian taps (FP32), and updates every sample's gains from the
+smoothed sums; the oracle convolves by direct double sums in FP64.  Tolerance: max ||dg|| / ||g||
+over the gain slots <= 1e-5 (iterates, FP32), converged grids against the oracle run from the same
+start to the same tolerance; per-sample chi^2 within 1e-4.
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import per_slot_relerr
+from oracle import diagonal, smooth
+from paper_1502_06974_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(b):
+    return (torch.from_numpy(b.vis).cuda(), torch.from_numpy(b.model).cuda(), torch.from_numpy(b.g0()).cuda())
+
+
+def _grid(b):
+    nt, nf = b.meta['n_t'], b.meta['n_fb']
+    nb, na = int(b.n_bl[0]), int(b.n_ant[0])
+    sh = b.vis.shape[1:]
+    return (b.vis.reshape((nt, nf, nb) + sh), b.model.reshape((nt, nf, nb) + sh),
+            b.g0().reshape((nt, nf, na) + sh), nt, nf, nb, na)
+
+
+@pytest.mark.parametrize("kind", ['scalar', 'jones'])
+@pytest.mark.parametrize("sig", [(0.0, 0.0), (1.0, 0.0), (1.5, 1.0), (3.0, 2.5)])
+def test_iterates_match(gpu_lib, kind, sig):
+    b = synth.make_smooth(kind, n_ant=10, n_t=9, n_chan=7)
+    vis, model, g0 = _dev(b)
+    g, it, _, st = api.calibrate_di_smooth(vis, model, b.meta['n_t'], b.meta['n_fb'], b.ant1, b.ant2, 10, g0,
+                                           sig[0], sig[1], tol=0.0, max_iter=4)
+    v, m, gs, nt, nf, nb, na = _grid(b)
+    ref = smooth.iterate_smooth(kind, gs, v, m, b.ant1, b.ant2, na, sig[0], sig[1], tol=0.0, max_iter=4)
+    assert int(it[0]) == 4
+    assert per_slot_relerr(g.cpu().numpy(), ref['g'].reshape(g.shape)) < 1e-5
+
+
+@pytest.mark.parametrize("kind", ['scalar', 'jones'])
+def test_converged_and_chi2(gpu_lib, kind):
+    b = synth.make_smooth(kind, n_ant=8, n_t=6, n_chan=4)
+    vis, model, g0 = _dev(b)
+    g, it, chi2, st = api.calibrate_di_smooth(vis, model, 6, 4, b.ant1, b.ant2, 8, g0, 2.0, 1.5, tol=1e-6,
+                                              max_iter=3000, compute_chi2=True)
+    assert (int(st[0]) & 15) == 0
+    v, m, gs, nt, nf, nb, na = _grid(b)
+    ref = smooth.iterate_smooth(kind, gs, v, m, b.ant1, b.ant2, na, 2.0, 1.5, tol=1e-6, max_iter=3000)
+    assert ref['converged'] and abs(ref['iters'] - int(it[0])) <= 2
+    gg = g.cpu().numpy()
+    assert per_slot_relerr(gg, ref['g'].reshape(gg.shape)) < 1e-5
+    c = chi2.cpu().numpy()
+    gr = gg.reshape((nt, nf, na) + gg.shape[1:])
+    for t, f in ((0, 0), (3, 2), (5, 3)):
+        want = diagonal.chi2_interval(kind, gr[t, f], v[t, f][None], m[t, f][None], b.ant1, b.ant2)
+        assert abs(c[t * nf + f] - want) <= 1e-4 * want
+
+
+def test_smoothing_beats_per_sample_solutions_on_smooth_gains(gpu_lib):
+    """Noisy per-sample data (sigma 2) with gains from a process that is smooth in time (30 min) and
+    flat over the band: smoothing along time (sigma_t = 4 samples) brings the solutions closer to
+    the true gains than the per-sample (zero-width kernel) ones, by more than a factor 2 (the oracle
+    gives 0.023 against 0.100 on this grid)."""
+    nt, nf, na = 24, 4, 12
+    b = synth.make_smooth('jones', n_ant=na, n_t=nt, n_chan=nf, sigma=2.0, f_corr_hz=1e9)
+    vis, model, g0 = _dev(b)
+    err = {}
+    for sig in (0.0, 4.0):
+        g, it, _, st = api.calibrate_di_smooth(vis, model, nt, nf, b.ant1, b.ant2, na, g0.clone(), sig, 0.0,
+                                               tol=1e-6, max_iter=1500)
+        gg = g.cpu().numpy().reshape(nt * nf, na, 2, 2)
+        gt = b.g_true.reshape(nt * nf, na, 2, 2)
+        ph = np.angle(np.sum(gt * np.conj(gg), axis=(1, 2, 3)))[:, None, None, None]   # per-sample phase gauge
+        err[sig] = float(np.sqrt(np.mean(np.abs(gg * np.exp(1j * ph) - gt) ** 2)))
+    assert err[4.0] < 0.5 * err[0.0], err
