@@ -482,6 +482,159 @@ def dd_block(dev, args, peaks, which):
                                      "FP32 Cholesky in registers + one float-float refinement step)", "moments_bytes": int(np.sum(b.n_bl)) * (nd * (nd + 1) // 2 + nd) * 8}}
 
 
+def fp32_peak(dev, peaks):
+    """(TFLOP/s, source): the FP32 FMA issue rate, 128 lanes per SM at the maximum SM clock."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return n_sm * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop (FMA) x {mhz:.0f} MHz"
+
+
+def _median_ms(dev, fn, reps=3):
+    """Median over reps of fn() bracketed by CUDA events on the current stream (after one warm-up)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    out = fn()
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times)), out
+
+
+ALLJONES_WORKLOAD = ("dd_alljones: the CohJones geometry (62 ant, 9 directions x 3 sources, 120 t x 16 ch, intervals "
+                     "10 t x 16 ch) with source fluxes within 10:1 (log10 S in [-0.5, 0.5]), tol 1e-6")
+
+
+def alljones_block(dev, args, peaks, which):
+    """Scalar AllJones (Sect. 3.2.3) against CohJones on one workload where both converge."""
+    import torch
+    from paper_1502_06974_gb300 import api, synth
+    b = synth.make_dd(log_flux=(-0.5, 0.5))
+    vis, model = torch.from_numpy(b.vis).to(dev), torch.from_numpy(b.model).to(dev)
+    g0 = torch.from_numpy(b.g0()).to(dev)
+    lay = api.Layout.from_batch(b)
+    out = {"workload": ALLJONES_WORKLOAD, "metric": METRIC, "unit": UNIT, "rows": b.n_rows}
+    for name, fn in (("alljones", api.calibrate_dd_alljones), ("cohjones", api.calibrate_dd_cohjones)):
+        ms, (_, it, _, st) = _median_ms(dev, lambda: fn(vis, model, lay, g0.clone(), tol=TOL, max_iter=MAX_ITER))
+        it = it.cpu().numpy()
+        out[name] = {"ms": ms, "value": b.n_rows / (ms / 1e3), "iters_median": int(np.median(it)),
+                     "iters_max": int(it.max()), "converged": int(np.sum((st.cpu().numpy() & 15) == 0))}
+    fn = api.calibrate_dd_alljones
+    fn(vis, model, lay, g0.clone(), tol=TOL, max_iter=MAX_ITER, profile=True)
+    it_ms, it_n, _ = api.profile_last()
+    out["alljones"]["avg_iteration_launch_us"] = it_ms * 1e3 / max(it_n, 1)
+    return out
+
+
+DDPOL_WORKLOAD = ("dd_jones2x2: 62 ant (1891 bl), 9 directions x 3 polarized sources (fractional polarization "
+                  "0.3-0.7), 120 t x 16 ch, intervals 10 t x 16 ch (12), 2x2 gains per direction, sigma 0.02")
+DDPOL_MAX_ITER = 3000
+
+
+def ddpol_block(dev, args, peaks, which):
+    """Polarized CohJones / AllJones (Sect. 4.4): calibration to tol 1e-6 (or the iteration cap: these
+    methods contract slowly on 2x2 problems), and the Gram moment pass (vis + 9 model planes, 320 B
+    per row read once; 16 complex products per Gram tile and sample: ALU-bound) against both roofs."""
+    import torch
+    from paper_1502_06974_gb300 import api, synth
+    b = synth.make_dd_jones()
+    vis, model = torch.from_numpy(b.vis).to(dev), torch.from_numpy(b.model).to(dev)
+    g0 = torch.from_numpy(b.g0()).to(dev)
+    lay = api.Layout.from_batch(b)
+    nd = b.n_dir
+    T = nd + 1
+    NT = T * (T + 1) // 2
+    out = {"workload": DDPOL_WORKLOAD, "metric": METRIC, "unit": UNIT, "rows": b.n_rows, "max_iter": DDPOL_MAX_ITER}
+    for name, fn in (("cohjones", api.calibrate_dd_cohjones2x2), ("alljones", api.calibrate_dd_alljones2x2)):
+        ms, (_, it, _, st) = _median_ms(dev, lambda: fn(vis, model, lay, g0.clone(), tol=TOL, max_iter=DDPOL_MAX_ITER),
+                                        reps=1)
+        it = it.cpu().numpy()
+        fn(vis, model, lay, g0.clone(), tol=TOL, max_iter=DDPOL_MAX_ITER, profile=True)
+        it_ms, it_n, _ = api.profile_last()
+        mom_ms, _, _ = api.profile_detail()
+        out[name] = {"ms": ms, "value": b.n_rows / (ms / 1e3), "iters_median": int(np.median(it)),
+                     "iters_max": int(it.max()), "converged": int(np.sum((st.cpu().numpy() & 15) == 0)),
+                     "avg_iteration_launch_us": it_ms * 1e3 / max(it_n, 1), "moment_pass_ms": mom_ms}
+    mom_ms = out["cohjones"]["moment_pass_ms"]
+    rd = b.n_rows * 32 * (1 + nd)
+    wr = int(np.sum(b.n_bl)) * NT * 16 * 8
+    flops = b.n_rows * NT * 16 * 8
+    peak_tf, src = fp32_peak(dev, peaks)
+    out["roofline_moment_pass"] = {
+        "bound": "alu", "kernel": f"ddpol_moment_kernel<{nd}> (Hermitian Gram of [D, M^(1)..M^(9)] per baseline)",
+        "achieved": flops / (mom_ms / 1e3) / 1e12, "unit": "TFLOP/s", "peak": peak_tf,
+        "frac": flops / (mom_ms / 1e3) / 1e12 / peak_tf, "flop": flops, "peak_source": src,
+        "hbm": {"bytes": rd + wr, "achieved": (rd + wr) / (mom_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                "frac": (rd + wr) / (mom_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "peak_source": which}}
+    return out
+
+
+WEIGHTS_WORKLOAD = ("the headline 2x2 workload with per-row weights U(0.5, 2) and 10% of the rows flagged (weight 0); "
+                    "StefCal x20 then LM on J^H W J to a relative step of 1e-6")
+
+
+def weights_block(dev, args, b, vis, model, lay, g0):
+    """Per-row weights (Sect. 2.4) on the headline workload: time, and the error against the oracle's
+    weighted least-squares gains on a sampled interval."""
+    import torch
+    from oracle import diagonal, gauge, wirtinger
+    from paper_1502_06974_gb300 import api, synth
+    r = synth.rng_for(12, 31)
+    w = r.uniform(0.5, 2.0, b.n_rows)
+    w[r.uniform(size=b.n_rows) < 0.1] = 0.0
+    wd = torch.from_numpy(w.astype(np.float32)).to(dev)
+    ms, (g, it, _, st) = _median_ms(dev, lambda: api.calibrate_di_jones2x2(vis, model, lay, g0.clone(), tol=TOL,
+                                                                           max_iter=MAX_ITER, weights=wd, **SCHED))
+    it = it.cpu().numpy()
+    iv = b.interval(0)
+    wi = w[int(b.row_off[0]):int(b.row_off[0]) + int(b.n_samp[0]) * int(b.n_bl[0])].reshape(int(b.n_samp[0]), -1)
+    st0 = diagonal.iterate('jones', b.g0()[iv['gain_slice']].astype(np.complex128), iv['vis'], iv['model'],
+                           iv['ant1'], iv['ant2'], iv['n_ant'], tol=0.0, max_iter=LM_AFTER, weights=wi)
+    prob = wirtinger.ClosedFormProblem('jones', iv['vis'], iv['model'], iv['ant1'], iv['ant2'], iv['n_ant'], weights=wi)
+    ref, _, _ = wirtinger.levenberg_marquardt(prob, st0['g'], tol=1e-12, max_iter=400, lam0=1e-2, K=10.0, gauge=True)
+    err = gauge.rel_error('jones', g.cpu().numpy()[iv['gain_slice']], ref)
+    return {"workload": WEIGHTS_WORKLOAD, "metric": METRIC, "unit": UNIT, "ms": ms, "value": b.n_rows / (ms / 1e3),
+            "iters_median": int(np.median(it)), "iters_max": int(it.max()),
+            "converged": int(np.sum((st.cpu().numpy() & 15) == 0)), "max_err_vs_oracle_interval0": err}
+
+
+SMOOTH_WORKLOAD = ("smooth: per-sample gains (Gaussian process, 30 min / 1 GHz), 64 ant (2016 bl), {nt} t x 64 ch, "
+                   "one solution per sample, sigma {sig}; Gaussian kernel sigma_t 4 samples, sigma_f 0")
+
+
+def smooth_block(dev, args, peaks, which):
+    """Smoothing in time and frequency (Sect. 3.4), scalar and 2x2: wall time, iterations, and the
+    per-iteration accumulation pass (the rows read once per iteration, HBM-bound) against HBM."""
+    import torch
+    from paper_1502_06974_gb300 import api, synth
+    out = {}
+    for kind, nt, sig, max_iter in (("scalar", 240, 2.0, 2000), ("jones", 120, 2.0, 100)):
+        b = synth.make_smooth(kind, n_ant=64, n_t=nt, n_chan=64, sigma=sig, f_corr_hz=1e9)
+        vis, model = torch.from_numpy(b.vis).to(dev), torch.from_numpy(b.model).to(dev)
+        g0 = torch.from_numpy(b.g0()).to(dev)
+        call = lambda: api.calibrate_di_smooth(vis, model, nt, 64, b.ant1, b.ant2, 64, g0.clone(), 4.0, 0.0,
+                                               tol=TOL, max_iter=max_iter)
+        ms, (_, it, _, st) = _median_ms(dev, call, reps=1)
+        iters = int(it.cpu().numpy()[0])
+        row_b = 16 if kind == "scalar" else 64
+        out[kind] = {"workload": SMOOTH_WORKLOAD.format(nt=nt, sig=sig) + (" (2x2: a fixed iteration cap; the "
+                     "polarized update contracts slowly)" if kind == "jones" else ""),
+                     "rows": b.n_rows, "ms": ms, "iters": iters, "status": int(st.cpu().numpy()[0]),
+                     "ms_per_iteration": ms / max(iters, 1),
+                     "rows_read_per_iteration_gbs": b.n_rows * row_b / (ms / max(iters, 1) / 1e3) / 1e9,
+                     "hbm_frac_rows_only": b.n_rows * row_b / (ms / max(iters, 1) / 1e3) / 1e9 / peaks["hbm_gbs"],
+                     "peak_source": which}
+        del vis, model
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, world, local = _env_rank()
@@ -675,6 +828,8 @@ def run_gpu(args):
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_block(b, 0)
             out["cpu_baseline_openmp"] = cpu_openmp_block(rank_seed(0))
+        if not args.no_weights and world == 1:
+            out["weights"] = weights_block(dev, args, b, vis, model, lay, g0)
         if not args.no_warm and world == 1:
             del vis, model
             torch.cuda.empty_cache()
@@ -683,6 +838,11 @@ def run_gpu(args):
             out["dd_cohjones"] = dd_block(dev, args, peaks, which)
         if not args.no_uneven and world == 1:
             out["uneven"] = uneven_block(dev, args)
+        if not args.no_dd and world == 1:
+            out["dd_alljones"] = alljones_block(dev, args, peaks, which)
+            out["dd_jones2x2"] = ddpol_block(dev, args, peaks, which)
+        if not args.no_smooth and world == 1:
+            out["smooth"] = smooth_block(dev, args, peaks, which)
         print(json.dumps(out))
     if dist:
         dist.barrier()
@@ -703,6 +863,8 @@ def main():
     ap.add_argument('--no-dd', action='store_true', help='skip the direction-dependent (CohJones) workload')
     ap.add_argument('--dd-only', action='store_true', help='run only the direction-dependent workload')
     ap.add_argument('--no-uneven', action='store_true', help='skip the uneven batched workload')
+    ap.add_argument('--no-weights', action='store_true', help='skip the weighted headline solve')
+    ap.add_argument('--no-smooth', action='store_true', help='skip the smoothing workloads')
     ap.add_argument('--uneven-intervals', type=int, default=4096, help='intervals of the uneven workload')
     ap.add_argument('--path', type=int, default=0,
                     help='StefCal schedule only: 0 auto (moments), 1 raw-row streaming, 2 resident, 3 moments')
