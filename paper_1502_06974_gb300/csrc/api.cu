@@ -1320,8 +1320,6 @@ static int run_smooth(int kind, const void* vis, const void* model, const gc_smo
   int rc = validate_layout(&L, 1);
   if (rc != GC_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  DIPlan* P = nullptr;
-  if ((rc = get_di_plan(0, kind, GC_DTYPE_C64, 1, &L, &P, stream))) return rc;
   // Gaussian taps exp(-x^2 / 2 sigma^2), |x| <= ceil(3 sigma) (one tap of 1 for sigma = 0)
   auto taps = [](double sigma, std::vector<float>& w) {
     const int R = sigma > 0.0 ? (int)std::ceil(3.0 * sigma) : 0;
@@ -1331,50 +1329,63 @@ static int run_smooth(int kind, const void* vis, const void* model, const gc_smo
   };
   std::vector<float> wt, wf;
   const int Rt = taps(sm->sigma_t, wt), Rf = taps(sm->sigma_f, wf);
+  // every antenna's (baseline * 2 + side) list in baseline order, the same for every sample, and
+  // the baselines' antenna pairs
+  std::vector<int32_t> ant_off(sm->n_ant + 1, 0), ent(2 * (size_t)sm->n_bl), a12(2 * (size_t)sm->n_bl);
+  for (int b = 0; b < sm->n_bl; ++b) { ant_off[sm->ant1[b] + 1]++; ant_off[sm->ant2[b] + 1]++; }
+  for (int p = 0; p < sm->n_ant; ++p) ant_off[p + 1] += ant_off[p];
+  {
+    std::vector<int32_t> fill(ant_off.begin(), ant_off.end() - 1);
+    for (int b = 0; b < sm->n_bl; ++b) {
+      const int p = sm->ant1[b], q = sm->ant2[b];
+      ent[fill[p]++] = 2 * b;
+      ent[fill[q]++] = 2 * b + 1;
+      a12[2 * b] = p;
+      a12[2 * b + 1] = q;
+    }
+  }
   const int64_t n_gain = n_s * sm->n_ant;
-  const int JD = kind == 0 ? 2 : 8, JJ = kind == 0 ? 1 : 8, GW = kind == 0 ? 2 : 8;
-  void *jd = nullptr, *jj = nullptr, *tmp = nullptr, *sjd = nullptr, *sjj = nullptr, *gnew = nullptr, *aux = nullptr;
+  const int NC = kind == 0 ? 3 : 12, GW = kind == 0 ? 2 : 8;
+  void *sums = nullptr, *tmp = nullptr, *ssum = nullptr, *gnew = nullptr, *aux = nullptr;
   const size_t tb = (wt.size() + wf.size()) * sizeof(float);
-  if ((rc = ws_get("sm_jd", (size_t)n_gain * JD * 4, &jd)) || (rc = ws_get("sm_jj", (size_t)n_gain * JJ * 4, &jj)) ||
-      (rc = ws_get("sm_tmp", (size_t)n_gain * 8 * 4, &tmp)) || (rc = ws_get("sm_sjd", (size_t)n_gain * JD * 4, &sjd)) ||
-      (rc = ws_get("sm_sjj", (size_t)n_gain * JJ * 4, &sjj)) || (rc = ws_get("sm_gnew", (size_t)n_gain * GW * 4, &gnew)) ||
-      (rc = ws_get("sm_aux", tb + 32 + (size_t)n_int * 3 * 8, &aux)))
+  const size_t lb = (ant_off.size() + ent.size() + a12.size()) * sizeof(int32_t);
+  if ((rc = ws_get("sm_sums", (size_t)n_gain * NC * 4, &sums)) || (rc = ws_get("sm_tmp", (size_t)n_gain * NC * 4, &tmp)) ||
+      (rc = ws_get("sm_ssum", (size_t)n_gain * NC * 4, &ssum)) || (rc = ws_get("sm_gnew", (size_t)n_gain * GW * 4, &gnew)) ||
+      (rc = ws_get("sm_aux", tb + 32 + (size_t)n_int * 3 * 8 + lb, &aux)))
     return rc;
   float* dtaps = (float*)aux;
   int* state = (int*)((char*)aux + ((tb + 15) & ~(size_t)15));
   double* partials = (double*)(state + 4);
+  int32_t* d_a12 = (int32_t*)(partials + 3 * (size_t)n_int);  // 8-byte aligned: read as int2
+  int32_t* d_off = d_a12 + a12.size();
+  int32_t* d_ent = d_off + ant_off.size();
   GC_CUDA(cudaMemcpyAsync(dtaps, wt.data(), wt.size() * 4, cudaMemcpyHostToDevice, s));
   GC_CUDA(cudaMemcpyAsync(dtaps + wt.size(), wf.data(), wf.size() * 4, cudaMemcpyHostToDevice, s));
-  GC_CUDA(cudaMemsetAsync(jd, 0, (size_t)n_gain * JD * 4, s));  // antennas without data stay zero
-  GC_CUDA(cudaMemsetAsync(jj, 0, (size_t)n_gain * JJ * 4, s));
+  GC_CUDA(cudaMemcpyAsync(d_off, ant_off.data(), ant_off.size() * 4, cudaMemcpyHostToDevice, s));
+  GC_CUDA(cudaMemcpyAsync(d_ent, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice, s));
+  GC_CUDA(cudaMemcpyAsync(d_a12, a12.data(), a12.size() * 4, cudaMemcpyHostToDevice, s));
   GC_CUDA_I(sm_launch_init(state, stream));
-  DIArgs a = P->args;
-  a.kbase = nullptr;
-  a.vis = vis;
-  a.model = model;
-  a.gains = gains;
-  a.jhd_out = jd;
-  a.jhj_out = jj;
-  a.k = 1;
-  if (P->scr_elems > 0) {
-    void* scr = nullptr;
-    if ((rc = ws_get("di_scratch", (size_t)P->scr_elems * 4, &scr))) return rc;
-    a.scratch = scr;
-  }
   int* flag = nullptr;
   if ((rc = pinned_flag(&flag))) return rc;
-  const int64_t per_s = (int64_t)sm->n_ant;  // gain slots per sample
+  const int64_t inner = (int64_t)sm->n_ant * NC;  // floats per sample
   for (int k = 1; k <= opt->max_iter; ++k) {
-    GC_CUDA_I(di_launch_init(a, P->n_int, P->n_active0, stream));
-    GC_CUDA_I(di_launch_iter(kind, GC_DTYPE_C64, 1, a, P->grid, P->smem, stream));
-    // frequency, then time: [n_t][n_f][n_ant * W] with W floats per slot
-    GC_CUDA_I(sm_launch_conv((const float*)jd, (float*)tmp, sm->n_t, sm->n_f, per_s * JD, dtaps + wt.size(), Rf, stream));
-    GC_CUDA_I(sm_launch_conv((const float*)tmp, (float*)sjd, 1, sm->n_t, (int64_t)sm->n_f * per_s * JD, dtaps, Rt, stream));
-    GC_CUDA_I(sm_launch_conv((const float*)jj, (float*)tmp, sm->n_t, sm->n_f, per_s * JJ, dtaps + wt.size(), Rf, stream));
-    GC_CUDA_I(sm_launch_conv((const float*)tmp, (float*)sjj, 1, sm->n_t, (int64_t)sm->n_f * per_s * JJ, dtaps, Rt, stream));
-    GC_CUDA_I(sm_launch_update(kind, (const float*)sjd, (const float*)sjj, (const float*)gains, (float*)gnew, n_int,
-                               sm->n_ant, k, opt->schedule, opt->max_iter, opt->tol, state, partials, stream));
-    g_launches += 9;
+    GC_CUDA_I(sm_launch_acc(kind, (const float*)vis, (const float*)model, (const float*)gains, n_int, sm->n_bl,
+                            sm->n_ant, d_off, d_ent, d_a12, state, (float*)sums, stream));
+    // frequency, then time: [n_t][n_f][n_ant * NC]; an axis without smoothing (one tap of 1) is skipped
+    const float* cur = (const float*)sums;
+    if (Rf > 0) {
+      GC_CUDA_I(sm_launch_conv(cur, (float*)tmp, sm->n_t, sm->n_f, inner, dtaps + wt.size(), Rf, stream));
+      cur = (const float*)tmp;
+      g_launches++;
+    }
+    if (Rt > 0) {
+      GC_CUDA_I(sm_launch_conv(cur, (float*)ssum, 1, sm->n_t, (int64_t)sm->n_f * inner, dtaps, Rt, stream));
+      cur = (const float*)ssum;
+      g_launches++;
+    }
+    GC_CUDA_I(sm_launch_update(kind, cur, (const float*)gains, (float*)gnew, n_int, sm->n_ant, k, opt->schedule,
+                               opt->max_iter, opt->tol, state, partials, stream));
+    g_launches += 4;
     GC_CUDA(cudaMemcpyAsync(flag, state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     GC_CUDA(cudaStreamSynchronize(s));
     if (flag[0]) break;
@@ -1382,6 +1393,12 @@ static int run_smooth(int kind, const void* vis, const void* model, const gc_smo
   if (iters_out) GC_CUDA(cudaMemcpyAsync(iters_out, state + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   if (status_out) GC_CUDA(cudaMemcpyAsync(status_out, state + 2, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   if (chi2_out && opt->compute_chi2) {
+    DIPlan* P = nullptr;
+    if ((rc = get_di_plan(0, kind, GC_DTYPE_C64, 1, &L, &P, stream))) return rc;
+    DIArgs a = P->args;
+    a.kbase = nullptr;
+    a.vis = vis;
+    a.model = model;
     a.gains = gains;
     GC_CUDA_I(di_launch_chi2(kind, GC_DTYPE_C64, a, P->chi2_items, chi2_out, P->n_int, P->grid, stream));
     g_launches += 2;

@@ -105,15 +105,20 @@ int di_launch_iter(int kind, int dtype, int acc_only, const DIArgs& a, int grid,
 int di_launch_init(const DIArgs& a, int n_int, int n_active0, void* stream);
 int di_macc_smem(int kind, int na_max, int red_chunks, int prefetch);
 int di_macc_bulk_smem(int kind, int na_max, int tblk_max);
-// Smoothing in time and frequency (smooth.cu): separable convolution along one axis of a
+// Smoothing in time and frequency (smooth.cu): per-sample per-antenna sums (one CTA per sample; the
+// antennas' (baseline, side) lists ant_off / ent sorted by baseline, a12 the pairs [n_bl][2]);
+// separable convolution along one axis of a
 // [n_outer][n_axis][inner] float array with 2R + 1 taps; the update of every sample (phase
 // alignment, schedule, canonical gauge) and the grid-wide stopping rule (state [4] ints: done,
 // iterations, status, apply; partials 3 doubles per sample), then the staged gains copied over the
 // current ones when the step is kept.
 int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int64_t inner, const float* taps, int R,
                    void* stream);
-int sm_launch_update(int kind, const float* jd, const float* jj, const float* gains, float* gnew, int n_s, int n_ant,
-                     int k, int schedule, int max_iter, double tol, int* state, double* partials, void* stream);
+int sm_launch_acc(int kind, const float* vis, const float* model, const float* gains, int n_s, int n_bl, int n_ant,
+                  const int32_t* ant_off, const int32_t* ent, const int32_t* a12, const int* state, float* sums,
+                  void* stream);
+int sm_launch_update(int kind, const float* sums, const float* gains, float* gnew, int n_s, int n_ant, int k,
+                     int schedule, int max_iter, double tol, int* state, double* partials, void* stream);
 int sm_launch_init(int* state, void* stream);
 // Tries of the bulk-copy accumulate kernel's first wait per tile on the current device (< 0: the
 // default bound).  Returns cudaError_t as int.

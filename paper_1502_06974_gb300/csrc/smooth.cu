@@ -1,10 +1,9 @@
 // Smoothing in time and frequency (Sect. 3.4): every sample of a time x frequency grid has its own
 // gains, updated by the ratio of two kernel convolutions (eq. JHJ:diag:smooth),
 //     scalar: g_p = (w o alpha_p) / (w o beta_p),  2x2: G_p = (w o C_p) (w o H_p)^-1,
-// with alpha_p, beta_p (C_p, H_p) the per-sample sums of StefCal's update.  The per-sample sums come
-// from the library's accumulation pass (every sample one solution interval); this file holds the
-// separable convolution along one axis of the grid, the update with the schedule, and the
-// convergence test over the whole grid.
+// with alpha_p, beta_p (C_p, H_p) the per-sample sums of StefCal's update: a per-sample
+// accumulation, the separable convolution along one axis of the grid, the update with the
+// schedule and the phase conventions, and the convergence test over the whole grid.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,25 +30,170 @@ __global__ void sm_conv_kernel(const float* __restrict__ in, float* __restrict__
   out[idx] = s;
 }
 
-// The smoothed sums of every gain slot in the layout K::solve reads: scalar [Re c, Im c, A] from
-// jhd (complex) and jhj (real); 2x2 [C (8), H00, H11, Re H01, Im H01] from jhd (C, 2x2 complex)
-// and jhj (H, 2x2 complex).
-template <class K> struct SmoothIn;
-template <> struct SmoothIn<ScalarKind<float>> {
-  static constexpr int JD = 2, JJ = 1;  // floats per slot in jhd, jhj
-  static GC_DEV void load(const float* jd, const float* jj, int64_t x, float* v) {
-    v[0] = jd[2 * x]; v[1] = jd[2 * x + 1]; v[2] = jj[x];
+// One side of a row's contribution to StefCal's per-antenna sums, in the component order K::solve
+// reads (scalar [Re c, Im c, A]; 2x2 [C (8), H00, H11, Re H01, Im H01]).  Stored row (p, q), antenna
+// p: y = m conj(g_q), c += conj(y) d, A += |y|^2 (2x2: Y = M G_q^H, C += D Y^H, H += Y Y^H).
+// Conjugate row, antenna q: w = g_p m, c += w conj(d), A += |w|^2 (2x2: W = G_p M, C += D^H W,
+// H += W^H W).  o: the other antenna's gain.
+template <class K> struct SmoothRow;
+template <> struct SmoothRow<ScalarKind<float>> {
+  static GC_DEV void add(const float* vis, const float* mod, int64_t r, const Cx<float>& o, bool conj_side,
+                         float* v) {
+    const Cx<float> d = Vec<float>::ld1(vis + 2 * r), m = Vec<float>::ld1(mod + 2 * r);
+    if (!conj_side) {
+      const Cx<float> y = mulc_(m, o);
+      v[0] = fmaf(y.x, d.x, fmaf(y.y, d.y, 0.f));
+      v[1] = fmaf(y.x, d.y, -y.y * d.x);
+      v[2] = abs2_(y);
+    } else {
+      const Cx<float> w = mul_(o, m);
+      v[0] = fmaf(w.x, d.x, w.y * d.y);
+      v[1] = fmaf(w.y, d.x, -w.x * d.y);
+      v[2] = abs2_(w);
+    }
   }
 };
-template <> struct SmoothIn<JonesKind<float>> {
-  static constexpr int JD = 8, JJ = 8;
-  static GC_DEV void load(const float* jd, const float* jj, int64_t x, float* v) {
+template <> struct SmoothRow<JonesKind<float>> {
+  static GC_DEV void add(const float* vis, const float* mod, int64_t r, const M2<float>& o, bool conj_side,
+                         float* v) {
+    const M2<float> D = Vec<float>::ld4(vis + 8 * r), M = Vec<float>::ld4(mod + 8 * r);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = jd[8 * x + c];
-    const float* h = jj + 8 * x;
-    v[8] = h[0]; v[9] = h[6]; v[10] = h[2]; v[11] = h[3];
+    for (int c = 0; c < 12; ++c) v[c] = 0.f;
+    if (!conj_side) {
+      const M2<float> Y = mmh_(M, o);
+      fmac2(v[0], v[1], D.a, Y.a); fmac2(v[0], v[1], D.b, Y.b);
+      fmac2(v[2], v[3], D.a, Y.c); fmac2(v[2], v[3], D.b, Y.d);
+      fmac2(v[4], v[5], D.c, Y.a); fmac2(v[4], v[5], D.d, Y.b);
+      fmac2(v[6], v[7], D.c, Y.c); fmac2(v[6], v[7], D.d, Y.d);
+      v[8] = abs2_(Y.a) + abs2_(Y.b);
+      v[9] = abs2_(Y.c) + abs2_(Y.d);
+      fmac2(v[10], v[11], Y.a, Y.c); fmac2(v[10], v[11], Y.b, Y.d);
+    } else {
+      const M2<float> W = mm_(o, M);
+      cfma2(v[0], v[1], D.a, W.a); cfma2(v[0], v[1], D.c, W.c);
+      cfma2(v[2], v[3], D.a, W.b); cfma2(v[2], v[3], D.c, W.d);
+      cfma2(v[4], v[5], D.b, W.a); cfma2(v[4], v[5], D.d, W.c);
+      cfma2(v[6], v[7], D.b, W.b); cfma2(v[6], v[7], D.d, W.d);
+      v[8] = abs2_(W.a) + abs2_(W.c);
+      v[9] = abs2_(W.b) + abs2_(W.d);
+      cfma2(v[10], v[11], W.a, W.b); cfma2(v[10], v[11], W.c, W.d);
+    }
   }
 };
+
+// Per-sample sums: one CTA per sample.  The sample's baselines are taken in tiles of TB: every
+// thread forms both sides of its baselines' contributions from coalesced row loads (each row read
+// once) into shared memory; then kSmSplit threads per antenna add the tile's entries of its
+// (baseline, side) list -- sorted by baseline, so each tile's entries are the next ones of the
+// list -- each a fixed share, into compensated FP32 sums combined in a fixed order.  The sample's
+// gains are staged in shared memory.  sums [n_s][n_ant][NC].  Used for the scalar kind.
+template <class K> struct SmoothTile { static constexpr int TB = 1024; };
+constexpr int kSmSplit = 4;  // threads per antenna in the per-antenna sums
+
+template <class K>
+__global__ void __launch_bounds__(256) sm_acc_kernel(const float* __restrict__ vis, const float* __restrict__ mod,
+                                                     const float* __restrict__ gains, int n_bl, int n_ant,
+                                                     const int32_t* __restrict__ ant_off,
+                                                     const int32_t* __restrict__ ent, const int32_t* __restrict__ a12,
+                                                     const int* state, float* __restrict__ sums) {
+  constexpr int NC = K::NC, GW = K::GW, TB = SmoothTile<K>::TB;
+  extern __shared__ __align__(16) float smem[];
+  float* gs = smem;                        // [n_ant][GW]
+  float* con = smem + n_ant * GW;          // [TB][2][NC] contributions of the tile's baselines
+  if (state[0]) return;
+  const int smp = blockIdx.x, tid = threadIdx.x;
+  const int64_t g0 = (int64_t)smp * n_ant, r0 = (int64_t)smp * n_bl;
+  for (int x = tid; x < n_ant * GW; x += blockDim.x) gs[x] = gains[g0 * GW + x];
+  __syncthreads();
+  // antenna p = pb + tid / kSmSplit, part j = tid % kSmSplit: the part's share of the antenna's
+  // entries of every tile (entries j, j + kSmSplit, ..); the parts combine in a fixed order at the end
+  const int j = tid % kSmSplit;
+  for (int pb = 0; pb < n_ant; pb += blockDim.x / kSmSplit) {
+    const int p = pb + tid / kSmSplit;
+    float acc[NC], cmp[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = cmp[c] = 0.f;
+    int e = p < n_ant ? __ldg(ant_off + p) : 0;
+    const int e1 = p < n_ant ? __ldg(ant_off + p + 1) : 0;
+    for (int b0 = 0; b0 < n_bl; b0 += TB) {
+      const int nb = min(TB, n_bl - b0);
+      for (int bl = tid; bl < nb; bl += blockDim.x) {
+        const int b = b0 + bl;
+        const int2 pq = __ldg(reinterpret_cast<const int2*>(a12) + b);
+        SmoothRow<K>::add(vis, mod, r0 + b, K::ld_gain(gs + GW * pq.y), false, con + (2 * bl) * NC);
+        SmoothRow<K>::add(vis, mod, r0 + b, K::ld_gain(gs + GW * pq.x), true, con + (2 * bl + 1) * NC);
+      }
+      __syncthreads();
+      // the tile's entries of the antenna are e .. e_end - 1
+      int e_end = e;
+      while (e_end < e1 && (__ldg(ent + e_end) >> 1) < b0 + nb) ++e_end;
+      for (int x = e + j; x < e_end; x += kSmSplit) {
+        const int en = __ldg(ent + x);
+        const float* v = con + (2 * ((en >> 1) - b0) + (en & 1)) * NC;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) kahan_add(acc[c], cmp[c], v[c]);
+      }
+      e = e_end;
+      __syncthreads();
+    }
+    // combine the kSmSplit parts (consecutive lanes) in part order
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float v = acc[c] - cmp[c];
+      float tot = 0.f;
+#pragma unroll
+      for (int q = 0; q < kSmSplit; ++q) tot += __shfl_sync(0xffffffffu, v, (threadIdx.x & 31 & ~(kSmSplit - 1)) + q);
+      if (p < n_ant && j == 0) sums[(g0 + p) * NC + c] = tot;
+    }
+  }
+}
+
+// The same sums with one thread per antenna reading its rows directly (four rows' contributions
+// formed before they are added, in list order), each row read by the two threads of its antennas
+// (the second read from L1): faster for the 64-byte 2x2 rows, whose tiles of contributions would
+// fill shared memory.
+template <class K>
+__global__ void __launch_bounds__(64) sm_acc_ant_kernel(const float* __restrict__ vis, const float* __restrict__ mod,
+                                                        const float* __restrict__ gains, int n_bl, int n_ant,
+                                                        const int32_t* __restrict__ ant_off,
+                                                        const int32_t* __restrict__ ent,
+                                                        const int32_t* __restrict__ a12, const int* state,
+                                                        float* __restrict__ sums) {
+  constexpr int NC = K::NC, GW = K::GW, U = 4;
+  extern __shared__ __align__(16) float gs[];  // [n_ant][GW]
+  if (state[0]) return;
+  const int smp = blockIdx.x, tid = threadIdx.x;
+  const int64_t g0 = (int64_t)smp * n_ant, r0 = (int64_t)smp * n_bl;
+  for (int x = tid; x < n_ant * GW; x += blockDim.x) gs[x] = gains[g0 * GW + x];
+  __syncthreads();
+  for (int p = tid; p < n_ant; p += blockDim.x) {
+    float acc[NC], cmp[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = cmp[c] = 0.f;
+    const int e0 = __ldg(ant_off + p), e1 = __ldg(ant_off + p + 1);
+    for (int e = e0; e < e1; e += U) {
+      float v[U][NC];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (e + u < e1) {
+          const int en = __ldg(ent + e + u);
+          const int other = __ldg(a12 + 2 * (en >> 1) + ((en & 1) ? 0 : 1));
+          SmoothRow<K>::add(vis, mod, r0 + (en >> 1), K::ld_gain(gs + GW * other), en & 1, v[u]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) v[u][c] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) kahan_add(acc[c], cmp[c], v[u][c]);
+    }
+    float* out = sums + (g0 + p) * NC;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[c] = acc[c] - cmp[c];
+  }
+}
 
 // Complex sums over a sample's antennas for the phase conventions: scalar sum conj(a) b, 2x2
 // sum tr(A^H B) (alignment); scalar sum g, 2x2 sum tr G (canonical gauge).
@@ -75,79 +219,95 @@ template <> struct SmoothPhase<JonesKind<float>> {
   }
 };
 
-// e^{-i arg z} (1 for z = 0)
+// e^{-i arg z} (1 for z = 0); the sum is formed in FP64, the unit factor in FP32
 GC_DEV Cx<float> unphase(double zx, double zy) {
-  const double m = sqrt(zx * zx + zy * zy);
-  return m > 0.0 ? cx<float>((float)(zx / m), (float)(-zy / m)) : cx<float>(1.f, 0.f);
+  const float x = (float)zx, y = (float)zy;
+  const float m2 = fmaf(x, x, y * y);
+  if (!(m2 > 0.f)) return cx<float>(1.f, 0.f);
+  const float r = rsqrtf(m2);
+  return cx<float>(x * r, -y * r);
 }
 
-// One CTA per sample: for its antennas the GN gains from the smoothed sums, rotated by the common
+constexpr int kSmWarps = 8;  // samples per update CTA (one warp each)
+
+GC_DEV double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One warp per sample: for its antennas the GN gains from the smoothed sums, rotated by the common
 // phase that best aligns them with the current gains; the schedule (odd k: those gains, even k:
 // their average with the current ones); the result put in the canonical gauge (sum of the gains,
-// 2x2 of their traces, real and non-negative) and staged in gnew; the sample's step norms.
+// 2x2 of their traces, real and non-negative) and staged in gnew; the sample's step norms, summed
+// over the CTA's samples in warp order into one partial per CTA.
 // state[0] done, [1] iterations, [2] status, [3] apply the staged gains.
-// partials: per sample {|dg|^2, |g|^2 (FP64), flags (bit 0 non-finite, bit 1 singular)}.
+// partials: per CTA {|dg|^2, |g|^2 (FP64), flags (bit 0 non-finite, bit 1 singular)}.
 template <class K>
-__global__ void __launch_bounds__(64) sm_update_kernel(const float* __restrict__ jd, const float* __restrict__ jj,
-                                                       const float* __restrict__ gains, float* __restrict__ gnew,
-                                                       int n_ant, int k, int schedule, const int* state,
-                                                       double* partials) {
+__global__ void __launch_bounds__(32 * kSmWarps) sm_update_kernel(const float* __restrict__ sums,
+                                                                  const float* __restrict__ gains,
+                                                                  float* __restrict__ gnew, int n_s, int n_ant, int k,
+                                                                  int schedule, const int* state, double* partials) {
   using P = SmoothPhase<K>;
-  __shared__ double red[32];
+  __shared__ double red[kSmWarps][3];
   if (state[0]) return;
-  const int smp = blockIdx.x, tid = threadIdx.x;
-  const int64_t g0 = (int64_t)smp * n_ant;
-  const bool gn_step = schedule == GC_SCHED_GN || (k & 1);
-  int sing = 0;
-  // GN gains and their alignment sum
-  double ax = 0.0, ay = 0.0;
-  for (int p = tid; p < n_ant; p += blockDim.x) {
-    float v[K::NC];
-    SmoothIn<K>::load(jd, jj, g0 + p, v);
-    const typename K::G old = K::ld_gain(gains + K::GW * (g0 + p));
-    typename K::G gn;
-    if (!K::solve(v, old, gn)) sing = 1;
-    K::st_gain(gnew + K::GW * (g0 + p), gn);
-    const Cx<float> t = P::inner(old, gn);
-    ax += t.x; ay += t.y;
-  }
-  ax = block_sum<double>(ax, red);
-  ay = block_sum<double>(ay, red);
-  const Cx<float> ea = unphase(ax, ay);
-  // aligned, scheduled gains and their canonical-gauge sum
-  double sx = 0.0, sy = 0.0;
-  for (int p = tid; p < n_ant; p += blockDim.x) {
-    const typename K::G old = K::ld_gain(gains + K::GW * (g0 + p));
-    const typename K::G gn = P::rot(K::ld_gain(gnew + K::GW * (g0 + p)), ea);
-    const typename K::G nw = gn_step ? gn : K::avg(old, gn);
-    K::st_gain(gnew + K::GW * (g0 + p), nw);
-    const Cx<float> t = P::trace(nw);
-    sx += t.x; sy += t.y;
-  }
-  sx = block_sum<double>(sx, red);
-  sy = block_sum<double>(sy, red);
-  const Cx<float> ec = unphase(sx, sy);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int smp = blockIdx.x * kSmWarps + w;
   double d2 = 0.0, n2 = 0.0;
-  int nonfin = 0;
-  for (int p = tid; p < n_ant; p += blockDim.x) {
-    const typename K::G old = K::ld_gain(gains + K::GW * (g0 + p));
-    const typename K::G nw = P::rot(K::ld_gain(gnew + K::GW * (g0 + p)), ec);
-    if (!K::finite(nw)) nonfin = 1;
-    d2 += (double)K::dist2(nw, old);
-    n2 += (double)K::norm2(nw);
-    K::st_gain(gnew + K::GW * (g0 + p), nw);
+  int fl = 0;
+  if (smp < n_s) {  // warp-uniform
+    const int64_t g0 = (int64_t)smp * n_ant;
+    const bool gn_step = schedule == GC_SCHED_GN || (k & 1);
+    int sing = 0;
+    double ax = 0.0, ay = 0.0;
+    for (int p = lane; p < n_ant; p += 32) {
+      float v[K::NC];
+#pragma unroll
+      for (int c = 0; c < K::NC; ++c) v[c] = sums[(g0 + p) * K::NC + c];
+      const typename K::G old = K::ld_gain(gains + K::GW * (g0 + p));
+      typename K::G gn;
+      if (!K::solve(v, old, gn)) sing = 1;
+      K::st_gain(gnew + K::GW * (g0 + p), gn);
+      const Cx<float> t = P::inner(old, gn);
+      ax += t.x; ay += t.y;
+    }
+    const Cx<float> ea = unphase(warp_sum_d(ax), warp_sum_d(ay));
+    double sx = 0.0, sy = 0.0;
+    for (int p = lane; p < n_ant; p += 32) {
+      const typename K::G old = K::ld_gain(gains + K::GW * (g0 + p));
+      const typename K::G gn = P::rot(K::ld_gain(gnew + K::GW * (g0 + p)), ea);
+      const typename K::G nw = gn_step ? gn : K::avg(old, gn);
+      K::st_gain(gnew + K::GW * (g0 + p), nw);
+      const Cx<float> t = P::trace(nw);
+      sx += t.x; sy += t.y;
+    }
+    const Cx<float> ec = unphase(warp_sum_d(sx), warp_sum_d(sy));
+    int nonfin = 0;
+    for (int p = lane; p < n_ant; p += 32) {
+      const typename K::G old = K::ld_gain(gains + K::GW * (g0 + p));
+      const typename K::G nw = P::rot(K::ld_gain(gnew + K::GW * (g0 + p)), ec);
+      if (!K::finite(nw)) nonfin = 1;
+      d2 += (double)K::dist2(nw, old);
+      n2 += (double)K::norm2(nw);
+      K::st_gain(gnew + K::GW * (g0 + p), nw);
+    }
+    d2 = warp_sum_d(d2);
+    n2 = warp_sum_d(n2);
+    fl = (__any_sync(0xffffffffu, nonfin) ? 1 : 0) | (__any_sync(0xffffffffu, sing) ? 2 : 0);
   }
-  d2 = block_sum<double>(d2, red);
-  n2 = block_sum<double>(n2, red);
-  const int fl = __syncthreads_or(nonfin) | (__syncthreads_or(sing) << 1);
-  if (tid == 0) {
-    double* q = partials + 3 * smp;
-    q[0] = d2; q[1] = n2; q[2] = (double)fl;
+  if (lane == 0) { red[w][0] = d2; red[w][1] = n2; red[w][2] = (double)fl; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double D = 0.0, N = 0.0;
+    int f = 0;
+    for (int j = 0; j < kSmWarps; ++j) { D += red[j][0]; N += red[j][1]; f |= (int)red[j][2]; }
+    double* q = partials + 3 * blockIdx.x;
+    q[0] = D; q[1] = N; q[2] = (double)f;
   }
 }
 
-// One CTA: the grid's step norms from the per-sample partials (each thread a fixed stride, then a
-// fixed tree), the stopping rule, and whether the staged gains are applied.
+// One CTA: the grid's step norms from the per-CTA partials of the update (each thread a fixed
+// stride, then a fixed tree), the stopping rule, and whether the staged gains are applied.
 __global__ void __launch_bounds__(256) sm_final_kernel(const double* partials, int n_s, int k, int max_iter,
                                                        double tol, int* state) {
   __shared__ double red[32];
@@ -194,14 +354,35 @@ int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int
   return (int)cudaGetLastError();
 }
 
-int sm_launch_update(int kind, const float* jd, const float* jj, const float* gains, float* gnew, int n_s, int n_ant,
-                     int k, int schedule, int max_iter, double tol, int* state, double* partials, void* stream) {
+int sm_launch_acc(int kind, const float* vis, const float* model, const float* gains, int n_s, int n_bl, int n_ant,
+                  const int32_t* ant_off, const int32_t* ent, const int32_t* a12, const int* state, float* sums,
+                  void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
+  if (kind == 0) {
+    using K = ScalarKind<float>;
+    const size_t smem = sizeof(float) * ((size_t)n_ant * K::GW + (size_t)SmoothTile<K>::TB * 2 * K::NC);
+    cudaError_t e = cudaFuncSetAttribute(sm_acc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    sm_acc_kernel<K><<<n_s, 256, smem, s>>>(vis, model, gains, n_bl, n_ant, ant_off, ent, a12, state, sums);
+  } else {
+    using K = JonesKind<float>;
+    const size_t smem = sizeof(float) * (size_t)n_ant * K::GW;
+    sm_acc_ant_kernel<K><<<n_s, 64, smem, s>>>(vis, model, gains, n_bl, n_ant, ant_off, ent, a12, state, sums);
+  }
+  return (int)cudaGetLastError();
+}
+
+int sm_launch_update(int kind, const float* sums, const float* gains, float* gnew, int n_s, int n_ant, int k,
+                     int schedule, int max_iter, double tol, int* state, double* partials, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (n_s + kSmWarps - 1) / kSmWarps;
   if (kind == 0)
-    sm_update_kernel<ScalarKind<float>><<<n_s, 64, 0, s>>>(jd, jj, gains, gnew, n_ant, k, schedule, state, partials);
+    sm_update_kernel<ScalarKind<float>><<<nb, 32 * kSmWarps, 0, s>>>(sums, gains, gnew, n_s, n_ant, k, schedule, state,
+                                                                     partials);
   else
-    sm_update_kernel<JonesKind<float>><<<n_s, 64, 0, s>>>(jd, jj, gains, gnew, n_ant, k, schedule, state, partials);
-  sm_final_kernel<<<1, 256, 0, s>>>(partials, n_s, k, max_iter, tol, state);
+    sm_update_kernel<JonesKind<float>><<<nb, 32 * kSmWarps, 0, s>>>(sums, gains, gnew, n_s, n_ant, k, schedule, state,
+                                                                    partials);
+  sm_final_kernel<<<1, 256, 0, s>>>(partials, nb, k, max_iter, tol, state);
   const int64_t nf = (int64_t)n_s * n_ant * (kind == 0 ? 2 : 8);
   sm_apply_kernel<<<(unsigned)std::min<int64_t>((nf + 255) / 256, 4 * 152), 256, 0, s>>>(gnew, const_cast<float*>(gains),
                                                                                         nf, state);
