@@ -154,7 +154,7 @@ __device__ bool chol_solve_warp(const double2* Aup, const double2* b, double2* x
 // r >= ND shadow row ND - 1 and store nothing).  False when an FP32 pivot is not positive: the
 // caller then runs the FP64 factorisation, which alone decides singularity.
 // Ls: [ND][ND] of shared memory (the factor, rows); the solution goes to x.
-template <int ND>
+template <int ND, int NR = 1>
 __device__ bool chol_solve_warp_mixed(const Cx<float>* Ah, const Cx<float>* Al, const Cx<float>* bh,
                                       const Cx<float>* bl, Cx<float>* x, Cx<float>* Ls) {
   constexpr unsigned kAll = 0xffffffffu;
@@ -212,9 +212,12 @@ __device__ bool chol_solve_warp_mixed(const Cx<float>* Ah, const Cx<float>* Al, 
     }
     return v;
   };
-  const Cx<float> x0 = subst(bh[r]);
+  for (int rr = 0; rr < NR; ++rr) {  // right-hand sides [NR][ND], one factorisation
+  const Cx<float>* bhr = bh + rr * ND;
+  const Cx<float>* blr = bl + rr * ND;
+  const Cx<float> x0 = subst(bhr[r]);
   // residual in float-float: r_r = b_r - sum_j A[r][j] x0_j, two interleaved partial sums per part
-  FF rx0{bh[r].x, bl[r].x}, ry0{bh[r].y, bl[r].y}, rx1{0.f, 0.f}, ry1{0.f, 0.f};
+  FF rx0{bhr[r].x, blr[r].x}, ry0{bhr[r].y, blr[r].y}, rx1{0.f, 0.f}, ry1{0.f, 0.f};
   float lox = 0.f, loy = 0.f;
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
@@ -234,7 +237,8 @@ __device__ bool chol_solve_warp_mixed(const Cx<float>* Ah, const Cx<float>* Al, 
   const FF rx = ff_add(rx0, rx1), ry = ff_add(ry0, ry1);
   const Cx<float> dres = cx<float>(rx.hi + (rx.lo - lox), ry.hi + (ry.lo - loy));
   const Cx<float> d = subst(dres);
-  if (lane < ND) x[lane] = add_(x0, d);
+  if (lane < ND) x[rr * ND + lane] = add_(x0, d);
+  }
   __syncwarp();
   return true;
 }

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(PolShape<ND>::ITHR) ddpol_iter_kernel(const DD
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<float>* gs = reinterpret_cast<Cx<float>*>(smem_raw);        // [n_ant][ND][4]
   float4* red = reinterpret_cast<float4*>(gs + (size_t)a.na_max * W);  // [LANES][NOUT]
-  __shared__ Cx<float> Hh[NU2], Hl[NU2], Ch[2 * N2], Cl[2 * N2], xs[W], rh[N2], rl[N2], xv[N2];
+  __shared__ Cx<float> Hh[NU2], Hl[NU2], Ch[2 * N2], Cl[2 * N2], xs[W], rh[2 * N2], rl[2 * N2], xv[2 * N2];
   __shared__ Cx<float> Ls[N2 * N2];
   __shared__ int s_last, s_sing, s_nf;
   __shared__ double s_red[80];
@@ -364,34 +364,35 @@ __global__ void __launch_bounds__(PolShape<ND>::ITHR) ddpol_iter_kernel(const DD
   if (a.method == 1) {
     if (tid < 32) ddpol_alljones_warp<ND>(Hh, Hl, Ch, Cl, gs + (size_t)p * W, xs, &s_sing);
   } else if (tid < 32) {
-    // CohJones: H X^H = CD^H, one right-hand side per row k of X
-    for (int kk = 0; kk < 2 && !s_sing; ++kk) {
-      for (int r = tid; r < N2; r += 32) {
-        rh[r] = conj_(Ch[kk * N2 + r]);
-        rl[r] = conj_(Cl[kk * N2 + r]);
-      }
-      __syncwarp();
-      bool ok = chol_solve_warp_mixed<N2>(Hh, Hl, rh, rl, xv, Ls);
-      if (!ok) {  // rare: not positive definite in FP32; FP64 decides
-        __shared__ double2 Ad[NU2], bd[N2], xd[N2], Am[N2 * N2];
-        __shared__ double dinv[N2];
-        __shared__ int s_ok;
-        for (int u = tid; u < NU2; u += 32)
-          Ad[u] = make_double2((double)Hh[u].x + (double)Hl[u].x, (double)Hh[u].y + (double)Hl[u].y);
-        for (int r = tid; r < N2; r += 32)
-          bd[r] = make_double2((double)rh[r].x + (double)rl[r].x, (double)rh[r].y + (double)rl[r].y);
-        __syncwarp();
-        ok = chol_solve_warp<N2>(Ad, bd, xd, Am, dinv, &s_ok);
-        for (int r = tid; r < N2; r += 32) xv[r] = cx<float>((float)xd[r].x, (float)xd[r].y);
-        __syncwarp();
-      }
-      if (!ok) {
-        if (tid == 0) s_sing = 1;
-      } else {
-        for (int r = tid; r < N2; r += 32) xs[(r >> 1) * 4 + 2 * kk + (r & 1)] = conj_(xv[r]);
-      }
-      __syncwarp();
+    // CohJones: H X^H = CD^H, one right-hand side per row k of X, one FP32 factorisation
+    for (int u = tid; u < 2 * N2; u += 32) {
+      rh[u] = conj_(Ch[u]);
+      rl[u] = conj_(Cl[u]);
     }
+    __syncwarp();
+    bool ok = chol_solve_warp_mixed<N2, 2>(Hh, Hl, rh, rl, xv, Ls);
+    for (int kk = 0; kk < 2 && !ok; ++kk) {  // rare: not positive definite in FP32; FP64 decides
+      __shared__ double2 Ad[NU2], bd[N2], xd[N2], Am[N2 * N2];
+      __shared__ double dinv[N2];
+      __shared__ int s_ok;
+      for (int u = tid; u < NU2; u += 32)
+        Ad[u] = make_double2((double)Hh[u].x + (double)Hl[u].x, (double)Hh[u].y + (double)Hl[u].y);
+      for (int r = tid; r < N2; r += 32)
+        bd[r] = make_double2((double)rh[kk * N2 + r].x + (double)rl[kk * N2 + r].x,
+                             (double)rh[kk * N2 + r].y + (double)rl[kk * N2 + r].y);
+      __syncwarp();
+      const bool ok64 = chol_solve_warp<N2>(Ad, bd, xd, Am, dinv, &s_ok);
+      for (int r = tid; r < N2; r += 32) xv[kk * N2 + r] = cx<float>((float)xd[r].x, (float)xd[r].y);
+      __syncwarp();
+      if (!ok64) { if (tid == 0) s_sing = 1; break; }
+      if (kk == 1) ok = true;
+    }
+    if (ok)
+      for (int u = tid; u < 2 * N2; u += 32) {
+        const int kk = u / N2, r = u - kk * N2;
+        xs[(r >> 1) * 4 + 2 * kk + (r & 1)] = conj_(xv[u]);
+      }
+    __syncwarp();
   }
   __syncthreads();
   for (int x = tid; x < W; x += blockDim.x) {
