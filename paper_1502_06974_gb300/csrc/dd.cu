@@ -181,68 +181,151 @@ __device__ void alljones_update_warp(const Cx<float>* Ah, const Cx<float>* Al, c
 }
 
 // ------------------------------------------------------------------------------------ iteration
+// Decision on iteration kp of interval i, from the per-antenna partials its launch left in
+// conv / cflag (parity kp & 1): the status that ends the interval (GC_ST_NONFINITE, GC_ST_OK,
+// GC_ST_NOT_CONVERGED at kp >= max_iter) or -1 to go on; *sing the OR of the singular flags.
+// Called by one whole warp of every CTA of the interval: the same slots summed in the same order
+// (lane-strided float-float sums, a fixed tree to lane 0, then lane 0's result broadcast), so
+// every CTA takes the same decision.
+__device__ inline int dd_decide(const DDArgs& a, int kp, int64_t go, int na, int* sing) {
+  const int lane = threadIdx.x & 31;
+  const float4* cv = a.conv + (size_t)(kp & 1) * a.n_gain + go;
+  const int32_t* cf = a.cflag + (size_t)(kp & 1) * a.n_gain + go;
+  FF d2{0.f, 0.f}, n2{0.f, 0.f};
+  int fl = 0;
+  for (int q = lane; q < na; q += 32) {
+    const float4 v = __ldcg(cv + q);
+    d2 = ff_add(d2, FF{v.x, v.y});
+    n2 = ff_add(n2, FF{v.z, v.w});
+    fl |= __ldcg(cf + q);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const FF d{__shfl_down_sync(0xffffffffu, d2.hi, o), __shfl_down_sync(0xffffffffu, d2.lo, o)};
+    const FF n{__shfl_down_sync(0xffffffffu, n2.hi, o), __shfl_down_sync(0xffffffffu, n2.lo, o)};
+    if (lane + o < 32) { d2 = ff_add(d2, d); n2 = ff_add(n2, n); }
+  }
+  fl = __reduce_or_sync(0xffffffffu, fl);
+  d2 = FF{__shfl_sync(0xffffffffu, d2.hi, 0), __shfl_sync(0xffffffffu, d2.lo, 0)};
+  n2 = FF{__shfl_sync(0xffffffffu, n2.hi, 0), __shfl_sync(0xffffffffu, n2.lo, 0)};
+  *sing = (fl >> 1) & 1;
+  if (fl & 1) return GC_ST_NONFINITE;
+  if (ff_value(d2) <= a.tol * a.tol * ff_value(n2)) return GC_ST_OK;
+  if (kp >= a.max_iter) return GC_ST_NOT_CONVERGED;
+  return -1;
+}
+
+constexpr int kIterEntries = 64;  // entries (baseline, side) of an antenna staged per chunk
+
+template <int ND>
+constexpr size_t dd_iter_smem(int na_max) {
+  constexpr int NO = DDShape<ND>::NO, CS = (NO + 31) / 32 * 32;
+  constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
+  return (size_t)na_max * ND * sizeof(Cx<float>) + (size_t)LANES * NO * sizeof(float4) +
+         (size_t)kIterEntries * NO * sizeof(float2);
+}
+
+// One CTA per (interval, antenna p), launch k of the loop: iteration k of the interval, from
+// g^(k-1) (gbuf parity (k-1) & 1) to g^(k) (parity k & 1).
+//  * The antenna's entries and their moments (constant over the iterations) are fetched first,
+//    before the wait on the previous launch (programmatic dependent launch), by cp.async.
+//  * The interval's stop decision on iteration k - 1 comes next (dd_decide): a CTA of a finished
+//    interval copies its antenna's final gains out (g^(k-1), or g^(k-2) after a non-finite
+//    iteration) and the antenna-0 CTA records status and iterations; no CTA of the interval writes
+//    anything else.  The launch after max_iter only decides.
+//  * Otherwise: the block sum from the moments (lane-strided compensated FP32, lanes combined in
+//    float-float), the CohJones solve (FP32 Cholesky in registers by one warp, one float-float
+//    refinement, FP64 when a pivot fails) or the AllJones step, the schedule for antenna p (odd k
+//    or GN: the new gains; even k: their average with g^(k-1)), and the antenna's convergence
+//    partials |g^(k) - g^(k-1)|^2, |g^(k)|^2 (float-float) and flags for the next launch.
+// No CTA waits for another within a launch: the interval-wide test is deferred by one launch.
 template <int ND>
 __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a) {
   constexpr int NU = DDShape<ND>::NU, NO = DDShape<ND>::NO;
   constexpr int CS = (NO + 31) / 32 * 32;       // component slots per lane group
   constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
+  static_assert(kIterEntries % LANES == 0, "every chunk starts at lane 0");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cx<float>* gs = reinterpret_cast<Cx<float>*>(smem_raw);            // [n_ant][ND]
-  float4* red = reinterpret_cast<float4*>(gs + a.na_max * ND);       // [LANES][NO] float-float (re, im)
+  Cx<float>* gs = reinterpret_cast<Cx<float>*>(smem_raw);                       // [n_ant][ND]
+  float4* red = reinterpret_cast<float4*>(gs + a.na_max * ND);                  // [LANES][NO]
+  float2* smom = reinterpret_cast<float2*>(red + LANES * NO);                   // [kIterEntries][NO]
   __shared__ Cx<float> Ah[NU], Al[NU], bh[ND], bl[ND], xs[ND];
-  __shared__ int s_last, s_sing, s_nf;
-  __shared__ double s_red[80];  // >= 160 floats for the end-of-update reduction
-  __shared__ int2 s_ent[kIterThreads];
+  __shared__ int s_sing, s_nf, s_st, s_sg;
+  __shared__ int2 s_ent[kIterEntries];
+  pdl_launch_dependents();
   const int it = blockIdx.x;
   if (it >= a.n_iitems) return;
-  const int i = a.iitem_int[it];
   const int k = *a.kbase + a.k;
-  if (a.active[i] == 0 || k > a.max_iter) return;
+  if (k > a.max_iter + 1) return;
+  const int i = a.iitem_int[it];
   const int p = a.iitem_ant[it];
+  const int e0 = a.iitem_e0[it], e1 = a.iitem_e1[it];
   const int na = a.n_ant[i];
   const int64_t go = a.gain_off[i];
   const int tid = threadIdx.x;
-  for (int x = tid; x < na * ND; x += blockDim.x)
-    gs[x] = cx<float>(a.gains[2 * (go * ND + x)], a.gains[2 * (go * ND + x) + 1]);
   const int comp = tid % CS, lane = tid / CS;
   const bool worker = comp < NO && lane < LANES;
+  const float2* mom = a.moments + a.mom_off[i];
+  // entries base .. base + kIterEntries - 1 and their moments into shared memory (cp.async)
+  auto stage = [&](int base) {
+    const int m = min(kIterEntries, e1 - base);
+    if (tid < m) s_ent[tid] = make_int2(a.ent[base + tid], a.entq[base + tid]);
+    __syncthreads();
+    if (worker)
+      for (int idx = lane; idx < m; idx += LANES)
+        dd_cp_async8(smom + idx * NO + comp, mom + (int64_t)(s_ent[idx].x >> 1) * NO + comp);
+    dd_cp_commit();
+    return m;
+  };
+  const int m0 = e1 > e0 ? stage(e0) : 0;
+  pdl_wait();  // g^(k-1), the partials of iteration k - 1 and the flags come from the previous launch
+  if (__ldcg(a.active + i) == 0) { dd_cp_wait<0>(); return; }
+  if (k >= 2) {
+    if (tid < 32) {
+      int sg = 0;
+      const int st = dd_decide(a, k - 1, go, na, &sg);
+      if (tid == 0) { s_st = st; s_sg = sg; }
+    }
+    __syncthreads();
+    if (s_st >= 0) {
+      const size_t src = (size_t)((s_st == GC_ST_NONFINITE ? k - 2 : k - 1) & 1) * a.n_gain * ND;
+      if (tid < 2 * ND) a.gains[2 * ((go + p) * ND) + tid] = __ldcg(a.gbuf + 2 * (src + (go + p) * ND) + tid);
+      if (p == 0 && tid == 0) {
+        a.active[i] = 0;
+        a.iters[i] = k - 1;
+        a.status[i] = s_st | (s_sg ? GC_ST_SINGULAR_FLAG : 0);
+        atomicSub(a.n_active, 1);
+      }
+      dd_cp_wait<0>();
+      return;
+    }
+  }
+  if (k > a.max_iter) { dd_cp_wait<0>(); return; }  // iteration max_iter was decided above
+  const float* gcur = a.gbuf + (size_t)((k - 1) & 1) * a.n_gain * ND * 2;
+  for (int x = tid; x < na * ND; x += blockDim.x)
+    gs[x] = cx<float>(__ldcg(gcur + 2 * (go * ND + x)), __ldcg(gcur + 2 * (go * ND + x) + 1));
   int c = 0, d = 0;
   if (comp < NU) upper_cd(ND, comp, c, d);
   else c = comp - NU;
   float sx = 0.f, sxc = 0.f, sy = 0.f, syc = 0.f;
-  const float2* mom = a.moments + a.mom_off[i];
-  const int e0 = a.iitem_e0[it], e1 = a.iitem_e1[it];
-  // the antenna's entries, kIterThreads at a time, staged in shared memory so that every moment
-  // load's address is known at once; each lane takes entries lane, lane + LANES, ... in order
-  for (int base = e0; base < e1; base += kIterThreads) {
-    const int n = min(kIterThreads, e1 - base);
-    if (tid < n) s_ent[tid] = make_int2(a.ent[base + tid], a.entq[base + tid]);
-    __syncthreads();
-    if (worker) {
-      constexpr int U = 8;
-      for (int j = lane; j < n; j += U * LANES) {
-        float2 v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int idx = j + u * LANES;
-          const int en = idx < n ? s_ent[idx].x : 0;
-          v[u] = idx < n ? mom[(int64_t)(en >> 1) * NO + comp] : make_float2(0.f, 0.f);
-          if (en & 1) v[u].y = -v[u].y;  // conjugate baseline: conj(X), conj(B)
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int idx = j + u * LANES;
-          if (idx >= n) continue;
-          const int q = s_ent[idx].y;
-          Cx<float> t;
-          if (comp < NU) t = mul_(mulc_(gs[q * ND + c], gs[q * ND + d]), cx<float>(v[u].x, v[u].y));
-          else t = mul_(gs[q * ND + c], cx<float>(v[u].x, v[u].y));
-          kahan_add(sx, sxc, t.x);
-          kahan_add(sy, syc, t.y);
-        }
+  // each lane takes entries lane, lane + LANES, ... of every chunk, in order
+  for (int base = e0; base < e1; base += kIterEntries) {
+    const int m = base == e0 ? m0 : stage(base);
+    dd_cp_wait<0>();
+    __syncthreads();  // every thread's copies (and, on the first chunk, the staged gains) visible
+    if (worker)
+      for (int idx = lane; idx < m; idx += LANES) {
+        float2 v = smom[idx * NO + comp];
+        const int2 e = s_ent[idx];
+        if (e.x & 1) v.y = -v.y;  // conjugate baseline: conj(X), conj(B)
+        const int q = e.y;
+        Cx<float> t;
+        if (comp < NU) t = mul_(mulc_(gs[q * ND + c], gs[q * ND + d]), cx<float>(v.x, v.y));
+        else t = mul_(gs[q * ND + c], cx<float>(v.x, v.y));
+        kahan_add(sx, sxc, t.x);
+        kahan_add(sy, syc, t.y);
       }
-    }
-    __syncthreads();  // before the next chunk replaces the staged entries
+    __syncthreads();  // before the next chunk replaces the staged entries and moments
   }
   if (e1 <= e0) __syncthreads();  // the gains are staged even for an antenna without baselines
   if (worker) red[lane * NO + comp] = make_float4(sx, -sxc, sy, -syc);  // Kahan: the sum is s - c
@@ -283,21 +366,35 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
     if (tid == 0) s_sing = ok ? 0 : 1;
   }
   __syncthreads();
-  if (tid < ND) {
-    Cx<float> g = (s_sing && a.method != 1) ? gs[p * ND + tid] : xs[tid];
-    if (s_nf) g = cx<float>(__int_as_float(0x7fc00000), 0.f);  // reported as non-finite gains
-    a.gnew[2 * ((go + p) * ND + tid)] = g.x;
-    a.gnew[2 * ((go + p) * ND + tid) + 1] = g.y;
+  // schedule for antenna p, g^(k) out, and this antenna's convergence partials
+  if (tid < 32) {
+    FF d2{0.f, 0.f}, n2{0.f, 0.f};
+    int nonfin = 0;
+    if (tid < ND) {
+      const Cx<float> old = gs[p * ND + tid];
+      Cx<float> g = (s_sing && a.method != 1) ? old : xs[tid];
+      if (s_nf) g = cx<float>(__int_as_float(0x7fc00000), 0.f);  // reported as non-finite gains
+      const bool gn_step = (a.schedule == GC_SCHED_GN) || (k & 1);
+      const Cx<float> nw = gn_step ? g : cx<float>(0.5f * (old.x + g.x), 0.5f * (old.y + g.y));
+      float* gout = a.gbuf + (size_t)(k & 1) * a.n_gain * ND * 2 + 2 * ((go + p) * ND + tid);
+      gout[0] = nw.x;
+      gout[1] = nw.y;
+      d2 = FF{abs2_(sub_(nw, old)), 0.f};
+      n2 = FF{abs2_(nw), 0.f};
+      nonfin = !isfinite(nw.x) || !isfinite(nw.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const FF dd{__shfl_down_sync(0xffffffffu, d2.hi, o), __shfl_down_sync(0xffffffffu, d2.lo, o)};
+      const FF nn{__shfl_down_sync(0xffffffffu, n2.hi, o), __shfl_down_sync(0xffffffffu, n2.lo, o)};
+      if (tid + o < 32) { d2 = ff_add(d2, dd); n2 = ff_add(n2, nn); }
+    }
+    nonfin = __any_sync(0xffffffffu, nonfin);
+    if (tid == 0) {
+      a.conv[(size_t)(k & 1) * a.n_gain + go + p] = make_float4(d2.hi, d2.lo, n2.hi, n2.lo);
+      a.cflag[(size_t)(k & 1) * a.n_gain + go + p] = nonfin | (s_sing << 1);
+    }
   }
-  if (tid == 0) a.sing[go + p] = s_sing;
-  // the last antenna of the interval to finish applies the schedule and the convergence test
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&a.counters[i], 1) == na - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  dd_interval_update(a, i, k, na, go, ND, gs, reinterpret_cast<float*>(s_red));
 }
 
 // chi^2 per moment item (interval, 32-baseline tile) over all its rows, then per interval.
@@ -436,6 +533,8 @@ int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s, int64_t mom_per
   const size_t p_counters = add(nullptr, (size_t)n * 4);
   const size_t p_misc = add(nullptr, 64);
   const size_t p_sing = add(nullptr, (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 4);
+  const size_t p_conv = add(nullptr, (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 2 * sizeof(float4));
+  const size_t p_cflag = add(nullptr, (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 2 * 4);
   const size_t p_chi2 = add(nullptr, mint.size() * 8);
   const size_t p_chi2o = add(nullptr, (size_t)(n > 0 ? n : 1) * 8);
   const size_t total = off;
@@ -477,6 +576,9 @@ int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s, int64_t mom_per
   a.n_active = (int32_t*)at(p_misc);
   a.kbase = a.n_active + 1;
   a.sing = (int32_t*)at(p_sing);
+  a.conv = (float4*)at(p_conv);
+  a.cflag = (int32_t*)at(p_cflag);
+  a.n_gain = L->n_gain;
   a.na_max = na_max;
   P.chi2_first = (int32_t*)at(p_cfirst);
   P.chi2_count = (int32_t*)at(p_ccount);
@@ -491,12 +593,9 @@ int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s, int64_t mom_per
 
 template <int ND>
 static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag, double* prof_ms) {
-  constexpr int NO = DDShape<ND>::NO;
-  constexpr int CS = (NO + 31) / 32 * 32;
-  constexpr int LANES = kIterThreads / CS > 0 ? kIterThreads / CS : 1;
   DDArgs& a = P.args;
   const size_t msmem = dd_moment_smem<ND>();
-  const size_t ismem = (size_t)a.na_max * ND * sizeof(Cx<float>) + (size_t)LANES * NO * sizeof(float4) + 16;
+  const size_t ismem = dd_iter_smem<ND>(a.na_max);
   DD_CUDA(cudaFuncSetAttribute(dd_moment_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
   DD_CUDA(cudaFuncSetAttribute(dd_iter_kernel<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
   dd_init_kernel<<<(P.n_int + 255) / 256, 256, 0, s>>>(a, P.n_int, P.n_active0);
@@ -525,10 +624,23 @@ static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag
       cudaError_t ce2 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       int crc = ce2 == cudaSuccess ? 0 : (int)ce2;
       for (int j = 1; j <= S && !crc; ++j) {
+        // programmatic dependent launches: launch j + 1 stages its entries and moments while
+        // launch j finishes
         DDArgs x = ga;
         x.k = j;
-        dd_iter_kernel<ND><<<a.n_iitems, kIterThreads, ismem, cs>>>(x);
-        crc = (int)cudaGetLastError();
+        void* kargs[] = {&x};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(a.n_iitems);
+        cfg.blockDim = dim3(kIterThreads);
+        cfg.dynamicSmemBytes = ismem;
+        cfg.stream = cs;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        crc = (int)cudaLaunchKernelExC(&cfg, (const void*)&dd_iter_kernel<ND>, kargs);
+        if (!crc) crc = (int)cudaGetLastError();
       }
       if (!crc) crc = di_launch_advance(a.kbase, S, cs);
       cudaGraph_t g = nullptr;
@@ -545,7 +657,8 @@ static int dd_run_nd(DDPlan& P, const gc_options* opt, cudaStream_t s, int* flag
       P.gS = S;
       P.gnd = ND;
     }
-    for (int k0 = 0; k0 < opt->max_iter; k0 += S) {
+    // launch max_iter + 1 only takes the decision on iteration max_iter
+    for (int k0 = 0; k0 <= opt->max_iter; k0 += S) {
       it.before(s);
       DD_CUDA(cudaGraphLaunch(P.gexec, s));
       it.after(s);
@@ -619,6 +732,11 @@ int run_dd(const void* vis, const void* model, const gc_layout* L, void* gains, 
   }
   if (gb) DD_CUDA(cudaMemcpyAsync(dg, gains, gb, opt->host_buffers ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   a.gains = (float*)dg;
+  // iterates by parity; g^(0) = the starting gains
+  void* gbuf = nullptr;
+  if ((rc = ws_get("dd_gbuf", gb > 0 ? 2 * gb : 16, &gbuf))) return rc;
+  if (gb) DD_CUDA(cudaMemcpyAsync(gbuf, dg, gb, cudaMemcpyDeviceToDevice, s));
+  a.gbuf = (float*)gbuf;
   void *mom, *gnew;
   if ((rc = ws_get("dd_moments", (size_t)(P.n_mom > 0 ? P.n_mom : 1) * sizeof(float2), &mom))) return rc;
   if ((rc = ws_get("dd_gnew", gb > 0 ? gb : 8, &gnew))) return rc;

@@ -56,6 +56,13 @@ struct DDArgs {
   int32_t k;                 // position within the segment: the iteration is *kbase + k
   int32_t na_max;
   int32_t method;            // 0 CohJones (antenna-block inverse), 1 AllJones (diagonal, residual form)
+  // scalar DD iteration state: iterates by parity ([2][n_gain][n_dir] complex; g^(k) at k & 1) and
+  // per-antenna convergence partials (float-float |dg|^2, |g|^2) and flags (bit 0 non-finite,
+  // bit 1 singular), [2][n_gain] each, read by the next launch
+  float* gbuf;
+  float4* conv;
+  int32_t* cflag;
+  int64_t n_gain;
 };
 
 // Component index -> (c, d) for the upper triangle, row-major: (0,0) (0,1) .. (0,ND-1) (1,1) ..
