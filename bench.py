@@ -479,7 +479,9 @@ def dd_block(dev, args, peaks, which):
                                      "peak_source": which},
             "iterations": {"launches": it_n, "avg_launch_us": it_ms * 1e3 / max(it_n, 1),
                            "kernel": "dd_iter_kernel<9> (per (interval, antenna): 9x9 block from the moments, "
-                                     "FP32 Cholesky in registers + one float-float refinement step)", "moments_bytes": int(np.sum(b.n_bl)) * (nd * (nd + 1) // 2 + nd) * 8}}
+                                     "FP32 Cholesky in registers + one float-float refinement step; the stop "
+                                     "decision deferred to the next launch)",
+                           "moments_bytes": int(np.sum(b.n_bl)) * (nd * (nd + 1) // 2 + nd) * 8}}
 
 
 def fp32_peak(dev, peaks):

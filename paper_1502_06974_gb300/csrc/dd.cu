@@ -181,23 +181,23 @@ __device__ void alljones_update_warp(const Cx<float>* Ah, const Cx<float>* Al, c
 }
 
 // ------------------------------------------------------------------------------------ iteration
-// Decision on iteration kp of interval i, from the per-antenna partials its launch left in
-// conv / cflag (parity kp & 1): the status that ends the interval (GC_ST_NONFINITE, GC_ST_OK,
-// GC_ST_NOT_CONVERGED at kp >= max_iter) or -1 to go on; *sing the OR of the singular flags.
-// Called by one whole warp of every CTA of the interval: the same slots summed in the same order
-// (lane-strided float-float sums, a fixed tree to lane 0, then lane 0's result broadcast), so
-// every CTA takes the same decision.
-__device__ inline int dd_decide(const DDArgs& a, int kp, int64_t go, int na, int* sing) {
+// Stop decision on iteration kp of an interval from its na per-antenna partials cv (float-float
+// |dg|^2, |g|^2) and flags cf (bit 0 non-finite, bit 1 singular): the status that ends the
+// interval (GC_ST_NONFINITE, GC_ST_OK, GC_ST_NOT_CONVERGED at kp >= max_iter) or -1 to go on;
+// *sing the OR of the singular flags.  Called by one whole warp: lane-strided float-float sums,
+// a fixed tree to lane 0 and lane 0's result broadcast, so that every caller that reads the same
+// slots takes the same decision.  GLOBAL: the slots are in global memory (read through L2).
+template <bool GLOBAL>
+__device__ inline int dd_decide(const float4* cv, const int32_t* cf, int na, double tol, int kp, int max_iter,
+                                int* sing) {
   const int lane = threadIdx.x & 31;
-  const float4* cv = a.conv + (size_t)(kp & 1) * a.n_gain + go;
-  const int32_t* cf = a.cflag + (size_t)(kp & 1) * a.n_gain + go;
   FF d2{0.f, 0.f}, n2{0.f, 0.f};
   int fl = 0;
   for (int q = lane; q < na; q += 32) {
-    const float4 v = __ldcg(cv + q);
+    const float4 v = GLOBAL ? __ldcg(cv + q) : cv[q];
     d2 = ff_add(d2, FF{v.x, v.y});
     n2 = ff_add(n2, FF{v.z, v.w});
-    fl |= __ldcg(cf + q);
+    fl |= GLOBAL ? __ldcg(cf + q) : cf[q];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -210,8 +210,8 @@ __device__ inline int dd_decide(const DDArgs& a, int kp, int64_t go, int na, int
   n2 = FF{__shfl_sync(0xffffffffu, n2.hi, 0), __shfl_sync(0xffffffffu, n2.lo, 0)};
   *sing = (fl >> 1) & 1;
   if (fl & 1) return GC_ST_NONFINITE;
-  if (ff_value(d2) <= a.tol * a.tol * ff_value(n2)) return GC_ST_OK;
-  if (kp >= a.max_iter) return GC_ST_NOT_CONVERGED;
+  if (ff_value(d2) <= tol * tol * ff_value(n2)) return GC_ST_OK;
+  if (kp >= max_iter) return GC_ST_NOT_CONVERGED;
   return -1;
 }
 
@@ -279,31 +279,33 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
   };
   const int m0 = e1 > e0 ? stage(e0) : 0;
   pdl_wait();  // g^(k-1), the partials of iteration k - 1 and the flags come from the previous launch
-  if (__ldcg(a.active + i) == 0) { dd_cp_wait<0>(); return; }
-  if (k >= 2) {
-    if (tid < 32) {
-      int sg = 0;
-      const int st = dd_decide(a, k - 1, go, na, &sg);
-      if (tid == 0) { s_st = st; s_sg = sg; }
+  // the active flag, the decision on iteration k - 1 (warp 0) and g^(k-1) (the other warps) are
+  // read at once; the gains are used only if the interval goes on
+  const float* gcur = a.gbuf + (size_t)((k - 1) & 1) * a.n_gain * ND * 2;
+  if (tid < 32) {
+    int sg = 0;
+    const size_t so = (size_t)((k - 1) & 1) * a.n_gain + go;  // the partials of iteration k - 1
+    const int st = k >= 2 ? dd_decide<true>(a.conv + so, a.cflag + so, na, a.tol, k - 1, a.max_iter, &sg) : -1;
+    if (tid == 0) { s_st = __ldcg(a.active + i) == 0 ? -2 : st; s_sg = sg; }
+  } else {
+    for (int x = tid - 32; x < na * ND; x += blockDim.x - 32)
+      gs[x] = cx<float>(__ldcg(gcur + 2 * (go * ND + x)), __ldcg(gcur + 2 * (go * ND + x) + 1));
+  }
+  __syncthreads();
+  if (s_st == -2) { dd_cp_wait<0>(); return; }  // finished in an earlier launch
+  if (s_st >= 0) {
+    const size_t src = (size_t)((s_st == GC_ST_NONFINITE ? k - 2 : k - 1) & 1) * a.n_gain * ND;
+    if (tid < 2 * ND) a.gains[2 * ((go + p) * ND) + tid] = __ldcg(a.gbuf + 2 * (src + (go + p) * ND) + tid);
+    if (p == 0 && tid == 0) {
+      a.active[i] = 0;
+      a.iters[i] = k - 1;
+      a.status[i] = s_st | (s_sg ? GC_ST_SINGULAR_FLAG : 0);
+      atomicSub(a.n_active, 1);
     }
-    __syncthreads();
-    if (s_st >= 0) {
-      const size_t src = (size_t)((s_st == GC_ST_NONFINITE ? k - 2 : k - 1) & 1) * a.n_gain * ND;
-      if (tid < 2 * ND) a.gains[2 * ((go + p) * ND) + tid] = __ldcg(a.gbuf + 2 * (src + (go + p) * ND) + tid);
-      if (p == 0 && tid == 0) {
-        a.active[i] = 0;
-        a.iters[i] = k - 1;
-        a.status[i] = s_st | (s_sg ? GC_ST_SINGULAR_FLAG : 0);
-        atomicSub(a.n_active, 1);
-      }
-      dd_cp_wait<0>();
-      return;
-    }
+    dd_cp_wait<0>();
+    return;
   }
   if (k > a.max_iter) { dd_cp_wait<0>(); return; }  // iteration max_iter was decided above
-  const float* gcur = a.gbuf + (size_t)((k - 1) & 1) * a.n_gain * ND * 2;
-  for (int x = tid; x < na * ND; x += blockDim.x)
-    gs[x] = cx<float>(__ldcg(gcur + 2 * (go * ND + x)), __ldcg(gcur + 2 * (go * ND + x) + 1));
   int c = 0, d = 0;
   if (comp < NU) upper_cd(ND, comp, c, d);
   else c = comp - NU;
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
   for (int base = e0; base < e1; base += kIterEntries) {
     const int m = base == e0 ? m0 : stage(base);
     dd_cp_wait<0>();
-    __syncthreads();  // every thread's copies (and, on the first chunk, the staged gains) visible
+    __syncthreads();  // every thread's copies visible
     if (worker)
       for (int idx = lane; idx < m; idx += LANES) {
         float2 v = smom[idx * NO + comp];
@@ -327,7 +329,6 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
       }
     __syncthreads();  // before the next chunk replaces the staged entries and moments
   }
-  if (e1 <= e0) __syncthreads();  // the gains are staged even for an antenna without baselines
   if (worker) red[lane * NO + comp] = make_float4(sx, -sxc, sy, -syc);  // Kahan: the sum is s - c
   if (tid == 0) s_nf = 0;
   __syncthreads();
@@ -396,6 +397,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
     }
   }
 }
+
 
 // chi^2 per moment item (interval, 32-baseline tile) over all its rows, then per interval.
 template <int ND>

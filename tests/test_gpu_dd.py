@@ -18,6 +18,7 @@ from paper_1502_06974_gb300 import api, synth
 pytestmark = pytest.mark.gpu
 
 
+
 @pytest.mark.parametrize("k", [1, 2, 5])
 def test_cohjones_iterates_match(gpu_lib, k):
     b = synth.make_config(3, small=True)
@@ -114,3 +115,13 @@ def test_dd_host_buffers(gpu_lib):
     gh, ith, _, _ = api.calibrate_dd_cohjones(vis.cpu().pin_memory(), model.cpu().pin_memory(), lay, gh, tol=1e-6,
                                               max_iter=500, host_buffers=True)
     assert torch.equal(gd.cpu(), gh) and torch.equal(itd.cpu(), ith)
+
+
+def test_cohjones_many_antennas_iterates(gpu_lib):
+    """70 antennas, 2 directions (entries beyond one staged chunk of 64): the iterates follow the oracle."""
+    b = synth.make_dd(n_ant=70, n_dir=2, n_t=2, n_chan=4, t_per=2, f_per=4)
+    vis, model, g0, lay = device_batch(b)
+    g, iters, _, st = api.calibrate_dd_cohjones(vis, model, lay, g0, tol=0.0, max_iter=3)
+    gr, _, _ = diagonal.solve_batch(b, tol=0.0, max_iter=3)
+    assert (iters.cpu().numpy() == 3).all()
+    assert per_slot_relerr(g.cpu().numpy(), gr) < 1e-5
