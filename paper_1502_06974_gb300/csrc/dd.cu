@@ -231,8 +231,9 @@ constexpr size_t dd_iter_smem(int na_max) {
 //    before the wait on the previous launch (programmatic dependent launch), by cp.async.
 //  * The interval's stop decision on iteration k - 1 comes next (dd_decide): a CTA of a finished
 //    interval copies its antenna's final gains out (g^(k-1), or g^(k-2) after a non-finite
-//    iteration) and the antenna-0 CTA records status and iterations; no CTA of the interval writes
-//    anything else.  The launch after max_iter only decides.
+//    iteration) and the antenna-0 CTA records status, iterations and the deciding launch (stopk);
+//    no CTA of the interval writes anything else.  Later launches skip the interval by stopk,
+//    never by a flag written in the same launch.  The launch after max_iter only decides.
 //  * Otherwise: the block sum from the moments (lane-strided compensated FP32, lanes combined in
 //    float-float), the CohJones solve (FP32 Cholesky in registers by one warp, one float-float
 //    refinement, FP64 when a pivot fails) or the AllJones step, the schedule for antenna p (odd k
@@ -286,7 +287,13 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
     int sg = 0;
     const size_t so = (size_t)((k - 1) & 1) * a.n_gain + go;  // the partials of iteration k - 1
     const int st = k >= 2 ? dd_decide<true>(a.conv + so, a.cflag + so, na, a.tol, k - 1, a.max_iter, &sg) : -1;
-    if (tid == 0) { s_st = __ldcg(a.active + i) == 0 ? -2 : st; s_sg = sg; }
+    // an interval decided by an earlier launch is left alone; one decided by this launch (its
+    // antenna-0 CTA may already have recorded it) is decided again, identically, by every CTA
+    if (tid == 0) {
+      const int sk = __ldcg(a.stopk + i);
+      s_st = (sk != 0 && sk < k) ? -2 : st;
+      s_sg = sg;
+    }
   } else {
     for (int x = tid - 32; x < na * ND; x += blockDim.x - 32)
       gs[x] = cx<float>(__ldcg(gcur + 2 * (go * ND + x)), __ldcg(gcur + 2 * (go * ND + x) + 1));
@@ -297,6 +304,7 @@ __global__ void __launch_bounds__(kIterThreads, 5) dd_iter_kernel(const DDArgs a
     const size_t src = (size_t)((s_st == GC_ST_NONFINITE ? k - 2 : k - 1) & 1) * a.n_gain * ND;
     if (tid < 2 * ND) a.gains[2 * ((go + p) * ND) + tid] = __ldcg(a.gbuf + 2 * (src + (go + p) * ND) + tid);
     if (p == 0 && tid == 0) {
+      a.stopk[i] = k;
       a.active[i] = 0;
       a.iters[i] = k - 1;
       a.status[i] = s_st | (s_sg ? GC_ST_SINGULAR_FLAG : 0);
@@ -537,6 +545,7 @@ int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s, int64_t mom_per
   const size_t p_sing = add(nullptr, (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 4);
   const size_t p_conv = add(nullptr, (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 2 * sizeof(float4));
   const size_t p_cflag = add(nullptr, (size_t)(L->n_gain > 0 ? L->n_gain : 1) * 2 * 4);
+  const size_t p_stopk = add(nullptr, (size_t)(n > 0 ? n : 1) * 4);
   const size_t p_chi2 = add(nullptr, mint.size() * 8);
   const size_t p_chi2o = add(nullptr, (size_t)(n > 0 ? n : 1) * 8);
   const size_t total = off;
@@ -580,6 +589,7 @@ int build_dd_plan(const gc_layout* L, DDPlan& P, cudaStream_t s, int64_t mom_per
   a.sing = (int32_t*)at(p_sing);
   a.conv = (float4*)at(p_conv);
   a.cflag = (int32_t*)at(p_cflag);
+  a.stopk = (int32_t*)at(p_stopk);
   a.n_gain = L->n_gain;
   a.na_max = na_max;
   P.chi2_first = (int32_t*)at(p_cfirst);

@@ -63,6 +63,7 @@ struct DDArgs {
   float4* conv;
   int32_t* cflag;
   int64_t n_gain;
+  int32_t* stopk;  // [n_int] the launch that took the interval's stop decision (0: none yet)
 };
 
 // Component index -> (c, d) for the upper triangle, row-major: (0,0) (0,1) .. (0,ND-1) (1,1) ..
@@ -259,6 +260,7 @@ static __global__ void dd_init_kernel(DDArgs a, int n_int, int n_active0) {
     a.iters[i] = 0;
     a.status[i] = rows > 0 ? GC_ST_NOT_CONVERGED : GC_ST_NODATA;
     a.counters[i] = 0;
+    if (a.stopk) a.stopk[i] = 0;
   }
 }
 
