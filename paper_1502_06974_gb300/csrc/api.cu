@@ -1344,11 +1344,21 @@ static int run_smooth(int kind, const void* vis, const void* model, const gc_smo
       a12[2 * b + 1] = q;
     }
   }
+  // per tile of the accumulation, every antenna's first entry at or after the tile's first baseline
+  const int TBr = sm_tile_rows(kind), n_tiles = (sm->n_bl + TBr - 1) / TBr;
+  std::vector<int32_t> tent((size_t)(n_tiles + 1) * sm->n_ant);
+  for (int p = 0; p < sm->n_ant; ++p) {
+    int e = ant_off[p];
+    for (int t = 0; t <= n_tiles; ++t) {
+      while (e < ant_off[p + 1] && (ent[e] >> 1) < t * TBr) ++e;
+      tent[(size_t)t * sm->n_ant + p] = e;
+    }
+  }
   const int64_t n_gain = n_s * sm->n_ant;
   const int NC = kind == 0 ? 3 : 12, GW = kind == 0 ? 2 : 8;
   void *sums = nullptr, *tmp = nullptr, *ssum = nullptr, *gnew = nullptr, *aux = nullptr;
   const size_t tb = (wt.size() + wf.size()) * sizeof(float);
-  const size_t lb = (ant_off.size() + ent.size() + a12.size()) * sizeof(int32_t);
+  const size_t lb = (ant_off.size() + ent.size() + a12.size() + tent.size()) * sizeof(int32_t);
   if ((rc = ws_get("sm_sums", (size_t)n_gain * NC * 4, &sums)) || (rc = ws_get("sm_tmp", (size_t)n_gain * NC * 4, &tmp)) ||
       (rc = ws_get("sm_ssum", (size_t)n_gain * NC * 4, &ssum)) || (rc = ws_get("sm_gnew", (size_t)n_gain * GW * 4, &gnew)) ||
       (rc = ws_get("sm_aux", tb + 32 + (size_t)n_int * 3 * 8 + lb, &aux)))
@@ -1359,18 +1369,20 @@ static int run_smooth(int kind, const void* vis, const void* model, const gc_smo
   int32_t* d_a12 = (int32_t*)(partials + 3 * (size_t)n_int);  // 8-byte aligned: read as int2
   int32_t* d_off = d_a12 + a12.size();
   int32_t* d_ent = d_off + ant_off.size();
+  int32_t* d_tent = d_ent + ent.size();
   GC_CUDA(cudaMemcpyAsync(dtaps, wt.data(), wt.size() * 4, cudaMemcpyHostToDevice, s));
   GC_CUDA(cudaMemcpyAsync(dtaps + wt.size(), wf.data(), wf.size() * 4, cudaMemcpyHostToDevice, s));
   GC_CUDA(cudaMemcpyAsync(d_off, ant_off.data(), ant_off.size() * 4, cudaMemcpyHostToDevice, s));
   GC_CUDA(cudaMemcpyAsync(d_ent, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice, s));
   GC_CUDA(cudaMemcpyAsync(d_a12, a12.data(), a12.size() * 4, cudaMemcpyHostToDevice, s));
+  GC_CUDA(cudaMemcpyAsync(d_tent, tent.data(), tent.size() * 4, cudaMemcpyHostToDevice, s));
   GC_CUDA_I(sm_launch_init(state, stream));
   int* flag = nullptr;
   if ((rc = pinned_flag(&flag))) return rc;
   const int64_t inner = (int64_t)sm->n_ant * NC;  // floats per sample
   for (int k = 1; k <= opt->max_iter; ++k) {
     GC_CUDA_I(sm_launch_acc(kind, (const float*)vis, (const float*)model, (const float*)gains, n_int, sm->n_bl,
-                            sm->n_ant, d_off, d_ent, d_a12, state, (float*)sums, stream));
+                            sm->n_ant, d_off, d_ent, d_a12, d_tent, state, (float*)sums, stream));
     // frequency, then time: [n_t][n_f][n_ant * NC]; an axis without smoothing (one tap of 1) is skipped
     const float* cur = (const float*)sums;
     if (Rf > 0) {

@@ -114,9 +114,12 @@ int di_macc_bulk_smem(int kind, int na_max, int tblk_max);
 // current ones when the step is kept.
 int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int64_t inner, const float* taps, int R,
                    void* stream);
+// Baselines per tile of the per-sample accumulation of this kind; tent [n_tiles + 1][n_ant]: the
+// index in ent of antenna p's first entry with a baseline of tile t or later.
+int sm_tile_rows(int kind);
 int sm_launch_acc(int kind, const float* vis, const float* model, const float* gains, int n_s, int n_bl, int n_ant,
-                  const int32_t* ant_off, const int32_t* ent, const int32_t* a12, const int* state, float* sums,
-                  void* stream);
+                  const int32_t* ant_off, const int32_t* ent, const int32_t* a12, const int32_t* tent,
+                  const int* state, float* sums, void* stream);
 int sm_launch_update(int kind, const float* sums, const float* gains, float* gnew, int n_s, int n_ant, int k,
                      int schedule, int max_iter, double tol, int* state, double* partials, void* stream);
 int sm_launch_init(int* state, void* stream);

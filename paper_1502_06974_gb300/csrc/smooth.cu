@@ -85,9 +85,10 @@ template <> struct SmoothRow<JonesKind<float>> {
 // thread forms both sides of its baselines' contributions from coalesced row loads (each row read
 // once) into shared memory; then kSmSplit threads per antenna add the tile's entries of its
 // (baseline, side) list -- sorted by baseline, so each tile's entries are the next ones of the
-// list -- each a fixed share, into compensated FP32 sums combined in a fixed order.  The sample's
-// gains are staged in shared memory.  sums [n_s][n_ant][NC].  Used for the scalar kind.
+// list, from tent -- each a fixed share, into compensated FP32 sums combined in a fixed order.
+// The sample's gains are staged in shared memory.  sums [n_s][n_ant][NC].
 template <class K> struct SmoothTile { static constexpr int TB = 1024; };
+template <> struct SmoothTile<JonesKind<float>> { static constexpr int TB = 256; };
 constexpr int kSmSplit = 4;  // threads per antenna in the per-antenna sums
 
 template <class K>
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(256) sm_acc_kernel(const float* __restrict__ v
                                                      const float* __restrict__ gains, int n_bl, int n_ant,
                                                      const int32_t* __restrict__ ant_off,
                                                      const int32_t* __restrict__ ent, const int32_t* __restrict__ a12,
-                                                     const int* state, float* __restrict__ sums) {
+                                                     const int32_t* __restrict__ tent, const int* state,
+                                                     float* __restrict__ sums) {
   constexpr int NC = K::NC, GW = K::GW, TB = SmoothTile<K>::TB;
   extern __shared__ __align__(16) float smem[];
   float* gs = smem;                        // [n_ant][GW]
@@ -113,9 +115,7 @@ __global__ void __launch_bounds__(256) sm_acc_kernel(const float* __restrict__ v
     float acc[NC], cmp[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = cmp[c] = 0.f;
-    int e = p < n_ant ? __ldg(ant_off + p) : 0;
-    const int e1 = p < n_ant ? __ldg(ant_off + p + 1) : 0;
-    for (int b0 = 0; b0 < n_bl; b0 += TB) {
+    for (int b0 = 0, t = 0; b0 < n_bl; b0 += TB, ++t) {
       const int nb = min(TB, n_bl - b0);
       for (int bl = tid; bl < nb; bl += blockDim.x) {
         const int b = b0 + bl;
@@ -125,15 +125,14 @@ __global__ void __launch_bounds__(256) sm_acc_kernel(const float* __restrict__ v
       }
       __syncthreads();
       // the tile's entries of the antenna are e .. e_end - 1
-      int e_end = e;
-      while (e_end < e1 && (__ldg(ent + e_end) >> 1) < b0 + nb) ++e_end;
+      const int e = p < n_ant ? __ldg(tent + (int64_t)t * n_ant + p) : 0;
+      const int e_end = p < n_ant ? __ldg(tent + (int64_t)(t + 1) * n_ant + p) : 0;
       for (int x = e + j; x < e_end; x += kSmSplit) {
         const int en = __ldg(ent + x);
         const float* v = con + (2 * ((en >> 1) - b0) + (en & 1)) * NC;
 #pragma unroll
         for (int c = 0; c < NC; ++c) kahan_add(acc[c], cmp[c], v[c]);
       }
-      e = e_end;
       __syncthreads();
     }
     // combine the kSmSplit parts (consecutive lanes) in part order
@@ -145,53 +144,6 @@ __global__ void __launch_bounds__(256) sm_acc_kernel(const float* __restrict__ v
       for (int q = 0; q < kSmSplit; ++q) tot += __shfl_sync(0xffffffffu, v, (threadIdx.x & 31 & ~(kSmSplit - 1)) + q);
       if (p < n_ant && j == 0) sums[(g0 + p) * NC + c] = tot;
     }
-  }
-}
-
-// The same sums with one thread per antenna reading its rows directly (four rows' contributions
-// formed before they are added, in list order), each row read by the two threads of its antennas
-// (the second read from L1): faster for the 64-byte 2x2 rows, whose tiles of contributions would
-// fill shared memory.
-template <class K>
-__global__ void __launch_bounds__(64) sm_acc_ant_kernel(const float* __restrict__ vis, const float* __restrict__ mod,
-                                                        const float* __restrict__ gains, int n_bl, int n_ant,
-                                                        const int32_t* __restrict__ ant_off,
-                                                        const int32_t* __restrict__ ent,
-                                                        const int32_t* __restrict__ a12, const int* state,
-                                                        float* __restrict__ sums) {
-  constexpr int NC = K::NC, GW = K::GW, U = 4;
-  extern __shared__ __align__(16) float gs[];  // [n_ant][GW]
-  if (state[0]) return;
-  const int smp = blockIdx.x, tid = threadIdx.x;
-  const int64_t g0 = (int64_t)smp * n_ant, r0 = (int64_t)smp * n_bl;
-  for (int x = tid; x < n_ant * GW; x += blockDim.x) gs[x] = gains[g0 * GW + x];
-  __syncthreads();
-  for (int p = tid; p < n_ant; p += blockDim.x) {
-    float acc[NC], cmp[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = cmp[c] = 0.f;
-    const int e0 = __ldg(ant_off + p), e1 = __ldg(ant_off + p + 1);
-    for (int e = e0; e < e1; e += U) {
-      float v[U][NC];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (e + u < e1) {
-          const int en = __ldg(ent + e + u);
-          const int other = __ldg(a12 + 2 * (en >> 1) + ((en & 1) ? 0 : 1));
-          SmoothRow<K>::add(vis, mod, r0 + (en >> 1), K::ld_gain(gs + GW * other), en & 1, v[u]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) v[u][c] = 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) kahan_add(acc[c], cmp[c], v[u][c]);
-    }
-    float* out = sums + (g0 + p) * NC;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) out[c] = acc[c] - cmp[c];
   }
 }
 
@@ -354,21 +306,30 @@ int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int
   return (int)cudaGetLastError();
 }
 
+int sm_tile_rows(int kind) {
+  return kind == 0 ? SmoothTile<ScalarKind<float>>::TB : SmoothTile<JonesKind<float>>::TB;
+}
+
+template <class K>
+static int sm_launch_tiled(const float* vis, const float* model, const float* gains, int n_s, int n_bl, int n_ant,
+                           const int32_t* ant_off, const int32_t* ent, const int32_t* a12, const int32_t* tent,
+                           const int* state, float* sums, cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)n_ant * K::GW + (size_t)SmoothTile<K>::TB * 2 * K::NC);
+  cudaError_t e = cudaFuncSetAttribute(sm_acc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  sm_acc_kernel<K><<<n_s, 256, smem, s>>>(vis, model, gains, n_bl, n_ant, ant_off, ent, a12, tent, state, sums);
+  return 0;
+}
+
 int sm_launch_acc(int kind, const float* vis, const float* model, const float* gains, int n_s, int n_bl, int n_ant,
-                  const int32_t* ant_off, const int32_t* ent, const int32_t* a12, const int* state, float* sums,
-                  void* stream) {
+                  const int32_t* ant_off, const int32_t* ent, const int32_t* a12, const int32_t* tent,
+                  const int* state, float* sums, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (kind == 0) {
-    using K = ScalarKind<float>;
-    const size_t smem = sizeof(float) * ((size_t)n_ant * K::GW + (size_t)SmoothTile<K>::TB * 2 * K::NC);
-    cudaError_t e = cudaFuncSetAttribute(sm_acc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    sm_acc_kernel<K><<<n_s, 256, smem, s>>>(vis, model, gains, n_bl, n_ant, ant_off, ent, a12, state, sums);
-  } else {
-    using K = JonesKind<float>;
-    const size_t smem = sizeof(float) * (size_t)n_ant * K::GW;
-    sm_acc_ant_kernel<K><<<n_s, 64, smem, s>>>(vis, model, gains, n_bl, n_ant, ant_off, ent, a12, state, sums);
-  }
+  const int rc = kind == 0 ? sm_launch_tiled<ScalarKind<float>>(vis, model, gains, n_s, n_bl, n_ant, ant_off, ent, a12,
+                                                                tent, state, sums, s)
+                           : sm_launch_tiled<JonesKind<float>>(vis, model, gains, n_s, n_bl, n_ant, ant_off, ent, a12,
+                                                               tent, state, sums, s);
+  if (rc) return rc;
   return (int)cudaGetLastError();
 }
 
