@@ -88,7 +88,7 @@ template <> struct SmoothRow<JonesKind<float>> {
 // list, from tent -- each a fixed share, into compensated FP32 sums combined in a fixed order.
 // The sample's gains are staged in shared memory.  sums [n_s][n_ant][NC].
 template <class K> struct SmoothTile { static constexpr int TB = 1024; };
-template <> struct SmoothTile<JonesKind<float>> { static constexpr int TB = 256; };
+template <> struct SmoothTile<JonesKind<float>> { static constexpr int TB = 512; };
 constexpr int kSmSplit = 4;  // threads per antenna in the per-antenna sums
 
 template <class K>
