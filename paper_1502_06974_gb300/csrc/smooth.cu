@@ -30,6 +30,40 @@ __global__ void sm_conv_kernel(const float* __restrict__ in, float* __restrict__
   out[idx] = s;
 }
 
+// The same convolution with the inputs staged once: a CTA takes kCvE consecutive inner columns and
+// kCvA consecutive outputs along the axis of one outer slice, copies the kCvA + 2R inputs they need
+// (coalesced rows of kCvE floats) and the taps into shared memory, and each thread forms outputs
+// of one column with the same terms in the same order as sm_conv_kernel (identical results).
+constexpr int kCvE = 32, kCvA = 64, kCvThreads = 256;
+__global__ void __launch_bounds__(kCvThreads) sm_conv_tiled_kernel(const float* __restrict__ in,
+                                                                  float* __restrict__ out, int n_axis, int64_t inner,
+                                                                  const float* __restrict__ taps, int R) {
+  extern __shared__ __align__(16) float cv_smem[];
+  float* st = cv_smem;                                  // taps [2R + 1]
+  float* tile = cv_smem + (2 * R + 1 + 3) / 4 * 4;      // [(kCvA + 2R)][kCvE]
+  const int64_t o = blockIdx.z;
+  const int64_t e0 = (int64_t)blockIdx.x * kCvE;
+  const int a_0 = (int)blockIdx.y * kCvA;
+  const int lo_in = max(0, a_0 - R), hi_in = min(n_axis - 1, a_0 + kCvA - 1 + R);
+  const int nin = hi_in - lo_in + 1;
+  for (int x = threadIdx.x; x < 2 * R + 1; x += blockDim.x) st[x] = taps[x];
+  const int ec = threadIdx.x % kCvE, ar = threadIdx.x / kCvE;
+  constexpr int kRows = kCvThreads / kCvE;
+  const int64_t e = e0 + ec;
+  const bool ev = e < inner;
+  const float* src = in + o * n_axis * inner;
+  for (int r = ar; r < nin; r += kRows) tile[r * kCvE + ec] = ev ? src[(int64_t)(lo_in + r) * inner + e] : 0.f;
+  __syncthreads();
+  float* dst = out + o * n_axis * inner;
+  const int a_end = min(n_axis, a_0 + kCvA);
+  for (int a0 = a_0 + ar; a0 < a_end; a0 += kRows) {
+    const int lo = max(0, a0 - R), hi = min(n_axis - 1, a0 + R);
+    float s = 0.f;
+    for (int a = lo; a <= hi; ++a) s = fmaf(st[a - a0 + R], tile[(a - lo_in) * kCvE + ec], s);
+    if (ev) dst[(int64_t)a0 * inner + e] = s;
+  }
+}
+
 // One side of a row's contribution to StefCal's per-antenna sums, in the component order K::solve
 // reads (scalar [Re c, Im c, A]; 2x2 [C (8), H00, H11, Re H01, Im H01]).  Stored row (p, q), antenna
 // p: y = m conj(g_q), c += conj(y) d, A += |y|^2 (2x2: Y = M G_q^H, C += D Y^H, H += Y Y^H).
@@ -301,8 +335,17 @@ int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int
                    void* stream) {
   const int64_t total = n_outer * n_axis * inner;
   if (total <= 0) return 0;
-  sm_conv_kernel<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, out, n_axis, inner, taps, R,
-                                                                                    total);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t smem = sizeof(float) * (((size_t)2 * R + 1 + 3) / 4 * 4 + (size_t)(kCvA + 2 * R) * kCvE);
+  const int64_t gx = (inner + kCvE - 1) / kCvE, gy = (n_axis + kCvA - 1) / kCvA;
+  if (smem <= 96 * 1024 && n_outer <= 65535 && gy <= 65535 && gx <= 0x7fffffff) {
+    cudaError_t e = cudaFuncSetAttribute(sm_conv_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    sm_conv_tiled_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)n_outer), kCvThreads, smem, s>>>(in, out, n_axis,
+                                                                                                    inner, taps, R);
+  } else {
+    sm_conv_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(in, out, n_axis, inner, taps, R, total);
+  }
   return (int)cudaGetLastError();
 }
 
