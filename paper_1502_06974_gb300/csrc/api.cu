@@ -1386,21 +1386,26 @@ static int run_smooth(int kind, const void* vis, const void* model, const gc_smo
     // frequency, then time: [n_t][n_f][n_ant * NC]; an axis without smoothing (one tap of 1) is skipped
     const float* cur = (const float*)sums;
     if (Rf > 0) {
-      GC_CUDA_I(sm_launch_conv(cur, (float*)tmp, sm->n_t, sm->n_f, inner, dtaps + wt.size(), Rf, stream));
+      GC_CUDA_I(sm_launch_conv(cur, (float*)tmp, sm->n_t, sm->n_f, inner, dtaps + wt.size(), Rf, state, stream));
       cur = (const float*)tmp;
       g_launches++;
     }
     if (Rt > 0) {
-      GC_CUDA_I(sm_launch_conv(cur, (float*)ssum, 1, sm->n_t, (int64_t)sm->n_f * inner, dtaps, Rt, stream));
+      GC_CUDA_I(sm_launch_conv(cur, (float*)ssum, 1, sm->n_t, (int64_t)sm->n_f * inner, dtaps, Rt, state, stream));
       cur = (const float*)ssum;
       g_launches++;
     }
     GC_CUDA_I(sm_launch_update(kind, cur, (const float*)gains, (float*)gnew, n_int, sm->n_ant, k, opt->schedule,
                                opt->max_iter, opt->tol, state, partials, stream));
     g_launches += 4;
-    GC_CUDA(cudaMemcpyAsync(flag, state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    GC_CUDA(cudaStreamSynchronize(s));
-    if (flag[0]) break;
+    // the host looks at the state every kSmCheck iterations: once the grid is done every kernel of
+    // the iterations launched after it returns at once (the apply kernel copies the same gains)
+    constexpr int kSmCheck = 4;
+    if (k % kSmCheck == 0 || k == opt->max_iter) {
+      GC_CUDA(cudaMemcpyAsync(flag, state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaStreamSynchronize(s));
+      if (flag[0]) break;
+    }
   }
   if (iters_out) GC_CUDA(cudaMemcpyAsync(iters_out, state + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   if (status_out) GC_CUDA(cudaMemcpyAsync(status_out, state + 2, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));

@@ -113,7 +113,7 @@ int di_macc_bulk_smem(int kind, int na_max, int tblk_max);
 // iterations, status, apply; partials 3 doubles per sample), then the staged gains copied over the
 // current ones when the step is kept.
 int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int64_t inner, const float* taps, int R,
-                   void* stream);
+                   const int* state, void* stream);
 // Baselines per tile of the per-sample accumulation of this kind; tent [n_tiles + 1][n_ant]: the
 // index in ent of antenna p's first entry with a baseline of tile t or later.
 int sm_tile_rows(int kind);

@@ -17,7 +17,8 @@ namespace gc {
 // out[o][a0][e] = sum_{|a - a0| <= R, 0 <= a < n_axis} taps[a - a0 + R] in[o][a][e]; arrays
 // [n_outer][n_axis][inner] floats, one thread per output value.
 __global__ void sm_conv_kernel(const float* __restrict__ in, float* __restrict__ out, int n_axis, int64_t inner,
-                               const float* __restrict__ taps, int R, int64_t total) {
+                               const float* __restrict__ taps, int R, int64_t total, const int* state) {
+  if (state[0]) return;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int64_t e = idx % inner;
@@ -37,7 +38,9 @@ __global__ void sm_conv_kernel(const float* __restrict__ in, float* __restrict__
 constexpr int kCvE = 32, kCvA = 64, kCvThreads = 256;
 __global__ void __launch_bounds__(kCvThreads) sm_conv_tiled_kernel(const float* __restrict__ in,
                                                                   float* __restrict__ out, int n_axis, int64_t inner,
-                                                                  const float* __restrict__ taps, int R) {
+                                                                  const float* __restrict__ taps, int R,
+                                                                  const int* state) {
+  if (state[0]) return;
   extern __shared__ __align__(16) float cv_smem[];
   float* st = cv_smem;                                  // taps [2R + 1]
   float* tile = cv_smem + (2 * R + 1 + 3) / 4 * 4;      // [(kCvA + 2R)][kCvE]
@@ -332,7 +335,7 @@ __global__ void sm_init_kernel(int* state) {
 }
 
 int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int64_t inner, const float* taps, int R,
-                   void* stream) {
+                   const int* state, void* stream) {
   const int64_t total = n_outer * n_axis * inner;
   if (total <= 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
@@ -342,9 +345,9 @@ int sm_launch_conv(const float* in, float* out, int64_t n_outer, int n_axis, int
     cudaError_t e = cudaFuncSetAttribute(sm_conv_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     sm_conv_tiled_kernel<<<dim3((unsigned)gx, (unsigned)gy, (unsigned)n_outer), kCvThreads, smem, s>>>(in, out, n_axis,
-                                                                                                    inner, taps, R);
+                                                                                                    inner, taps, R, state);
   } else {
-    sm_conv_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(in, out, n_axis, inner, taps, R, total);
+    sm_conv_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(in, out, n_axis, inner, taps, R, total, state);
   }
   return (int)cudaGetLastError();
 }
