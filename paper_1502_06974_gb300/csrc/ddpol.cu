@@ -236,9 +236,11 @@ __device__ void ddpol_alljones_warp(const Cx<float>* Hh, const Cx<float>* Hl, co
 // One CTA per (interval, antenna): the antenna's H (upper 2x2 blocks) and CD from the moments of
 // its baselines, summed with compensation per thread and in float-float across lanes; then the
 // CohJones solve (method 0) or the AllJones step (method 1) by one warp; the interval's last
-// antenna applies the schedule and the convergence test.
+// antenna applies the schedule and the convergence test.  Registers are capped for three CTAs per
+// SM (80 per thread; the solver spills a little): unbounded, the kernel takes 121 and fits two,
+// and the 744 CTAs of the 62-antenna 9-direction workload then need three rounds instead of two.
 template <int ND>
-__global__ void __launch_bounds__(PolShape<ND>::ITHR) ddpol_iter_kernel(const DDArgs a) {
+__global__ void __launch_bounds__(PolShape<ND>::ITHR, 3) ddpol_iter_kernel(const DDArgs a) {
   using S = PolShape<ND>;
   constexpr int T = S::T, NO = S::NO, NBH = S::NBH, NOUT = S::NOUT, LANES = S::LANES, N2 = S::N2,
                 NU2 = S::NU2, W = 4 * ND;
