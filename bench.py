@@ -657,6 +657,11 @@ def run_gpu(args):
             peaks, which = measured_peaks()
             print(json.dumps(dd_block(dev, args, peaks, which)))
         return 0
+    if args.ddpol_only:  # the polarized direction-dependent workload alone (one JSON line)
+        if rank == 0:
+            peaks, which = measured_peaks()
+            print(json.dumps(ddpol_block(dev, args, peaks, which)))
+        return 0
     b = make_workload(rank)
     lay = api.Layout.from_batch(b)
     vis = torch.from_numpy(b.vis).to(dev)
@@ -868,6 +873,7 @@ def main():
     ap.add_argument('--no-warm', action='store_true', help='skip the learned warm start comparison')
     ap.add_argument('--no-dd', action='store_true', help='skip the direction-dependent (CohJones) workload')
     ap.add_argument('--dd-only', action='store_true', help='run only the direction-dependent workload')
+    ap.add_argument('--ddpol-only', action='store_true', help='run only the polarized direction-dependent workload')
     ap.add_argument('--no-uneven', action='store_true', help='skip the uneven batched workload')
     ap.add_argument('--no-weights', action='store_true', help='skip the weighted headline solve')
     ap.add_argument('--no-smooth', action='store_true', help='skip the smoothing workloads')
